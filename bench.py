@@ -1,0 +1,385 @@
+#!/usr/bin/env python3
+"""Benchmark: Jet refinement throughput (Medges/s) and partition time at k=64.
+
+Workload: the 128^3 7-point mesh (2,097,152 vertices, 6,242,304 edges),
+vertex weights U[1,4], edge weights U[1,10], k = 64, eps = 0.03, seed 1 —
+the paper's artificial-mesh class (its 200^3 cube), generated synthetically.
+
+A step is one jet_partition call: heavy-edge coarsening, greedy initial
+partition and Jet refinement (Jetlp + Jetrw/Jetrs) on every level.  `value`
+is refinement edges per second: sum over levels of (iterations x edges of
+the level) divided by the refinement time (CUDA events on the library's
+stream), with the graph resident in HBM.  `e2e` is the same numerator over
+the time of jet_partition_host (host arrays in pinned memory; copies in).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Multi-GPU: the path does not shard (one graph per GPU); N ranks run N
+independent replicas (weak scaling) and rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Jet refinement Medges/s & partition ms at k=64; cutsize vs CPU oracle"
+UNIT = "Medges/s"
+K_PARTS, EPS, SEED = 64, 0.03, 1
+WORKLOAD = "grid3d 128x128x128 (7-point), vwgt U[1,4], adjwgt U[1,10], k=64, eps=0.03, seed=1"
+FLUSH_BYTES = 512 << 20          # written between steps (L2 is 129 MB)
+ROOFLINE_KERNEL = "k_lp_select_small (Jetlp select, finest level)"
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "lp_select_grid3d_128_k64.txt")
+
+
+def parse_args(argv=None):
+    p = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing (debug runs)")
+    p.add_argument("--scale", type=int, default=128, help="mesh side (128 is the benchmark workload)")
+    p.add_argument("--hostloop", action="store_true",
+                   help="drive refinement iterations from the host (same kernels and launch configuration; "
+                        "used for profiler launch lists)")
+    p.add_argument("--kernel-probe", action="store_true",
+                   help="run one profiled partition and report per-level select launches (profiler target)")
+    return p.parse_args(argv)
+
+
+def workload_graph(scale):
+    import graphgen
+    return graphgen.grid3d(scale, scale, scale, vw=(1, 4), ew=(1, 10), seed=SEED)
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# --------------------------------------------------------------------------
+# multi-process plumbing (torchrun): one replica per rank
+# --------------------------------------------------------------------------
+def dist_info():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def dist_init(ws, backend):
+    if ws <= 1:
+        return None
+    import torch.distributed as dist
+    os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+    dist.init_process_group(backend=backend)
+    return dist
+
+
+def aggregate(units, seconds, extra_max=(), dist=None, device=None):
+    """Whole-job throughput over ranks: (sum of units) / (max of seconds).
+    Returns (total_units, max_seconds, [max of each extra value])."""
+    if dist is None:
+        return float(units), float(seconds), [float(x) for x in extra_max]
+    import torch
+    t = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    m = torch.tensor([float(seconds)] + [float(x) for x in extra_max], dtype=torch.float64, device=device)
+    dist.all_reduce(m, op=dist.ReduceOp.MAX)
+    return float(t.item()), float(m[0].item()), [float(x) for x in m[1:].tolist()]
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+# --------------------------------------------------------------------------
+# clocks during the timed region
+# --------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="jet_clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# --------------------------------------------------------------------------
+# the oracle (CPU baseline / reference arm): a bounded sample of refinement
+# --------------------------------------------------------------------------
+def oracle_sample(g, iters, repeats=1):
+    """Oracle Jet refinement of the finest level, starting from the greedy
+    initial partition of the whole mesh, capped at `iters` iterations.
+    Returns (edge passes, seconds, iterations run)."""
+    import oracle
+    part0 = oracle.initial_partition(g, K_PARTS)
+    opts = oracle.Options(max_iters=iters)
+    units = secs = its = 0
+    for _ in range(repeats):
+        t0 = time.perf_counter()
+        r = oracle.refine(g, K_PARTS, part0, eps=EPS, is_finest=True, seed=SEED, opts=opts, trace_cap=1)
+        secs += time.perf_counter() - t0
+        units += r.iters * g.m
+        its += r.iters
+    return units, secs, its
+
+
+def run_reference(args):
+    ws, rank, _ = dist_info()
+    if rank != 0:
+        return 0
+    g = workload_graph(args.scale)
+    iters = 6
+    for _ in range(args.warmup):
+        oracle_sample(g, iters)
+    units = secs = 0
+    per_step = []
+    for _ in range(args.steps):
+        u, s, _ = oracle_sample(g, iters)
+        units += u; secs += s
+        per_step.append(s)
+    value = units / secs / 1e6
+    sample = (f"oracle Jet refinement of the finest level (128^3 mesh, k=64) from the greedy initial partition, "
+              f"{iters} iterations per step, single thread")
+    out = {"impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * statistics.mean(per_step), 3),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+           "data": "synthetic", "config": {"workload": WORKLOAD, "n": g.n, "m": g.m, "sample": sample},
+           "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------
+# our arm
+# --------------------------------------------------------------------------
+def kernel_source_hash():
+    h = hashlib.sha256()
+    with open(os.path.join(ROOT, "paper_2304_13194_gb300", "csrc", "jet_refine.cu"), "rb") as f:
+        h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic_per_launch():
+    """DRAM bytes per select launch from the committed ncu summary, if it was
+    taken on the current kernel source (else None)."""
+    try:
+        kv = {}
+        with open(PROFILE_SUMMARY) as f:
+            for line in f:
+                if ":" in line:
+                    a, b = line.split(":", 1)
+                    kv[a.strip()] = b.strip()
+        if kv.get("kernel_source_sha256_16") != kernel_source_hash():
+            return None
+        return int(float(kv["traffic_bytes_per_launch"]))
+    except Exception:
+        return None
+
+
+def run_probe(args):
+    """One partition of the workload with the select kernels bracketed by
+    CUDA events; prints how many select launches precede the finest level."""
+    import torch
+    import paper_2304_13194_gb300 as jet
+    torch.cuda.set_device(0)
+    g = workload_graph(args.scale)
+    dev = torch.device("cuda", 0)
+    t = [torch.from_numpy(a).to(dev) for a in (g.xadj, g.adjncy, g.vwgt, g.adjwgt)]
+    with jet.Context(0, flags=jet.FLAG_PROFILE) as ctx:
+        _, cut, st = ctx.partition(*t, k=K_PARTS, eps=EPS, seed=SEED, return_stats=True)
+    skip = sum(st.sel_launches[1:])
+    print(json.dumps({"probe": "lp_select", "cut": cut, "levels": st.levels, "sel_launches": st.sel_launches,
+                      "sel_ms": [round(x, 4) for x in st.sel_ms], "sel_bytes": st.sel_bytes,
+                      "skip_before_finest": skip}), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_info()
+    torch.cuda.set_device(local)
+    dist = dist_init(ws, "nccl")
+    device = torch.device("cuda", local)
+    import paper_2304_13194_gb300 as jet
+
+    g = workload_graph(args.scale)
+    xadj = torch.from_numpy(g.xadj).to(device)
+    adj = torch.from_numpy(g.adjncy).to(device)
+    vw = torch.from_numpy(g.vwgt).to(device)
+    ew = torch.from_numpy(g.adjwgt).to(device)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=device)
+    ctx = jet.Context(local, flags=jet.FLAG_HOSTLOOP if args.hostloop else 0)
+    stream = torch.cuda.current_stream(device)
+
+    def step():
+        return ctx.partition(xadj, adj, vw, ew, k=K_PARTS, eps=EPS, seed=SEED, return_stats=True)
+
+    for _ in range(max(args.warmup, 0)):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+
+    # ---- timed region: K device-resident partitions ----------------------
+    sampler = ClockSampler(local)
+    barrier(dist)
+    torch.cuda.synchronize()
+    sampler.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    stats, cuts, parts = [], [], None
+    for i in range(args.steps):
+        flush.zero_()                          # evict L2 between steps (outside the step's events)
+        ev[i][0].record(stream)
+        part, cut, st = step()
+        ev[i][1].record(stream)
+        stats.append(st); cuts.append(cut); parts = part
+    torch.cuda.synchronize()
+    barrier(dist)
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    units = sum(s.edge_iters for s in stats)
+    refine_s = sum(s.ms_refine for s in stats) / 1e3
+    launches = sum(s.kernel_launches for s in stats)
+    tot_units, max_refine_s, (max_step_ms,) = aggregate(units, refine_s, [statistics.mean(step_ms)], dist, device)
+    value = tot_units / max_refine_s / 1e6
+
+    # ---- end to end through the host-pointer entry point -----------------
+    hx = torch.from_numpy(g.xadj).pin_memory(); ha = torch.from_numpy(g.adjncy).pin_memory()
+    hv = torch.from_numpy(g.vwgt).pin_memory(); hw = torch.from_numpy(g.adjwgt).pin_memory()
+    hp = torch.empty(g.n, dtype=torch.int32).pin_memory()
+    ctx.partition_host(hx, ha, hv, hw, k=K_PARTS, eps=EPS, seed=SEED, part_out=hp)   # warm
+    e2e_units = 0
+    e2e_ev = []
+    barrier(dist)
+    torch.cuda.synchronize()
+    for _ in range(args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        _, _, st = ctx.partition_host(hx, ha, hv, hw, k=K_PARTS, eps=EPS, seed=SEED, part_out=hp, return_stats=True)
+        b.record(stream)
+        e2e_units += st.edge_iters
+        e2e_ev.append((a, b))
+    torch.cuda.synchronize()
+    e2e_s = sum(a.elapsed_time(b) for a, b in e2e_ev) / 1e3
+    e2e_tot, e2e_max, _ = aggregate(e2e_units, e2e_s, [], dist, device)
+    h2d = g.xadj.nbytes + g.adjncy.nbytes + g.vwgt.nbytes + g.adjwgt.nbytes
+    d2h = g.n * 4
+
+    # ---- roofline of the dominant kernel: CUDA events around each select
+    # launch (profiling mode drives the same kernels from the host) ----------
+    pctx = jet.Context(local, flags=jet.FLAG_PROFILE)
+    flush.zero_()
+    _, pcut, pst = pctx.partition(xadj, adj, vw, ew, k=K_PARTS, eps=EPS, seed=SEED, return_stats=True)
+    pctx.close()
+    sel_bytes, sel_ms, sel_n = pst.sel_bytes[0], pst.sel_ms[0], pst.sel_launches[0]
+    peak, peak_kind = peaks()
+    achieved = sel_bytes / (sel_ms / 1e3) / 1e9 if sel_ms > 0 else 0.0
+    traffic = ncu_traffic_per_launch()
+
+    # ---- CPU baseline: the oracle on a bounded sample (rank 0, N = 1) ----
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        iters = 100
+        u, s, its = oracle_sample(g, iters)
+        cpu = {"value": round(u / s / 1e6, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"oracle Jet refinement of the finest level (same mesh, k=64) from the greedy initial "
+                         f"partition, {its} iterations ({s:.1f} s), single thread"}
+
+    if rank == 0:
+        st0 = stats[-1]
+        out = {
+            "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(max_step_ms, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": g.n, "m": g.m, "k": K_PARTS, "eps": EPS, "seed": SEED,
+                       "parallelism": "replicas" if ws > 1 else "single GPU",
+                       "l2": f"{FLUSH_BYTES >> 20} MB buffer written before every step",
+                       "levels": st0.levels, "cut": cuts[-1], "max_part_w": st0.max_part_w,
+                       "refine_ms": round(st0.ms_refine, 3), "coarsen_ms": round(st0.ms_coarsen, 3),
+                       "initpart_ms": round(st0.ms_init, 3), "finest_refine_ms": round(st0.ms_refine_finest, 3),
+                       "edge_iters_per_step": st0.edge_iters, "bytes_model_per_step": st0.bytes_model},
+            "roofline": {"bound": "hbm", "kernel": ROOFLINE_KERNEL, "achieved": round(achieved, 1),
+                         "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4) if peak else None,
+                         "bytes_per_launch": int(sel_bytes / max(sel_n, 1)),
+                         "ms_per_launch": round(sel_ms / max(sel_n, 1), 5), "launches": sel_n,
+                         "traffic": traffic},
+            "cpu_baseline": cpu,
+            "e2e": {"value": round(e2e_tot / e2e_max / 1e6, 3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches,
+            "clocks": clocks,
+        }
+        print(json.dumps(out), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    if args.kernel_probe:
+        return run_probe(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

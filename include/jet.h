@@ -1,0 +1,233 @@
+/*
+ * jet.h — C ABI of the GB300 (sm_103a) Jet multilevel k-way graph partitioner.
+ *
+ * Method: Gilbert, Madduri, Boman, Rajamanickam, "Jet: Multilevel Graph
+ * Partitioning on Graphics Processing Units".  Citations below name the
+ * paper's sections, algorithms and equations.
+ *
+ * Graph format (Sec. 2.1 "Problem Definition"): an undirected graph without
+ * self-loops or parallel edges in CSR form —
+ *   xadj   int64[n+1], xadj[0] = 0, non-decreasing;
+ *   adjncy int32[xadj[n]], every edge {u,v} stored as v in u's row and u in v's;
+ *   vwgt   int32[n]  positive vertex weights, or NULL for unit weights;
+ *   adjwgt int32[xadj[n]] positive edge weights, equal in both directions, or
+ *          NULL for unit weights.
+ * Limits: n < 2^31; sum of vwgt < 2^31; sum of adjwgt over all xadj[n] entries
+ * < 2^31 (connectivities are exact 32-bit sums; cut and part weights are
+ * 64-bit); 1 <= k <= JET_MAX_K.
+ *
+ * Memory: unless a function says otherwise, every array argument is a DEVICE
+ * pointer on the context's device, allocated and owned by the caller; the
+ * library never frees it.  Scalars returned through pointers (cut_out, ...)
+ * are HOST pointers.  The library allocates its own device scratch (stream-
+ * ordered, on the context's stream) and releases it before returning, except
+ * for the hierarchy objects, which jet_hier_destroy releases.
+ *
+ * Streams and synchronisation: all work is enqueued on the context's stream;
+ * every call returns only after its results are final (it synchronises that
+ * stream), so callers may read outputs immediately.
+ *
+ * Determinism: results are a pure function of the inputs, k, eps, the options
+ * and the seed — bit-identical across runs and equal to the CPU oracle's.
+ * Ties are broken by the lowest part id, then the lowest vertex id.
+ *
+ * Errors: every call returns a status (JET_OK = 0, warnings > 0, errors < 0);
+ * no exception or abort crosses the ABI.  After JET_ECUDA the context may be
+ * unusable (the CUDA error is sticky); destroy it.
+ */
+#ifndef JET_H
+#define JET_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define JET_MAX_K 1024
+#define JET_MAX_LEVELS 64
+
+/* status codes */
+#define JET_OK 0
+#define JET_WUNBALANCED 1   /* warning: the best partition found violates the balance limit */
+#define JET_WITERLIMIT 2    /* warning: a level hit max_iters_per_level before the stop rule */
+#define JET_EINVAL (-1)     /* bad argument: n < 0, k out of range, eps < 0, NULL required pointer */
+#define JET_EGRAPH (-2)     /* invalid graph (only with JET_FLAG_VALIDATE): asymmetric, self-loop,
+                               parallel edge, weight <= 0, id out of range */
+#define JET_ENOMEM (-3)     /* device allocation failed */
+#define JET_ECUDA (-4)      /* a CUDA call failed */
+#define JET_ETIMEOUT (-5)   /* a bounded device wait ran out */
+#define JET_EOVERFLOW (-6)  /* weight sums exceed the 2^31 limits above */
+
+/* jet_options.flags */
+#define JET_FLAG_VALIDATE 1u       /* check the input graph on the device first */
+#define JET_FLAG_HOSTLOOP 2u       /* drive refinement iterations from the host (one launch
+                                      sequence per iteration, mode read back each time)
+                                      instead of the device-resident CUDA-graph loop */
+#define JET_FLAG_PROFILE 4u        /* implies JET_FLAG_HOSTLOOP; records CUDA events around every
+                                      Jetlp select launch (same kernels, same launch configuration)
+                                      and fills jet_stats.sel_ms */
+#define JET_FLAG_NO_LOCKS 16u      /* Jetlp ablations (Sec. 6.1.4, Table 2): ignore lock bits */
+#define JET_FLAG_NO_AFTERBURN 32u  /*   M = X (skip the second filter) */
+#define JET_FLAG_WEAK_AFTERBURN 64u/*   first filter keeps only F >= 0 */
+#define JET_FLAG_BASELINE_LP 128u  /*   baseline LP: move iff F > 0, no afterburner, no locks */
+
+/* Hyper-parameters the paper names (defaults from jet_options_default):
+ *   c_fine = 0.25, c_coarse = 0.75  first-filter ratio c (Sec. 4.1.2, Eq. gainconn_filter);
+ *                                   held internally as round(c * 65536) / 65536
+ *   phi = 0.999                     tolerance of Alg. 3 (held as round(phi * 1e6) / 1e6)
+ *   max_no_improve = 12             iterations without a new best before stopping (Sec. 4)
+ *   weak_limit = 2                  b_max Jetrw iterations before Jetrs (Sec. 4.2.2)
+ *   coarsen_target = 0              stop coarsening at <= max(8k, 256) vertices (Sec. 3)
+ *   max_levels = 64, max_iters_per_level = 10000 (safety caps), hem_rounds = 8 */
+typedef struct {
+    double c_fine, c_coarse, phi;
+    int32_t max_no_improve, weak_limit, coarsen_target, max_levels, max_iters_per_level, hem_rounds;
+    uint32_t flags;
+} jet_options;
+
+/* Per-call statistics (jet_partition / jet_uncoarsen).  Times are CUDA-event
+ * milliseconds on the context's stream. */
+typedef struct {
+    int32_t levels;
+    int64_t n[JET_MAX_LEVELS], m[JET_MAX_LEVELS];          /* vertices / undirected edges per level */
+    int32_t iters_lp[JET_MAX_LEVELS], iters_rw[JET_MAX_LEVELS], iters_rs[JET_MAX_LEVELS];
+    int64_t cut_level[JET_MAX_LEVELS];                     /* cut after refining each level */
+    int64_t edge_iters;        /* sum over levels of (iterations x m_level): refinement edge passes */
+    int64_t fin_edge_iters;    /* the same, finest level only */
+    float ms_coarsen, ms_init, ms_refine, ms_refine_finest, ms_total;
+    int64_t cut, max_part_w;
+    int64_t bytes_model;        /* algorithmic DRAM bytes of all refinement passes (byte model:
+                                   compulsory streams, neighbour gathers taken as cache hits) */
+    int64_t kernel_launches;    /* kernels executed by this call, device-loop iterations included */
+    int64_t sel_launches[JET_MAX_LEVELS];  /* Jetlp select passes per level */
+    int64_t sel_bytes[JET_MAX_LEVELS];     /* their algorithmic bytes, summed */
+    float sel_ms[JET_MAX_LEVELS];          /* their CUDA-event time, summed (JET_FLAG_PROFILE only) */
+} jet_stats;
+
+typedef struct jet_ctx jet_ctx;
+typedef struct jet_hier jet_hier;
+
+/* Fill *opt with the defaults listed above. */
+void jet_options_default(jet_options *opt);
+
+/* Create a context on CUDA device `device` that enqueues on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  opt may be NULL for
+ * defaults.  The context owns no caller memory.  Returns JET_EINVAL for a bad
+ * device or option, JET_ECUDA if the device cannot be used. */
+int jet_ctx_create(int device, void *cuda_stream, const jet_options *opt, jet_ctx **out);
+void jet_ctx_destroy(jet_ctx *ctx);
+
+/* MLCoarsen of Alg. 1 (Sec. 3.1): repeated heavy-edge matching and edge
+ * contraction (Alg. 2) until the graph has at most coarsen_target vertices,
+ * coarsening stalls (a level keeps more than 95% of the vertices) or
+ * max_levels is reached.  seed drives the matching's tie-break hash.  *out is
+ * a device-resident hierarchy owned by the library (jet_hier_destroy); level 0
+ * refers to the caller's arrays, which must stay valid while *out is used. */
+int jet_coarsen(jet_ctx *ctx, int32_t n, const int64_t *xadj, const int32_t *adjncy,
+                const int32_t *vwgt, const int32_t *adjwgt, int32_t k, uint64_t seed, jet_hier **out);
+void jet_hier_destroy(jet_hier *h);
+
+/* Level count and per-level sizes (host arrays of at least JET_MAX_LEVELS
+ * entries; any may be NULL).  m is the number of undirected edges. */
+int jet_hier_info(const jet_hier *h, int32_t *levels, int64_t *n_per_level, int64_t *m_per_level);
+
+/* Device pointers of one level's CSR (rows sorted ascending, weights summed
+ * over merged edges) and of its coarse map cmap (level -> level+1; NULL on the
+ * coarsest level).  Valid until jet_hier_destroy. */
+int jet_hier_level(const jet_hier *h, int32_t level, int32_t *n, const int64_t **xadj,
+                   const int32_t **adjncy, const int32_t **vwgt, const int32_t **adjwgt,
+                   const int32_t **cmap);
+
+/* Alg. 1 after MLCoarsen: InitialPartition of the coarsest level (greedy
+ * graph growing: vertices ordered by component, BFS level from the component's
+ * lowest id, then id; cut into k consecutive pieces by weight), then
+ * RefinePartition (Alg. 3) on it and, for each finer level, ProjectPartition
+ * (P_i[v] = P_{i+1}[C_i[v]]) followed by RefinePartition.  part_out: device
+ * int32[n of level 0].  stats may be NULL. */
+int jet_uncoarsen(jet_ctx *ctx, const jet_hier *h, int32_t k, double eps, uint64_t seed,
+                  int32_t *part_out, int64_t *cut_out, jet_stats *stats);
+
+/* Jet refinement of one graph (Alg. 3 with Alg. 4 Jetlp, Alg. 5 Jetrw and the
+ * Jetrs of Sec. 4.2.2) starting from part_inout (device int32[n], values in
+ * [0,k)), which receives P_best.  is_finest selects c_fine (else c_coarse).
+ * seed drives Jetrw's random destination.  *cut_out = cost of P_best.
+ * Returns JET_WUNBALANCED if P_best still violates the limit
+ * floor(ceil(W/k) * (10^6 + round(eps*10^6)) / 10^6). */
+int jet_refine(jet_ctx *ctx, int32_t n, const int64_t *xadj, const int32_t *adjncy,
+               const int32_t *vwgt, const int32_t *adjwgt, int32_t k, double eps,
+               int32_t is_finest, uint64_t seed, int32_t *part_inout, int64_t *cut_out);
+
+/* Host copy of the per-iteration record of the most recent jet_refine (or of
+ * the finest level of the most recent jet_partition / jet_uncoarsen): kind
+ * (0 Jetlp, 1 Jetrw, 2 Jetrs), |X| for Jetlp or the number of rebalancing
+ * candidates, |M|, cut and max part weight after the iteration.  Host arrays
+ * of `cap` entries (any may be NULL); *iters_out = iterations run. */
+int jet_last_trace(jet_ctx *ctx, int32_t cap, int32_t *kind, int64_t *nx, int64_t *nm,
+                   int64_t *cut, int64_t *maxw, int32_t *iters_out);
+
+/* Alg. 1 end to end: jet_coarsen, then jet_uncoarsen.  part_out: device
+ * int32[n].  stats may be NULL. */
+int jet_partition(jet_ctx *ctx, int32_t n, const int64_t *xadj, const int32_t *adjncy,
+                  const int32_t *vwgt, const int32_t *adjwgt, int32_t k, double eps,
+                  uint64_t seed, int32_t *part_out, int64_t *cut_out, jet_stats *stats);
+
+/* jet_partition on HOST arrays (same layout; vwgt/adjwgt may be NULL):
+ * copies the graph to the device on the context's stream, partitions it and
+ * copies part_out (host int32[n]) back. */
+int jet_partition_host(jet_ctx *ctx, int32_t n, const int64_t *xadj, const int32_t *adjncy,
+                       const int32_t *vwgt, const int32_t *adjwgt, int32_t k, double eps,
+                       uint64_t seed, int32_t *part_out, int64_t *cut_out, jet_stats *stats);
+
+/* --- single passes (for composition and per-pass checks) ---------------- */
+
+/* Cost (Sec. 2.1) and part weights of `part`.  pw_out: device int64[k] or
+ * NULL. */
+int jet_cut(jet_ctx *ctx, int32_t n, const int64_t *xadj, const int32_t *adjncy,
+            const int32_t *vwgt, const int32_t *adjwgt, int32_t k, const int32_t *part,
+            int64_t *cut_out, int64_t *pw_out);
+
+/* One Jetlp pass (Alg. 4) on `part` with lock set `locked` (device uint8[n],
+ * nonzero = locked; NULL = none), first-filter ratio c.  Device outputs, each
+ * int32/uint8 [n]: pd_out = P_d (P_s where undefined), gain_out = F
+ * (INT32_MIN for negative infinity), inx_out = X membership, f2_out = the
+ * afterburner gain F2 (0 outside X), inm_out = M membership.  Any output may
+ * be NULL.  flags: the JET_FLAG_* ablation bits. */
+int jet_lp_pass(jet_ctx *ctx, int32_t n, const int64_t *xadj, const int32_t *adjncy,
+                const int32_t *vwgt, const int32_t *adjwgt, int32_t k, const int32_t *part,
+                const uint8_t *locked, double c, uint32_t flags, int32_t *pd_out, int32_t *gain_out,
+                uint8_t *inx_out, int32_t *f2_out, uint8_t *inm_out);
+
+/* One rebalancing pass on `part`: strong = 0 runs Jetrw (Alg. 5; seed and
+ * iter feed its random destination), strong = 1 runs Jetrs (Sec. 4.2.2).
+ * dest_out: device int32[n], the new part of each moved vertex, -1 for the
+ * others.  loss_out (device int32[n] or NULL): the eviction loss of each
+ * candidate, INT32_MIN for non-candidates.  *nmoves_out / *ncand_out: host
+ * counts (may be NULL). */
+int jet_rebalance_pass(jet_ctx *ctx, int32_t n, const int64_t *xadj, const int32_t *adjncy,
+                       const int32_t *vwgt, const int32_t *adjwgt, int32_t k, double eps,
+                       int32_t strong, uint64_t seed, int32_t iter, const int32_t *part,
+                       int32_t *dest_out, int32_t *loss_out, int64_t *nmoves_out, int64_t *ncand_out);
+
+/* Heavy-edge matching of Sec. 3.1 (handshake rounds, see jet_coarsen) on one
+ * graph: mate_out device int32[n] (partner or -1).  level salts the hash. */
+int jet_hem(jet_ctx *ctx, int32_t n, const int64_t *xadj, const int32_t *adjncy,
+            const int32_t *adjwgt, uint64_t seed, int32_t level, int32_t rounds, int32_t *mate_out);
+
+/* InitialPartition of Alg. 1 (the greedy graph growing described at
+ * jet_uncoarsen) on one graph: part_out device int32[n]. */
+int jet_initial_partition(jet_ctx *ctx, int32_t n, const int64_t *xadj, const int32_t *adjncy,
+                          const int32_t *vwgt, int32_t k, int32_t *part_out);
+
+/* Human-readable name of a status code (static storage). */
+const char *jet_status_string(int status);
+
+/* Text describing the last failed CUDA call on the calling thread (for
+ * diagnostics after JET_ECUDA / JET_ENOMEM; thread-local storage). */
+const char *jet_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* JET_H */

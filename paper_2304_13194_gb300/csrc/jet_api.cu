@@ -1,0 +1,570 @@
+// C ABI of libjet (include/jet.h): context, argument checks, the multilevel
+// driver of Alg. 1 and the single-pass entry points.
+#include "jet_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <new>
+
+namespace jet {
+
+static thread_local char g_err[512] = "";
+
+void record_cuda_error(cudaError_t e, const char *what, const char *file, int line) {
+    snprintf(g_err, sizeof(g_err), "%s: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
+}
+
+const char *last_error_text() { return g_err; }
+
+int dev_alloc(DevBuf &b, size_t bytes, cudaStream_t s) {
+    b.release();
+    b.s = s;
+    bytes = std::max<size_t>(256, (bytes + 255) & ~size_t(255));
+    cudaError_t e = cudaMallocAsync(&b.p, bytes, s);
+    if (e != cudaSuccess) {
+        b.p = nullptr;
+        record_cuda_error(e, "cudaMallocAsync", __FILE__, __LINE__);
+        cudaGetLastError();
+        return JET_ENOMEM;
+    }
+    b.bytes = bytes;
+    return JET_OK;
+}
+
+int num_sms() {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 1;
+}
+
+// Balance limit of Sec. 2.1 in integers: opt = ceil(W/k),
+// L = floor(opt * (10^6 + round(eps * 10^6)) / 10^6).
+int64_t balance_limit(int64_t W, int32_t k, double eps, int64_t *opt) {
+    int64_t o = (W + k - 1) / k;
+    int64_t e = llround(eps * 1e6);
+    if (opt) *opt = o;
+    return o * (1000000 + e) / 1000000;
+}
+
+int sync_stream(Ctx &c) {
+    JET_CUDA_TRY(cudaStreamSynchronize(c.stream));
+    return JET_OK;
+}
+
+static uint64_t host_splitmix64(uint64_t x) {
+    uint64_t z = x + 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+// Seed of Jetrw's random destination on level i of the hierarchy.
+static uint64_t level_seed(uint64_t seed, int32_t level) {
+    return host_splitmix64(seed ^ (0xA0761D6478BD642FULL * (uint64_t)(level + 1)));
+}
+
+// ---------------------------------------------------------------------------
+// input checks
+// ---------------------------------------------------------------------------
+struct CheckOut {
+    long long sum_vw, sum_ew, bad;
+};
+
+__global__ void k_check(int32_t n, const int64_t *xadj, const int32_t *adj, const int32_t *vw, const int32_t *ew,
+                        int validate, CheckOut *out) {
+    __shared__ long long sh[40];
+    long long svw = 0, sew = 0, bad = 0;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        int64_t beg = xadj[v], end = xadj[v + 1];
+        svw += vw ? vw[v] : 1;
+        if (validate) {
+            if (end < beg) { bad = 1; continue; }
+            if (vw && vw[v] <= 0) bad = 1;
+        }
+        for (int64_t j = beg; j < end; ++j) {
+            int32_t w = ew ? ew[j] : 1;
+            sew += w;
+            if (!validate) continue;
+            int32_t u = adj[j];
+            if (u < 0 || u >= n || u == (int32_t)v || w <= 0) { bad = 1; continue; }
+            // exactly one entry (v, w) in u's row: symmetric and no parallel edge
+            int64_t ub = xadj[u], ue = xadj[(int64_t)u + 1];
+            int cnt = 0;
+            bool wok = false;
+            for (int64_t t = ub; t < ue; ++t)
+                if (adj[t] == (int32_t)v) { ++cnt; wok = (ew ? ew[t] : 1) == w; }
+            if (cnt != 1 || !wok) bad = 1;
+        }
+    }
+    svw = block_sum_i64(svw, sh);
+    sew = block_sum_i64(sew, sh);
+    bad = block_sum_i64(bad, sh);
+    if (threadIdx.x == 0) {
+        atomic_add_i64(reinterpret_cast<int64_t *>(&out->sum_vw), svw);
+        atomic_add_i64(reinterpret_cast<int64_t *>(&out->sum_ew), sew);
+        if (bad) atomic_add_i64(reinterpret_cast<int64_t *>(&out->bad), bad);
+    }
+}
+
+__global__ void k_ones32(int32_t *p, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) p[i] = 1;
+}
+
+__global__ void k_check_part(int32_t n, const int32_t *part, int32_t k, int *bad) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+        if (part[v] < 0 || part[v] >= k) atomicOr(bad, 1);
+}
+
+// Argument checks plus the overflow limits of jet.h (and the full graph
+// check with JET_FLAG_VALIDATE).  Fills g; materialises unit vertex weights
+// into `ones` when vwgt is NULL.
+static int prepare_graph(Ctx &c, int32_t n, const int64_t *xadj, const int32_t *adjncy, const int32_t *vwgt,
+                         const int32_t *adjwgt, DGraph &g, DevBuf &ones, bool need_vw) {
+    if (n < 0 || !xadj) return JET_EINVAL;
+    cudaStream_t s = c.stream;
+    int64_t nnz = 0;
+    JET_CUDA_TRY(cudaMemcpyAsync(c.pinned, xadj + n, 8, cudaMemcpyDeviceToHost, s));
+    JET_CUDA_TRY(cudaStreamSynchronize(s));
+    nnz = c.pinned[0];
+    if (nnz < 0) return JET_EGRAPH;
+    if (nnz > 0 && !adjncy) return JET_EINVAL;
+    DevBuf cb;
+    JET_TRY(dev_alloc(cb, sizeof(CheckOut), s));
+    JET_CUDA_TRY(cudaMemsetAsync(cb.p, 0, sizeof(CheckOut), s));
+    int validate = (c.opt.flags & JET_FLAG_VALIDATE) ? 1 : 0;
+    if (n > 0)
+        k_check<<<std::min(num_sms() * 8, grid_for(n, kTB)), kTB, 0, s>>>(n, xadj, adjncy, vwgt, adjwgt, validate,
+                                                                         cb.as<CheckOut>());
+    JET_CUDA_TRY(cudaGetLastError());
+    JET_CUDA_TRY(cudaMemcpyAsync(c.pinned, cb.p, sizeof(CheckOut), cudaMemcpyDeviceToHost, s));
+    JET_CUDA_TRY(cudaStreamSynchronize(s));
+    CheckOut h;
+    memcpy(&h, c.pinned, sizeof(h));
+    if (h.bad) return JET_EGRAPH;
+    if (h.sum_vw >= (1LL << 31) || h.sum_ew >= (1LL << 31)) return JET_EOVERFLOW;
+    g.n = n;
+    g.nnz = nnz;
+    g.xadj = xadj;
+    g.adj = adjncy;
+    g.ew = adjwgt;
+    g.vw = vwgt;
+    if (!vwgt && need_vw) {
+        JET_TRY(dev_alloc(ones, (size_t)std::max(n, 1) * 4, s));
+        if (n > 0) k_ones32<<<grid_for(n, kTB, 8192), kTB, 0, s>>>(ones.as<int32_t>(), n);
+        JET_CUDA_TRY(cudaGetLastError());
+        g.vw = ones.as<int32_t>();
+    }
+    return JET_OK;
+}
+
+static int check_part(Ctx &c, int32_t n, const int32_t *part, int32_t k) {
+    if (n == 0) return JET_OK;
+    if (!part) return JET_EINVAL;
+    DevBuf b;
+    JET_TRY(dev_alloc(b, 16, c.stream));
+    JET_CUDA_TRY(cudaMemsetAsync(b.p, 0, 16, c.stream));
+    k_check_part<<<grid_for(n, kTB, 8192), kTB, 0, c.stream>>>(n, part, k, b.as<int>());
+    JET_CUDA_TRY(cudaGetLastError());
+    JET_CUDA_TRY(cudaMemcpyAsync(c.pinned, b.p, 4, cudaMemcpyDeviceToHost, c.stream));
+    JET_CUDA_TRY(cudaStreamSynchronize(c.stream));
+    return (c.pinned[0] & 0xFFFFFFFF) ? JET_EINVAL : JET_OK;
+}
+
+static bool bad_k_eps(int32_t k, double eps) { return k < 1 || k > JET_MAX_K || !(eps >= 0.0) || !std::isfinite(eps); }
+
+static int use_device(Ctx &c) {
+    JET_CUDA_TRY(cudaSetDevice(c.device));
+    return JET_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Alg. 1 after coarsening
+// ---------------------------------------------------------------------------
+struct EventTimer {
+    cudaEvent_t e[6] = {};
+    bool ok = true;
+    EventTimer() {
+        for (auto &x : e)
+            if (cudaEventCreate(&x) != cudaSuccess) ok = false;
+    }
+    ~EventTimer() {
+        for (auto &x : e)
+            if (x) cudaEventDestroy(x);
+    }
+    float ms(int a, int b) {
+        float t = 0.f;
+        if (!ok || cudaEventElapsedTime(&t, e[a], e[b]) != cudaSuccess) { cudaGetLastError(); return 0.f; }
+        return t;
+    }
+};
+
+static int uncoarsen(Ctx &c, const jet_hier *h, int32_t k, double eps, uint64_t seed, int32_t *part_out, int64_t *cut_out,
+                     jet_stats *st) {
+    cudaStream_t s = c.stream;
+    int32_t l = h->levels - 1;
+    int32_t nmax = 1;
+    for (int32_t i = 1; i < h->levels; ++i) nmax = std::max(nmax, h->n[i]);
+    DevBuf pa, pb;
+    if (l > 0) {
+        JET_TRY(dev_alloc(pa, (size_t)nmax * 4, s));
+        JET_TRY(dev_alloc(pb, (size_t)nmax * 4, s));
+    }
+    int32_t *cur = l == 0 ? part_out : pa.as<int32_t>();
+    int32_t *other = pb.as<int32_t>();
+    EventTimer ev;
+    cudaEventRecord(ev.e[0], s);
+    auto level_graph = [&](int32_t i) {
+        DGraph g;
+        g.n = h->n[i]; g.nnz = h->nnz[i]; g.xadj = h->xadj[i]; g.adj = h->adj[i]; g.vw = h->vw[i]; g.ew = h->ew[i];
+        return g;
+    };
+    JET_TRY(initial_partition(c, level_graph(l), k, cur));
+    c.launches += 1;
+    cudaEventRecord(ev.e[1], s);
+    int status = JET_OK;
+    int64_t cut = 0, maxw = 0;
+    int64_t edge_iters = 0, fin_edge_iters = 0;
+    for (int32_t i = l; i >= 0; --i) {
+        DGraph g = level_graph(i);
+        if (i < l) {
+            int32_t *dst = i == 0 ? part_out : other;
+            JET_TRY(project(c, g.n, h->cmap[i], cur, dst));
+            c.launches += 1;
+            other = cur;
+            cur = dst;
+        }
+        if (i == 0) cudaEventRecord(ev.e[2], s);
+        LevelReport rep;
+        int r = refine_level(c, g, k, eps, i == 0, level_seed(seed, i), cur, &cut, &maxw, &rep);
+        if (r < 0) return r;
+        status = r;
+        int64_t m = h->nnz[i] / 2;
+        edge_iters += (int64_t)rep.iters * m;
+        if (i == 0) fin_edge_iters = (int64_t)rep.iters * m;
+        if (st) {
+            st->iters_lp[i] = rep.kinds[0]; st->iters_rw[i] = rep.kinds[1]; st->iters_rs[i] = rep.kinds[2];
+            st->cut_level[i] = cut;
+            st->sel_launches[i] = rep.sel_launches;
+            st->sel_bytes[i] = rep.sel_bytes;
+            st->sel_ms[i] = rep.sel_ms;
+            st->bytes_model += rep.bytes_model;
+        }
+    }
+    cudaEventRecord(ev.e[3], s);
+    JET_CUDA_TRY(cudaStreamSynchronize(s));
+    if (cut_out) *cut_out = cut;
+    if (st) {
+        st->levels = h->levels;
+        for (int32_t i = 0; i < h->levels; ++i) { st->n[i] = h->n[i]; st->m[i] = h->nnz[i] / 2; }
+        st->edge_iters = edge_iters;
+        st->fin_edge_iters = fin_edge_iters;
+        st->ms_init = ev.ms(0, 1);
+        st->ms_refine = ev.ms(1, 3);
+        st->ms_refine_finest = ev.ms(2, 3);
+        st->cut = cut;
+        st->max_part_w = maxw;
+    }
+    return status;
+}
+
+}  // namespace jet
+
+using namespace jet;
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+void jet_options_default(jet_options *o) {
+    if (!o) return;
+    o->c_fine = 0.25;
+    o->c_coarse = 0.75;
+    o->phi = 0.999;
+    o->max_no_improve = 12;
+    o->weak_limit = 2;
+    o->coarsen_target = 0;
+    o->max_levels = JET_MAX_LEVELS;
+    o->max_iters_per_level = 10000;
+    o->hem_rounds = 8;
+    o->flags = 0;
+}
+
+int jet_ctx_create(int device, void *cuda_stream, const jet_options *opt, jet_ctx **out) {
+    if (!out) return JET_EINVAL;
+    *out = nullptr;
+    jet_options o;
+    jet_options_default(&o);
+    if (opt) o = *opt;
+    if (!(o.c_fine >= 0 && o.c_fine <= 1 && o.c_coarse >= 0 && o.c_coarse <= 1 && o.phi > 0 && o.phi <= 1) ||
+        o.max_no_improve < 0 || o.weak_limit < 0 || o.coarsen_target < 0 || o.max_levels < 1 ||
+        o.max_iters_per_level < 0 || o.hem_rounds < 0 || o.hem_rounds > 64)
+        return JET_EINVAL;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess) { cudaGetLastError(); return JET_ECUDA; }
+    if (device < 0 || device >= ndev) return JET_EINVAL;
+    if (cudaSetDevice(device) != cudaSuccess) { cudaGetLastError(); return JET_ECUDA; }
+    jet_ctx *c = new (std::nothrow) jet_ctx;
+    if (!c) return JET_ENOMEM;
+    c->c.device = device;
+    c->c.stream = static_cast<cudaStream_t>(cuda_stream);
+    c->c.opt = o;
+    if (cudaMallocHost(&c->c.pinned, 4096) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return JET_ENOMEM;
+    }
+    *out = c;
+    return JET_OK;
+}
+
+void jet_ctx_destroy(jet_ctx *ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->c.device);
+    cudaStreamSynchronize(ctx->c.stream);
+    if (ctx->c.pinned) cudaFreeHost(ctx->c.pinned);
+    delete ctx;
+}
+
+int jet_coarsen(jet_ctx *ctx, int32_t n, const int64_t *xadj, const int32_t *adjncy, const int32_t *vwgt,
+                const int32_t *adjwgt, int32_t k, uint64_t seed, jet_hier **out) {
+    if (!ctx || !out || bad_k_eps(k, 0.0)) return JET_EINVAL;
+    *out = nullptr;
+    Ctx &c = ctx->c;
+    JET_TRY(use_device(c));
+    DGraph g;
+    DevBuf ones;
+    JET_TRY(prepare_graph(c, n, xadj, adjncy, vwgt, adjwgt, g, ones, false));
+    jet_hier *h = new (std::nothrow) jet_hier;
+    if (!h) return JET_ENOMEM;
+    h->ctx = ctx;
+    EventTimer ev;
+    cudaEventRecord(ev.e[0], c.stream);
+    int64_t l0 = c.launches;
+    int r = coarsen(c, g, k, seed, h);
+    h->launches = c.launches - l0;
+    cudaEventRecord(ev.e[1], c.stream);
+    if (r >= 0) {
+        cudaError_t e = cudaStreamSynchronize(c.stream);
+        if (e != cudaSuccess) { record_cuda_error(e, "sync", __FILE__, __LINE__); r = JET_ECUDA; }
+    }
+    if (r < 0) { delete h; return r; }
+    h->ms_coarsen = ev.ms(0, 1);
+    *out = h;
+    return JET_OK;
+}
+
+void jet_hier_destroy(jet_hier *h) {
+    if (!h) return;
+    cudaSetDevice(h->ctx->c.device);
+    h->bufs.clear();
+    cudaStreamSynchronize(h->ctx->c.stream);
+    delete h;
+}
+
+int jet_hier_info(const jet_hier *h, int32_t *levels, int64_t *n_per_level, int64_t *m_per_level) {
+    if (!h) return JET_EINVAL;
+    if (levels) *levels = h->levels;
+    for (int32_t i = 0; i < h->levels; ++i) {
+        if (n_per_level) n_per_level[i] = h->n[i];
+        if (m_per_level) m_per_level[i] = h->nnz[i] / 2;
+    }
+    return JET_OK;
+}
+
+int jet_hier_level(const jet_hier *h, int32_t level, int32_t *n, const int64_t **xadj, const int32_t **adjncy,
+                   const int32_t **vwgt, const int32_t **adjwgt, const int32_t **cmap) {
+    if (!h || level < 0 || level >= h->levels) return JET_EINVAL;
+    if (n) *n = h->n[level];
+    if (xadj) *xadj = h->xadj[level];
+    if (adjncy) *adjncy = h->adj[level];
+    if (vwgt) *vwgt = h->vw[level];
+    if (adjwgt) *adjwgt = h->ew[level];
+    if (cmap) *cmap = level + 1 < h->levels ? h->cmap[level] : nullptr;
+    return JET_OK;
+}
+
+int jet_uncoarsen(jet_ctx *ctx, const jet_hier *h, int32_t k, double eps, uint64_t seed, int32_t *part_out,
+                  int64_t *cut_out, jet_stats *stats) {
+    if (!ctx || !h || bad_k_eps(k, eps) || (h->n[0] > 0 && !part_out)) return JET_EINVAL;
+    Ctx &c = ctx->c;
+    JET_TRY(use_device(c));
+    if (stats) {
+        memset(stats, 0, sizeof(*stats));
+        stats->ms_coarsen = h->ms_coarsen;
+    }
+    if (h->n[0] == 0) {
+        if (cut_out) *cut_out = 0;
+        return JET_OK;
+    }
+    int64_t l0 = c.launches;
+    int r = uncoarsen(c, h, k, eps, seed, part_out, cut_out, stats);
+    if (stats) {
+        stats->ms_total = stats->ms_coarsen + stats->ms_init + stats->ms_refine;
+        stats->kernel_launches = h->launches + (c.launches - l0);
+    }
+    return r;
+}
+
+int jet_refine(jet_ctx *ctx, int32_t n, const int64_t *xadj, const int32_t *adjncy, const int32_t *vwgt,
+               const int32_t *adjwgt, int32_t k, double eps, int32_t is_finest, uint64_t seed, int32_t *part_inout,
+               int64_t *cut_out) {
+    if (!ctx || bad_k_eps(k, eps)) return JET_EINVAL;
+    Ctx &c = ctx->c;
+    JET_TRY(use_device(c));
+    DGraph g;
+    DevBuf ones;
+    JET_TRY(prepare_graph(c, n, xadj, adjncy, vwgt, adjwgt, g, ones, true));
+    JET_TRY(check_part(c, n, part_inout, k));
+    if (n == 0) {
+        if (cut_out) *cut_out = 0;
+        c.last_trace.rec.clear();
+        c.last_trace.iters = 0;
+        return JET_OK;
+    }
+    return refine_level(c, g, k, eps, is_finest ? 1 : 0, seed, part_inout, cut_out, nullptr, nullptr);
+}
+
+int jet_last_trace(jet_ctx *ctx, int32_t cap, int32_t *kind, int64_t *nx, int64_t *nm, int64_t *cut, int64_t *maxw,
+                   int32_t *iters_out) {
+    if (!ctx || cap < 0) return JET_EINVAL;
+    const TraceHost &t = ctx->c.last_trace;
+    int32_t m = std::min<int32_t>(cap, (int32_t)t.rec.size());
+    for (int32_t i = 0; i < m; ++i) {
+        const TraceRec &r = t.rec[(size_t)i];
+        if (kind) kind[i] = r.kind;
+        if (nx) nx[i] = r.nx;
+        if (nm) nm[i] = r.nm;
+        if (cut) cut[i] = r.cut;
+        if (maxw) maxw[i] = r.maxw;
+    }
+    if (iters_out) *iters_out = t.iters;
+    return JET_OK;
+}
+
+int jet_partition(jet_ctx *ctx, int32_t n, const int64_t *xadj, const int32_t *adjncy, const int32_t *vwgt,
+                  const int32_t *adjwgt, int32_t k, double eps, uint64_t seed, int32_t *part_out, int64_t *cut_out,
+                  jet_stats *stats) {
+    if (!ctx || bad_k_eps(k, eps) || (n > 0 && !part_out)) return JET_EINVAL;
+    jet_hier *h = nullptr;
+    int r = jet_coarsen(ctx, n, xadj, adjncy, vwgt, adjwgt, k, seed, &h);
+    if (r < 0) return r;
+    r = jet_uncoarsen(ctx, h, k, eps, seed, part_out, cut_out, stats);
+    jet_hier_destroy(h);
+    return r;
+}
+
+int jet_partition_host(jet_ctx *ctx, int32_t n, const int64_t *xadj, const int32_t *adjncy, const int32_t *vwgt,
+                       const int32_t *adjwgt, int32_t k, double eps, uint64_t seed, int32_t *part_out, int64_t *cut_out,
+                       jet_stats *stats) {
+    if (!ctx || n < 0 || !xadj || bad_k_eps(k, eps) || (n > 0 && !part_out)) return JET_EINVAL;
+    Ctx &c = ctx->c;
+    JET_TRY(use_device(c));
+    cudaStream_t s = c.stream;
+    int64_t nnz = xadj[n];
+    if (nnz < 0 || (nnz > 0 && !adjncy)) return JET_EINVAL;
+    DevBuf dx, da, dv, dw, dp;
+    JET_TRY(dev_alloc(dx, (size_t)(n + 1) * 8, s));
+    JET_TRY(dev_alloc(da, (size_t)std::max<int64_t>(nnz, 1) * 4, s));
+    JET_TRY(dev_alloc(dp, (size_t)std::max(n, 1) * 4, s));
+    JET_CUDA_TRY(cudaMemcpyAsync(dx.p, xadj, (size_t)(n + 1) * 8, cudaMemcpyHostToDevice, s));
+    if (nnz > 0) JET_CUDA_TRY(cudaMemcpyAsync(da.p, adjncy, (size_t)nnz * 4, cudaMemcpyHostToDevice, s));
+    if (vwgt) {
+        JET_TRY(dev_alloc(dv, (size_t)std::max(n, 1) * 4, s));
+        JET_CUDA_TRY(cudaMemcpyAsync(dv.p, vwgt, (size_t)n * 4, cudaMemcpyHostToDevice, s));
+    }
+    if (adjwgt) {
+        JET_TRY(dev_alloc(dw, (size_t)std::max<int64_t>(nnz, 1) * 4, s));
+        if (nnz > 0) JET_CUDA_TRY(cudaMemcpyAsync(dw.p, adjwgt, (size_t)nnz * 4, cudaMemcpyHostToDevice, s));
+    }
+    int r = jet_partition(ctx, n, dx.as<int64_t>(), da.as<int32_t>(), vwgt ? dv.as<int32_t>() : nullptr,
+                          adjwgt ? dw.as<int32_t>() : nullptr, k, eps, seed, dp.as<int32_t>(), cut_out, stats);
+    if (r < 0) return r;
+    if (n > 0) JET_CUDA_TRY(cudaMemcpyAsync(part_out, dp.p, (size_t)n * 4, cudaMemcpyDeviceToHost, s));
+    JET_CUDA_TRY(cudaStreamSynchronize(s));
+    return r;
+}
+
+int jet_cut(jet_ctx *ctx, int32_t n, const int64_t *xadj, const int32_t *adjncy, const int32_t *vwgt,
+            const int32_t *adjwgt, int32_t k, const int32_t *part, int64_t *cut_out, int64_t *pw_out) {
+    if (!ctx || bad_k_eps(k, 0.0)) return JET_EINVAL;
+    Ctx &c = ctx->c;
+    JET_TRY(use_device(c));
+    DGraph g;
+    DevBuf ones;
+    JET_TRY(prepare_graph(c, n, xadj, adjncy, vwgt, adjwgt, g, ones, true));
+    JET_TRY(check_part(c, n, part, k));
+    return cut_and_weights(c, g, k, part, cut_out, pw_out);
+}
+
+int jet_lp_pass(jet_ctx *ctx, int32_t n, const int64_t *xadj, const int32_t *adjncy, const int32_t *vwgt,
+                const int32_t *adjwgt, int32_t k, const int32_t *part, const uint8_t *locked, double cval,
+                uint32_t flags, int32_t *pd_out, int32_t *gain_out, uint8_t *inx_out, int32_t *f2_out,
+                uint8_t *inm_out) {
+    if (!ctx || bad_k_eps(k, 0.0) || !(cval >= 0 && cval <= 1)) return JET_EINVAL;
+    Ctx &c = ctx->c;
+    JET_TRY(use_device(c));
+    DGraph g;
+    DevBuf ones;
+    JET_TRY(prepare_graph(c, n, xadj, adjncy, vwgt, adjwgt, g, ones, true));
+    JET_TRY(check_part(c, n, part, k));
+    return lp_pass(c, g, k, part, locked, cval, flags, pd_out, gain_out, inx_out, f2_out, inm_out);
+}
+
+int jet_rebalance_pass(jet_ctx *ctx, int32_t n, const int64_t *xadj, const int32_t *adjncy, const int32_t *vwgt,
+                       const int32_t *adjwgt, int32_t k, double eps, int32_t strong, uint64_t seed, int32_t iter,
+                       const int32_t *part, int32_t *dest_out, int32_t *loss_out, int64_t *nmoves_out,
+                       int64_t *ncand_out) {
+    if (!ctx || bad_k_eps(k, eps) || iter < 0) return JET_EINVAL;
+    Ctx &c = ctx->c;
+    JET_TRY(use_device(c));
+    DGraph g;
+    DevBuf ones;
+    JET_TRY(prepare_graph(c, n, xadj, adjncy, vwgt, adjwgt, g, ones, true));
+    JET_TRY(check_part(c, n, part, k));
+    return rebalance_pass(c, g, k, eps, strong, seed, iter, part, dest_out, loss_out, nmoves_out, ncand_out);
+}
+
+int jet_hem(jet_ctx *ctx, int32_t n, const int64_t *xadj, const int32_t *adjncy, const int32_t *adjwgt, uint64_t seed,
+            int32_t level, int32_t rounds, int32_t *mate_out) {
+    if (!ctx || rounds < 0 || rounds > 64 || level < 0 || (n > 0 && !mate_out)) return JET_EINVAL;
+    Ctx &c = ctx->c;
+    JET_TRY(use_device(c));
+    DGraph g;
+    DevBuf ones;
+    JET_TRY(prepare_graph(c, n, xadj, adjncy, nullptr, adjwgt, g, ones, true));
+    return hem(c, g, seed, level, rounds, mate_out);
+}
+
+int jet_initial_partition(jet_ctx *ctx, int32_t n, const int64_t *xadj, const int32_t *adjncy, const int32_t *vwgt,
+                          int32_t k, int32_t *part_out) {
+    if (!ctx || bad_k_eps(k, 0.0) || (n > 0 && !part_out)) return JET_EINVAL;
+    Ctx &c = ctx->c;
+    JET_TRY(use_device(c));
+    DGraph g;
+    DevBuf ones;
+    JET_TRY(prepare_graph(c, n, xadj, adjncy, vwgt, nullptr, g, ones, true));
+    return initial_partition(c, g, k, part_out);
+}
+
+const char *jet_status_string(int s) {
+    switch (s) {
+    case JET_OK: return "ok";
+    case JET_WUNBALANCED: return "warning: result violates the balance limit";
+    case JET_WITERLIMIT: return "warning: a level hit max_iters_per_level";
+    case JET_EINVAL: return "invalid argument";
+    case JET_EGRAPH: return "invalid graph";
+    case JET_ENOMEM: return "device allocation failed";
+    case JET_ECUDA: return "CUDA error";
+    case JET_ETIMEOUT: return "device wait timed out";
+    case JET_EOVERFLOW: return "weight sums exceed 2^31";
+    default: return "unknown status";
+    }
+}
+
+/* Text of the last CUDA error recorded on this thread (diagnostics). */
+const char *jet_last_error(void) { return last_error_text(); }
+
+}  // extern "C"

@@ -1,0 +1,652 @@
+// Coarsening (Sec. 3.1): heavy-edge matching, coarse mapping, edge
+// contraction (Alg. 2), projection (Alg. 1 ProjectPartition) and the greedy
+// initial partition of the coarsest graph (Alg. 1 InitialPartition).
+//
+// Matching is a deterministic handshake: every unmatched vertex proposes its
+// heaviest unmatched neighbour (ties: smaller splitmix64 hash of the
+// neighbour, then smaller id) and mutual proposals match, round after round.
+// Contraction merges each coarse vertex's (at most two) fine rows, sorts the
+// mapped neighbour ids and sums duplicate entries: rows of <= 32 entries in
+// one warp (register bitonic network), longer rows in one block (bitonic sort
+// in shared memory, or in a global scratch segment for very long rows).
+#include "jet_internal.cuh"
+
+#include <algorithm>
+
+namespace jet {
+
+template <bool EW>
+__device__ __forceinline__ int32_t cw(const DGraph &g, int64_t j) {
+    if constexpr (EW) return __ldg(g.ew + j);
+    else return 1;
+}
+
+// Phase 2 of device_exscan: exclusive scan of the tile sums (one block).
+__global__ void __launch_bounds__(1024) k_scan_sums(int64_t *tile_sums, int64_t ntiles, int64_t *total_dev) {
+    __shared__ long long sh[40];
+    long long carry = 0;
+    for (int64_t t0 = 0; t0 < ntiles; t0 += blockDim.x) {
+        int64_t t = t0 + threadIdx.x;
+        long long x = t < ntiles ? tile_sums[t] : 0;
+        long long tot = 0;
+        long long ex = block_exscan_i64(x, sh, &tot);
+        if (t < ntiles) tile_sums[t] = carry + ex;
+        carry += tot;
+    }
+    if (threadIdx.x == 0 && total_dev) *total_dev = carry;
+}
+
+struct HemCtl {
+    int32_t stop;
+    int32_t pad;
+    int64_t added[64];
+};
+
+__device__ __forceinline__ bool hem_better(int32_t w1, uint64_t h1, int32_t u1, int32_t w2, uint64_t h2, int32_t u2) {
+    if (u2 < 0) return u1 >= 0;
+    if (u1 < 0) return false;
+    if (w1 != w2) return w1 > w2;
+    if (h1 != h2) return h1 < h2;
+    return u1 < u2;
+}
+
+__device__ __forceinline__ uint64_t hem_hash(uint64_t seed, uint64_t salt, int32_t u) {
+    return splitmix64(seed ^ salt ^ (uint64_t)(uint32_t)u);
+}
+
+__device__ __forceinline__ bool hem_skip(const HemCtl *hc, int r) {
+    return r > 0 && (hc->stop || hc->added[r - 1] == 0);
+}
+
+// One proposal round (short rows): prop[v] = chosen neighbour or -1.
+template <bool EW>
+__global__ void __launch_bounds__(kTB) k_hem_propose_small(DGraph g, const int32_t *mate, int32_t *prop, uint64_t seed,
+                                                           uint64_t salt, int r, HemCtl *hc) {
+    if (hem_skip(hc, r)) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) hc->stop = 1;
+        return;
+    }
+    int32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= g.n) return;
+    int64_t beg = ld_xadj(g.xadj, v), end = ld_xadj(g.xadj, (int64_t)v + 1);
+    if (end - beg > kSmallDeg) return;
+    int32_t bu = -1, bw = 0;
+    uint64_t bh = 0;
+    if (mate[v] < 0) {
+        for (int64_t j = beg; j < end; ++j) {
+            int32_t u = __ldg(g.adj + j);
+            if (mate[u] >= 0) continue;
+            int32_t w = cw<EW>(g, j);
+            uint64_t h = hem_hash(seed, salt, u);
+            if (hem_better(u >= 0 ? w : 0, h, u, bw, bh, bu)) { bu = u; bw = w; bh = h; }
+        }
+    }
+    prop[v] = bu;
+}
+
+template <bool EW>
+__global__ void __launch_bounds__(kTB) k_hem_propose_big(DGraph g, const int32_t *bigv, int32_t nbig, const int32_t *mate,
+                                                         int32_t *prop, uint64_t seed, uint64_t salt, int r, HemCtl *hc) {
+    if (hem_skip(hc, r)) return;
+    const int warps = blockDim.x >> 5;
+    const unsigned lane = lane_id();
+    for (int64_t w = (int64_t)blockIdx.x * warps + (threadIdx.x >> 5); w < nbig; w += (int64_t)gridDim.x * warps) {
+        int32_t v = bigv[w];
+        int32_t bu = -1, bw = 0;
+        uint64_t bh = 0;
+        if (mate[v] < 0) {
+            int64_t beg = ld_xadj(g.xadj, v), end = ld_xadj(g.xadj, (int64_t)v + 1);
+            for (int64_t j = beg + lane; j < end; j += 32) {
+                int32_t u = __ldg(g.adj + j);
+                if (mate[u] >= 0) continue;
+                int32_t ww = cw<EW>(g, j);
+                uint64_t h = hem_hash(seed, salt, u);
+                if (hem_better(ww, h, u, bw, bh, bu)) { bu = u; bw = ww; bh = h; }
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            int32_t ou = __shfl_xor_sync(0xffffffffu, bu, o);
+            int32_t ow = __shfl_xor_sync(0xffffffffu, bw, o);
+            uint64_t oh = __shfl_xor_sync(0xffffffffu, bh, o);
+            if (hem_better(ow, oh, ou, bw, bh, bu)) { bu = ou; bw = ow; bh = oh; }
+        }
+        if (lane == 0) prop[v] = bu;
+    }
+}
+
+// Mutual proposals match (synchronous: every proposal of the round is read
+// before any mate changes matter, since proposals only name unmatched ones).
+__global__ void __launch_bounds__(kTB) k_hem_match(int32_t n, int32_t *mate, const int32_t *prop, int r, HemCtl *hc) {
+    __shared__ long long red[40];
+    if (hc->stop) return;
+    long long c = 0;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        int32_t u = prop[v];
+        if (u >= 0 && prop[u] == (int32_t)v) { mate[v] = u; ++c; }
+    }
+    c = block_sum_i64(c, red);
+    if (threadIdx.x == 0 && c) atomic_add_i64(&hc->added[r], c);
+}
+
+__global__ void k_collect_rows(DGraph g, int32_t *list, int32_t *count) {
+    int32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+    bool big = v < g.n && ld_xadj(g.xadj, (int64_t)v + 1) - ld_xadj(g.xadj, v) > kSmallDeg;
+    int slot = warp_append(count, big);
+    if (big) list[slot] = v;
+}
+
+__global__ void k_fill(int32_t *p, int64_t n, int32_t val) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) p[i] = val;
+}
+
+static int big_rows(Ctx &c, const DGraph &g, DevBuf &buf, int32_t &nbig) {
+    cudaStream_t s = c.stream;
+    JET_TRY(dev_alloc(buf, (size_t)std::max<int64_t>(g.n, 1) * 4 + 256, s));
+    int32_t *cnt = reinterpret_cast<int32_t *>(buf.as<char>() + (size_t)std::max<int64_t>(g.n, 1) * 4);
+    cnt = reinterpret_cast<int32_t *>((reinterpret_cast<uintptr_t>(cnt) + 15) & ~uintptr_t(15));
+    JET_CUDA_TRY(cudaMemsetAsync(cnt, 0, 4, s));
+    if (g.n > 0) k_collect_rows<<<grid_for(g.n, kTB), kTB, 0, s>>>(g, buf.as<int32_t>(), cnt);
+    if (g.n > 0) c.launches += 1;
+    JET_CUDA_TRY(cudaGetLastError());
+    JET_CUDA_TRY(cudaMemcpyAsync(c.pinned, cnt, 4, cudaMemcpyDeviceToHost, s));
+    JET_CUDA_TRY(cudaStreamSynchronize(s));
+    nbig = (int32_t)(c.pinned[0] & 0xFFFFFFFF);
+    return JET_OK;
+}
+
+int hem(Ctx &c, const DGraph &g, uint64_t seed, int32_t level, int32_t rounds, int32_t *mate) {
+    cudaStream_t s = c.stream;
+    if (g.n == 0) return JET_OK;
+    DevBuf bigbuf, pbuf, hbuf;
+    int32_t nbig = 0;
+    JET_TRY(big_rows(c, g, bigbuf, nbig));
+    JET_TRY(dev_alloc(pbuf, (size_t)g.n * 4, s));
+    JET_TRY(dev_alloc(hbuf, sizeof(HemCtl), s));
+    HemCtl *hc = hbuf.as<HemCtl>();
+    JET_CUDA_TRY(cudaMemsetAsync(hc, 0, sizeof(HemCtl), s));
+    k_fill<<<grid_for(g.n, kTB, 4096), kTB, 0, s>>>(mate, g.n, -1);
+    c.launches += 1;
+    rounds = std::min(rounds, 64);
+    int gl = num_sms() * 8;
+    for (int r = 0; r < rounds; ++r) {
+        uint64_t salt = 0xD1B54A32D192ED03ULL * (uint64_t)(64 * (int64_t)level + r + 1);
+        if (g.ew) k_hem_propose_small<true><<<grid_for(g.n, kTB), kTB, 0, s>>>(g, mate, pbuf.as<int32_t>(), seed, salt, r, hc);
+        else k_hem_propose_small<false><<<grid_for(g.n, kTB), kTB, 0, s>>>(g, mate, pbuf.as<int32_t>(), seed, salt, r, hc);
+        c.launches += 1;
+        if (nbig > 0) {
+            int gb = std::min(gl, grid_for(nbig, kTB / 32));
+            if (g.ew) k_hem_propose_big<true><<<gb, kTB, 0, s>>>(g, bigbuf.as<int32_t>(), nbig, mate, pbuf.as<int32_t>(), seed, salt, r, hc);
+            else k_hem_propose_big<false><<<gb, kTB, 0, s>>>(g, bigbuf.as<int32_t>(), nbig, mate, pbuf.as<int32_t>(), seed, salt, r, hc);
+            c.launches += 1;
+        }
+        k_hem_match<<<std::min(gl, grid_for(g.n, kTB)), kTB, 0, s>>>(g.n, mate, pbuf.as<int32_t>(), r, hc);
+        c.launches += 1;
+    }
+    JET_CUDA_TRY(cudaGetLastError());
+    JET_CUDA_TRY(cudaStreamSynchronize(s));
+    return JET_OK;
+}
+
+// ---------------------------------------------------------------------------
+// coarse mapping: representatives are unmatched vertices and the smaller id
+// of each pair; C[v] = rank of v's representative
+// ---------------------------------------------------------------------------
+struct RepFlag {
+    const int32_t *mate;
+    __device__ int64_t operator()(int64_t v) const {
+        int32_t m = mate[v];
+        return (m < 0 || v < m) ? 1 : 0;
+    }
+};
+
+__global__ void k_cmap(int32_t n, const int32_t *mate, const int64_t *cidx, int32_t *cmap, int32_t *crep) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        int32_t m = mate[v];
+        int64_t r = (m >= 0 && m < v) ? m : v;
+        cmap[v] = (int32_t)cidx[r];
+        if (r == v) crep[cidx[v]] = (int32_t)v;
+    }
+}
+
+struct RowBound {
+    const int64_t *xadj;
+    const int32_t *crep, *mate;
+    __device__ int64_t operator()(int64_t c) const {
+        int32_t r = crep[c];
+        int32_t m = mate[r];
+        int64_t b = xadj[r + 1] - xadj[r];
+        if (m >= 0) b += xadj[(int64_t)m + 1] - xadj[m];
+        return b;
+    }
+};
+
+constexpr int kSortSmem = 4096;   // entries sorted in shared memory by one block
+
+__host__ __device__ inline int64_t pow2ceil(int64_t x) {
+    int64_t p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+struct HugeScratch {
+    const int64_t *boff;
+    const int64_t *btot;   // unused by the functor
+    const int32_t *crep, *mate;
+    const int64_t *xadj;
+    __device__ int64_t operator()(int64_t c) const {
+        int32_t r = crep[c];
+        int32_t m = mate[r];
+        int64_t b = xadj[r + 1] - xadj[r];
+        if (m >= 0) b += xadj[(int64_t)m + 1] - xadj[m];
+        return b > kSortSmem ? pow2ceil(b) : 0;
+    }
+};
+
+__global__ void k_coarse_vw(int32_t nc, const int32_t *crep, const int32_t *mate, const int32_t *vw, int32_t *vwc,
+                            int32_t *small_list, int32_t *large_list, int32_t *counts, const int64_t *boff,
+                            const int64_t *btot) {
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ((int64_t)nc + 31) / 32 * 32;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        bool valid = c < nc;
+        bool small = false;
+        if (valid) {
+            int32_t r = crep[c];
+            int32_t m = mate[r];
+            vwc[c] = vw[r] + (m >= 0 ? vw[m] : 0);
+            int64_t b = (c + 1 < nc ? boff[c + 1] : *btot) - boff[c];
+            small = b <= 32;
+        }
+        int s1 = warp_append(&counts[0], valid && small);
+        if (valid && small) small_list[s1] = (int32_t)c;
+        int s2 = warp_append(&counts[1], valid && !small);
+        if (valid && !small) large_list[s2] = (int32_t)c;
+    }
+}
+
+// Gathers entry i (0 <= i < bound) of coarse row c: (C[u] << 32) | w.
+template <bool EW>
+__device__ __forceinline__ unsigned long long row_entry(const DGraph &g, const int32_t *cmap, int32_t r, int32_t m,
+                                                        int64_t degr, int64_t i) {
+    int64_t j = i < degr ? ld_xadj(g.xadj, r) + i : ld_xadj(g.xadj, m) + (i - degr);
+    int32_t cu = cmap[__ldg(g.adj + j)];
+    return ((unsigned long long)(uint32_t)cu << 32) | (uint32_t)cw<EW>(g, j);
+}
+
+// Rows of <= 32 entries: one warp, register bitonic sort, segmented sums.
+template <bool EW>
+__global__ void __launch_bounds__(kTB) k_contract_small(DGraph g, const int32_t *cmap, const int32_t *mate,
+                                                        const int32_t *crep, const int32_t *list, const int32_t *counts,
+                                                        const int64_t *boff, int32_t *tadj, int32_t *tw, int32_t *rowcnt) {
+    const int warps = blockDim.x >> 5;
+    const unsigned lane = lane_id();
+    const int32_t nrows = counts[0];
+    for (int64_t w = (int64_t)blockIdx.x * warps + (threadIdx.x >> 5); w < nrows; w += (int64_t)gridDim.x * warps) {
+        int32_t c = list[w];
+        int32_t r = crep[c], m = mate[r];
+        int64_t degr = ld_xadj(g.xadj, (int64_t)r + 1) - ld_xadj(g.xadj, r);
+        int64_t bound = degr + (m >= 0 ? ld_xadj(g.xadj, (int64_t)m + 1) - ld_xadj(g.xadj, m) : 0);
+        unsigned long long key = ~0ull;
+        if ((int64_t)lane < bound) key = row_entry<EW>(g, cmap, r, m, degr, lane);
+#pragma unroll
+        for (int kk = 2; kk <= 32; kk <<= 1) {
+#pragma unroll
+            for (int j = kk >> 1; j > 0; j >>= 1) {
+                unsigned long long o = __shfl_xor_sync(0xffffffffu, key, j);
+                bool up = (lane & kk) == 0;
+                bool lower = (lane & j) == 0;
+                key = (lower == up) ? (key < o ? key : o) : (key > o ? key : o);
+            }
+        }
+        uint32_t ck = (uint32_t)(key >> 32);
+        uint32_t prev = __shfl_up_sync(0xffffffffu, ck, 1);
+        bool head = key != ~0ull && (lane == 0 || prev != ck) && ck != (uint32_t)c;
+        long long sum = 0;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            uint32_t cj = __shfl_sync(0xffffffffu, ck, j);
+            unsigned long long kj = __shfl_sync(0xffffffffu, key, j);
+            if (j >= (int)lane && cj == ck && kj != ~0ull) sum += (long long)(uint32_t)(kj & 0xFFFFFFFFull);
+        }
+        unsigned hm = __ballot_sync(0xffffffffu, head);
+        int pos = __popc(hm & ((1u << lane) - 1u));
+        int64_t base = boff[c];
+        if (head) { tadj[base + pos] = (int32_t)ck; tw[base + pos] = (int32_t)sum; }
+        if (lane == 0) rowcnt[c] = __popc(hm);
+    }
+}
+
+// Longer rows: one block per row; bitonic sort in shared memory (or in the
+// row's global scratch segment when longer than kSortSmem).
+template <bool EW>
+__global__ void __launch_bounds__(kTB) k_contract_large(DGraph g, const int32_t *cmap, const int32_t *mate,
+                                                        const int32_t *crep, const int32_t *list, const int32_t *counts,
+                                                        const int64_t *boff, const int64_t *hoff,
+                                                        unsigned long long *hscr, int32_t *tadj, int32_t *tw,
+                                                        int32_t *rowcnt) {
+    __shared__ unsigned long long sk[kSortSmem];
+    __shared__ long long sh[40];
+    const int32_t nrows = counts[1];
+    for (int64_t w = blockIdx.x; w < nrows; w += gridDim.x) {
+        int32_t c = list[w];
+        int32_t r = crep[c], m = mate[r];
+        int64_t degr = ld_xadj(g.xadj, (int64_t)r + 1) - ld_xadj(g.xadj, r);
+        int64_t bound = degr + (m >= 0 ? ld_xadj(g.xadj, (int64_t)m + 1) - ld_xadj(g.xadj, m) : 0);
+        int64_t P = pow2ceil(bound);
+        unsigned long long *keys = P <= kSortSmem ? sk : hscr + hoff[c];
+        for (int64_t i = threadIdx.x; i < P; i += blockDim.x)
+            keys[i] = i < bound ? row_entry<EW>(g, cmap, r, m, degr, i) : ~0ull;
+        __syncthreads();
+        for (int64_t kk = 2; kk <= P; kk <<= 1) {
+            for (int64_t j = kk >> 1; j > 0; j >>= 1) {
+                for (int64_t i = threadIdx.x; i < P; i += blockDim.x) {
+                    int64_t ixj = i ^ j;
+                    if (ixj > i) {
+                        unsigned long long a = keys[i], b = keys[ixj];
+                        bool up = (i & kk) == 0;
+                        if ((a > b) == up) { keys[i] = b; keys[ixj] = a; }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        // heads of runs with equal coarse id, summed, self id dropped; written in order
+        int64_t base = boff[c];
+        long long written = 0;
+        for (int64_t i0 = 0; i0 < bound; i0 += blockDim.x) {
+            int64_t i = i0 + threadIdx.x;
+            bool head = false;
+            uint32_t ck = 0;
+            long long sum = 0;
+            if (i < bound) {
+                unsigned long long key = keys[i];
+                ck = (uint32_t)(key >> 32);
+                head = (i == 0 || (uint32_t)(keys[i - 1] >> 32) != ck) && ck != (uint32_t)c;
+                if (head) {
+                    for (int64_t t = i; t < bound && (uint32_t)(keys[t] >> 32) == ck; ++t)
+                        sum += (long long)(uint32_t)(keys[t] & 0xFFFFFFFFull);
+                }
+            }
+            long long tot = 0;
+            long long pos = block_exscan_i64(head ? 1 : 0, sh, &tot);
+            if (head) { tadj[base + written + pos] = (int32_t)ck; tw[base + written + pos] = (int32_t)sum; }
+            written += tot;
+        }
+        if (threadIdx.x == 0) rowcnt[c] = (int32_t)written;
+        __syncthreads();
+    }
+}
+
+struct CountVal {
+    const int32_t *cnt;
+    __device__ int64_t operator()(int64_t c) const { return cnt[c]; }
+};
+
+__global__ void k_finish_xadj(int32_t nc, const int64_t *ex, const int64_t *tot, int64_t *xadj_c) {
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c <= nc; c += (int64_t)gridDim.x * blockDim.x)
+        xadj_c[c] = c < nc ? ex[c] : *tot;
+}
+
+__global__ void k_copy_rows(int32_t nc, const int64_t *boff, const int64_t *xadj_c, const int32_t *tadj, const int32_t *tw,
+                            int32_t *adj_c, int32_t *ew_c) {
+    const int warps = blockDim.x >> 5;
+    const unsigned lane = lane_id();
+    for (int64_t c = (int64_t)blockIdx.x * warps + (threadIdx.x >> 5); c < nc; c += (int64_t)gridDim.x * warps) {
+        int64_t src = boff[c], dst = xadj_c[c], len = xadj_c[c + 1] - dst;
+        for (int64_t i = lane; i < len; i += 32) {
+            adj_c[dst + i] = tadj[src + i];
+            ew_c[dst + i] = tw[src + i];
+        }
+    }
+}
+
+// One coarsening level: matching, map, contraction.  Returns JET_OK and sets
+// stalled=true (without building the level) when n_c > 0.95 n.
+static int coarsen_level(Ctx &c, const DGraph &g, uint64_t seed, int32_t level, jet_hier *h, bool &stalled) {
+    cudaStream_t s = c.stream;
+    stalled = false;
+    int64_t n = g.n;
+    DevBuf mbuf, cidxb, scan_scr, tot;
+    JET_TRY(dev_alloc(mbuf, (size_t)n * 4, s));
+    int32_t *mate = mbuf.as<int32_t>();
+    JET_TRY(hem(c, g, seed, level, c.opt.hem_rounds, mate));
+    JET_TRY(dev_alloc(cidxb, (size_t)n * 8, s));
+    JET_TRY(dev_alloc(scan_scr, (size_t)std::max<int64_t>(scan_tiles_for(n), 1) * 8 * 2 + 64, s));
+    JET_TRY(dev_alloc(tot, 64, s));
+    int64_t *totp = tot.as<int64_t>();
+    c.launches += 3;
+    JET_TRY(device_exscan(RepFlag{mate}, n, cidxb.as<int64_t>(), totp, scan_scr.as<int64_t>(), s));
+    JET_CUDA_TRY(cudaMemcpyAsync(c.pinned, totp, 8, cudaMemcpyDeviceToHost, s));
+    JET_CUDA_TRY(cudaStreamSynchronize(s));
+    int64_t nc = c.pinned[0];
+    if (100 * nc > 95 * n) { stalled = true; return JET_OK; }
+    // cmap (owned by the hierarchy) and representatives
+    DevBuf cmapb, crepb;
+    JET_TRY(dev_alloc(cmapb, (size_t)n * 4, s));
+    JET_TRY(dev_alloc(crepb, (size_t)std::max<int64_t>(nc, 1) * 4, s));
+    int32_t *cmap = cmapb.as<int32_t>(), *crep = crepb.as<int32_t>();
+    k_cmap<<<grid_for(n, kTB, 8192), kTB, 0, s>>>(g.n, mate, cidxb.as<int64_t>(), cmap, crep);
+    c.launches += 1;
+    // bounds of the coarse rows
+    DevBuf boffb, hoffb;
+    JET_TRY(dev_alloc(boffb, (size_t)std::max<int64_t>(nc, 1) * 8, s));
+    JET_TRY(dev_alloc(hoffb, (size_t)std::max<int64_t>(nc, 1) * 8, s));
+    int64_t *boff = boffb.as<int64_t>(), *hoff = hoffb.as<int64_t>();
+    c.launches += 3;
+    JET_TRY(device_exscan(RowBound{g.xadj, crep, mate}, nc, boff, totp, scan_scr.as<int64_t>(), s));
+    c.launches += 3;
+    JET_TRY(device_exscan(HugeScratch{boff, totp, crep, mate, g.xadj}, nc, hoff, totp + 1, scan_scr.as<int64_t>(), s));
+    JET_CUDA_TRY(cudaMemcpyAsync(c.pinned, totp, 16, cudaMemcpyDeviceToHost, s));
+    JET_CUDA_TRY(cudaStreamSynchronize(s));
+    int64_t btotal = c.pinned[0], htotal = c.pinned[1];
+    // coarse vertex weights and row classes
+    DevBuf vwcb, lists, tadjb, twb, cntb, hscrb;
+    JET_TRY(dev_alloc(vwcb, (size_t)std::max<int64_t>(nc, 1) * 4, s));
+    JET_TRY(dev_alloc(lists, (size_t)std::max<int64_t>(nc, 1) * 8 + 64, s));
+    int32_t *small_list = lists.as<int32_t>(), *large_list = small_list + std::max<int64_t>(nc, 1);
+    int32_t *counts = reinterpret_cast<int32_t *>(large_list + std::max<int64_t>(nc, 1));
+    JET_CUDA_TRY(cudaMemsetAsync(counts, 0, 8, s));
+    k_coarse_vw<<<grid_for(nc, kTB, 8192), kTB, 0, s>>>((int32_t)nc, crep, mate, g.vw, vwcb.as<int32_t>(), small_list,
+                                                         large_list, counts, boff, totp);
+    JET_TRY(dev_alloc(tadjb, (size_t)std::max<int64_t>(btotal, 1) * 4, s));
+    JET_TRY(dev_alloc(twb, (size_t)std::max<int64_t>(btotal, 1) * 4, s));
+    JET_TRY(dev_alloc(cntb, (size_t)std::max<int64_t>(nc, 1) * 4, s));
+    JET_TRY(dev_alloc(hscrb, (size_t)std::max<int64_t>(htotal, 1) * 8, s));
+    int gl = num_sms() * 8;
+    int gsmall = std::min(gl, grid_for(nc, kTB / 32));
+    int glarge = std::min(num_sms() * 4, (int)std::max<int64_t>(1, nc));
+    if (g.ew) {
+        k_contract_small<true><<<gsmall, kTB, 0, s>>>(g, cmap, mate, crep, small_list, counts, boff, tadjb.as<int32_t>(), twb.as<int32_t>(), cntb.as<int32_t>());
+        c.launches += 1;
+        k_contract_large<true><<<glarge, kTB, 0, s>>>(g, cmap, mate, crep, large_list, counts, boff, hoff, hscrb.as<unsigned long long>(), tadjb.as<int32_t>(), twb.as<int32_t>(), cntb.as<int32_t>());
+        c.launches += 1;
+    } else {
+        k_contract_small<false><<<gsmall, kTB, 0, s>>>(g, cmap, mate, crep, small_list, counts, boff, tadjb.as<int32_t>(), twb.as<int32_t>(), cntb.as<int32_t>());
+        c.launches += 1;
+        k_contract_large<false><<<glarge, kTB, 0, s>>>(g, cmap, mate, crep, large_list, counts, boff, hoff, hscrb.as<unsigned long long>(), tadjb.as<int32_t>(), twb.as<int32_t>(), cntb.as<int32_t>());
+        c.launches += 1;
+    }
+    JET_CUDA_TRY(cudaGetLastError());
+    // coarse xadj
+    DevBuf xcb, exb;
+    JET_TRY(dev_alloc(xcb, (size_t)(nc + 1) * 8, s));
+    JET_TRY(dev_alloc(exb, (size_t)std::max<int64_t>(nc, 1) * 8, s));
+    c.launches += 3;
+    JET_TRY(device_exscan(CountVal{cntb.as<int32_t>()}, nc, exb.as<int64_t>(), totp + 2, scan_scr.as<int64_t>(), s));
+    k_finish_xadj<<<grid_for(nc + 1, kTB, 8192), kTB, 0, s>>>((int32_t)nc, exb.as<int64_t>(), totp + 2, xcb.as<int64_t>());
+    c.launches += 1;
+    JET_CUDA_TRY(cudaMemcpyAsync(c.pinned, totp + 2, 8, cudaMemcpyDeviceToHost, s));
+    JET_CUDA_TRY(cudaStreamSynchronize(s));
+    int64_t nnzc = c.pinned[0];
+    DevBuf adjcb, ewcb;
+    JET_TRY(dev_alloc(adjcb, (size_t)std::max<int64_t>(nnzc, 1) * 4, s));
+    JET_TRY(dev_alloc(ewcb, (size_t)std::max<int64_t>(nnzc, 1) * 4, s));
+    k_copy_rows<<<std::min(gl, grid_for(nc, kTB / 32)), kTB, 0, s>>>((int32_t)nc, boff, xcb.as<int64_t>(), tadjb.as<int32_t>(),
+                                                                    twb.as<int32_t>(), adjcb.as<int32_t>(), ewcb.as<int32_t>());
+    JET_CUDA_TRY(cudaGetLastError());
+    int32_t i = h->levels;
+    h->cmap[i - 1] = cmap;
+    h->n[i] = (int32_t)nc;
+    h->nnz[i] = nnzc;
+    h->xadj[i] = xcb.as<int64_t>();
+    h->adj[i] = adjcb.as<int32_t>();
+    h->vw[i] = vwcb.as<int32_t>();
+    h->ew[i] = ewcb.as<int32_t>();
+    h->levels = i + 1;
+    h->bufs.push_back(std::move(cmapb));
+    h->bufs.push_back(std::move(xcb));
+    h->bufs.push_back(std::move(adjcb));
+    h->bufs.push_back(std::move(vwcb));
+    h->bufs.push_back(std::move(ewcb));
+    JET_CUDA_TRY(cudaStreamSynchronize(s));
+    return JET_OK;
+}
+
+__global__ void k_ones(int32_t *p, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) p[i] = 1;
+}
+
+// MLCoarsen of Alg. 1 (see jet_coarsen in jet.h for the stop rules).
+int coarsen(Ctx &c, const DGraph &g0, int32_t k, uint64_t seed, jet_hier *h) {
+    cudaStream_t s = c.stream;
+    h->levels = 1;
+    h->k = k;
+    h->n[0] = g0.n;
+    h->nnz[0] = g0.nnz;
+    h->xadj[0] = g0.xadj;
+    h->adj[0] = g0.adj;
+    h->ew[0] = g0.ew;
+    if (g0.vw) {
+        h->vw[0] = g0.vw;
+    } else {
+        DevBuf ones;
+        JET_TRY(dev_alloc(ones, (size_t)std::max<int32_t>(g0.n, 1) * 4, s));
+        if (g0.n > 0) k_ones<<<grid_for(g0.n, kTB, 8192), kTB, 0, s>>>(ones.as<int32_t>(), g0.n);
+        if (g0.n > 0) c.launches += 1;
+        JET_CUDA_TRY(cudaGetLastError());
+        h->vw[0] = ones.as<int32_t>();
+        h->bufs.push_back(std::move(ones));
+    }
+    int32_t T = c.opt.coarsen_target > 0 ? c.opt.coarsen_target : std::max(8 * k, 256);
+    int32_t maxl = std::min<int32_t>(c.opt.max_levels, JET_MAX_LEVELS);
+    while (h->n[h->levels - 1] > T && h->levels < maxl) {
+        int32_t i = h->levels - 1;
+        DGraph gi;
+        gi.n = h->n[i]; gi.nnz = h->nnz[i]; gi.xadj = h->xadj[i]; gi.adj = h->adj[i]; gi.vw = h->vw[i]; gi.ew = h->ew[i];
+        bool stalled = false;
+        JET_TRY(coarsen_level(c, gi, seed, i, h, stalled));
+        if (stalled) break;
+    }
+    return JET_OK;
+}
+
+// ---------------------------------------------------------------------------
+// projection (Alg. 1 ProjectPartition)
+// ---------------------------------------------------------------------------
+__global__ void k_project(int32_t n, const int32_t *cmap, const int32_t *pc, int32_t *pf) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+        pf[v] = pc[cmap[v]];
+}
+
+int project(Ctx &c, int32_t n_fine, const int32_t *cmap, const int32_t *coarse_part, int32_t *fine_part) {
+    if (n_fine > 0) k_project<<<grid_for(n_fine, kTB, 8192), kTB, 0, c.stream>>>(n_fine, cmap, coarse_part, fine_part);
+    if (n_fine > 0) c.launches += 1;
+    JET_CUDA_TRY(cudaGetLastError());
+    return JET_OK;
+}
+
+// ---------------------------------------------------------------------------
+// greedy initial partition: order by (component's lowest id, BFS level from
+// it, id); P(v) = floor(k S(v) / W) with S(v) the weight before v.  One block.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_initial_partition(DGraph g, int32_t k, int32_t *root, int32_t *dist,
+                                                            ulonglong2 *keys, int64_t P, int32_t *part) {
+    __shared__ long long sh[40];
+    const int32_t n = g.n;
+    for (int32_t v = threadIdx.x; v < n; v += blockDim.x) root[v] = v;
+    __syncthreads();
+    // components: minimum id by relaxation and pointer jumping
+    for (;;) {
+        int changed = 0;
+        for (int32_t v = threadIdx.x; v < n; v += blockDim.x) {
+            int32_t r = root[v];
+            int64_t e = ld_xadj(g.xadj, (int64_t)v + 1);
+            for (int64_t j = ld_xadj(g.xadj, v); j < e; ++j) {
+                int32_t ru = root[__ldg(g.adj + j)];
+                r = ru < r ? ru : r;
+            }
+            int32_t rr = root[r];
+            r = rr < r ? rr : r;
+            if (r < root[v]) { root[v] = r; changed = 1; }
+        }
+        if (!__syncthreads_or(changed)) break;
+    }
+    // BFS levels from each component's lowest id
+    for (int32_t v = threadIdx.x; v < n; v += blockDim.x) dist[v] = root[v] == v ? 0 : INT32_MAX;
+    __syncthreads();
+    for (int32_t l = 0;; ++l) {
+        int any = 0;
+        for (int32_t v = threadIdx.x; v < n; v += blockDim.x) {
+            if (dist[v] != l) continue;
+            int64_t e = ld_xadj(g.xadj, (int64_t)v + 1);
+            for (int64_t j = ld_xadj(g.xadj, v); j < e; ++j) {
+                int32_t u = __ldg(g.adj + j);
+                if (dist[u] == INT32_MAX) { dist[u] = l + 1; any = 1; }
+            }
+        }
+        if (!__syncthreads_or(any)) break;
+    }
+    // sort (root, dist, id)
+    for (int64_t i = threadIdx.x; i < P; i += blockDim.x) {
+        ulonglong2 kv;
+        if (i < n) { kv.x = ((unsigned long long)(uint32_t)root[i] << 32) | (uint32_t)dist[i]; kv.y = (unsigned long long)i; }
+        else { kv.x = ~0ull; kv.y = ~0ull; }
+        keys[i] = kv;
+    }
+    __syncthreads();
+    for (int64_t kk = 2; kk <= P; kk <<= 1) {
+        for (int64_t j = kk >> 1; j > 0; j >>= 1) {
+            for (int64_t i = threadIdx.x; i < P; i += blockDim.x) {
+                int64_t ixj = i ^ j;
+                if (ixj > i) {
+                    ulonglong2 a = keys[i], b = keys[ixj];
+                    bool agt = a.x > b.x || (a.x == b.x && a.y > b.y);
+                    bool up = (i & kk) == 0;
+                    if (agt == up) { keys[i] = b; keys[ixj] = a; }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    // total weight, then prefix in sorted order
+    long long W = 0;
+    for (int32_t v = threadIdx.x; v < n; v += blockDim.x) W += g.vw[v];
+    W = block_sum_i64(W, sh);
+    long long carry = 0;
+    for (int64_t i0 = 0; i0 < n; i0 += blockDim.x) {
+        int64_t i = i0 + threadIdx.x;
+        int32_t v = i < n ? (int32_t)keys[i].y : 0;
+        long long w = i < n ? (long long)g.vw[v] : 0;
+        long long tot = 0;
+        long long S = carry + block_exscan_i64(w, sh, &tot);
+        if (i < n) part[v] = (int32_t)(((long long)k * S) / W);
+        carry += tot;
+    }
+}
+
+int initial_partition(Ctx &c, const DGraph &g, int32_t k, int32_t *part) {
+    cudaStream_t s = c.stream;
+    if (g.n == 0) return JET_OK;
+    int64_t P = pow2ceil(g.n);
+    DevBuf b;
+    JET_TRY(dev_alloc(b, (size_t)g.n * 8 + (size_t)P * 16 + 512, s));
+    int32_t *root = b.as<int32_t>(), *dist = root + g.n;
+    ulonglong2 *keys = reinterpret_cast<ulonglong2 *>((reinterpret_cast<uintptr_t>(dist + g.n) + 255) & ~uintptr_t(255));
+    k_initial_partition<<<1, 1024, 0, s>>>(g, k, root, dist, keys, P, part);
+    c.launches += 1;
+    JET_CUDA_TRY(cudaGetLastError());
+    JET_CUDA_TRY(cudaStreamSynchronize(s));
+    return JET_OK;
+}
+
+}  // namespace jet

@@ -1,0 +1,410 @@
+// Internal definitions shared by the CUDA translation units of libjet.
+// Nothing here is part of the C ABI (include/jet.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstddef>
+#include <cstring>
+#include <vector>
+
+#include "jet.h"
+
+namespace jet {
+
+// ---------------------------------------------------------------------------
+// constants
+// ---------------------------------------------------------------------------
+constexpr int32_t kNoneGain = INT32_MIN;   // "negative infinity" gain (Alg. 4)
+constexpr int kSlots = 33;                 // slot() values 0..32 for 32-bit losses (Sec. 4.2.1)
+constexpr int kSmallDeg = 16;              // rows up to this length: one thread per vertex
+constexpr int kTB = 256;                   // default block size
+constexpr int kRbTile = 1024;              // vertices per rebalancing tile (ordered prefixes)
+constexpr int kTrace = 4096;               // per-level trace records kept on the device
+
+enum Mode : int32_t { MODE_LP = 0, MODE_RW = 1, MODE_RS = 2, MODE_DONE = 3 };
+
+// Internal ablation bits (match the JET_FLAG_* values)
+constexpr uint32_t ABL_NO_LOCKS = JET_FLAG_NO_LOCKS;
+constexpr uint32_t ABL_NO_AFTERBURN = JET_FLAG_NO_AFTERBURN;
+constexpr uint32_t ABL_WEAK_AFTERBURN = JET_FLAG_WEAK_AFTERBURN;
+constexpr uint32_t ABL_BASELINE_LP = JET_FLAG_BASELINE_LP;
+
+// ---------------------------------------------------------------------------
+// error handling
+// ---------------------------------------------------------------------------
+#define JET_CUDA_TRY(expr)                                                          \
+    do {                                                                            \
+        cudaError_t e__ = (expr);                                                   \
+        if (e__ != cudaSuccess) {                                                   \
+            ::jet::record_cuda_error(e__, #expr, __FILE__, __LINE__);               \
+            return e__ == cudaErrorMemoryAllocation ? JET_ENOMEM : JET_ECUDA;       \
+        }                                                                           \
+    } while (0)
+
+#define JET_TRY(expr)                                                               \
+    do {                                                                            \
+        int s__ = (expr);                                                           \
+        if (s__ < 0) return s__;                                                    \
+    } while (0)
+
+void record_cuda_error(cudaError_t e, const char *what, const char *file, int line);
+const char *last_error_text();
+
+// ---------------------------------------------------------------------------
+// device memory owned by the library: stream-ordered allocations
+// ---------------------------------------------------------------------------
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    cudaStream_t s = nullptr;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    DevBuf(DevBuf &&o) noexcept : p(o.p), bytes(o.bytes), s(o.s) { o.p = nullptr; o.bytes = 0; }
+    DevBuf &operator=(DevBuf &&o) noexcept {
+        if (this != &o) { release(); p = o.p; bytes = o.bytes; s = o.s; o.p = nullptr; o.bytes = 0; }
+        return *this;
+    }
+    ~DevBuf() { release(); }
+    void release() {
+        if (p) { cudaFreeAsync(p, s); p = nullptr; bytes = 0; }
+    }
+    template <class T> T *as() const { return static_cast<T *>(p); }
+};
+
+// Allocate `bytes` (rounded up to 256) on stream s; returns JET_OK/JET_ENOMEM.
+int dev_alloc(DevBuf &b, size_t bytes, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// graph view
+// ---------------------------------------------------------------------------
+struct DGraph {
+    int32_t n = 0;
+    int64_t nnz = 0;
+    const int64_t *xadj = nullptr;
+    const int32_t *adj = nullptr;
+    const int32_t *vw = nullptr;   // never null inside the library (materialised)
+    const int32_t *ew = nullptr;   // null: unit edge weights
+};
+
+// ---------------------------------------------------------------------------
+// device control block of one refinement level (Alg. 3 state)
+// ---------------------------------------------------------------------------
+struct TraceRec {
+    int32_t kind, pad;
+    int64_t nx, nm, cut, maxw;
+    int64_t degx;   // sum of row lengths over X (Jetlp) or over the rebalancing candidates
+    int64_t degm;   // sum of row lengths over M
+};
+
+struct Ctl {
+    int32_t mode;        // kind of the iteration about to run (Mode)
+    int32_t it;          // iterations completed on this level
+    int32_t noimp;       // iterations since the last reset (Alg. 3 "iteration counter")
+    int32_t weak;        // Jetrw iterations since the last Jetlp
+    int32_t lp_epoch;    // iteration index of the last Jetlp (its movers are locked)
+    int32_t copy_best;   // set by the controller: P_best <- P_iter this iteration
+    int32_t best_bal;
+    int32_t nA, nB;      // rebalancing classes for the current iteration
+    int32_t nX, nXb;     // X list lengths (small / large rows)
+    int32_t nM, nMb;     // M list lengths
+    int32_t hit_cap;     // stopped by max_iters
+    int32_t pad0;
+    int32_t kcount[4];   // iterations run per kind (Jetlp, Jetrw, Jetrs)
+    int64_t ncand;       // rebalancing candidates (trace)
+    int64_t degx, degm;  // row-length sums over X / candidates and over M (byte model)
+    int64_t cut;         // cost of P_iter
+    int64_t dcut;        // cut change accumulated by the apply kernel
+    int64_t maxw;        // max part weight of P_iter
+    int64_t best_cut, best_maxw;
+    int64_t L, opt, sigma;
+    // coarsening
+    int32_t hem_stop;
+    int32_t pad1;
+    int64_t hem_added[64];
+    int64_t scratch[8];
+};
+
+// Parameters of one refinement level, passed by value to every kernel.
+struct Level {
+    DGraph g;
+    int32_t k;
+    int32_t cq16;            // c * 65536
+    int64_t phi_ppm;         // phi * 1e6
+    int32_t max_no_improve, weak_limit, max_iters;
+    uint32_t abl;
+    uint64_t seed;
+    // per-vertex state
+    int32_t *part, *best, *nxt, *prio, *mstamp, *lstamp, *key;
+    int32_t *listX, *listXb, *listM, *listMb;
+    const int32_t *bigv;
+    int32_t nbig;
+    // per-part state
+    int64_t *pw;
+    int32_t *aidx, *Bs;
+    uint8_t *inB;
+    int64_t *capC;           // nB+1 capacity prefix (Jetrs)
+    int64_t *excess;         // [nA]
+    int64_t *bucketw;        // [nA * kSlots]
+    int32_t *sstar;          // [nA] boundary slot
+    int64_t *need;           // [nA] weight still to take inside the boundary slot
+    int32_t *tilehist;       // [ntiles * k]
+    int32_t ntiles;
+    int64_t *tiletaken;      // [ntiles]
+    int64_t *etaken;         // [n] Jetrs: weight of v in the evicted list (0 if not evicted)
+    TraceRec *trace;
+    Ctl *ctl;
+    // CUDA-graph loop control (0 when driven from the host)
+    unsigned long long h_loop, h_mode;
+    int32_t use_graph;
+};
+
+// ---------------------------------------------------------------------------
+// small device helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+    uint64_t z = x + 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ int slot_of(int64_t x) {
+    if (x < 0) return 0;
+    if (x == 0) return 1;
+    return 2 + (63 - __clzll((unsigned long long)x));
+}
+
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long t = __shfl_xor_sync(0xffffffffu, v, o);
+        v = t > v ? t : v;
+    }
+    return v;
+}
+
+__device__ __forceinline__ long long warp_sum_i64(long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ int warp_sum_i32(int v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Append from any subset of a warp's lanes: one atomic per warp; returns the
+// slot for the calling lane.  All lanes of the warp must call it (pred may be
+// false).
+__device__ __forceinline__ int warp_append(int32_t *counter, bool pred) {
+    unsigned m = __ballot_sync(0xffffffffu, pred);
+    if (!m) return -1;
+    int leader = __ffs(m) - 1;
+    int base = 0;
+    if ((int)lane_id() == leader) base = atomicAdd(counter, __popc(m));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    return pred ? base + __popc(m & ((1u << lane_id()) - 1u)) : -1;
+}
+
+__device__ __forceinline__ void atomic_add_i64(int64_t *p, int64_t v) {
+    atomicAdd(reinterpret_cast<unsigned long long *>(p), (unsigned long long)v);
+}
+
+__device__ __forceinline__ int64_t ld_xadj(const int64_t *x, int64_t i) { return __ldg(x + i); }
+
+// block-wide sum (blockDim.x multiple of 32, <= 1024); result valid in all threads
+__device__ __forceinline__ long long block_sum_i64(long long v, long long *sh /* >= 32 */) {
+    v = warp_sum_i64(v);
+    unsigned w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane_id() == 0) sh[w] = v;
+    __syncthreads();
+    unsigned nw = (blockDim.x + 31) >> 5;
+    long long t = (threadIdx.x < nw) ? sh[threadIdx.x] : 0;
+    if (threadIdx.x < 32) t = warp_sum_i64(t);
+    if (threadIdx.x == 0) sh[0] = t;
+    __syncthreads();
+    long long r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+// block-wide exclusive scan of one int64 per thread; *total gets the sum
+__device__ __forceinline__ long long block_exscan_i64(long long v, long long *sh /* >= 33 */, long long *total) {
+    unsigned lane = lane_id(), w = threadIdx.x >> 5;
+    long long x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        long long t = __shfl_up_sync(0xffffffffu, x, o);
+        if ((int)lane >= o) x += t;
+    }
+    __syncthreads();
+    if (lane == 31) sh[w] = x;
+    __syncthreads();
+    unsigned nw = (blockDim.x + 31) >> 5;
+    if (threadIdx.x < 32) {
+        long long s = (threadIdx.x < nw) ? sh[threadIdx.x] : 0;
+        long long y = s;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            long long t = __shfl_up_sync(0xffffffffu, y, o);
+            if ((int)lane >= o) y += t;
+        }
+        if (threadIdx.x < nw) sh[threadIdx.x] = y - s;  // exclusive warp offsets
+        if (threadIdx.x == nw - 1) sh[32] = y;
+    }
+    __syncthreads();
+    long long r = sh[w] + x - v;
+    if (total) *total = sh[32];
+    __syncthreads();
+    return r;
+}
+
+inline int grid_for(int64_t items, int per_block, int cap = 1 << 30) {
+    int64_t g = (items + per_block - 1) / per_block;
+    if (g < 1) g = 1;
+    if (g > cap) g = cap;
+    return (int)g;
+}
+
+int num_sms();
+
+// ---------------------------------------------------------------------------
+// device-wide exclusive scan (3 phases: tile sums, scan of tile sums, tiles)
+// ---------------------------------------------------------------------------
+// out[i] = sum_{j<i} f(j) for i in [0, n); *total_dev = sum (device int64).
+// Functor F: __device__ int64_t operator()(int64_t i) const.
+template <class F> __global__ void k_scan_tiles(F f, int64_t n, int64_t *tile_sums);
+template <class F> __global__ void k_scan_apply(F f, int64_t n, const int64_t *tile_off, int64_t *out);
+__global__ void k_scan_sums(int64_t *tile_sums, int64_t ntiles, int64_t *total_dev);
+
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kTB * kScanItems;
+
+template <class F>
+__global__ void __launch_bounds__(kTB) k_scan_tiles(F f, int64_t n, int64_t *tile_sums) {
+    __shared__ long long sh[40];
+    int64_t base = (int64_t)blockIdx.x * kScanTile;
+    long long s = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        int64_t idx = base + (int64_t)threadIdx.x * kScanItems + i;
+        if (idx < n) s += f(idx);
+    }
+    s = block_sum_i64(s, sh);
+    if (threadIdx.x == 0) tile_sums[blockIdx.x] = s;
+}
+
+template <class F>
+__global__ void __launch_bounds__(kTB) k_scan_apply(F f, int64_t n, const int64_t *tile_off, int64_t *out) {
+    __shared__ long long sh[40];
+    int64_t base = (int64_t)blockIdx.x * kScanTile;
+    long long vals[kScanItems];
+    long long s = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        int64_t idx = base + (int64_t)threadIdx.x * kScanItems + i;
+        vals[i] = idx < n ? f(idx) : 0;
+        s += vals[i];
+    }
+    long long off = block_exscan_i64(s, sh, nullptr) + tile_off[blockIdx.x];
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        int64_t idx = base + (int64_t)threadIdx.x * kScanItems + i;
+        if (idx < n) out[idx] = off;
+        off += vals[i];
+    }
+}
+
+// Scratch for a scan of n items: (ntiles) int64.
+inline int64_t scan_tiles_for(int64_t n) { return (n + kScanTile - 1) / kScanTile; }
+
+template <class F>
+int device_exscan(F f, int64_t n, int64_t *out, int64_t *total_dev, int64_t *tile_scratch, cudaStream_t s) {
+    int64_t nt = scan_tiles_for(n);
+    if (nt < 1) nt = 1;
+    k_scan_tiles<F><<<(unsigned)nt, kTB, 0, s>>>(f, n, tile_scratch);
+    k_scan_sums<<<1, 1024, 0, s>>>(tile_scratch, nt, total_dev);
+    k_scan_apply<F><<<(unsigned)nt, kTB, 0, s>>>(f, n, tile_scratch, out);
+    JET_CUDA_TRY(cudaGetLastError());
+    return JET_OK;
+}
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+struct TraceHost {
+    std::vector<TraceRec> rec;
+    int32_t iters = 0;
+};
+
+// What one refinement level did (for jet_stats).
+struct LevelReport {
+    int32_t iters = 0, kinds[3] = {0, 0, 0};
+    int64_t sel_launches = 0, sel_bytes = 0, bytes_model = 0;
+    float sel_ms = 0.f;
+};
+
+struct Ctx {
+    int64_t launches = 0;        // kernels launched (graph-loop iterations counted per executed kernel)
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    jet_options opt{};
+    int64_t *pinned = nullptr;   // small pinned host buffer for scalar readbacks
+    TraceHost last_trace;
+};
+
+}  // namespace jet
+
+struct jet_ctx {
+    jet::Ctx c;
+};
+
+// hierarchy: level 0 borrows the caller's arrays (weights materialised when
+// NULL), coarser levels are owned
+struct jet_hier {
+    jet_ctx *ctx = nullptr;
+    int32_t levels = 0;
+    int32_t k = 0;
+    int32_t n[JET_MAX_LEVELS] = {};
+    int64_t nnz[JET_MAX_LEVELS] = {};
+    const int64_t *xadj[JET_MAX_LEVELS] = {};
+    const int32_t *adj[JET_MAX_LEVELS] = {};
+    const int32_t *vw[JET_MAX_LEVELS] = {};
+    const int32_t *ew[JET_MAX_LEVELS] = {};
+    const int32_t *cmap[JET_MAX_LEVELS] = {};
+    std::vector<jet::DevBuf> bufs;
+    float ms_coarsen = 0.f;
+    int64_t launches = 0;     // kernels jet_coarsen executed
+};
+
+namespace jet {
+
+// ----- functions implemented in the .cu files ------------------------------
+// jet_refine.cu
+int refine_level(Ctx &c, const DGraph &g, int32_t k, double eps, int32_t is_finest, uint64_t seed,
+                 int32_t *part_inout, int64_t *cut_out, int64_t *maxw_out, LevelReport *rep);
+int lp_pass(Ctx &c, const DGraph &g, int32_t k, const int32_t *part, const uint8_t *locked, double cval,
+            uint32_t flags, int32_t *pd_out, int32_t *gain_out, uint8_t *inx_out, int32_t *f2_out,
+            uint8_t *inm_out);
+int rebalance_pass(Ctx &c, const DGraph &g, int32_t k, double eps, int32_t strong, uint64_t seed, int32_t iter,
+                   const int32_t *part, int32_t *dest_out, int32_t *loss_out, int64_t *nmoves, int64_t *ncand);
+int cut_and_weights(Ctx &c, const DGraph &g, int32_t k, const int32_t *part, int64_t *cut_out, int64_t *pw_dev);
+
+// jet_coarsen.cu
+int hem(Ctx &c, const DGraph &g, uint64_t seed, int32_t level, int32_t rounds, int32_t *mate);
+int coarsen(Ctx &c, const DGraph &g0, int32_t k, uint64_t seed, jet_hier *h);
+int initial_partition(Ctx &c, const DGraph &g, int32_t k, int32_t *part);
+int project(Ctx &c, int32_t n_fine, const int32_t *cmap, const int32_t *coarse_part, int32_t *fine_part);
+
+// host helpers (jet_api.cu)
+int64_t balance_limit(int64_t W, int32_t k, double eps, int64_t *opt);
+int sync_stream(Ctx &c);
+
+}  // namespace jet

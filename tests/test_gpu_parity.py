@@ -1,0 +1,363 @@
+"""GPU parity: every step of the CUDA path, called through the C ABI, against
+the oracle on the same seeded inputs — bit-exact (all results are integers).
+Sizes span several thread blocks, warp-path rows (> 16 entries) and ragged
+tails; the full-size workloads are at the end."""
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import graphgen
+import oracle
+from helpers import graph_from_triples
+
+pytestmark = pytest.mark.gpu
+
+jet = pytest.importorskip("paper_2304_13194_gb300")
+NONE32 = -(2 ** 31)
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    c = jet.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def ctx_hostloop():
+    c = jet.Context(0, flags=jet.FLAG_HOSTLOOP)
+    yield c
+    c.close()
+
+
+def _np(t):
+    return t.cpu().numpy()
+
+
+def _vw(g, unit):
+    return None if unit else g.vwgt
+
+
+def _ew(g, unit):
+    return None if unit else g.adjwgt
+
+
+def graphs_small():
+    """Inputs shaped like the paper's workloads, small enough for the oracle."""
+    star = graph_from_triples(301, [[0, i, 1 + i % 7] for i in range(1, 301)] +
+                              [[i, i + 1, 2] for i in range(1, 300, 2)])
+    return [
+        ("grid2d_40x33", graphgen.grid2d(40, 33), True),
+        ("grid3d_17x13x11_w", graphgen.grid3d(17, 13, 11, vw=(1, 4), ew=(1, 10), seed=3), False),
+        ("rmat_s12", graphgen.rmat(12, seed=5), True),
+        ("rmat_s11_w", graphgen.rmat(11, seed=7, vw=(1, 3), ew=(1, 5)), False),
+        ("rgg_5000", graphgen.rgg(5000, seed=2), True),
+        ("gnp_700_dense", graphgen.gnp(700, 0.06, seed=4, ew=(1, 9)), False),   # rows of ~42: warp path
+        ("star_300", star, False),
+    ]
+
+
+# --------------------------------------------------------------------------
+# single passes
+# --------------------------------------------------------------------------
+
+def test_lp_pass_hand_cases(ctx, golden_dir):
+    data = json.load(open(os.path.join(golden_dir, "jetlp_cases.json")))
+    for case in data["cases"]:
+        g = graph_from_triples(case["n"], case["edges"])
+        r = ctx.lp_pass(g.xadj, g.adjncy, g.vwgt, g.adjwgt, case["k"], np.array(case["part"], np.int32),
+                        np.array(case["locked"], np.uint8), c=case["c"])
+        assert _np(r["Pd"]).tolist() == case["Pd"], case["name"]
+        F = [None if f == NONE32 else int(f) for f in _np(r["F"])]
+        assert F == case["F"], case["name"]
+        assert np.flatnonzero(_np(r["inX"])).tolist() == case["X"], case["name"]
+        for v, f2 in case["F2"].items():
+            assert int(_np(r["F2"])[int(v)]) == f2
+        assert np.flatnonzero(_np(r["inM"])).tolist() == case["M"], case["name"]
+
+
+@pytest.mark.parametrize("name,g,unit", graphs_small(), ids=[x[0] for x in graphs_small()])
+@pytest.mark.parametrize("k,c,abl", [(8, 0.25, 0), (64, 0.75, 0), (5, 0.25, jet.FLAG_NO_AFTERBURN),
+                                     (16, 0.25, jet.FLAG_WEAK_AFTERBURN), (16, 0.25, jet.FLAG_BASELINE_LP)])
+def test_lp_pass_random(ctx, name, g, unit, k, c, abl):
+    rng = np.random.default_rng(k + abl)
+    part = oracle.initial_partition(g, k)
+    noise = rng.random(g.n) < 0.1
+    part[noise] = rng.integers(0, k, int(noise.sum()))
+    locked = (rng.random(g.n) < 0.15).astype(np.uint8)
+    vw, ew = _vw(g, unit), _ew(g, unit)
+    og = graphgen.Graph(g.n, g.xadj, g.adjncy, vw, ew)
+    oabl = sum(o for f, o in [(jet.FLAG_NO_LOCKS, oracle.ABL_NO_LOCKS), (jet.FLAG_NO_AFTERBURN, oracle.ABL_NO_AFTERBURN),
+                              (jet.FLAG_WEAK_AFTERBURN, oracle.ABL_WEAK_AFTERBURN),
+                              (jet.FLAG_BASELINE_LP, oracle.ABL_BASELINE_LP)] if abl & f)
+    ref = oracle.jetlp(og, k, part, locked, c=c, ablation=oabl)
+    r = ctx.lp_pass(g.xadj, g.adjncy, vw, ew, k, part, locked, c=c, flags=abl)
+    F = _np(r["F"]).astype(np.int64)
+    refF = np.where(ref["F"] == oracle.NONE, NONE32, ref["F"])
+    assert (F == refF).all()
+    assert (_np(r["Pd"]) == ref["Pd"]).all()
+    assert (_np(r["inX"]) == ref["inX"]).all()
+    inX = ref["inX"]
+    if not abl & (jet.FLAG_NO_AFTERBURN | jet.FLAG_BASELINE_LP):
+        assert (_np(r["F2"])[inX] == ref["F2"][inX]).all()
+    assert (_np(r["inM"]) == ref["inM"]).all()
+
+
+def test_rebalance_hand_cases(ctx, golden_dir):
+    data = json.load(open(os.path.join(golden_dir, "rebalance_cases.json")))
+    for case in data["cases"]:
+        g = graph_from_triples(case["n"], case["edges"])
+        vw = np.array(case["vwgt"], np.int32)
+        r = ctx.rebalance_pass(g.xadj, g.adjncy, vw, g.adjwgt, case["k"], np.array(case["part"], np.int32),
+                               eps=case["eps"], strong=case["kind"] == "rs", seed=1, it=0)
+        assert _np(r["dest"]).tolist() == case["dest"], case["name"]
+        for v, lo in case["loss"].items():
+            assert int(_np(r["loss"])[int(v)]) == lo, (case["name"], v)
+
+
+@pytest.mark.parametrize("name,g,unit", graphs_small(), ids=[x[0] for x in graphs_small()])
+@pytest.mark.parametrize("k", [2, 7, 64])
+@pytest.mark.parametrize("strong", [False, True])
+def test_rebalance_pass_random(ctx, name, g, unit, k, strong):
+    rng = np.random.default_rng(k)
+    part = rng.integers(0, k, g.n).astype(np.int32)
+    part[rng.random(g.n) < 0.3] = 0          # part 0 (and maybe others) oversized
+    vw, ew = _vw(g, unit), _ew(g, unit)
+    og = graphgen.Graph(g.n, g.xadj, g.adjncy, vw, ew)
+    if strong:
+        ref = oracle.jetrs(og, k, part, eps=0.03)
+    else:
+        ref = oracle.jetrw(og, k, part, eps=0.03, seed=17, it=5)
+    r = ctx.rebalance_pass(g.xadj, g.adjncy, vw, ew, k, part, eps=0.03, strong=strong, seed=17, it=5)
+    assert r["ncand"] == ref["ncand"]
+    loss = _np(r["loss"]).astype(np.int64)
+    refl = np.where(ref["loss"] == oracle.NONE, NONE32, ref["loss"])
+    assert (loss == refl).all()
+    assert (_np(r["dest"]) == ref["dest"]).all()
+    assert r["nmoves"] == ref["nmoves"]
+
+
+@pytest.mark.parametrize("name,g,unit", graphs_small(), ids=[x[0] for x in graphs_small()])
+def test_cut_and_weights(ctx, name, g, unit):
+    k = 13
+    part = np.random.default_rng(1).integers(0, k, g.n).astype(np.int32)
+    vw, ew = _vw(g, unit), _ew(g, unit)
+    og = graphgen.Graph(g.n, g.xadj, g.adjncy, vw, ew)
+    cut, pw = ctx.cut(g.xadj, g.adjncy, vw, ew, k, part)
+    assert cut == oracle.cut(og, part)
+    assert (_np(pw) == oracle.part_weights(og, part, k)).all()
+
+
+@pytest.mark.parametrize("name,g,unit", graphs_small(), ids=[x[0] for x in graphs_small()])
+def test_hem_matches_oracle(ctx, name, g, unit):
+    ew = _ew(g, unit)
+    og = graphgen.Graph(g.n, g.xadj, g.adjncy, None, ew)
+    for level, rounds in [(0, 8), (3, 2), (1, 64)]:
+        ref = oracle.hem(og, seed=9, level=level, rounds=rounds)
+        got = _np(ctx.hem(g.xadj, g.adjncy, ew, seed=9, level=level, rounds=rounds))
+        assert (got == ref).all()
+
+
+@pytest.mark.parametrize("name,g,unit", graphs_small(), ids=[x[0] for x in graphs_small()])
+def test_initial_partition_matches_oracle(ctx, name, g, unit):
+    vw = _vw(g, unit)
+    og = graphgen.Graph(g.n, g.xadj, g.adjncy, vw, None)
+    for k in (2, 8, 64):
+        assert (_np(ctx.initial_partition(g.xadj, g.adjncy, vw, k)) == oracle.initial_partition(og, k)).all()
+
+
+@pytest.mark.parametrize("name,g,unit", graphs_small(), ids=[x[0] for x in graphs_small()])
+def test_coarsen_hierarchy_matches_oracle(ctx, name, g, unit):
+    vw, ew = _vw(g, unit), _ew(g, unit)
+    og = graphgen.Graph(g.n, g.xadj, g.adjncy, vw, ew)
+    k = 8
+    ref = oracle.coarsen(og, k, seed=3)
+    h = ctx.coarsen(g.xadj, g.adjncy, vw, ew, k=k, seed=3)
+    try:
+        lv, ns, ms = h.info()
+        assert lv == len(ref)
+        for i in range(lv):
+            L = h.level(i)
+            R = ref[i].graph
+            assert L["n"] == R.n
+            assert (_np(L["xadj"]) == R.xadj).all()
+            assert (_np(L["adjncy"]) == R.adjncy).all()
+            assert (_np(L["vwgt"]) == R.vwgt).all()
+            if i > 0 or ew is not None:
+                assert (_np(L["adjwgt"]) == R.adjwgt).all()
+            if i + 1 < lv:
+                assert (_np(L["cmap"]) == ref[i].cmap).all()
+    finally:
+        h.close()
+
+
+# --------------------------------------------------------------------------
+# one level of refinement (Alg. 3): result and the whole trajectory
+# --------------------------------------------------------------------------
+
+def _check_refine(ctx, g, unit, k, part0, is_finest, seed, eps=0.03):
+    vw, ew = _vw(g, unit), _ew(g, unit)
+    og = graphgen.Graph(g.n, g.xadj, g.adjncy, vw, ew)
+    ref = oracle.refine(og, k, part0, eps=eps, is_finest=is_finest, seed=seed)
+    p, cut = ctx.refine(g.xadj, g.adjncy, vw, ew, k, part0, eps=eps, is_finest=is_finest, seed=seed)
+    tr = ctx.last_trace()
+    assert tr["iters"] == ref.iters
+    n = min(len(tr["kind"]), len(ref.trace["kind"]))
+    for key in ("kind", "nx", "nm", "cut", "maxw"):
+        assert (tr[key][:n] == ref.trace[key][:n]).all(), key
+    assert cut == ref.cut
+    assert (_np(p) == ref.part).all()
+
+
+@pytest.mark.parametrize("name,g,unit", graphs_small(), ids=[x[0] for x in graphs_small()])
+@pytest.mark.parametrize("k", [4, 64])
+def test_refine_matches_oracle(ctx, name, g, unit, k):
+    og = graphgen.Graph(g.n, g.xadj, g.adjncy, _vw(g, unit), None)
+    part0 = oracle.initial_partition(og, k)
+    _check_refine(ctx, g, unit, k, part0, True, seed=5)
+    _check_refine(ctx, g, unit, k, part0, False, seed=6)
+
+
+def test_refine_hostloop_equals_graph_loop(ctx, ctx_hostloop):
+    g = graphgen.grid3d(20, 20, 20, vw=(1, 4), ew=(1, 10), seed=9)
+    part0 = oracle.initial_partition(g, 16)
+    a = ctx.refine(g.xadj, g.adjncy, g.vwgt, g.adjwgt, 16, part0, seed=2)
+    ta = ctx.last_trace()
+    b = ctx_hostloop.refine(g.xadj, g.adjncy, g.vwgt, g.adjwgt, 16, part0, seed=2)
+    tb = ctx_hostloop.last_trace()
+    assert a[1] == b[1] and (_np(a[0]) == _np(b[0])).all()
+    assert all((ta[key] == tb[key]).all() for key in ("kind", "nx", "nm", "cut", "maxw"))
+
+
+# --------------------------------------------------------------------------
+# the whole pipeline (Alg. 1)
+# --------------------------------------------------------------------------
+
+def _check_partition(ctx, g, unit, k, eps=0.03, seed=1):
+    vw, ew = _vw(g, unit), _ew(g, unit)
+    og = graphgen.Graph(g.n, g.xadj, g.adjncy, vw, ew)
+    ref = oracle.partition(og, k, eps, seed)
+    part, cut, st = ctx.partition(g.xadj, g.adjncy, vw, ew, k=k, eps=eps, seed=seed, return_stats=True)
+    assert st.levels == ref.stats["levels"]
+    assert st.n == ref.stats["n"] and st.m == ref.stats["m"]
+    assert st.iters_lp == ref.stats["it_lp"] and st.iters_rw == ref.stats["it_rw"] and st.iters_rs == ref.stats["it_rs"]
+    assert st.cut_level == ref.stats["cut_level"]
+    assert st.edge_iters == ref.stats["edge_iters"]
+    assert cut == ref.cut == st.cut
+    assert (_np(part) == ref.part).all()
+    return part, cut, st
+
+
+def test_partition_grid_64x64_k8(ctx):
+    g = graphgen.grid2d(64, 64)
+    _check_partition(ctx, g, True, 8)
+
+
+@pytest.mark.parametrize("name,g,unit", graphs_small(), ids=[x[0] for x in graphs_small()])
+@pytest.mark.parametrize("k", [2, 8, 64])
+def test_partition_matches_oracle(ctx, name, g, unit, k):
+    _check_partition(ctx, g, unit, k, seed=k)
+
+
+def test_partition_hostloop(ctx_hostloop):
+    g = graphgen.grid3d(24, 24, 24, vw=(1, 4), ew=(1, 10), seed=1)
+    _check_partition(ctx_hostloop, g, False, 64)
+
+
+def test_partition_host_entry_point(ctx):
+    g = graphgen.grid3d(16, 16, 16, vw=(1, 4), ew=(1, 10), seed=4)
+    ref = oracle.partition(g, 32, 0.03, 3)
+    part, cut = ctx.partition_host(g.xadj, g.adjncy, g.vwgt, g.adjwgt, k=32, eps=0.03, seed=3)
+    assert cut == ref.cut and (part == ref.part).all()
+
+
+def test_partition_deterministic_and_seed_sensitive(ctx):
+    g = graphgen.rgg(20000, seed=11)
+    a = ctx.partition(g.xadj, g.adjncy, None, None, k=16, seed=4)
+    b = ctx.partition(g.xadj, g.adjncy, None, None, k=16, seed=4)
+    c = ctx.partition(g.xadj, g.adjncy, None, None, k=16, seed=5)
+    assert a[1] == b[1] and (_np(a[0]) == _np(b[0])).all()
+    assert not (_np(a[0]) == _np(c[0])).all()
+
+
+# --------------------------------------------------------------------------
+# edge cases
+# --------------------------------------------------------------------------
+
+def test_edge_cases(ctx):
+    # empty graph
+    e = graphgen.Graph(0, np.zeros(1, np.int64), np.zeros(0, np.int32), np.zeros(0, np.int32), np.zeros(0, np.int32))
+    part, cut = ctx.partition(e.xadj, e.adjncy, None, None, k=4)
+    assert part.numel() == 0 and cut == 0
+    # edgeless graph, k = 3
+    iso = graphgen.Graph(10, np.zeros(11, np.int64), np.zeros(0, np.int32), np.ones(10, np.int32), np.zeros(0, np.int32))
+    _check_partition(ctx, iso, True, 3)
+    # k = 1 and k > n
+    g = graphgen.grid2d(7, 5)
+    _check_partition(ctx, g, True, 1)
+    _check_partition(ctx, g, True, 50)
+    # the largest supported k
+    g = graphgen.rgg(30000, seed=3)
+    _check_partition(ctx, g, True, jet.JET_MAX_K)
+    # a vertex heavier than the balance limit: cannot be balanced
+    g = graphgen.grid2d(10, 10)
+    vw = np.ones(g.n, np.int32); vw[0] = 60
+    og = graphgen.Graph(g.n, g.xadj, g.adjncy, vw, None)
+    ref = oracle.partition(og, 4, 0.03, 1)
+    part, cut = ctx.partition(g.xadj, g.adjncy, vw, None, k=4)
+    assert ref.status == 1 and ctx.last_status == 1   # JET_WUNBALANCED
+    assert cut == ref.cut and (_np(part) == ref.part).all()
+
+
+def test_errors(ctx):
+    g = graphgen.grid2d(6, 6)
+    with pytest.raises(jet.JetError) as ei:
+        ctx.partition(g.xadj, g.adjncy, None, None, k=0)
+    assert ei.value.status == -1
+    with pytest.raises(jet.JetError):
+        ctx.partition(g.xadj, g.adjncy, None, None, k=jet.JET_MAX_K + 1)
+    with pytest.raises(jet.JetError):
+        ctx.partition(g.xadj, g.adjncy, None, None, k=4, eps=-0.1)
+    # overflowing weight sums
+    big = np.full(g.nnz, 2 ** 30, np.int32)
+    with pytest.raises(jet.JetError) as ei:
+        ctx.partition(g.xadj, g.adjncy, None, big, k=4)
+    assert ei.value.status == -6
+    # invalid graphs are caught with JET_FLAG_VALIDATE
+    with jet.Context(0, flags=jet.FLAG_VALIDATE) as vctx:
+        ok = vctx.partition(g.xadj, g.adjncy, None, None, k=4)
+        assert ok[1] >= 0
+        bad = g.adjncy.copy(); bad[0] = 0            # self-loop at vertex 0
+        with pytest.raises(jet.JetError) as ei:
+            vctx.partition(g.xadj, bad, None, None, k=4)
+        assert ei.value.status == -2
+        asym = g.adjwgt.copy(); asym[0] = 5           # asymmetric weight
+        with pytest.raises(jet.JetError) as ei:
+            vctx.partition(g.xadj, g.adjncy, None, asym, k=4)
+        assert ei.value.status == -2
+    # out-of-range partition passed to refine
+    with pytest.raises(jet.JetError):
+        ctx.refine(g.xadj, g.adjncy, None, None, 4, np.full(g.n, 7, np.int32))
+
+
+# --------------------------------------------------------------------------
+# full-size workloads (the benchmark's launch configuration)
+# --------------------------------------------------------------------------
+
+def test_partition_grid_128cube_k64_full_size(ctx):
+    """128^3 mesh, vwgt U[1,4], adjwgt U[1,10], k = 64, eps = 0.03, seed 1:
+    the benchmark workload; the oracle runs it end to end."""
+    g = graphgen.grid3d(128, 128, 128, vw=(1, 4), ew=(1, 10), seed=1)
+    part, cut, st = _check_partition(ctx, g, False, 64, seed=1)
+    L, _ = oracle.limit(int(g.vwgt.sum()), 64, 0.03)
+    assert st.max_part_w <= L
+
+
+def test_partition_rmat_s16_k64(ctx):
+    g = graphgen.rmat(16, seed=1)
+    _check_partition(ctx, g, True, 64)
