@@ -209,6 +209,29 @@ int jet_rebalance_pass(jet_ctx *ctx, int32_t n, const int64_t *xadj, const int32
                        int32_t strong, uint64_t seed, int32_t iter, const int32_t *part,
                        int32_t *dest_out, int32_t *loss_out, int64_t *nmoves_out, int64_t *ncand_out);
 
+/* jet_lp_pass without any device allocation.  The paper has no counterpart:
+ * this is for callers that cannot let a library allocate device memory — a
+ * process whose memory is reserved up front by its own pool, a latency-bound
+ * loop in which cudaMalloc/cudaFree would synchronise the device or grow the
+ * memory pool, a host framework that only lends memory it owns.  Arguments,
+ * outputs and results are those of jet_lp_pass (the JET_FLAG_VALIDATE graph
+ * check is not run).
+ * Scratch: a fixed device array of about 11 MiB inside the library, sized for
+ * n <= JET_NOALLOC_MAX_N vertices; every GPU that loads the library holds it
+ * until the process exits.  Larger n is rejected with JET_EINVAL (see
+ * jet_last_error).  The first call on each device looks up the array's
+ * device address (cudaGetSymbolAddress); make that first call before any
+ * stream capture.  All calls share the one array, which keeps the previous
+ * call's contents (the pass clears what must start at zero): calls that can
+ * overlap on the GPU — from several contexts, streams or host threads on the
+ * same device — race and must be serialised by the caller.  No cudaMalloc,
+ * cudaFree or allocating library routine is called. */
+#define JET_NOALLOC_MAX_N 262144
+int jet_lp_pass_noalloc(jet_ctx *ctx, int32_t n, const int64_t *xadj, const int32_t *adjncy,
+                        const int32_t *vwgt, const int32_t *adjwgt, int32_t k, const int32_t *part,
+                        const uint8_t *locked, double c, uint32_t flags, int32_t *pd_out, int32_t *gain_out,
+                        uint8_t *inx_out, int32_t *f2_out, uint8_t *inm_out);
+
 /* Heavy-edge matching of Sec. 3.1 (handshake rounds, see jet_coarsen) on one
  * graph: mate_out device int32[n] (partner or -1).  level salts the hash. */
 int jet_hem(jet_ctx *ctx, int32_t n, const int64_t *xadj, const int32_t *adjncy,

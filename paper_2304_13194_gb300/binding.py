@@ -26,8 +26,9 @@ EXPORTED_SYMBOLS = [
     "jet_options_default", "jet_ctx_create", "jet_ctx_destroy", "jet_coarsen", "jet_hier_destroy",
     "jet_hier_info", "jet_hier_level", "jet_uncoarsen", "jet_refine", "jet_last_trace", "jet_partition",
     "jet_partition_host", "jet_cut", "jet_lp_pass", "jet_rebalance_pass", "jet_hem", "jet_initial_partition",
-    "jet_status_string", "jet_last_error",
+    "jet_status_string", "jet_last_error", "jet_lp_pass_noalloc",
 ]
+JET_NOALLOC_MAX_N = 262144
 
 _STATUS = {0: "JET_OK", 1: "JET_WUNBALANCED", 2: "JET_WITERLIMIT", -1: "JET_EINVAL", -2: "JET_EGRAPH",
            -3: "JET_ENOMEM", -4: "JET_ECUDA", -5: "JET_ETIMEOUT", -6: "JET_EOVERFLOW"}
@@ -137,6 +138,8 @@ def load_library(path: str | None = None):
             "jet_partition_host": (ctypes.c_int, [vp, i32, vp, vp, vp, vp, i32, f64, u64, vp, P(i64), P(_CStats)]),
             "jet_cut": (ctypes.c_int, [vp, i32, vp, vp, vp, vp, i32, vp, P(i64), vp]),
             "jet_lp_pass": (ctypes.c_int, [vp, i32, vp, vp, vp, vp, i32, vp, vp, f64, u32, vp, vp, vp, vp, vp]),
+            "jet_lp_pass_noalloc": (ctypes.c_int, [vp, i32, vp, vp, vp, vp, i32, vp, vp, f64, u32, vp, vp, vp, vp,
+                                                   vp]),
             "jet_rebalance_pass": (ctypes.c_int, [vp, i32, vp, vp, vp, vp, i32, f64, i32, u64, i32, vp, vp, vp,
                                                   P(i64), P(i64)]),
             "jet_hem": (ctypes.c_int, [vp, i32, vp, vp, vp, u64, i32, i32, vp]),
@@ -386,6 +389,23 @@ class Context:
                                           _ptr(p), _ptr(lk), float(c), int(flags), _ptr(pd), _ptr(gain), _ptr(inx),
                                           _ptr(f2), _ptr(inm)), "jet_lp_pass")
         return dict(Pd=pd, F=gain, inX=inx.bool(), F2=f2, inM=inm.bool())
+
+    def lp_pass_noalloc(self, xadj, adjncy, vwgt, adjwgt, k, part, locked=None, c=0.25, flags=0, out=None):
+        """jet_lp_pass_noalloc: the Jetlp pass of lp_pass with the library's
+        scratch in its fixed device array (n <= JET_NOALLOC_MAX_N).  ``out``
+        may hold preallocated output tensors (keys Pd, F, inX, F2, inM)."""
+        torch = _torch()
+        n, xadj, adjncy, vwgt, adjwgt = self._graph(xadj, adjncy, vwgt, adjwgt)
+        p = self._dev(part, torch.int32, "part", n)
+        lk = self._dev(locked, torch.uint8, "locked", n, allow_none=True)
+        if out is None:
+            out = dict(Pd=self._out(n), F=self._out(n), inX=self._out(n, torch.uint8), F2=self._out(n),
+                       inM=self._out(n, torch.uint8))
+        _check(load_library().jet_lp_pass_noalloc(self._h, n, _ptr(xadj), _ptr(adjncy), _ptr(vwgt), _ptr(adjwgt),
+                                                  int(k), _ptr(p), _ptr(lk), float(c), int(flags), _ptr(out["Pd"]),
+                                                  _ptr(out["F"]), _ptr(out["inX"]), _ptr(out["F2"]),
+                                                  _ptr(out["inM"])), "jet_lp_pass_noalloc")
+        return dict(Pd=out["Pd"], F=out["F"], inX=out["inX"].bool(), F2=out["F2"], inM=out["inM"].bool())
 
     def rebalance_pass(self, xadj, adjncy, vwgt, adjwgt, k, part, eps=0.03, strong=False, seed=1, it=0):
         torch = _torch()

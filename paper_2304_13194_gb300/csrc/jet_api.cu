@@ -15,6 +15,8 @@ void record_cuda_error(cudaError_t e, const char *what, const char *file, int li
     snprintf(g_err, sizeof(g_err), "%s: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
 }
 
+void record_error(const char *msg) { snprintf(g_err, sizeof(g_err), "%s", msg); }
+
 const char *last_error_text() { return g_err; }
 
 int dev_alloc(DevBuf &b, size_t bytes, cudaStream_t s) {

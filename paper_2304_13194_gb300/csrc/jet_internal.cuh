@@ -49,6 +49,7 @@ constexpr uint32_t ABL_BASELINE_LP = JET_FLAG_BASELINE_LP;
     } while (0)
 
 void record_cuda_error(cudaError_t e, const char *what, const char *file, int line);
+void record_error(const char *msg);
 const char *last_error_text();
 
 // ---------------------------------------------------------------------------
@@ -393,6 +394,16 @@ int refine_level(Ctx &c, const DGraph &g, int32_t k, double eps, int32_t is_fine
 int lp_pass(Ctx &c, const DGraph &g, int32_t k, const int32_t *part, const uint8_t *locked, double cval,
             uint32_t flags, int32_t *pd_out, int32_t *gain_out, uint8_t *inx_out, int32_t *f2_out,
             uint8_t *inm_out);
+// The same pass with every scratch array carved out of `scratch` (at least
+// lp_scratch_bytes(g.n) bytes of device memory, 256-byte aligned): no
+// allocation.  Used by jet_lp_pass_noalloc.
+constexpr size_t align256c(size_t x) { return (x + 255) & ~size_t(255); }
+constexpr size_t lp_scratch_bytes(int64_t n) {
+    return 11 * align256c((size_t)(n > 0 ? n : 1) * 4) + align256c(sizeof(Ctl)) + 256;
+}
+int lp_pass_in_scratch(Ctx &c, const DGraph &g, int32_t k, const int32_t *part, const uint8_t *locked, double cval,
+                       uint32_t flags, int32_t *pd_out, int32_t *gain_out, uint8_t *inx_out, int32_t *f2_out,
+                       uint8_t *inm_out, char *scratch);
 int rebalance_pass(Ctx &c, const DGraph &g, int32_t k, double eps, int32_t strong, uint64_t seed, int32_t iter,
                    const int32_t *part, int32_t *dest_out, int32_t *loss_out, int64_t *nmoves, int64_t *ncand);
 int cut_and_weights(Ctx &c, const DGraph &g, int32_t k, const int32_t *part, int64_t *cut_out, int64_t *pw_dev);

@@ -1526,4 +1526,53 @@ int cut_and_weights(Ctx &c, const DGraph &g, int32_t k, const int32_t *part, int
     return JET_OK;
 }
 
+// ---- a single Jetlp pass in caller-provided scratch ------------------------
+// Same kernels and launch configuration as lp_pass; the level arrays, the
+// control block and the row-class counter live in `scratch` instead of
+// stream-ordered allocations.
+int lp_pass_in_scratch(Ctx &c, const DGraph &g, int32_t k, const int32_t *part, const uint8_t *locked, double cval,
+                       uint32_t flags, int32_t *pd_out, int32_t *gain_out, uint8_t *inx_out, int32_t *f2_out,
+                       uint8_t *inm_out, char *scratch) {
+    cudaStream_t s = c.stream;
+    if (g.n == 0) return JET_OK;
+    size_t nn = (size_t)g.n;
+    char *p = scratch;
+    auto take32 = [&]() { int32_t *r = reinterpret_cast<int32_t *>(p); p += align256c(nn * 4); return r; };
+    Level L{};
+    L.g = g;
+    L.k = k;
+    L.part = const_cast<int32_t *>(part);   // read only in this pass
+    L.nxt = take32(); L.prio = take32(); L.mstamp = take32(); L.lstamp = take32();
+    L.listX = take32(); L.listXb = take32(); L.listM = take32(); L.listMb = take32();
+    int32_t *bigv = take32();
+    int32_t *tmp_pd = take32(), *tmp_gain = take32();
+    L.ctl = reinterpret_cast<Ctl *>(p);
+    p += align256c(sizeof(Ctl));
+    int32_t *nbig_dev = reinterpret_cast<int32_t *>(p);
+    L.bigv = bigv;
+    fill_level_params(c, L, 1, 0);
+    L.cq16 = (int32_t)llround(cval * 65536.0);
+    L.abl = flags & (ABL_NO_LOCKS | ABL_NO_AFTERBURN | ABL_WEAK_AFTERBURN | ABL_BASELINE_LP);
+    // the array keeps the previous call's contents: clear what must start at zero
+    JET_CUDA_TRY(cudaMemsetAsync(L.ctl, 0, sizeof(Ctl), s));
+    JET_CUDA_TRY(cudaMemsetAsync(nbig_dev, 0, 16, s));
+    k_collect_big<<<grid_for(g.n, kTB), kTB, 0, s>>>(g, bigv, nbig_dev);
+    k_fill_i32<<<grid_for(g.n, kTB, 4096), kTB, 0, s>>>(L.mstamp, g.n, -2);
+    k_fill_i32<<<grid_for(g.n, kTB, 4096), kTB, 0, s>>>(L.prio, g.n, kNoneGain);
+    k_locks_from_mask<<<grid_for(g.n, kTB, 4096), kTB, 0, s>>>(locked, L.lstamp, g.n);
+    k_set_epoch<<<1, 1, 0, s>>>(L.ctl, 0, MODE_LP);
+    JET_CUDA_TRY(cudaGetLastError());
+    JET_CUDA_TRY(cudaMemcpyAsync(c.pinned, nbig_dev, 4, cudaMemcpyDeviceToHost, s));
+    JET_CUDA_TRY(cudaStreamSynchronize(s));
+    L.nbig = (int32_t)(c.pinned[0] & 0xFFFFFFFF);
+    LpExport ex{pd_out ? pd_out : tmp_pd, gain_out ? gain_out : tmp_gain, f2_out};
+    if (f2_out) JET_CUDA_TRY(cudaMemsetAsync(f2_out, 0, nn * 4, s));
+    int nk = 0;
+    JET_TRY(enqueue_lp(L, s, &nk, ex));
+    k_export_lp<<<grid_for(g.n, kTB, 4096), kTB, 0, s>>>(L, inx_out, inm_out);
+    JET_CUDA_TRY(cudaGetLastError());
+    JET_CUDA_TRY(cudaStreamSynchronize(s));
+    return JET_OK;
+}
+
 }  // namespace jet
