@@ -37,7 +37,7 @@ UNIT = "Medges/s"
 K_PARTS, EPS, SEED = 64, 0.03, 1
 WORKLOAD = "grid3d 128x128x128 (7-point), vwgt U[1,4], adjwgt U[1,10], k=64, eps=0.03, seed=1"
 FLUSH_BYTES = 512 << 20          # written between steps (L2 is 129 MB)
-ROOFLINE_KERNEL = "k_lp_select_small (Jetlp select, finest level)"
+ROOFLINE_KERNEL = "Jetlp select step: k_lp_scan + k_lp_select_list (finest level)"
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "lp_select_grid3d_128_k64.txt")
 
 
@@ -243,7 +243,9 @@ def run_probe(args):
     with jet.Context(0, flags=jet.FLAG_PROFILE) as ctx:
         _, cut, st = ctx.partition(*t, k=K_PARTS, eps=EPS, seed=SEED, return_stats=True)
     skip = sum(st.sel_launches[1:])
-    print(json.dumps({"probe": "lp_select", "cut": cut, "levels": st.levels, "sel_launches": st.sel_launches,
+    print(json.dumps({"probe": "lp_select", "cut": cut, "levels": st.levels, "n": st.n,
+                      "iters": [a + b + c for a, b, c in zip(st.iters_lp, st.iters_rw, st.iters_rs)],
+                      "ms_level": [round(x, 3) for x in st.ms_level], "sel_launches": st.sel_launches,
                       "sel_ms": [round(x, 4) for x in st.sel_ms], "sel_bytes": st.sel_bytes,
                       "skip_before_finest": skip}), flush=True)
     return 0
@@ -352,7 +354,8 @@ def run_ours(args):
                        "levels": st0.levels, "cut": cuts[-1], "max_part_w": st0.max_part_w,
                        "refine_ms": round(st0.ms_refine, 3), "coarsen_ms": round(st0.ms_coarsen, 3),
                        "initpart_ms": round(st0.ms_init, 3), "finest_refine_ms": round(st0.ms_refine_finest, 3),
-                       "edge_iters_per_step": st0.edge_iters, "bytes_model_per_step": st0.bytes_model},
+                       "edge_iters_per_step": st0.edge_iters, "bytes_model_per_step": st0.bytes_model,
+                       "ms_level": [round(x, 3) for x in st0.ms_level]},
             "roofline": {"bound": "hbm", "kernel": ROOFLINE_KERNEL, "achieved": round(achieved, 1),
                          "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                          "frac": round(achieved / peak, 4) if peak else None,

@@ -103,6 +103,7 @@ typedef struct {
     int64_t sel_launches[JET_MAX_LEVELS];  /* Jetlp select passes per level */
     int64_t sel_bytes[JET_MAX_LEVELS];     /* their algorithmic bytes, summed */
     float sel_ms[JET_MAX_LEVELS];          /* their CUDA-event time, summed (JET_FLAG_PROFILE only) */
+    float ms_level[JET_MAX_LEVELS];        /* CUDA-event time of each level's projection + refinement */
 } jet_stats;
 
 typedef struct jet_ctx jet_ctx;
@@ -216,7 +217,7 @@ int jet_rebalance_pass(jet_ctx *ctx, int32_t n, const int64_t *xadj, const int32
  * memory pool, a host framework that only lends memory it owns.  Arguments,
  * outputs and results are those of jet_lp_pass (the JET_FLAG_VALIDATE graph
  * check is not run).
- * Scratch: a fixed device array of about 11 MiB inside the library, sized for
+ * Scratch: a fixed device array of about 14 MiB inside the library, sized for
  * n <= JET_NOALLOC_MAX_N vertices; every GPU that loads the library holds it
  * until the process exits.  Larger n is rejected with JET_EINVAL (see
  * jet_last_error).  The first call on each device looks up the array's

@@ -71,7 +71,7 @@ class _CStats(ctypes.Structure):
                 ("cut", ctypes.c_int64), ("max_part_w", ctypes.c_int64),
                 ("bytes_model", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
                 ("sel_launches", ctypes.c_int64 * L), ("sel_bytes", ctypes.c_int64 * L),
-                ("sel_ms", ctypes.c_float * L)]
+                ("sel_ms", ctypes.c_float * L), ("ms_level", ctypes.c_float * L)]
 
 
 @dataclass
@@ -97,6 +97,7 @@ class Stats:
     sel_launches: list = field(default_factory=list)
     sel_bytes: list = field(default_factory=list)
     sel_ms: list = field(default_factory=list)
+    ms_level: list = field(default_factory=list)
 
     @classmethod
     def from_c(cls, s: _CStats) -> "Stats":
@@ -104,7 +105,8 @@ class Stats:
         return cls(lv, list(s.n[:lv]), list(s.m[:lv]), list(s.iters_lp[:lv]), list(s.iters_rw[:lv]),
                    list(s.iters_rs[:lv]), list(s.cut_level[:lv]), s.edge_iters, s.fin_edge_iters, s.ms_coarsen,
                    s.ms_init, s.ms_refine, s.ms_refine_finest, s.ms_total, s.cut, s.max_part_w, s.bytes_model,
-                   s.kernel_launches, list(s.sel_launches[:lv]), list(s.sel_bytes[:lv]), list(s.sel_ms[:lv]))
+                   s.kernel_launches, list(s.sel_launches[:lv]), list(s.sel_bytes[:lv]), list(s.sel_ms[:lv]),
+                   list(s.ms_level[:lv]))
 
 
 _lib = None

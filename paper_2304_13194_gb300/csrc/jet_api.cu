@@ -228,8 +228,12 @@ static int uncoarsen(Ctx &c, const jet_hier *h, int32_t k, double eps, uint64_t 
     int status = JET_OK;
     int64_t cut = 0, maxw = 0;
     int64_t edge_iters = 0, fin_edge_iters = 0;
+    cudaEvent_t lev[2] = {nullptr, nullptr};
+    cudaEventCreate(&lev[0]);
+    cudaEventCreate(&lev[1]);
     for (int32_t i = l; i >= 0; --i) {
         DGraph g = level_graph(i);
+        cudaEventRecord(lev[0], s);
         if (i < l) {
             int32_t *dst = i == 0 ? part_out : other;
             JET_TRY(project(c, g.n, h->cmap[i], cur, dst));
@@ -252,10 +256,17 @@ static int uncoarsen(Ctx &c, const jet_hier *h, int32_t k, double eps, uint64_t 
             st->sel_bytes[i] = rep.sel_bytes;
             st->sel_ms[i] = rep.sel_ms;
             st->bytes_model += rep.bytes_model;
+            cudaEventRecord(lev[1], s);
+            cudaEventSynchronize(lev[1]);
+            float t = 0.f;
+            if (cudaEventElapsedTime(&t, lev[0], lev[1]) == cudaSuccess) st->ms_level[i] = t;
+            else cudaGetLastError();
         }
     }
     cudaEventRecord(ev.e[3], s);
     JET_CUDA_TRY(cudaStreamSynchronize(s));
+    cudaEventDestroy(lev[0]);
+    cudaEventDestroy(lev[1]);
     if (cut_out) *cut_out = cut;
     if (st) {
         st->levels = h->levels;

@@ -19,7 +19,7 @@ constexpr int32_t kNoneGain = INT32_MIN;   // "negative infinity" gain (Alg. 4)
 constexpr int kSlots = 33;                 // slot() values 0..32 for 32-bit losses (Sec. 4.2.1)
 constexpr int kSmallDeg = 16;              // rows up to this length: one thread per vertex
 constexpr int kTB = 256;                   // default block size
-constexpr int kRbTile = 1024;              // vertices per rebalancing tile (ordered prefixes)
+constexpr int kRbTile = 256;               // vertices per rebalancing tile (ordered prefixes)
 constexpr int kTrace = 4096;               // per-level trace records kept on the device
 
 enum Mode : int32_t { MODE_LP = 0, MODE_RW = 1, MODE_RS = 2, MODE_DONE = 3 };
@@ -95,8 +95,11 @@ struct DGraph {
 struct TraceRec {
     int32_t kind, pad;
     int64_t nx, nm, cut, maxw;
-    int64_t degx;   // sum of row lengths over X (Jetlp) or over the rebalancing candidates
-    int64_t degm;   // sum of row lengths over M
+    int64_t degx;     // sum of row lengths over X (Jetlp) or over the rebalancing candidates
+    int64_t degm;     // sum of row lengths over M
+    int64_t nbnd;     // Jetlp: boundary vertices; rebalancing: candidates whose rows were read
+    int64_t nexam;    // Jetlp: unlocked boundary vertices whose rows were read
+    int64_t degexam;  // total row length over those rows
 };
 
 struct Ctl {
@@ -109,12 +112,16 @@ struct Ctl {
     int32_t best_bal;
     int32_t nA, nB;      // rebalancing classes for the current iteration
     int32_t nX, nXb;     // X list lengths (small / large rows)
+    int32_t nW, nWb;     // work lists of the current pass (boundary / candidate rows: short / long)
     int32_t nM, nMb;     // M list lengths
     int32_t hit_cap;     // stopped by max_iters
     int32_t pad0;
     int32_t kcount[4];   // iterations run per kind (Jetlp, Jetrw, Jetrs)
     int64_t ncand;       // rebalancing candidates (trace)
     int64_t degx, degm;  // row-length sums over X / candidates and over M (byte model)
+    int64_t nbnd;        // Jetlp select: boundary vertices (ext > 0) seen
+    int64_t nexam;       // ... of which unlocked (rows streamed)
+    int64_t degexam;     // ... their total row length
     int64_t cut;         // cost of P_iter
     int64_t dcut;        // cut change accumulated by the apply kernel
     int64_t maxw;        // max part weight of P_iter
@@ -138,7 +145,11 @@ struct Level {
     uint64_t seed;
     // per-vertex state
     int32_t *part, *best, *nxt, *prio, *mstamp, *lstamp, *key;
+    int32_t *ext;            // neighbours in other parts (exact, kept by the apply kernel)
+    int32_t *wdeg;           // weighted degree (rebalancing of interior vertices)
+    int32_t *rbloss;         // rebalancing loss export (single-pass API only; may be null)
     int32_t *listX, *listXb, *listM, *listMb;
+    int32_t *listW, *listWb;  // work lists: vertices whose rows a pass must read (short / long rows)
     const int32_t *bigv;
     int32_t nbig;
     // per-part state
@@ -212,6 +223,52 @@ __device__ __forceinline__ int warp_append(int32_t *counter, bool pred) {
     base = __shfl_sync(0xffffffffu, base, leader);
     return pred ? base + __popc(m & ((1u << lane_id()) - 1u)) : -1;
 }
+
+// Block-aggregated append into a global list.  Members are staged in shared
+// memory (CAP entries) and reserved in the global list with one atomic per
+// flush, instead of one atomic per warp on a single hot counter.  Between two
+// flush() calls every thread may add() at most `adds` times (see flush).
+template <int CAP>
+struct BlockAppender {
+    int32_t *sbuf;
+    int *scount;
+    int *gbase;
+    __device__ __forceinline__ void init() {
+        if (threadIdx.x == 0) *scount = 0;
+        __syncthreads();
+    }
+    __device__ __forceinline__ void add(bool pred, int32_t v) {   // called by all threads of a warp
+        unsigned m = __ballot_sync(0xffffffffu, pred);
+        if (!m) return;
+        int leader = __ffs(m) - 1;
+        int base = 0;
+        if ((int)(threadIdx.x & 31u) == leader) base = atomicAdd(scount, __popc(m));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (pred) sbuf[base + __popc(m & ((1u << (threadIdx.x & 31u)) - 1u))] = v;
+    }
+    // Flushes when the buffer could overflow on the next round (each thread
+    // adding up to `adds` members), or always when force is set.  Called by
+    // all threads of the block.
+    __device__ __forceinline__ void flush(int32_t *gcount, int32_t *glist, bool force, int adds = 1) {
+        __syncthreads();
+        int c = *scount;
+        if (c > 0 && (force || c > CAP - adds * (int)blockDim.x)) {
+            if (threadIdx.x == 0) *gbase = atomicAdd(gcount, c);
+            __syncthreads();
+            int b = *gbase;
+            for (int i = threadIdx.x; i < c; i += blockDim.x) glist[b + i] = sbuf[i];
+            __syncthreads();
+            if (threadIdx.x == 0) *scount = 0;
+            __syncthreads();
+        }
+    }
+};
+
+#define JET_BLOCK_APPENDER(name, CAP)                                                \
+    __shared__ int32_t name##_buf[CAP];                                              \
+    __shared__ int name##_cnt, name##_base;                                          \
+    BlockAppender<CAP> name{name##_buf, &name##_cnt, &name##_base};                  \
+    name.init()
 
 __device__ __forceinline__ void atomic_add_i64(int64_t *p, int64_t v) {
     atomicAdd(reinterpret_cast<unsigned long long *>(p), (unsigned long long)v);
@@ -399,7 +456,8 @@ int lp_pass(Ctx &c, const DGraph &g, int32_t k, const int32_t *part, const uint8
 // allocation.  Used by jet_lp_pass_noalloc.
 constexpr size_t align256c(size_t x) { return (x + 255) & ~size_t(255); }
 constexpr size_t lp_scratch_bytes(int64_t n) {
-    return 11 * align256c((size_t)(n > 0 ? n : 1) * 4) + align256c(sizeof(Ctl)) + 256;
+    return 14 * align256c((size_t)(n > 0 ? n : 1) * 4) + align256c(sizeof(Ctl)) + 256 +
+           align256c((size_t)JET_MAX_K * 8) + 256;
 }
 int lp_pass_in_scratch(Ctx &c, const DGraph &g, int32_t k, const int32_t *part, const uint8_t *locked, double cval,
                        uint32_t flags, int32_t *pd_out, int32_t *gain_out, uint8_t *inx_out, int32_t *f2_out,

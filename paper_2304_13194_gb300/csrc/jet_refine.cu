@@ -58,7 +58,8 @@ __device__ __forceinline__ int32_t key_conn(unsigned long long key) { return (in
 // ---------------------------------------------------------------------------
 template <bool EW>
 __global__ void __launch_bounds__(kTB) k_cut_pw(DGraph g, int32_t k, const int32_t *__restrict__ part,
-                                                 int64_t *__restrict__ pw, int64_t *__restrict__ cut2) {
+                                                 int64_t *__restrict__ pw, int64_t *__restrict__ cut2,
+                                                 int32_t *__restrict__ ext, int32_t *__restrict__ wdeg) {
     extern __shared__ long long shpw[];
     __shared__ long long red[40];
     for (int i = threadIdx.x; i < k; i += blockDim.x) shpw[i] = 0;
@@ -66,10 +67,19 @@ __global__ void __launch_bounds__(kTB) k_cut_pw(DGraph g, int32_t k, const int32
     long long c = 0;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < g.n; v += (int64_t)gridDim.x * blockDim.x) {
         int32_t p = part[v];
-        atomicAdd(reinterpret_cast<unsigned long long *>(&shpw[p]), (unsigned long long)(long long)g.vw[v]);
+        atomicAdd(reinterpret_cast<unsigned long long *>(&shpw[p]), (unsigned long long)(long long)(g.vw ? g.vw[v] : 1));
         int64_t e = ld_xadj(g.xadj, v + 1);
-        for (int64_t j = ld_xadj(g.xadj, v); j < e; ++j)
-            if (part[g.adj[j]] != p) c += edge_w<EW>(g, j);
+        int32_t nx = 0, wd = 0, cv = 0;
+        for (int64_t j = ld_xadj(g.xadj, v); j < e; ++j) {
+            int32_t w = edge_w<EW>(g, j);
+            bool other = part[g.adj[j]] != p;
+            cv += other ? w : 0;
+            nx += other ? 1 : 0;
+            wd += w;
+        }
+        c += cv;
+        if (ext) ext[v] = nx;
+        if (wdeg) wdeg[v] = wd;
     }
     c = block_sum_i64(c, red);
     if (threadIdx.x == 0 && c) atomic_add_i64(cut2, c);
@@ -167,8 +177,10 @@ __global__ void __launch_bounds__(1024) k_ctl_init(Level L, const int64_t *cut2)
         ctl->copy_best = 0; ctl->hit_cap = 0;
         ctl->kcount[0] = ctl->kcount[1] = ctl->kcount[2] = ctl->kcount[3] = 0;
         ctl->nX = ctl->nXb = ctl->nM = ctl->nMb = 0;
+        ctl->nW = ctl->nWb = 0;
         ctl->ncand = 0;
         ctl->degx = ctl->degm = 0;
+        ctl->nbnd = ctl->nexam = ctl->degexam = 0;
         ctl->mode = choose_mode(L, maxw <= ctl->L);
     }
     __syncthreads();
@@ -229,14 +241,17 @@ __global__ void __launch_bounds__(1024) k_controller(Level L) {
             r.nm = (int64_t)(ctl->nM + ctl->nMb);
             r.cut = cut; r.maxw = maxw;
             r.degx = ctl->degx; r.degm = ctl->degm;
+            r.nbnd = ctl->nbnd; r.nexam = ctl->nexam; r.degexam = ctl->degexam;
             L.trace[it] = r;
         }
         if (kind == MODE_LP) ctl->lp_epoch = it;
         ctl->kcount[kind] += 1;
         ctl->it = it + 1;
         ctl->nX = ctl->nXb = ctl->nM = ctl->nMb = 0;
+        ctl->nW = ctl->nWb = 0;
         ctl->ncand = 0;
         ctl->degx = ctl->degm = 0;
+        ctl->nbnd = ctl->nexam = ctl->degexam = 0;
         int32_t m = choose_mode(L, bal);
         ctl->mode = m;
         next_mode = m;
@@ -286,45 +301,104 @@ __device__ __forceinline__ void disarm_loop(const Level &L) {
         cudaGraphSetConditional((cudaGraphConditionalHandle)L.h_loop, 0u);
 }
 
-template <bool EW>
-__global__ void __launch_bounds__(kTB) k_lp_select_small(Level L, LpExport ex) {
+// Block-level sums of the select counters, one atomic per block.
+__device__ __forceinline__ void flush_counter(int64_t *dst, long long v, long long *red) {
+    v = block_sum_i64(v, red);
+    if (threadIdx.x == 0 && v) atomic_add_i64(dst, v);
+}
+
+// Jetlp step 0: the work list.  A vertex with no neighbour in another part
+// (ext == 0) has no destination (Alg. 4: A_v is empty) and a locked vertex is
+// skipped (Sec. 4.1.3); the scan reads ext four vertices at a time and lists
+// the others.  Interior rows are never read.
+__global__ void __launch_bounds__(kTB) k_lp_scan(Level L) {
     disarm_loop(L);
-    const Ctl *ctl = L.ctl;
+    __shared__ long long red[40];
+    JET_BLOCK_APPENDER(wapp, 4096);
+    Ctl *ctl = L.ctl;
     const int32_t epoch = ctl->lp_epoch;
+    const bool use_locks = !ablate_locks(L.abl);
+    const int64_t n = L.g.n, nq = (n + 3) / 4;
+    const bool vec = (reinterpret_cast<uintptr_t>(L.ext) & 15) == 0;
+    long long nb = 0;
+    for (int64_t q0 = (int64_t)blockIdx.x * blockDim.x; q0 < nq; q0 += (int64_t)gridDim.x * blockDim.x) {
+        int64_t q = q0 + threadIdx.x;
+        int64_t v0 = 4 * q;
+        int32_t e[4] = {0, 0, 0, 0};
+        if (q < nq) {
+            if (vec && v0 + 3 < n) {
+                int4 x = __ldg(reinterpret_cast<const int4 *>(L.ext + v0));
+                e[0] = x.x; e[1] = x.y; e[2] = x.z; e[3] = x.w;
+            } else {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) e[i] = v0 + i < n ? L.ext[v0 + i] : 0;
+            }
+        }
+        int32_t ls[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) ls[i] = (e[i] > 0 && use_locks) ? L.lstamp[v0 + i] : INT32_MIN;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            nb += e[i] > 0;
+            wapp.add(e[i] > 0 && ls[i] != epoch, (int32_t)(v0 + i));
+        }
+        wapp.flush(&ctl->nW, L.listW, false, 4);
+    }
+    wapp.flush(&ctl->nW, L.listW, true, 4);
+    flush_counter(&ctl->nbnd, nb, red);
+}
+
+// Jetlp step 1 (Alg. 4 first loop, Eq. for P_d, Eq. gainconn_filter) for the
+// listed vertices with rows of <= 16 entries: one thread per vertex, the row
+// preloaded into registers so all its loads are in flight together.  Longer
+// rows are passed on to the warp kernel.  prio holds F only for members of X;
+// every other entry stays kNoneGain (reset after the afterburner).
+template <bool EW>
+__global__ void __launch_bounds__(kTB, 4) k_lp_select_list(Level L, LpExport ex) {
+    __shared__ long long red[40];
+    Ctl *ctl = L.ctl;
+    const int32_t nW = ctl->nW;
+    if ((int64_t)blockIdx.x * blockDim.x >= nW) return;
+    JET_BLOCK_APPENDER(xapp, 2048);
+    JET_BLOCK_APPENDER(bapp, 1024);
     const DGraph g = L.g;
-    int32_t v = blockIdx.x * blockDim.x + threadIdx.x;
-    bool inX = false, big = false;
-    if (v < g.n) {
-        int64_t beg = ld_xadj(g.xadj, v), end = ld_xadj(g.xadj, (int64_t)v + 1);
-        int d = (int)(end - beg);
-        if (d > kSmallDeg) {
-            big = true;
-        } else {
-            int32_t F = kNoneGain, pd = -1;
+    long long nexam = 0, degexam = 0, degx = 0;
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < nW; i0 += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = i0 + threadIdx.x;
+        bool inX = false, big = false;
+        int32_t v = -1;
+        if (i < nW) {
+            v = L.listW[i];
+            int64_t beg = ld_xadj(g.xadj, v), end = ld_xadj(g.xadj, (int64_t)v + 1);
+            int d = (int)(end - beg);
             int32_t ps = L.part[v];
-            bool locked = !ablate_locks(L.abl) && L.lstamp[v] == epoch;
-            if (!locked && d > 0) {
+            if (d > kSmallDeg) {
+                big = true;
+            } else {
+                nexam += 1;
+                degexam += d;
+                int32_t F = kNoneGain, pd = -1;
                 int32_t pp[kSmallDeg], ww[kSmallDeg];
 #pragma unroll
-                for (int i = 0; i < kSmallDeg; ++i) {
-                    if (i < d) {
-                        pp[i] = __ldg(L.part + __ldg(g.adj + beg + i));
-                        ww[i] = edge_w<EW>(g, beg + i);
+                for (int t = 0; t < kSmallDeg; ++t) {
+                    if (t < d) {
+                        pp[t] = __ldg(L.part + __ldg(g.adj + beg + t));
+                        ww[t] = edge_w<EW>(g, beg + t);
                     } else {
-                        pp[i] = -1; ww[i] = 0;
+                        pp[t] = -1; ww[t] = 0;
                     }
                 }
                 int32_t conn_s = 0;
 #pragma unroll
-                for (int i = 0; i < kSmallDeg; ++i) conn_s += (pp[i] == ps) ? ww[i] : 0;
+                for (int t = 0; t < kSmallDeg; ++t) conn_s += (pp[t] == ps) ? ww[t] : 0;
                 unsigned long long best = 0;
 #pragma unroll
-                for (int i = 0; i < kSmallDeg; ++i) {
-                    if (i < d && pp[i] != ps) {
+                for (int t = 0; t < kSmallDeg; ++t) {
+                    if (t < d && pp[t] != ps) {
                         int32_t c = 0;
 #pragma unroll
-                        for (int j = 0; j < kSmallDeg; ++j) c += (pp[j] == pp[i]) ? ww[j] : 0;
-                        unsigned long long key = part_key(c, pp[i]);
+                        for (int u = 0; u < kSmallDeg; ++u) c += (pp[u] == pp[t]) ? ww[u] : 0;
+                        unsigned long long key = part_key(c, pp[t]);
                         best = key > best ? key : best;
                     }
                 }
@@ -333,17 +407,24 @@ __global__ void __launch_bounds__(kTB) k_lp_select_small(Level L, LpExport ex) {
                     F = key_conn(best) - conn_s;
                     inX = first_filter(F, conn_s, L.cq16, L.abl);
                 }
+                if (inX) {
+                    L.prio[v] = F;
+                    L.nxt[v] = pd;
+                    degx += d;
+                }
+                if (ex.pd) { ex.pd[v] = pd >= 0 ? pd : ps; ex.gain[v] = F; }
             }
-            L.prio[v] = inX ? F : kNoneGain;
-            if (inX) L.nxt[v] = pd;
-            if (ex.pd) { ex.pd[v] = pd >= 0 ? pd : ps; ex.gain[v] = F; }
         }
+        xapp.add(inX, v);
+        bapp.add(big, v);
+        xapp.flush(&ctl->nX, L.listX, false);
+        bapp.flush(&ctl->nWb, L.listWb, false);
     }
-    (void)big;
-    int slot = warp_append(&L.ctl->nX, inX);
-    if (inX) L.listX[slot] = v;
-    int dx = warp_sum_i32(inX ? (int)(ld_xadj(g.xadj, (int64_t)v + 1) - ld_xadj(g.xadj, v)) : 0);
-    if (lane_id() == 0 && dx) atomicAdd(reinterpret_cast<unsigned long long *>(&L.ctl->degx), (unsigned long long)dx);
+    xapp.flush(&ctl->nX, L.listX, true);
+    bapp.flush(&ctl->nWb, L.listWb, true);
+    flush_counter(&ctl->nexam, nexam, red);
+    flush_counter(&ctl->degexam, degexam, red);
+    flush_counter(&ctl->degx, degx, red);
 }
 
 // Long rows: one warp per vertex, dense per-warp table in shared memory.
@@ -352,54 +433,59 @@ __global__ void __launch_bounds__(kTB) k_lp_select_small(Level L, LpExport ex) {
 template <bool EW>
 __global__ void __launch_bounds__(kTB) k_lp_select_big(Level L, LpExport ex) {
     extern __shared__ int32_t tabs[];
+    __shared__ long long red[40];
+    Ctl *ctl = L.ctl;
+    const int32_t nWb = ctl->nWb;
     const int warps = blockDim.x >> 5;
+    if ((int64_t)blockIdx.x * warps >= nWb) return;
     int32_t *tab = tabs + (threadIdx.x >> 5) * L.k;
     for (int i = threadIdx.x; i < warps * L.k; i += blockDim.x) tabs[i] = 0;
     __syncthreads();
-    const Ctl *ctl = L.ctl;
-    const int32_t epoch = ctl->lp_epoch;
     const DGraph g = L.g;
     const unsigned lane = lane_id();
-    for (int64_t w = (int64_t)blockIdx.x * warps + (threadIdx.x >> 5); w < L.nbig; w += (int64_t)gridDim.x * warps) {
-        int32_t v = L.bigv[w];
+    long long nexam = 0, degexam = 0, degx = 0;
+    for (int64_t w = (int64_t)blockIdx.x * warps + (threadIdx.x >> 5); w < nWb; w += (int64_t)gridDim.x * warps) {
+        int32_t v = L.listWb[w];
         int32_t ps = L.part[v];
-        bool locked = !ablate_locks(L.abl) && L.lstamp[v] == epoch;
         int32_t F = kNoneGain, pd = -1;
         bool inX = false;
-        if (!locked) {
-            int64_t beg = ld_xadj(g.xadj, v), end = ld_xadj(g.xadj, (int64_t)v + 1);
-            for (int64_t j = beg + lane; j < end; j += 32)
-                atomicAdd(&tab[__ldg(L.part + __ldg(g.adj + j))], edge_w<EW>(g, j));
-            __syncwarp();
-            int32_t conn_s = tab[ps];
-            __syncwarp();
-            unsigned long long best = 0;
-            for (int64_t j = beg + lane; j < end; j += 32) {
-                int32_t p = __ldg(L.part + __ldg(g.adj + j));
-                int32_t c = atomicExch(&tab[p], 0);
-                if (c > 0 && p != ps) {
-                    unsigned long long key = part_key(c, p);
-                    best = key > best ? key : best;
-                }
-            }
-            __syncwarp();
-            best = warp_max_u64(best);
-            if (best) {
-                pd = key_part(best);
-                F = key_conn(best) - conn_s;
-                inX = first_filter(F, conn_s, L.cq16, L.abl);
+        int64_t beg = ld_xadj(g.xadj, v), end = ld_xadj(g.xadj, (int64_t)v + 1);
+        for (int64_t j = beg + lane; j < end; j += 32)
+            atomicAdd(&tab[__ldg(L.part + __ldg(g.adj + j))], edge_w<EW>(g, j));
+        __syncwarp();
+        int32_t conn_s = tab[ps];
+        __syncwarp();
+        unsigned long long best = 0;
+        for (int64_t j = beg + lane; j < end; j += 32) {
+            int32_t p = __ldg(L.part + __ldg(g.adj + j));
+            int32_t c = atomicExch(&tab[p], 0);
+            if (c > 0 && p != ps) {
+                unsigned long long key = part_key(c, p);
+                best = key > best ? key : best;
             }
         }
+        __syncwarp();
+        best = warp_max_u64(best);
+        if (best) {
+            pd = key_part(best);
+            F = key_conn(best) - conn_s;
+            inX = first_filter(F, conn_s, L.cq16, L.abl);
+        }
         if (lane == 0) {
-            L.prio[v] = inX ? F : kNoneGain;
+            nexam += 1;
+            degexam += end - beg;
             if (inX) {
+                L.prio[v] = F;
                 L.nxt[v] = pd;
-                L.listXb[atomicAdd(&L.ctl->nXb, 1)] = v;
-                atomic_add_i64(&L.ctl->degx, ld_xadj(g.xadj, (int64_t)v + 1) - ld_xadj(g.xadj, v));
+                L.listXb[atomicAdd(&ctl->nXb, 1)] = v;
+                degx += end - beg;
             }
             if (ex.pd) { ex.pd[v] = pd >= 0 ? pd : ps; ex.gain[v] = F; }
         }
     }
+    flush_counter(&ctl->nexam, nexam, red);
+    flush_counter(&ctl->degexam, degexam, red);
+    flush_counter(&ctl->degx, degx, red);
 }
 
 // ---------------------------------------------------------------------------
@@ -421,31 +507,53 @@ __device__ __forceinline__ bool is_big_row(const DGraph &g, int32_t v) {
     return ld_xadj(g.xadj, (int64_t)v + 1) - ld_xadj(g.xadj, v) > kSmallDeg;
 }
 
+// Short rows (X members are listed by row length): one thread per vertex, the
+// row preloaded so that the neighbours' gathers are all in flight together.
 template <bool EW>
-__global__ void __launch_bounds__(kTB) k_afterburn_small(Level L, LpExport ex) {
+__global__ void __launch_bounds__(kTB, 4) k_afterburn_small(Level L, LpExport ex) {
     Ctl *ctl = L.ctl;
     const int32_t nX = ctl->nX, it = ctl->it;
-    const int64_t lim = ((int64_t)nX + 31) & ~31LL;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < lim; i += (int64_t)gridDim.x * blockDim.x) {
+    if ((int64_t)blockIdx.x * blockDim.x >= nX) return;
+    JET_BLOCK_APPENDER(mapp, 2048);
+    const bool full = !(L.abl & (ABL_NO_AFTERBURN | ABL_BASELINE_LP));
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < nX; i0 += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = i0 + threadIdx.x;
         bool inM = false;
         int32_t v = -1;
         if (i < nX) {
             v = L.listX[i];
-            if (L.abl & (ABL_NO_AFTERBURN | ABL_BASELINE_LP)) {
+            if (!full) {
                 inM = true;
             } else {
                 int32_t Fv = L.prio[v], pd = L.nxt[v], ps = L.part[v];
-                int64_t beg = ld_xadj(L.g.xadj, v), end = ld_xadj(L.g.xadj, (int64_t)v + 1);
+                int64_t beg = ld_xadj(L.g.xadj, v);
+                int d = (int)(ld_xadj(L.g.xadj, (int64_t)v + 1) - beg);
+                int32_t uu[kSmallDeg], ww[kSmallDeg];
+#pragma unroll
+                for (int t = 0; t < kSmallDeg; ++t) {
+                    uu[t] = t < d ? __ldg(L.g.adj + beg + t) : -1;
+                    ww[t] = t < d ? edge_w<EW>(L.g, beg + t) : 0;
+                }
                 int32_t f2 = 0;
-                for (int64_t j = beg; j < end; ++j) f2 += afterburn_term<EW>(L, v, Fv, pd, ps, j);
+#pragma unroll
+                for (int t = 0; t < kSmallDeg; ++t) {
+                    if (t < d) {
+                        int32_t u = uu[t];
+                        int32_t pu = L.part[u];
+                        int32_t fu = L.prio[u];
+                        if (fu > Fv || (fu == Fv && u < v)) pu = L.nxt[u];
+                        f2 += pu == pd ? ww[t] : (pu == ps ? -ww[t] : 0);
+                    }
+                }
                 inM = f2 >= 0;
                 if (ex.f2) ex.f2[v] = f2;
             }
             if (inM) L.mstamp[v] = it;
         }
-        int slot = warp_append(&ctl->nM, inM);
-        if (inM) L.listM[slot] = v;
+        mapp.add(inM, v);
+        mapp.flush(&ctl->nM, L.listM, false);
     }
+    mapp.flush(&ctl->nM, L.listM, true);
 }
 
 template <bool EW>
@@ -481,25 +589,36 @@ __global__ void __launch_bounds__(kTB) k_afterburn_big(Level L, LpExport ex) {
 // Apply M (Alg. 3 updatePartsAndDS): exact cut change and part weights.
 // For an edge with both ends moving, the smaller id accounts for it.
 // ---------------------------------------------------------------------------
+// One edge of a moving vertex v (a -> b): cut change and, for a neighbour
+// that stays, its count of neighbours in other parts (ext).  For an edge with
+// both ends moving, the smaller id accounts for the cut.  Returns 1 in *other
+// when the edge joins different parts afterwards.
 template <bool EW>
-__device__ __forceinline__ int64_t apply_edge(const Level &L, int32_t v, int32_t a, int32_t b, int32_t it, int64_t j) {
+__device__ __forceinline__ int64_t apply_edge(const Level &L, int32_t v, int32_t a, int32_t b, int32_t it, int64_t j,
+                                              int32_t *other) {
     int32_t u = __ldg(L.g.adj + j);
     int32_t pu = L.part[u];
     bool mu = L.mstamp[u] == it;
-    if (mu && u < v) return 0;
     int32_t pn = mu ? L.nxt[u] : pu;
+    *other = pn != b;
+    if (!mu) {
+        int32_t dx = (int)(pn != b) - (int)(pu != a);
+        if (dx) atomicAdd(&L.ext[u], dx);
+    } else if (u < v) {
+        return 0;
+    }
     int32_t w = edge_w<EW>(L.g, j);
     return (int64_t)w * ((int)(pn != b) - (int)(pu != a));
 }
 
 template <bool EW>
-__global__ void __launch_bounds__(kTB) k_apply_small(Level L) {
+__global__ void __launch_bounds__(kTB, 4) k_apply_small(Level L) {
     extern __shared__ long long shpw[];
     __shared__ long long red[40];
     Ctl *ctl = L.ctl;
     if (ctl->mode == MODE_DONE) return;
     const int32_t nM = ctl->nM, it = ctl->it;
-    if (nM == 0 && ctl->nMb == 0) return;
+    if ((int64_t)blockIdx.x * blockDim.x >= nM) return;
     for (int i = threadIdx.x; i < L.k; i += blockDim.x) shpw[i] = 0;
     __syncthreads();
     long long dc = 0, dm = 0;
@@ -509,9 +628,32 @@ __global__ void __launch_bounds__(kTB) k_apply_small(Level L) {
         long long wv = L.g.vw[v];
         atomicAdd(reinterpret_cast<unsigned long long *>(&shpw[a]), (unsigned long long)(-wv));
         atomicAdd(reinterpret_cast<unsigned long long *>(&shpw[b]), (unsigned long long)wv);
-        int64_t beg = ld_xadj(L.g.xadj, v), end = ld_xadj(L.g.xadj, (int64_t)v + 1);
-        for (int64_t j = beg; j < end; ++j) dc += apply_edge<EW>(L, v, a, b, it, j);
-        dm += end - beg;
+        int64_t beg = ld_xadj(L.g.xadj, v);
+        int d = (int)(ld_xadj(L.g.xadj, (int64_t)v + 1) - beg);
+        // rows in listM are short (long ones are in listMb): preload them
+        int32_t uu[kSmallDeg];
+#pragma unroll
+        for (int t = 0; t < kSmallDeg; ++t) uu[t] = t < d ? __ldg(L.g.adj + beg + t) : -1;
+        int32_t ne = 0;
+#pragma unroll
+        for (int t = 0; t < kSmallDeg; ++t) {
+            if (t < d) {
+                int32_t u = uu[t];
+                int32_t pu = L.part[u];
+                bool mu = L.mstamp[u] == it;
+                int32_t pn = mu ? L.nxt[u] : pu;
+                int32_t diff = (int)(pn != b) - (int)(pu != a);
+                ne += pn != b;
+                if (!mu) {
+                    if (diff) atomicAdd(&L.ext[u], diff);
+                    dc += (long long)edge_w<EW>(L.g, beg + t) * diff;
+                } else if (u > v) {
+                    dc += (long long)edge_w<EW>(L.g, beg + t) * diff;
+                }
+            }
+        }
+        L.ext[v] = ne;
+        dm += d;
     }
     dc = block_sum_i64(dc, red);
     dm = block_sum_i64(dm, red);
@@ -534,14 +676,21 @@ __global__ void __launch_bounds__(kTB) k_apply_big(Level L) {
         int32_t a = L.part[v], b = L.nxt[v];
         int64_t beg = ld_xadj(L.g.xadj, v), end = ld_xadj(L.g.xadj, (int64_t)v + 1);
         long long dc = 0;
-        for (int64_t j = beg + lane; j < end; j += 32) dc += apply_edge<EW>(L, v, a, b, it, j);
+        int32_t ne = 0;
+        for (int64_t j = beg + lane; j < end; j += 32) {
+            int32_t o;
+            dc += apply_edge<EW>(L, v, a, b, it, j, &o);
+            ne += o;
+        }
         dc = warp_sum_i64(dc);
+        ne = warp_sum_i32(ne);
         if (lane == 0) {
             long long wv = L.g.vw[v];
             atomic_add_i64(&L.pw[a], -wv);
             atomic_add_i64(&L.pw[b], wv);
             if (dc) atomic_add_i64(&ctl->dcut, dc);
             atomic_add_i64(&ctl->degm, end - beg);
+            L.ext[v] = ne;
         }
     }
 }
@@ -558,6 +707,13 @@ __global__ void __launch_bounds__(kTB) k_commit(Level L) {
         int32_t v = i < nM ? L.listM[i] : L.listMb[i - nM];
         L.part[v] = L.nxt[v];
         if (kind == MODE_LP) L.lstamp[v] = it;
+    }
+    if (kind == MODE_LP) {
+        // back to "no priority" for every member of X (the afterburner is done)
+        const int32_t nX = ctl->nX, nXb = ctl->nXb;
+        int64_t tx = (int64_t)nX + nXb;
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < tx; i += (int64_t)gridDim.x * blockDim.x)
+            L.prio[i < nX ? L.listX[i] : L.listXb[i - nX]] = kNoneGain;
     }
 }
 
@@ -578,6 +734,8 @@ __device__ __forceinline__ int32_t random_B(const Level &L, int32_t v, int32_t i
     return L.Bs[h % (uint64_t)nB];
 }
 
+constexpr int kSmemBuckets = 1024;   // slot buckets aggregated per block when nA * kSlots fits
+
 // Adds w into bucketw[key] with one atomic per distinct key in the warp.
 __device__ __forceinline__ void bucket_add(const Level &L, int32_t key, long long w) {
     unsigned peers = __match_any_sync(0xffffffffu, key);
@@ -590,45 +748,174 @@ __device__ __forceinline__ void bucket_add(const Level &L, int32_t key, long lon
     if (key >= 0 && (int)lane_id() == __ffs(peers) - 1) atomic_add_i64(&L.bucketw[key], s);
 }
 
-template <bool EW, bool STRONG>
-__global__ void __launch_bounds__(kTB) k_rb_cand_small(Level L) {
+// Per-block slot buckets in shared memory when nA * kSlots keys fit.
+struct SmemBuckets {
+    long long *b;
+    int32_t nkeys;
+    bool on;
+    __device__ __forceinline__ void init(const Level &L, long long *buf) {
+        b = buf;
+        nkeys = L.ctl->nA * kSlots;
+        on = nkeys <= kSmemBuckets;
+        if (on)
+            for (int i = threadIdx.x; i < nkeys; i += blockDim.x) b[i] = 0;
+        __syncthreads();
+    }
+    // all threads of the warp call add (key may be -1)
+    __device__ __forceinline__ void add(const Level &L, int32_t key, long long w) {
+        if (on) {
+            if (key >= 0) atomicAdd(reinterpret_cast<unsigned long long *>(&b[key]), (unsigned long long)w);
+        } else {
+            bucket_add(L, key, w);
+        }
+    }
+    __device__ __forceinline__ void flush(const Level &L) {
+        if (!on) return;
+        __syncthreads();
+        for (int i = threadIdx.x; i < nkeys; i += blockDim.x)
+            if (b[i]) atomic_add_i64(&L.bucketw[i], b[i]);
+    }
+};
+
+// Rebalancing step 0 (Alg. 5 first loop): the candidates are the vertices of
+// oversized parts allowed to leave (heavy-vertex rule).  A candidate with no
+// neighbour in another part (ext == 0) touches no part of B (its own part is
+// oversized): conn(v, P_s) is its weighted degree, Jetrw sends it to a random
+// part of B and both losses equal that degree — it is finished here without
+// reading its row.  The others are listed for the row kernels.
+template <bool STRONG>
+__global__ void __launch_bounds__(kTB) k_rb_scan(Level L) {
     disarm_loop(L);
+    __shared__ long long red[40];
+    __shared__ long long sbuf[kSmemBuckets];
+    SmemBuckets sb;
+    sb.init(L, sbuf);
+    JET_BLOCK_APPENDER(wapp, 4096);
     Ctl *ctl = L.ctl;
     const int32_t it = ctl->it;
+    const int32_t nB = ctl->nB;
+    const int64_t opt = ctl->opt;
+    const int64_t n = L.g.n, nq = (n + 3) / 4;
+    const bool vec = (reinterpret_cast<uintptr_t>(L.part) & 15) == 0;
+    long long ncand = 0, nlist = 0;
+    for (int64_t q0 = (int64_t)blockIdx.x * blockDim.x; q0 < nq; q0 += (int64_t)gridDim.x * blockDim.x) {
+        int64_t q = q0 + threadIdx.x;
+        int64_t v0 = 4 * q;
+        int32_t pp[4] = {-1, -1, -1, -1};
+        if (q < nq) {
+            if (vec && v0 + 3 < n) {
+                int4 x = *reinterpret_cast<const int4 *>(L.part + v0);
+                pp[0] = x.x; pp[1] = x.y; pp[2] = x.z; pp[3] = x.w;
+            } else {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) pp[i] = v0 + i < n ? L.part[v0 + i] : -1;
+            }
+        }
+        // all loads of the four vertices are issued before any decision
+        int32_t aa[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) aa[i] = (pp[i] >= 0 && nB > 0) ? L.aidx[pp[i]] : -1;
+        long long pwv[4];
+        int32_t vwv[4], ex[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            bool c = aa[i] >= 0;
+            pwv[i] = c ? L.pw[pp[i]] : 0;
+            vwv[i] = c ? L.g.vw[v0 + i] : 0;
+            ex[i] = c ? L.ext[v0 + i] : 0;
+        }
+        bool cand[4];
+        int32_t wd[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            // heavy-vertex restriction (Sec. 4.2.2): stay if vwgt > 1.5 (w_p - opt)
+            cand[i] = aa[i] >= 0 && 2LL * vwv[i] <= 3LL * (pwv[i] - opt);
+            wd[i] = (cand[i] && ex[i] == 0) ? L.wdeg[v0 + i] : 0;
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            int32_t v = (int32_t)(v0 + i);
+            int32_t key = -1;
+            long long wv = 0;
+            bool listed = cand[i] && ex[i] != 0;
+            if (cand[i]) {
+                ncand += 1;
+                if (!listed) {
+                    int32_t loss = wd[i];
+                    if constexpr (!STRONG) L.nxt[v] = random_B(L, v, it);
+                    key = aa[i] * kSlots + slot_of(loss);
+                    wv = vwv[i];
+                    if (L.rbloss) L.rbloss[v] = loss;
+                }
+            }
+            if (pp[i] >= 0 && !listed) L.key[v] = key;
+            sb.add(L, key, wv);
+            wapp.add(listed, v);
+            nlist += listed;
+        }
+        wapp.flush(&ctl->nW, L.listW, false, 4);
+    }
+    wapp.flush(&ctl->nW, L.listW, true, 4);
+    sb.flush(L);
+    flush_counter(&ctl->ncand, ncand, red);
+    flush_counter(&ctl->nbnd, nlist, red);
+}
+
+// Rebalancing step 1 for listed candidates with rows of <= 16 entries: Jetrw
+// destination (best-connected part of B, lowest id on ties, else a random one)
+// and loss, or the Jetrs loss (Sec. 4.2.2), then the slot bucket.
+template <bool EW, bool STRONG>
+__global__ void __launch_bounds__(kTB, 4) k_rb_cand_list(Level L) {
+    __shared__ long long red[40];
+    __shared__ long long sbuf[kSmemBuckets];
+    Ctl *ctl = L.ctl;
+    const int32_t nW = ctl->nW;
+    if ((int64_t)blockIdx.x * blockDim.x >= nW) return;
+    SmemBuckets sb;
+    sb.init(L, sbuf);
+    JET_BLOCK_APPENDER(bapp, 1024);
+    const int32_t it = ctl->it;
     const DGraph g = L.g;
-    int32_t v = blockIdx.x * blockDim.x + threadIdx.x;
-    int32_t key = -1;
-    long long wv = 0;
-    bool cand = false;
-    if (v < g.n) {
-        int64_t beg = ld_xadj(g.xadj, v), end = ld_xadj(g.xadj, (int64_t)v + 1);
-        int d = (int)(end - beg);
-        int32_t ps = L.part[v], a;
-        if (d <= kSmallDeg) {
-            if (rb_eligible(L, v, ps, a)) {
+    long long degrows = 0;
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < nW; i0 += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = i0 + threadIdx.x;
+        int32_t key = -1;
+        long long wv = 0;
+        bool big = false;
+        int32_t v = -1;
+        if (i < nW) {
+            v = L.listW[i];
+            int32_t ps = L.part[v];
+            int32_t a = L.aidx[ps];
+            int64_t beg = ld_xadj(g.xadj, v), end = ld_xadj(g.xadj, (int64_t)v + 1);
+            int d = (int)(end - beg);
+            if (d > kSmallDeg) {
+                big = true;
+            } else {
+                degrows += d;
                 int32_t pp[kSmallDeg], ww[kSmallDeg];
 #pragma unroll
-                for (int i = 0; i < kSmallDeg; ++i) {
-                    if (i < d) {
-                        pp[i] = __ldg(L.part + __ldg(g.adj + beg + i));
-                        ww[i] = edge_w<EW>(g, beg + i);
+                for (int t = 0; t < kSmallDeg; ++t) {
+                    if (t < d) {
+                        pp[t] = __ldg(L.part + __ldg(g.adj + beg + t));
+                        ww[t] = edge_w<EW>(g, beg + t);
                     } else {
-                        pp[i] = -1; ww[i] = 0;
+                        pp[t] = -1; ww[t] = 0;
                     }
                 }
                 int32_t conn_s = 0;
 #pragma unroll
-                for (int i = 0; i < kSmallDeg; ++i) conn_s += (pp[i] == ps) ? ww[i] : 0;
+                for (int t = 0; t < kSmallDeg; ++t) conn_s += (pp[t] == ps) ? ww[t] : 0;
                 int32_t loss;
                 if constexpr (!STRONG) {
                     unsigned long long best = 0;
 #pragma unroll
-                    for (int i = 0; i < kSmallDeg; ++i) {
-                        if (i < d && L.inB[pp[i]]) {
+                    for (int t = 0; t < kSmallDeg; ++t) {
+                        if (t < d && L.inB[pp[t]]) {
                             int32_t c = 0;
 #pragma unroll
-                            for (int j = 0; j < kSmallDeg; ++j) c += (pp[j] == pp[i]) ? ww[j] : 0;
-                            unsigned long long k2 = part_key(c, pp[i]);
+                            for (int u = 0; u < kSmallDeg; ++u) c += (pp[u] == pp[t]) ? ww[u] : 0;
+                            unsigned long long k2 = part_key(c, pp[t]);
                             best = k2 > best ? k2 : best;
                         }
                     }
@@ -641,13 +928,13 @@ __global__ void __launch_bounds__(kTB) k_rb_cand_small(Level L) {
                     long long S = 0;
                     int32_t c = 0;
 #pragma unroll
-                    for (int i = 0; i < kSmallDeg; ++i) {
-                        if (i < d && L.inB[pp[i]]) {
-                            S += ww[i];
+                    for (int t = 0; t < kSmallDeg; ++t) {
+                        if (t < d && L.inB[pp[t]]) {
+                            S += ww[t];
                             bool first = true;
 #pragma unroll
-                            for (int j = 0; j < kSmallDeg; ++j)
-                                if (j < i && pp[j] == pp[i]) first = false;
+                            for (int u = 0; u < kSmallDeg; ++u)
+                                if (u < t && pp[u] == pp[t]) first = false;
                             c += first ? 1 : 0;
                         }
                     }
@@ -655,39 +942,37 @@ __global__ void __launch_bounds__(kTB) k_rb_cand_small(Level L) {
                 }
                 key = a * kSlots + slot_of(loss);
                 wv = g.vw[v];
-                cand = true;
-                L.prio[v] = loss;
-            } else {
-                L.prio[v] = kNoneGain;
+                if (L.rbloss) L.rbloss[v] = loss;
+                L.key[v] = key;
             }
-            L.key[v] = key;
         }
+        sb.add(L, key, wv);
+        bapp.add(big, v);
+        bapp.flush(&ctl->nWb, L.listWb, false);
     }
-    bucket_add(L, key, wv);
-    int c = warp_sum_i32(cand ? 1 : 0);
-    if (lane_id() == 0 && c) atomicAdd(reinterpret_cast<unsigned long long *>(&ctl->ncand), (unsigned long long)c);
-    int dx = warp_sum_i32(cand ? (int)(ld_xadj(g.xadj, (int64_t)v + 1) - ld_xadj(g.xadj, v)) : 0);
-    if (lane_id() == 0 && dx) atomicAdd(reinterpret_cast<unsigned long long *>(&ctl->degx), (unsigned long long)dx);
+    bapp.flush(&ctl->nWb, L.listWb, true);
+    sb.flush(L);
+    flush_counter(&ctl->degexam, degrows, red);
 }
 
+// Listed candidates with long rows: one warp per vertex.
 template <bool EW, bool STRONG>
 __global__ void __launch_bounds__(kTB) k_rb_cand_big(Level L) {
     extern __shared__ int32_t tabs[];
+    Ctl *ctl = L.ctl;
+    const int32_t nWb = ctl->nWb;
     const int warps = blockDim.x >> 5;
+    if ((int64_t)blockIdx.x * warps >= nWb) return;
     int32_t *tab = tabs + (threadIdx.x >> 5) * L.k;
     for (int i = threadIdx.x; i < warps * L.k; i += blockDim.x) tabs[i] = 0;
     __syncthreads();
-    Ctl *ctl = L.ctl;
     const int32_t it = ctl->it;
     const DGraph g = L.g;
     const unsigned lane = lane_id();
-    for (int64_t w = (int64_t)blockIdx.x * warps + (threadIdx.x >> 5); w < L.nbig; w += (int64_t)gridDim.x * warps) {
-        int32_t v = L.bigv[w];
-        int32_t ps = L.part[v], a;
-        if (!rb_eligible(L, v, ps, a)) {
-            if (lane == 0) { L.key[v] = -1; L.prio[v] = kNoneGain; }
-            continue;
-        }
+    for (int64_t w = (int64_t)blockIdx.x * warps + (threadIdx.x >> 5); w < nWb; w += (int64_t)gridDim.x * warps) {
+        int32_t v = L.listWb[w];
+        int32_t ps = L.part[v];
+        int32_t a = L.aidx[ps];
         int64_t beg = ld_xadj(g.xadj, v), end = ld_xadj(g.xadj, (int64_t)v + 1);
         for (int64_t j = beg + lane; j < end; j += 32)
             atomicAdd(&tab[__ldg(L.part + __ldg(g.adj + j))], edge_w<EW>(g, j));
@@ -726,10 +1011,9 @@ __global__ void __launch_bounds__(kTB) k_rb_cand_big(Level L) {
         int32_t key = a * kSlots + slot_of(loss);
         if (lane == 0) {
             L.key[v] = key;
-            L.prio[v] = loss;
+            if (L.rbloss) L.rbloss[v] = loss;
             atomic_add_i64(&L.bucketw[key], (long long)g.vw[v]);
-            atomicAdd(reinterpret_cast<unsigned long long *>(&ctl->ncand), 1ull);
-            atomic_add_i64(&ctl->degx, end - beg);
+            atomic_add_i64(&ctl->degexam, end - beg);
         }
     }
 }
@@ -738,20 +1022,39 @@ __global__ void __launch_bounds__(kTB) k_rb_cand_big(Level L) {
 // where the weight taken so far reaches the excess (Alg. 5 scan: a candidate
 // is taken while the weight before it is below w_p - L), and the weight still
 // to take inside s*.  s* = kSlots means every candidate is taken.
-__global__ void __launch_bounds__(1024) k_rb_plan(Level L) {
+__global__ void __launch_bounds__(kTB) k_rb_plan(Level L) {
     const Ctl *ctl = L.ctl;
-    int32_t nA = ctl->nA;
-    for (int a = threadIdx.x; a < nA; a += blockDim.x) {
-        long long before = 0, ex = L.excess[a];
-        int32_t ss = kSlots;
-        long long need = 0;
-        for (int s = 0; s < kSlots; ++s) {
-            long long t = L.bucketw[a * kSlots + s];
-            if (ss == kSlots && before + t >= ex) { ss = s; need = ex - before; }
-            before += t;
+    const int32_t nA = ctl->nA;
+    const int warps = blockDim.x >> 5;
+    const unsigned lane = lane_id();
+    for (int a = blockIdx.x * warps + (threadIdx.x >> 5); a < nA; a += gridDim.x * warps) {
+        // slots 0..31 on the lanes, slot 32 separately
+        long long t = L.bucketw[a * kSlots + lane];
+        long long t32 = L.bucketw[a * kSlots + 32];
+        long long x = t;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            long long y = __shfl_up_sync(0xffffffffu, x, o);
+            if ((int)lane >= o) x += y;
         }
-        L.sstar[a] = ss;
-        L.need[a] = need;
+        long long ex = L.excess[a];
+        unsigned m = __ballot_sync(0xffffffffu, x >= ex);
+        long long tot31 = __shfl_sync(0xffffffffu, x, 31);
+        int32_t ss;
+        long long need;
+        if (m) {
+            int s0 = __ffs(m) - 1;
+            long long before = __shfl_sync(0xffffffffu, x - t, s0);
+            ss = s0;
+            need = ex - before;
+        } else if (tot31 + t32 >= ex) {
+            ss = 32;
+            need = ex - tot31;
+        } else {
+            ss = kSlots;
+            need = 0;
+        }
+        if (lane == 0) { L.sstar[a] = ss; L.need[a] = need; }
     }
 }
 
@@ -777,24 +1080,32 @@ __global__ void __launch_bounds__(kTB) k_rb_tilehist(Level L) {
     for (int i = threadIdx.x; i < nA; i += blockDim.x) L.tilehist[(int64_t)blockIdx.x * nA + i] = h[i];
 }
 
-// Exclusive scan of each part's tile sums over the tiles (one warp per part).
-__global__ void __launch_bounds__(kTB) k_rb_tilescan(Level L) {
+// Exclusive scan of each part's tile sums over the tiles (one block per part,
+// eight consecutive tiles per thread).
+__global__ void __launch_bounds__(1024) k_rb_tilescan(Level L) {
+    __shared__ long long sh[40];
     const int32_t nA = L.ctl->nA;
-    const int warps = blockDim.x >> 5;
-    const unsigned lane = lane_id();
-    for (int a = blockIdx.x * warps + (threadIdx.x >> 5); a < nA; a += gridDim.x * warps) {
+    const int64_t nt = L.ntiles;
+    constexpr int kItems = 8;
+    for (int a = blockIdx.x; a < nA; a += gridDim.x) {
         long long carry = 0;
-        for (int64_t t0 = 0; t0 < L.ntiles; t0 += 32) {
-            int64_t t = t0 + lane;
-            long long x = t < L.ntiles ? L.tilehist[t * nA + a] : 0;
-            long long y = x;
+        for (int64_t t0 = 0; t0 < nt; t0 += (int64_t)blockDim.x * kItems) {
+            int64_t tb = t0 + (int64_t)threadIdx.x * kItems;
+            long long x[kItems];
+            long long s = 0;
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                long long z = __shfl_up_sync(0xffffffffu, y, o);
-                if ((int)lane >= o) y += z;
+            for (int i = 0; i < kItems; ++i) {
+                x[i] = tb + i < nt ? L.tilehist[(tb + i) * nA + a] : 0;
+                s += x[i];
             }
-            if (t < L.ntiles) L.tilehist[t * nA + a] = (int32_t)(carry + y - x);
-            carry += __shfl_sync(0xffffffffu, y, 31);
+            long long tot = 0;
+            long long pre = carry + block_exscan_i64(s, sh, &tot);
+#pragma unroll
+            for (int i = 0; i < kItems; ++i) {
+                if (tb + i < nt) L.tilehist[(tb + i) * nA + a] = (int32_t)pre;
+                pre += x[i];
+            }
+            carry += tot;
         }
     }
 }
@@ -813,16 +1124,23 @@ __global__ void __launch_bounds__(kTB) k_rb_take(Level L) {
     const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
     const unsigned lt_mask = (1u << lane) - 1u;
     long long tile_taken = 0;
+    JET_BLOCK_APPENDER(mapp, kRbTile + kTB);
     for (int r = 0; r < kRbTile / kTB; ++r) {
         int64_t vv = tile * kRbTile + r * kTB + threadIdx.x;
         int32_t kv = -1, a = 0, s = 0;
         if (vv < L.g.n) kv = L.key[vv];
+        if (!__syncthreads_or(kv >= 0)) {          // no candidate in this slice
+            if constexpr (STRONG) { if (vv < L.g.n) L.etaken[vv] = 0; }
+            continue;
+        }
         if (kv >= 0) { a = kv / kSlots; s = kv - a * kSlots; }
         int32_t ss = kv >= 0 ? L.sstar[a] : 0;
         bool member = kv >= 0 && s == ss;
         long long w = (kv >= 0) ? (long long)L.g.vw[vv] : 0;
         long long mine = 0;
-        for (unsigned wi = 0; wi < (blockDim.x >> 5); ++wi) {
+        // ordered prefix over the boundary-slot members only where there are some
+        const unsigned nphase = __syncthreads_or(member) ? (blockDim.x >> 5) : 0u;
+        for (unsigned wi = 0; wi < nphase; ++wi) {
             if (warp == wi) {
                 int32_t grp = member ? a : -(int32_t)lane - 1;
                 unsigned peers = __match_any_sync(0xffffffffu, grp);
@@ -843,8 +1161,7 @@ __global__ void __launch_bounds__(kTB) k_rb_take(Level L) {
         if constexpr (!STRONG) {
             if (taken) L.mstamp[vv] = it;
             bool big = taken && is_big_row(L.g, (int32_t)vv);
-            int slot = warp_append(&ctl->nM, taken && !big);
-            if (taken && !big) L.listM[slot] = (int32_t)vv;
+            mapp.add(taken && !big, (int32_t)vv);
             if (big) L.listMb[atomicAdd(&ctl->nMb, 1)] = (int32_t)vv;
         } else {
             if (vv < L.g.n) L.etaken[vv] = taken ? w : 0;
@@ -855,6 +1172,8 @@ __global__ void __launch_bounds__(kTB) k_rb_take(Level L) {
         __shared__ long long red[40];
         tile_taken = block_sum_i64(tile_taken, red);
         if (threadIdx.x == 0) L.tiletaken[tile] = tile_taken;
+    } else {
+        mapp.flush(&ctl->nM, L.listM, true);
     }
 }
 
@@ -892,6 +1211,7 @@ __global__ void __launch_bounds__(kTB) k_rb_cookie(Level L) {
     }
     long long pre = block_exscan_i64(s, sh, nullptr) + L.tiletaken[tile];
     const long long total2 = 2 * L.capC[nB];
+    JET_BLOCK_APPENDER(mapp, kRbTile + kTB);
 #pragma unroll
     for (int i = 0; i < kItems; ++i) {
         int64_t v = v0 + i;
@@ -911,10 +1231,10 @@ __global__ void __launch_bounds__(kTB) k_rb_cookie(Level L) {
         bool mv = dest >= 0;
         if (mv) { L.nxt[v] = dest; L.mstamp[v] = it; }
         bool big = mv && is_big_row(L.g, (int32_t)v);
-        int slot = warp_append(&ctl->nM, mv && !big);
-        if (mv && !big) L.listM[slot] = (int32_t)v;
+        mapp.add(mv && !big, (int32_t)v);
         if (big) L.listMb[atomicAdd(&ctl->nMb, 1)] = (int32_t)v;
     }
+    mapp.flush(&ctl->nM, L.listM, true);
 }
 
 // ---------------------------------------------------------------------------
@@ -959,8 +1279,9 @@ int setup_level(Ctx &c, const DGraph &g, int32_t k, LevelBufs &B) {
     int64_t n = g.n;
     size_t nn = (size_t)std::max<int64_t>(n, 1);
     int32_t ntiles = (int32_t)std::max<int64_t>((n + kRbTile - 1) / kRbTile, 1);
-    // per-vertex int32 arrays: best, nxt, prio, mstamp, lstamp, key, listX, listXb, listM, listMb, bigv
-    const int nv32 = 11;
+    // per-vertex int32 arrays: best, nxt, prio, mstamp, lstamp, key, listX, listXb, listM, listMb, bigv,
+    // ext, wdeg, listW, listWb
+    const int nv32 = 15;
     size_t vbytes = nv32 * align256(nn * 4) + align256(nn * 8) /* etaken */;
     JET_TRY(dev_alloc(B.vert, vbytes, s));
     char *p = B.vert.as<char>();
@@ -969,6 +1290,11 @@ int setup_level(Ctx &c, const DGraph &g, int32_t k, LevelBufs &B) {
     L.best = take32(); L.nxt = take32(); L.prio = take32(); L.mstamp = take32(); L.lstamp = take32();
     L.key = take32(); L.listX = take32(); L.listXb = take32(); L.listM = take32(); L.listMb = take32();
     int32_t *bigv = take32();
+    L.ext = take32();
+    L.wdeg = take32();
+    L.listW = take32();
+    L.listWb = take32();
+    L.rbloss = nullptr;
     L.etaken = reinterpret_cast<int64_t *>(p);
     p += align256(nn * 8);
     // per-part and control
@@ -1017,7 +1343,7 @@ int setup_level(Ctx &c, const DGraph &g, int32_t k, LevelBufs &B) {
     return JET_OK;
 }
 
-int list_grid() { return num_sms() * 8; }
+int list_grid() { return num_sms() * 4; }
 
 size_t table_smem(int32_t k) { return (size_t)(kTB / 32) * (size_t)k * sizeof(int32_t); }
 
@@ -1026,11 +1352,13 @@ size_t table_smem(int32_t k) { return (size_t)(kTB / 32) * (size_t)k * sizeof(in
 int enqueue_lp_select(const Level &L, cudaStream_t s, LpExport ex, int *nk) {
     int n = L.g.n;
     bool ew = L.g.ew != nullptr;
-    if (ew) k_lp_select_small<true><<<grid_for(n, kTB), kTB, 0, s>>>(L, ex);
-    else k_lp_select_small<false><<<grid_for(n, kTB), kTB, 0, s>>>(L, ex);
-    *nk = 1;
+    int lg = list_grid();
+    k_lp_scan<<<std::min(lg, grid_for((n + 3) / 4, kTB)), kTB, 0, s>>>(L);
+    if (ew) k_lp_select_list<true><<<lg, kTB, 0, s>>>(L, ex);
+    else k_lp_select_list<false><<<lg, kTB, 0, s>>>(L, ex);
+    *nk = 2;
     if (L.nbig > 0) {
-        int gb = std::min(list_grid(), grid_for(L.nbig, kTB / 32));
+        int gb = std::min(lg, grid_for(L.nbig, kTB / 32));
         if (ew) k_lp_select_big<true><<<gb, kTB, table_smem(L.k), s>>>(L, ex);
         else k_lp_select_big<false><<<gb, kTB, table_smem(L.k), s>>>(L, ex);
         *nk += 1;
@@ -1070,18 +1398,19 @@ int enqueue_rb_t(const Level &L, cudaStream_t s, int *nk) {
     int n = L.g.n;
     int lg = list_grid();
     bool ew = L.g.ew != nullptr;
-    if (ew) k_rb_cand_small<true, STRONG><<<grid_for(n, kTB), kTB, 0, s>>>(L);
-    else k_rb_cand_small<false, STRONG><<<grid_for(n, kTB), kTB, 0, s>>>(L);
-    *nk = 1;
+    k_rb_scan<STRONG><<<std::min(lg, grid_for((n + 3) / 4, kTB)), kTB, 0, s>>>(L);
+    if (ew) k_rb_cand_list<true, STRONG><<<lg, kTB, 0, s>>>(L);
+    else k_rb_cand_list<false, STRONG><<<lg, kTB, 0, s>>>(L);
+    *nk = 2;
     if (L.nbig > 0) {
         int gb = std::min(lg, grid_for(L.nbig, kTB / 32));
         if (ew) k_rb_cand_big<true, STRONG><<<gb, kTB, table_smem(L.k), s>>>(L);
         else k_rb_cand_big<false, STRONG><<<gb, kTB, table_smem(L.k), s>>>(L);
         *nk += 1;
     }
-    k_rb_plan<<<1, 1024, 0, s>>>(L);
+    k_rb_plan<<<std::max(1, (L.k + 7) / 8), kTB, 0, s>>>(L);
     k_rb_tilehist<<<L.ntiles, kTB, (size_t)L.k * 4, s>>>(L);
-    k_rb_tilescan<<<std::max(1, std::min(lg, (L.k + 7) / 8)), kTB, 0, s>>>(L);
+    k_rb_tilescan<<<L.k, 1024, 0, s>>>(L);
     k_rb_take<STRONG><<<L.ntiles, kTB, (size_t)L.k * 8, s>>>(L);
     *nk += 4;
     if (STRONG) {
@@ -1131,8 +1460,8 @@ int enqueue_init(Ctx &c, LevelBufs &B, int64_t L_lim, int64_t opt, int64_t sigma
     JET_CUDA_TRY(cudaMemcpyAsync(&L.ctl->L, consts, sizeof(consts), cudaMemcpyHostToDevice, s));
     if (n > 0) {
         int gcut = std::min(list_grid(), grid_for(n, kTB));
-        if (L.g.ew) k_cut_pw<true><<<gcut, kTB, (size_t)L.k * 8, s>>>(L.g, L.k, L.part, L.pw, B.cut2);
-        else k_cut_pw<false><<<gcut, kTB, (size_t)L.k * 8, s>>>(L.g, L.k, L.part, L.pw, B.cut2);
+        if (L.g.ew) k_cut_pw<true><<<gcut, kTB, (size_t)L.k * 8, s>>>(L.g, L.k, L.part, L.pw, B.cut2, L.ext, L.wdeg);
+        else k_cut_pw<false><<<gcut, kTB, (size_t)L.k * 8, s>>>(L.g, L.k, L.part, L.pw, B.cut2, L.ext, L.wdeg);
         c.launches += 1;
     }
     k_ctl_init<<<1, 1024, 0, s>>>(L, B.cut2);
@@ -1313,30 +1642,30 @@ static void fill_level_params(Ctx &c, Level &L, int32_t is_finest, uint64_t seed
 }
 
 // Algorithmic DRAM bytes of each pass, from the per-iteration trace (neighbour
-// gathers of part/prio/nxt are taken as cache hits; beta = bytes per CSR
-// entry: 8 with edge weights, 4 without):
-//   Jetlp select   16 n + 4 (n - |R|) + beta (nnz - deg R) + 8 |X|
-//                  (xadj, lock stamp, priority write; part and row of every
-//                   unlocked vertex; P_d and list entry of X)
-//   afterburner    20 |X| + beta deg X + 8 |M|
-//   rebalance      32 n + 12 c + beta deg C (+ 16 n for Jetrs)  (C: candidates)
+// gathers and scatters of part/prio/nxt/ext are taken as cache hits; beta =
+// bytes per CSR entry: 8 with edge weights, 4 without; "boundary" = ext > 0):
+//   Jetlp select   4 n + 4 nb + 28 w + beta deg(W) + 12 |X|
+//                  (ext of every vertex, lock stamp of the nb boundary
+//                   vertices; for the w listed ones: list write and read,
+//                   xadj pair, part, row; priority, P_d and list entry of X)
+//   afterburner    20 |X| + beta deg X + 8 |M|, plus 8 |X| to clear priorities
+//   rebalance      24 n + 16 c + 32 r + beta deg(R) (+ 16 n for Jetrs)
+//                  (part and key of every vertex, tile passes; ext, vwgt,
+//                   weighted degree or destination of the c candidates; list,
+//                   xadj pair, part, key, destination and row of the r listed)
 //   apply+commit   36 |M| + beta deg M + 16 k
-// R = M of the previous Jetlp (locks), deg S = total row length over S.
 static void byte_model(const std::vector<TraceRec> &tr, const DGraph &g, int32_t k, uint32_t abl, LevelReport &rep) {
-    int64_t n = g.n, nnz = g.nnz, beta = g.ew ? 8 : 4;
-    bool locks = !(abl & (ABL_NO_LOCKS | ABL_BASELINE_LP));
+    int64_t n = g.n, beta = g.ew ? 8 : 4;
     bool ab = !(abl & (ABL_NO_AFTERBURN | ABL_BASELINE_LP));
-    int64_t rn = 0, rdeg = 0;
     for (const TraceRec &r : tr) {
         int64_t b = 36 * r.nm + beta * r.degm + 16 * (int64_t)k;
         if (r.kind == MODE_LP) {
-            int64_t sel = 16 * n + 4 * (n - rn) + beta * (nnz - rdeg) + 8 * r.nx;
+            int64_t sel = 4 * n + 4 * r.nbnd + 28 * r.nexam + beta * r.degexam + 12 * r.nx;
             rep.sel_bytes += sel;
             rep.sel_launches += 1;
-            b += sel + (ab ? 20 * r.nx + beta * r.degx : 0) + 8 * r.nm;
-            if (locks) { rn = r.nm; rdeg = r.degm; }
+            b += sel + (ab ? 20 * r.nx + beta * r.degx : 0) + 8 * r.nm + 8 * r.nx;
         } else {
-            b += 32 * n + 12 * r.nx + beta * r.degx + (r.kind == MODE_RS ? 16 * n : 0);
+            b += 24 * n + 16 * r.nx + 32 * r.nbnd + beta * r.degexam + (r.kind == MODE_RS ? 16 * n : 0);
         }
         rep.bytes_model += b;
     }
@@ -1401,6 +1730,7 @@ __global__ void k_set_epoch(Ctl *ctl, int32_t epoch, int32_t mode) {
     ctl->lp_epoch = epoch;
     ctl->mode = mode;
     ctl->it = 0;
+    ctl->nW = ctl->nWb = 0;
     ctl->nX = ctl->nXb = ctl->nM = ctl->nMb = 0;
     ctl->ncand = 0;
 }
@@ -1424,6 +1754,11 @@ int lp_pass(Ctx &c, const DGraph &g, int32_t k, const int32_t *part, const uint8
     fill_level_params(c, L, 1, 0);
     L.cq16 = (int32_t)llround(cval * 65536.0);
     L.abl = flags & (ABL_NO_LOCKS | ABL_NO_AFTERBURN | ABL_WEAK_AFTERBURN | ABL_BASELINE_LP);
+    {
+        int gcut = std::min(list_grid(), grid_for(g.n, kTB));
+        if (g.ew) k_cut_pw<true><<<gcut, kTB, (size_t)k * 8, s>>>(g, k, L.part, L.pw, B.cut2, L.ext, nullptr);
+        else k_cut_pw<false><<<gcut, kTB, (size_t)k * 8, s>>>(g, k, L.part, L.pw, B.cut2, L.ext, nullptr);
+    }
     k_locks_from_mask<<<grid_for(g.n, kTB, 4096), kTB, 0, s>>>(locked, L.lstamp, g.n);
     k_set_epoch<<<1, 1, 0, s>>>(L.ctl, 0, MODE_LP);
     DevBuf tmp_pd, tmp_gain;
@@ -1435,6 +1770,9 @@ int lp_pass(Ctx &c, const DGraph &g, int32_t k, const int32_t *part, const uint8
         if (!ex.gain) ex.gain = tmp_gain.as<int32_t>();
     }
     if (f2_out) JET_CUDA_TRY(cudaMemsetAsync(f2_out, 0, (size_t)g.n * 4, s));
+    // the select writes P_d and F only for the vertices it examines
+    JET_CUDA_TRY(cudaMemcpyAsync(ex.pd, part, (size_t)g.n * 4, cudaMemcpyDeviceToDevice, s));
+    k_fill_i32<<<grid_for(g.n, kTB, 4096), kTB, 0, s>>>(ex.gain, g.n, kNoneGain);
     int nk = 0;
     JET_TRY(enqueue_lp(L, s, &nk, ex));
     k_export_lp<<<grid_for(g.n, kTB, 4096), kTB, 0, s>>>(L, inx_out, inm_out);
@@ -1447,7 +1785,7 @@ __global__ void k_export_rb(Level L, int32_t *dest, int32_t *loss) {
     const int32_t it = L.ctl->it;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < L.g.n; v += (int64_t)gridDim.x * blockDim.x) {
         if (dest) dest[v] = L.mstamp[v] == it ? L.nxt[v] : -1;
-        if (loss) loss[v] = L.key[v] >= 0 ? L.prio[v] : kNoneGain;
+        if (loss && L.key[v] < 0) loss[v] = kNoneGain;
     }
 }
 
@@ -1457,6 +1795,7 @@ __global__ void __launch_bounds__(1024) k_rb_pass_init(Level L, const int64_t *c
     if (threadIdx.x == 0) {
         ctl->cut = *cut2 / 2;
         ctl->it = 0; ctl->mode = mode;
+        ctl->nW = ctl->nWb = 0;
         ctl->nX = ctl->nXb = ctl->nM = ctl->nMb = 0;
         ctl->ncand = 0;
     }
@@ -1488,8 +1827,9 @@ int rebalance_pass(Ctx &c, const DGraph &g, int32_t k, double eps, int32_t stron
     int64_t consts[3] = {L_lim, opt, sigma};
     JET_CUDA_TRY(cudaMemcpyAsync(&L.ctl->L, consts, sizeof(consts), cudaMemcpyHostToDevice, s));
     int gcut = std::min(list_grid(), grid_for(g.n, kTB));
-    if (g.ew) k_cut_pw<true><<<gcut, kTB, (size_t)k * 8, s>>>(g, k, L.part, L.pw, B.cut2);
-    else k_cut_pw<false><<<gcut, kTB, (size_t)k * 8, s>>>(g, k, L.part, L.pw, B.cut2);
+    if (g.ew) k_cut_pw<true><<<gcut, kTB, (size_t)k * 8, s>>>(g, k, L.part, L.pw, B.cut2, L.ext, L.wdeg);
+    else k_cut_pw<false><<<gcut, kTB, (size_t)k * 8, s>>>(g, k, L.part, L.pw, B.cut2, L.ext, L.wdeg);
+    L.rbloss = loss_out;
     k_rb_pass_init<<<1, 1024, 0, s>>>(L, B.cut2, strong ? MODE_RS : MODE_RW);
     // the pass API takes the iteration index as a parameter: set ctl->it
     JET_CUDA_TRY(cudaMemcpyAsync(&L.ctl->it, &iter, 4, cudaMemcpyHostToDevice, s));
@@ -1516,8 +1856,8 @@ int cut_and_weights(Ctx &c, const DGraph &g, int32_t k, const int32_t *part, int
     JET_CUDA_TRY(cudaMemsetAsync(pw, 0, (size_t)k * 8, s));
     if (g.n > 0) {
         int gcut = std::min(list_grid(), grid_for(g.n, kTB));
-        if (g.ew) k_cut_pw<true><<<gcut, kTB, (size_t)k * 8, s>>>(g, k, part, pw, cut2);
-        else k_cut_pw<false><<<gcut, kTB, (size_t)k * 8, s>>>(g, k, part, pw, cut2);
+        if (g.ew) k_cut_pw<true><<<gcut, kTB, (size_t)k * 8, s>>>(g, k, part, pw, cut2, nullptr, nullptr);
+        else k_cut_pw<false><<<gcut, kTB, (size_t)k * 8, s>>>(g, k, part, pw, cut2, nullptr, nullptr);
     }
     JET_CUDA_TRY(cudaGetLastError());
     JET_CUDA_TRY(cudaMemcpyAsync(c.pinned, cut2, 8, cudaMemcpyDeviceToHost, s));
@@ -1546,9 +1886,16 @@ int lp_pass_in_scratch(Ctx &c, const DGraph &g, int32_t k, const int32_t *part, 
     L.listX = take32(); L.listXb = take32(); L.listM = take32(); L.listMb = take32();
     int32_t *bigv = take32();
     int32_t *tmp_pd = take32(), *tmp_gain = take32();
+    L.ext = take32();
+    L.listW = take32();
+    L.listWb = take32();
     L.ctl = reinterpret_cast<Ctl *>(p);
     p += align256c(sizeof(Ctl));
     int32_t *nbig_dev = reinterpret_cast<int32_t *>(p);
+    p += 256;
+    L.pw = reinterpret_cast<int64_t *>(p);
+    p += align256c((size_t)JET_MAX_K * 8);
+    int64_t *cut2 = reinterpret_cast<int64_t *>(p);
     L.bigv = bigv;
     fill_level_params(c, L, 1, 0);
     L.cq16 = (int32_t)llround(cval * 65536.0);
@@ -1556,6 +1903,13 @@ int lp_pass_in_scratch(Ctx &c, const DGraph &g, int32_t k, const int32_t *part, 
     // the array keeps the previous call's contents: clear what must start at zero
     JET_CUDA_TRY(cudaMemsetAsync(L.ctl, 0, sizeof(Ctl), s));
     JET_CUDA_TRY(cudaMemsetAsync(nbig_dev, 0, 16, s));
+    JET_CUDA_TRY(cudaMemsetAsync(L.pw, 0, (size_t)k * 8, s));
+    JET_CUDA_TRY(cudaMemsetAsync(cut2, 0, 16, s));
+    {
+        int gcut = std::min(list_grid(), grid_for(g.n, kTB));
+        if (g.ew) k_cut_pw<true><<<gcut, kTB, (size_t)k * 8, s>>>(g, k, L.part, L.pw, cut2, L.ext, nullptr);
+        else k_cut_pw<false><<<gcut, kTB, (size_t)k * 8, s>>>(g, k, L.part, L.pw, cut2, L.ext, nullptr);
+    }
     k_collect_big<<<grid_for(g.n, kTB), kTB, 0, s>>>(g, bigv, nbig_dev);
     k_fill_i32<<<grid_for(g.n, kTB, 4096), kTB, 0, s>>>(L.mstamp, g.n, -2);
     k_fill_i32<<<grid_for(g.n, kTB, 4096), kTB, 0, s>>>(L.prio, g.n, kNoneGain);
@@ -1567,6 +1921,8 @@ int lp_pass_in_scratch(Ctx &c, const DGraph &g, int32_t k, const int32_t *part, 
     L.nbig = (int32_t)(c.pinned[0] & 0xFFFFFFFF);
     LpExport ex{pd_out ? pd_out : tmp_pd, gain_out ? gain_out : tmp_gain, f2_out};
     if (f2_out) JET_CUDA_TRY(cudaMemsetAsync(f2_out, 0, nn * 4, s));
+    JET_CUDA_TRY(cudaMemcpyAsync(ex.pd, part, nn * 4, cudaMemcpyDeviceToDevice, s));
+    k_fill_i32<<<grid_for(g.n, kTB, 4096), kTB, 0, s>>>(ex.gain, g.n, kNoneGain);
     int nk = 0;
     JET_TRY(enqueue_lp(L, s, &nk, ex));
     k_export_lp<<<grid_for(g.n, kTB, 4096), kTB, 0, s>>>(L, inx_out, inm_out);
