@@ -52,6 +52,8 @@ def parse_args(argv=None):
     p.add_argument("--hostloop", action="store_true",
                    help="drive refinement iterations from the host (same kernels and launch configuration; "
                         "used for profiler launch lists)")
+    p.add_argument("--cluster-max-n", type=int, default=None,
+                   help="largest level refined by the one-cluster loop (library default if omitted; 0 = never)")
     p.add_argument("--kernel-probe", action="store_true",
                    help="run one profiled partition and report per-level select launches (profiler target)")
     return p.parse_args(argv)
@@ -265,7 +267,8 @@ def run_ours(args):
     vw = torch.from_numpy(g.vwgt).to(device)
     ew = torch.from_numpy(g.adjwgt).to(device)
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=device)
-    ctx = jet.Context(local, flags=jet.FLAG_HOSTLOOP if args.hostloop else 0)
+    copts = {} if args.cluster_max_n is None else {"cluster_max_n": args.cluster_max_n}
+    ctx = jet.Context(local, flags=jet.FLAG_HOSTLOOP if args.hostloop else 0, **copts)
     stream = torch.cuda.current_stream(device)
 
     def step():
@@ -355,7 +358,8 @@ def run_ours(args):
                        "refine_ms": round(st0.ms_refine, 3), "coarsen_ms": round(st0.ms_coarsen, 3),
                        "initpart_ms": round(st0.ms_init, 3), "finest_refine_ms": round(st0.ms_refine_finest, 3),
                        "edge_iters_per_step": st0.edge_iters, "bytes_model_per_step": st0.bytes_model,
-                       "ms_level": [round(x, 3) for x in st0.ms_level]},
+                       "ms_level": [round(x, 3) for x in st0.ms_level],
+                       "cluster_blocks": st0.cluster_blocks},
             "roofline": {"bound": "hbm", "kernel": ROOFLINE_KERNEL, "achieved": round(achieved, 1),
                          "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                          "frac": round(achieved / peak, 4) if peak else None,

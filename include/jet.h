@@ -79,11 +79,16 @@ extern "C" {
  *   max_no_improve = 12             iterations without a new best before stopping (Sec. 4)
  *   weak_limit = 2                  b_max Jetrw iterations before Jetrs (Sec. 4.2.2)
  *   coarsen_target = 0              stop coarsening at <= max(8k, 256) vertices (Sec. 3)
- *   max_levels = 64, max_iters_per_level = 10000 (safety caps), hem_rounds = 8 */
+ *   max_levels = 64, max_iters_per_level = 10000 (safety caps), hem_rounds = 8
+ * Execution choice (no counterpart in the paper; results do not depend on it):
+ *   cluster_max_n = 4096            levels with at most this many vertices run their whole
+ *                                   refinement loop in one thread-block-cluster launch; larger
+ *                                   levels use the CUDA-graph loop; 0 = never */
 typedef struct {
     double c_fine, c_coarse, phi;
     int32_t max_no_improve, weak_limit, coarsen_target, max_levels, max_iters_per_level, hem_rounds;
     uint32_t flags;
+    int32_t cluster_max_n;
 } jet_options;
 
 /* Per-call statistics (jet_partition / jet_uncoarsen).  Times are CUDA-event
@@ -104,6 +109,8 @@ typedef struct {
     int64_t sel_bytes[JET_MAX_LEVELS];     /* their algorithmic bytes, summed */
     float sel_ms[JET_MAX_LEVELS];          /* their CUDA-event time, summed (JET_FLAG_PROFILE only) */
     float ms_level[JET_MAX_LEVELS];        /* CUDA-event time of each level's projection + refinement */
+    int32_t cluster_blocks[JET_MAX_LEVELS]; /* blocks of the thread-block cluster that ran the level's
+                                               loop; 0 where the CUDA-graph or host loop ran it */
 } jet_stats;
 
 typedef struct jet_ctx jet_ctx;

@@ -46,7 +46,7 @@ class Options(ctypes.Structure):
                 ("max_no_improve", ctypes.c_int32), ("weak_limit", ctypes.c_int32),
                 ("coarsen_target", ctypes.c_int32), ("max_levels", ctypes.c_int32),
                 ("max_iters_per_level", ctypes.c_int32), ("hem_rounds", ctypes.c_int32),
-                ("flags", ctypes.c_uint32)]
+                ("flags", ctypes.c_uint32), ("cluster_max_n", ctypes.c_int32)]
 
     @classmethod
     def default(cls, **kw) -> "Options":
@@ -71,7 +71,8 @@ class _CStats(ctypes.Structure):
                 ("cut", ctypes.c_int64), ("max_part_w", ctypes.c_int64),
                 ("bytes_model", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
                 ("sel_launches", ctypes.c_int64 * L), ("sel_bytes", ctypes.c_int64 * L),
-                ("sel_ms", ctypes.c_float * L), ("ms_level", ctypes.c_float * L)]
+                ("sel_ms", ctypes.c_float * L), ("ms_level", ctypes.c_float * L),
+                ("cluster_blocks", ctypes.c_int32 * L)]
 
 
 @dataclass
@@ -98,6 +99,7 @@ class Stats:
     sel_bytes: list = field(default_factory=list)
     sel_ms: list = field(default_factory=list)
     ms_level: list = field(default_factory=list)
+    cluster_blocks: list = field(default_factory=list)
 
     @classmethod
     def from_c(cls, s: _CStats) -> "Stats":
@@ -106,7 +108,7 @@ class Stats:
                    list(s.iters_rs[:lv]), list(s.cut_level[:lv]), s.edge_iters, s.fin_edge_iters, s.ms_coarsen,
                    s.ms_init, s.ms_refine, s.ms_refine_finest, s.ms_total, s.cut, s.max_part_w, s.bytes_model,
                    s.kernel_launches, list(s.sel_launches[:lv]), list(s.sel_bytes[:lv]), list(s.sel_ms[:lv]),
-                   list(s.ms_level[:lv]))
+                   list(s.ms_level[:lv]), list(s.cluster_blocks[:lv]))
 
 
 _lib = None

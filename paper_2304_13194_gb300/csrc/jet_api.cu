@@ -255,6 +255,7 @@ static int uncoarsen(Ctx &c, const jet_hier *h, int32_t k, double eps, uint64_t 
             st->sel_launches[i] = rep.sel_launches;
             st->sel_bytes[i] = rep.sel_bytes;
             st->sel_ms[i] = rep.sel_ms;
+            st->cluster_blocks[i] = rep.cluster;
             st->bytes_model += rep.bytes_model;
             cudaEventRecord(lev[1], s);
             cudaEventSynchronize(lev[1]);
@@ -303,6 +304,7 @@ void jet_options_default(jet_options *o) {
     o->max_iters_per_level = 10000;
     o->hem_rounds = 8;
     o->flags = 0;
+    o->cluster_max_n = 4096;
 }
 
 int jet_ctx_create(int device, void *cuda_stream, const jet_options *opt, jet_ctx **out) {
@@ -313,7 +315,7 @@ int jet_ctx_create(int device, void *cuda_stream, const jet_options *opt, jet_ct
     if (opt) o = *opt;
     if (!(o.c_fine >= 0 && o.c_fine <= 1 && o.c_coarse >= 0 && o.c_coarse <= 1 && o.phi > 0 && o.phi <= 1) ||
         o.max_no_improve < 0 || o.weak_limit < 0 || o.coarsen_target < 0 || o.max_levels < 1 ||
-        o.max_iters_per_level < 0 || o.hem_rounds < 0 || o.hem_rounds > 64)
+        o.max_iters_per_level < 0 || o.hem_rounds < 0 || o.hem_rounds > 64 || o.cluster_max_n < 0)
         return JET_EINVAL;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess) { cudaGetLastError(); return JET_ECUDA; }

@@ -407,6 +407,7 @@ struct LevelReport {
     int32_t iters = 0, kinds[3] = {0, 0, 0};
     int64_t sel_launches = 0, sel_bytes = 0, bytes_model = 0;
     float sel_ms = 0.f;
+    int32_t cluster = 0;   // blocks of the cluster that ran the level loop (0: graph or host loop)
 };
 
 struct Ctx {

@@ -35,6 +35,22 @@ def ctx_hostloop():
     c.close()
 
 
+@pytest.fixture(scope="module")
+def ctx_cluster():
+    """Every level on the one-cluster loop."""
+    c = jet.Context(0, cluster_max_n=1 << 30)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def ctx_graph():
+    """Every level on the CUDA-graph loop (no thread-block-cluster loop)."""
+    c = jet.Context(0, cluster_max_n=0)
+    yield c
+    c.close()
+
+
 def _np(t):
     return t.cpu().numpy()
 
@@ -234,6 +250,38 @@ def test_refine_hostloop_equals_graph_loop(ctx, ctx_hostloop):
     assert all((ta[key] == tb[key]).all() for key in ("kind", "nx", "nm", "cut", "maxw"))
 
 
+@pytest.mark.parametrize("name,g,unit,k", [
+    ("grid3d_20_w", graphgen.grid3d(20, 20, 20, vw=(1, 4), ew=(1, 10), seed=9), False, 16),
+    ("rmat_s12", graphgen.rmat(12, seed=5), True, 64),                  # long rows: warp paths
+    ("gnp_700_dense", graphgen.gnp(700, 0.06, seed=4, ew=(1, 9)), False, 8),
+    ("rgg_30000", graphgen.rgg(30000, seed=3), True, 128),              # many 1024-vertex tiles
+])
+def test_refine_cluster_loop_equals_graph_loop(ctx_cluster, ctx_graph, name, g, unit, k):
+    vw, ew = _vw(g, unit), _ew(g, unit)
+    part0 = oracle.initial_partition(graphgen.Graph(g.n, g.xadj, g.adjncy, vw, None), k)
+    for is_finest in (True, False):
+        a = ctx_cluster.refine(g.xadj, g.adjncy, vw, ew, k, part0, seed=2, is_finest=is_finest)
+        ta = ctx_cluster.last_trace()
+        b = ctx_graph.refine(g.xadj, g.adjncy, vw, ew, k, part0, seed=2, is_finest=is_finest)
+        tb = ctx_graph.last_trace()
+        assert a[1] == b[1] and (_np(a[0]) == _np(b[0])).all()
+        assert ta["iters"] == tb["iters"]
+        assert all((ta[key] == tb[key]).all() for key in ("kind", "nx", "nm", "cut", "maxw"))
+
+
+def test_cluster_loop_is_used_on_small_levels(ctx, ctx_cluster, ctx_graph):
+    g = graphgen.grid3d(24, 24, 24, vw=(1, 4), ew=(1, 10), seed=1)
+    _, c1, st = ctx_cluster.partition(g.xadj, g.adjncy, g.vwgt, g.adjwgt, k=64, seed=1, return_stats=True)
+    assert all(b >= 2 for b in st.cluster_blocks)
+    _, c2, st2 = ctx_graph.partition(g.xadj, g.adjncy, g.vwgt, g.adjwgt, k=64, seed=1, return_stats=True)
+    assert all(b == 0 for b in st2.cluster_blocks)
+    assert st.kernel_launches < st2.kernel_launches and c1 == c2
+    # default threshold: only the small levels take the cluster loop
+    _, c3, st3 = ctx.partition(g.xadj, g.adjncy, g.vwgt, g.adjwgt, k=64, seed=1, return_stats=True)
+    limit = ctx.options.cluster_max_n
+    assert all((b > 0) == (nv <= limit) for b, nv in zip(st3.cluster_blocks, st3.n)) and c3 == c1
+
+
 # --------------------------------------------------------------------------
 # the whole pipeline (Alg. 1)
 # --------------------------------------------------------------------------
@@ -267,6 +315,11 @@ def test_partition_matches_oracle(ctx, name, g, unit, k):
 def test_partition_hostloop(ctx_hostloop):
     g = graphgen.grid3d(24, 24, 24, vw=(1, 4), ew=(1, 10), seed=1)
     _check_partition(ctx_hostloop, g, False, 64)
+
+
+@pytest.mark.parametrize("name,g,unit", graphs_small()[1:4], ids=[x[0] for x in graphs_small()[1:4]])
+def test_partition_graph_loop_matches_oracle(ctx_graph, name, g, unit):
+    _check_partition(ctx_graph, g, unit, 64, seed=3)
 
 
 def test_partition_host_entry_point(ctx):
