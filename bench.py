@@ -37,7 +37,7 @@ UNIT = "Medges/s"
 K_PARTS, EPS, SEED = 64, 0.03, 1
 WORKLOAD = "grid3d 128x128x128 (7-point), vwgt U[1,4], adjwgt U[1,10], k=64, eps=0.03, seed=1"
 FLUSH_BYTES = 512 << 20          # written between steps (L2 is 129 MB)
-ROOFLINE_KERNEL = "Jetlp select step: k_lp_scan + k_lp_select_list (finest level)"
+ROOFLINE_KERNEL = "Jetlp select step: k_lp_scan + k_lp_select (finest level)"
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "lp_select_grid3d_128_k64.txt")
 
 
@@ -371,6 +371,8 @@ def run_ours(args):
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
             "clocks": clocks,
+            "step_ms": [round(x, 3) for x in step_ms],
+            "refine_ms_steps": [round(s.ms_refine, 3) for s in stats],
         }
         print(json.dumps(out), flush=True)
     ctx.close()

@@ -224,7 +224,7 @@ int jet_rebalance_pass(jet_ctx *ctx, int32_t n, const int64_t *xadj, const int32
  * memory pool, a host framework that only lends memory it owns.  Arguments,
  * outputs and results are those of jet_lp_pass (the JET_FLAG_VALIDATE graph
  * check is not run).
- * Scratch: a fixed device array of about 14 MiB inside the library, sized for
+ * Scratch: a fixed device array of about 10 MiB inside the library, sized for
  * n <= JET_NOALLOC_MAX_N vertices; every GPU that loads the library holds it
  * until the process exits.  Larger n is rejected with JET_EINVAL (see
  * jet_last_error).  The first call on each device looks up the array's

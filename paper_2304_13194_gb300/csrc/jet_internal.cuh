@@ -111,9 +111,10 @@ struct Ctl {
     int32_t copy_best;   // set by the controller: P_best <- P_iter this iteration
     int32_t best_bal;
     int32_t nA, nB;      // rebalancing classes for the current iteration
-    int32_t nX, nXb;     // X list lengths (small / large rows)
-    int32_t nW, nWb;     // work lists of the current pass (boundary / candidate rows: short / long)
-    int32_t nM, nMb;     // M list lengths
+    int32_t nW;          // work list of the current pass (unlocked boundary vertices / listed candidates)
+    int32_t nX;          // X list length
+    int32_t nM;          // M list length
+    int32_t ticket;      // blocks of the current kernel that finished (last-block tails)
     int32_t hit_cap;     // stopped by max_iters
     int32_t pad0;
     int32_t kcount[4];   // iterations run per kind (Jetlp, Jetrw, Jetrs)
@@ -148,10 +149,9 @@ struct Level {
     int32_t *ext;            // neighbours in other parts (exact, kept by the apply kernel)
     int32_t *wdeg;           // weighted degree (rebalancing of interior vertices)
     int32_t *rbloss;         // rebalancing loss export (single-pass API only; may be null)
-    int32_t *listX, *listXb, *listM, *listMb;
-    int32_t *listW, *listWb;  // work lists: vertices whose rows a pass must read (short / long rows)
-    const int32_t *bigv;
-    int32_t nbig;
+    int32_t *listX, *listM;
+    int32_t *listW;          // work list: vertices whose rows a pass must read
+    int32_t nbig;            // vertices with rows longer than kSmallDeg (0: no per-warp tables needed)
     // per-part state
     int64_t *pw;
     int32_t *aidx, *Bs;
@@ -457,7 +457,7 @@ int lp_pass(Ctx &c, const DGraph &g, int32_t k, const int32_t *part, const uint8
 // allocation.  Used by jet_lp_pass_noalloc.
 constexpr size_t align256c(size_t x) { return (x + 255) & ~size_t(255); }
 constexpr size_t lp_scratch_bytes(int64_t n) {
-    return 14 * align256c((size_t)(n > 0 ? n : 1) * 4) + align256c(sizeof(Ctl)) + 256 +
+    return 10 * align256c((size_t)(n > 0 ? n : 1) * 4) + align256c(sizeof(Ctl)) + 256 +
            align256c((size_t)JET_MAX_K * 8) + 256;
 }
 int lp_pass_in_scratch(Ctx &c, const DGraph &g, int32_t k, const int32_t *part, const uint8_t *locked, double cval,

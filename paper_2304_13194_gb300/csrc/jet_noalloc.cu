@@ -18,7 +18,7 @@ constexpr size_t kNoallocCheckBytes = 256;
 constexpr size_t kNoallocCheckOffset = lp_scratch_bytes(JET_NOALLOC_MAX_N);
 constexpr size_t kNoallocBytes = kNoallocCheckOffset + kNoallocCheckBytes;
 
-// The whole scratch of jet_lp_pass_noalloc (about 14 MiB), shared by every
+// The whole scratch of jet_lp_pass_noalloc (about 10 MiB), shared by every
 // call on a device.  In host code this name is only a stand-in: the device
 // address comes from cudaGetSymbolAddress below.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];

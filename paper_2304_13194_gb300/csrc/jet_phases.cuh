@@ -10,17 +10,28 @@
 //  * No persistent vertex-part hash table (Sec. 4.3).  conn(v, .) is
 //    recomputed from the CSR row in registers (rows of <= 16 entries, one
 //    thread per vertex) or in a per-warp shared-memory table cleared as it
-//    is read (longer rows, one warp per vertex).
+//    is read (longer rows, one warp per vertex).  One list holds both kinds
+//    of rows: a block stages the long rows its threads meet and its warps
+//    take them afterwards, so a pass is one phase, not two.
 //  * ext[v] (neighbours in other parts) is kept exact by the apply phase, so
 //    passes list boundary vertices first and never stream interior rows.
+//  * The apply phase also commits the moves: nxt[v] packs the source and
+//    destination parts, so a neighbour's old part is known while part[] is
+//    being overwritten.
 //  * Lists are staged in shared memory and reserved with one atomic per
 //    block flush.
+//  * Serial end-of-phase work (the controller of Alg. 3, the rebalancing
+//    plan, the eviction scan of Jetrs) is a "tail" that one block runs once
+//    every block of the phase is done: the last block to finish in a kernel
+//    launch, block 0 after the barrier in the cluster loop.
 //  * Arrays that phases modify (part, prio, nxt, ext, stamps, lists) are read
 //    with ordinary loads, never through the non-coherent read-only path, so
 //    that the cluster-resident loop sees them after each cluster barrier.
 #pragma once
 
 #include "jet_internal.cuh"
+
+#include <cuda/atomic>
 
 namespace jet {
 
@@ -29,15 +40,35 @@ struct Grid {
     int nb;    // number of cooperating blocks
 };
 
-// Control values (counters, mode, part weights) written by other blocks
-// before the last kernel boundary or cluster barrier.  Plain loads: the
-// barrier's release/acquire order makes the writes visible, while volatile
-// (system-scope) loads cost about a microsecond each on a memory system that
-// is coherent with the host CPU.
-template <class T>
-__device__ __forceinline__ T vread(const T *p) { return *p; }
-
 __device__ __forceinline__ Grid launch_grid() { return Grid{(int)blockIdx.x, (int)gridDim.x}; }
+
+// The contiguous share [beg, end) of a list of `len` entries that block G.bid
+// takes (whole warps; every block gets one, so the warps of every block take
+// part in the long rows the list holds).
+struct Share {
+    int64_t beg, end;
+};
+__device__ __forceinline__ Share list_share(int64_t len, Grid G) {
+    int64_t seg = (len + G.nb - 1) / G.nb;
+    seg = (seg + 31) & ~int64_t(31);
+    int64_t b = (int64_t)G.bid * seg;
+    b = b < len ? b : len;
+    int64_t e = b + seg < len ? b + seg : len;
+    return Share{b, e};
+}
+
+// A value other blocks of the same kernel changed (atomics, stores before
+// their completion ticket): a device-scope load served by L2, never by a
+// stale L1 line.
+template <class T>
+__device__ __forceinline__ T ld_gpu(const T *p) {
+    return cuda::atomic_ref<T, cuda::thread_scope_device>(*const_cast<T *>(p)).load(cuda::memory_order_relaxed);
+}
+
+// nxt[v] = source part << 16 | destination part (k <= JET_MAX_K < 2^16).
+__device__ __forceinline__ int32_t nxt_pack(int32_t from, int32_t to) { return (int32_t)(((uint32_t)from << 16) | (uint32_t)to); }
+__device__ __forceinline__ int32_t nxt_to(int32_t x) { return x & 0xFFFF; }
+__device__ __forceinline__ int32_t nxt_from(int32_t x) { return (int32_t)((uint32_t)x >> 16); }
 
 struct LpExport {           // optional dense outputs of the single-pass API
     int32_t *pd;            // P_d (P_s where undefined)
@@ -75,10 +106,6 @@ __device__ __forceinline__ int32_t key_part(unsigned long long key) {
 }
 __device__ __forceinline__ int32_t key_conn(unsigned long long key) { return (int32_t)(key >> 32); }
 
-__device__ __forceinline__ bool is_big_row(const DGraph &g, int32_t v) {
-    return ld_xadj(g.xadj, (int64_t)v + 1) - ld_xadj(g.xadj, v) > kSmallDeg;
-}
-
 // Block-level sum of a counter, one atomic per block.
 __device__ __forceinline__ void flush_counter(int64_t *dst, long long v, long long *red) {
     v = block_sum_i64(v, red);
@@ -91,6 +118,25 @@ __device__ __forceinline__ void flush_counter(int64_t *dst, long long v, long lo
 __device__ __forceinline__ void disarm_loop(const Level &L, Grid G) {
     if (L.use_graph && G.bid == 0 && threadIdx.x == 0)
         cudaGraphSetConditional((cudaGraphConditionalHandle)L.h_loop, 0u);
+}
+
+// In a kernel launch: true in the last block to finish (all blocks call it
+// once, after their part of the phase).  Every thread fences its writes
+// before the block takes its ticket, so the last block sees all of them.
+// No block waits for another.
+__device__ __forceinline__ bool last_block(Ctl *ctl) {
+    __shared__ int s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int t = atomicAdd(&ctl->ticket, 1);
+        s_last = t == (int)gridDim.x - 1;
+        if (s_last) ctl->ticket = 0;   // for the next kernel that counts
+    }
+    __syncthreads();
+    bool last = s_last != 0;
+    if (last) __threadfence();
+    return last;
 }
 
 // Block-aggregated append into a global list: members are staged in shared
@@ -129,6 +175,21 @@ struct Appender {
             __syncthreads();
         }
     }
+    // Long rows staged for the block's warps: when another round could
+    // overflow the buffer (or with force), every warp takes staged rows in
+    // turn, `row(v)` being called by all 32 lanes.  All threads call it.
+    template <class Row>
+    __device__ __forceinline__ void drain(bool force, Row &&row) {
+        __syncthreads();
+        int c = *cnt;
+        if (c > 0 && (force || c > cap - (int)blockDim.x)) {
+            const int warps = blockDim.x >> 5;
+            for (int s = threadIdx.x >> 5; s < c; s += warps) row(buf[s]);
+            __syncthreads();
+            if (threadIdx.x == 0) *cnt = 0;
+            __syncthreads();
+        }
+    }
 };
 
 #define JET_APPENDER(name, bufptr, capacity)                    \
@@ -137,20 +198,37 @@ struct Appender {
     name.init()
 
 // ---------------------------------------------------------------------------
-// shared-memory arena per phase (bytes, for blocks of T threads)
+// shared-memory arena per phase (bytes, for blocks of T threads; `tables`:
+// the level has long rows, so the row phases need one k-entry table per warp)
 // ---------------------------------------------------------------------------
 constexpr int kScanCap = 4096;          // list staging of the scan phases
 constexpr int kListCap = 2048;          // X / M staging
-constexpr int kBigCap = 1024;           // long-row list staging
+constexpr int kBigCap = 1024;           // long-row staging
 constexpr int kSmemBuckets = 1024;      // slot buckets aggregated per block when nA * kSlots fits
 
-__host__ __device__ constexpr size_t arena_table(int32_t k, int T) { return (size_t)(T / 32) * (size_t)k * 4; }
+__host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 __host__ __device__ constexpr size_t arena_max(size_t a, size_t b) { return a > b ? a : b; }
+__host__ __device__ constexpr size_t arena_tables(int32_t k, int T, bool tables) {
+    return tables ? (size_t)(T / 32) * (size_t)k * 4 : 0;
+}
+__host__ __device__ constexpr size_t sm_lp_scan() { return (size_t)kScanCap * 4; }
+__host__ __device__ constexpr size_t sm_lp_select(int32_t k, int T, bool tables) {
+    return (size_t)(kListCap + kBigCap) * 4 + arena_tables(k, T, tables);
+}
+__host__ __device__ constexpr size_t sm_afterburn() { return (size_t)(kListCap + kBigCap) * 4; }
+__host__ __device__ constexpr size_t sm_apply(int32_t k) { return align16((size_t)k * 8) + (size_t)kBigCap * 4; }
+__host__ __device__ constexpr size_t sm_rb_scan() { return (size_t)kSmemBuckets * 8 + (size_t)kScanCap * 4; }
+__host__ __device__ constexpr size_t sm_rb_cand(int32_t k, int T, bool tables) {
+    return (size_t)kSmemBuckets * 8 + (size_t)kBigCap * 4 + arena_tables(k, T, tables);
+}
+__host__ __device__ constexpr size_t sm_rb_tilehist(int32_t k) { return (size_t)k * 4; }
+__host__ __device__ constexpr size_t sm_rb_take(int32_t k, int T) { return align16((size_t)k * 8) + (size_t)2 * T * 4; }
+__host__ __device__ constexpr size_t sm_rb_cookie(int T) { return (size_t)2 * T * 4; }
 // the largest arena any phase needs
 __host__ __device__ constexpr size_t arena_bytes(int32_t k, int T) {
-    return arena_max(arena_max(arena_max((size_t)kScanCap * 4, (size_t)(kListCap + kBigCap) * 4),
-                               arena_max((size_t)kSmemBuckets * 8 + (size_t)kScanCap * 4, arena_table(k, T))),
-                     arena_max((((size_t)k * 8 + 15) & ~size_t(15)) + (size_t)2 * T * 4, (size_t)k * 8));
+    return arena_max(arena_max(arena_max(sm_lp_scan(), sm_lp_select(k, T, true)), arena_max(sm_afterburn(), sm_apply(k))),
+                     arena_max(arena_max(sm_rb_scan(), sm_rb_cand(k, T, true)),
+                               arena_max(sm_rb_tilehist(k), arena_max(sm_rb_take(k, T), sm_rb_cookie(T)))));
 }
 
 // ---------------------------------------------------------------------------
@@ -159,7 +237,7 @@ __host__ __device__ constexpr size_t arena_bytes(int32_t k, int T) {
 __device__ inline long long block_max_pw(const int64_t *pw, int32_t k, long long *sh) {
     long long m = 0;
     for (int i = threadIdx.x; i < k; i += blockDim.x) {
-        long long w = vread(&pw[i]);
+        long long w = ld_gpu(&pw[i]);
         m = w > m ? w : m;
     }
 #pragma unroll
@@ -196,7 +274,7 @@ __device__ inline void compute_classes(const Level &L, long long *sh) {
         bool inA = false, inB = false;
         long long w = 0;
         if (p < L.k) {
-            w = vread(&L.pw[p]);
+            w = ld_gpu(&L.pw[p]);
             inA = w > ctl->L;
             inB = w <= ctl->sigma;
         }
@@ -226,23 +304,43 @@ __device__ inline void compute_classes(const Level &L, long long *sh) {
 
 // Mode of the next iteration (Alg. 3): balanced -> Jetlp; else Jetrw while the
 // weak counter is below b_max, else Jetrs; DONE by the stop rule or the cap.
-__device__ inline int32_t choose_mode(const Level &L, bool balanced) {
-    Ctl *ctl = L.ctl;
-    if (ctl->noimp >= L.max_no_improve) return MODE_DONE;
-    if (ctl->it >= L.max_iters) { ctl->hit_cap = 1; return MODE_DONE; }
-    if (balanced) { ctl->weak = 0; return MODE_LP; }
-    if (ctl->weak < L.weak_limit) { ctl->weak += 1; return MODE_RW; }
+// Updates the weak counter and the cap flag it is given.
+__device__ __forceinline__ int32_t next_mode_of(const Level &L, bool balanced, int32_t noimp, int32_t it,
+                                                int32_t &weak, int32_t &hit_cap) {
+    if (noimp >= L.max_no_improve) return MODE_DONE;
+    if (it >= L.max_iters) { hit_cap = 1; return MODE_DONE; }
+    if (balanced) { weak = 0; return MODE_LP; }
+    if (weak < L.weak_limit) { weak += 1; return MODE_RW; }
     return MODE_RS;
 }
 
-// End of an iteration (Alg. 3 after updatePartsAndDS), one block: exact cut,
-// max part weight, P_best / counters, trace record, next mode, rebalancing
-// classes for the next iteration.  Returns the next mode (all threads).
+__device__ inline int32_t choose_mode(const Level &L, bool balanced) {
+    Ctl *ctl = L.ctl;
+    int32_t weak = ctl->weak, cap = ctl->hit_cap;
+    int32_t m = next_mode_of(L, balanced, ctl->noimp, ctl->it, weak, cap);
+    ctl->weak = weak;
+    ctl->hit_cap = cap;
+    return m;
+}
+
+__device__ __forceinline__ void reset_counters(Ctl *ctl) {
+    ctl->nW = ctl->nX = ctl->nM = 0;
+    ctl->ncand = 0;
+    ctl->degx = ctl->degm = 0;
+    ctl->nbnd = ctl->nexam = ctl->degexam = 0;
+}
+
+// End of an iteration (Alg. 3 after updatePartsAndDS), one block, after every
+// block of the apply phase: exact cut, max part weight, P_best / counters,
+// trace record, next mode, rebalancing classes for the next iteration.
+// Thread 0 loads every control value it needs before it uses any (one memory
+// round trip), decides in registers, then stores.  Returns the next mode
+// (all threads).
 __device__ inline int32_t ph_controller(const Level &L) {
     __shared__ long long sh[40];
     __shared__ int32_t next_mode;
     Ctl *ctl = L.ctl;
-    int32_t kind = vread(&ctl->mode);
+    int32_t kind = ctl->mode;
     if (kind == MODE_DONE) {
         if (threadIdx.x == 0) {
             ctl->copy_best = 0;
@@ -255,44 +353,53 @@ __device__ inline int32_t ph_controller(const Level &L) {
     }
     long long maxw = block_max_pw(L.pw, L.k, sh);
     if (threadIdx.x == 0) {
-        long long cut = ctl->cut + vread(&ctl->dcut);
+        // gather: values of earlier kernels (plain loads) and of this one (ld_gpu)
+        const long long cut0 = ctl->cut, Llim = ctl->L, best_cut0 = ctl->best_cut, best_maxw0 = ctl->best_maxw;
+        const int32_t it = ctl->it, noimp0 = ctl->noimp, best_bal0 = ctl->best_bal, kc = ctl->kcount[kind];
+        int32_t weak = ctl->weak, hit_cap = ctl->hit_cap;
+        const int32_t nX = ctl->nX, nM = ctl->nM;
+        const long long ncand = ctl->ncand, degx = ctl->degx, nbnd = ctl->nbnd, nexam = ctl->nexam,
+                        degexam = ctl->degexam;
+        const long long dcut = ld_gpu(&ctl->dcut), degm = ld_gpu(&ctl->degm);
+        // decide
+        const long long cut = cut0 + dcut;
+        const bool bal = maxw <= Llim;
+        int32_t noimp = noimp0 + 1, best_bal = best_bal0, copy = 0;
+        long long best_cut = best_cut0, best_maxw = best_maxw0;
+        if (bal) {
+            if (!best_bal0 || cut < best_cut0) {
+                if (!best_bal0 || 1000000LL * cut < L.phi_ppm * best_cut0) noimp = 0;
+                best_cut = cut; best_maxw = maxw; best_bal = 1;
+                copy = 1;
+            }
+        } else if (!best_bal0 && maxw < best_maxw0) {
+            best_cut = cut; best_maxw = maxw; noimp = 0;
+            copy = 1;
+        }
+        const int32_t m = next_mode_of(L, bal, noimp, it + 1, weak, hit_cap);
+        // scatter
         ctl->dcut = 0;
         ctl->cut = cut;
         ctl->maxw = maxw;
-        int32_t it = ctl->it;              // index of the iteration just run
-        bool bal = maxw <= ctl->L;
-        ctl->noimp += 1;
-        int32_t copy = 0;
-        if (bal) {
-            if (!ctl->best_bal || cut < ctl->best_cut) {
-                if (!ctl->best_bal || 1000000LL * cut < L.phi_ppm * ctl->best_cut) ctl->noimp = 0;
-                ctl->best_cut = cut; ctl->best_maxw = maxw; ctl->best_bal = 1;
-                copy = 1;
-            }
-        } else if (!ctl->best_bal && maxw < ctl->best_maxw) {
-            ctl->best_cut = cut; ctl->best_maxw = maxw; ctl->noimp = 0;
-            copy = 1;
-        }
+        ctl->noimp = noimp;
+        ctl->best_cut = best_cut; ctl->best_maxw = best_maxw; ctl->best_bal = best_bal;
         ctl->copy_best = copy;
         if (it < kTrace && L.trace) {
             TraceRec r;
             r.kind = kind; r.pad = 0;
-            r.nx = (kind == MODE_LP) ? (int64_t)(vread(&ctl->nX) + vread(&ctl->nXb)) : vread(&ctl->ncand);
-            r.nm = (int64_t)(vread(&ctl->nM) + vread(&ctl->nMb));
+            r.nx = (kind == MODE_LP) ? (int64_t)nX : ncand;
+            r.nm = nM;
             r.cut = cut; r.maxw = maxw;
-            r.degx = vread(&ctl->degx); r.degm = vread(&ctl->degm);
-            r.nbnd = vread(&ctl->nbnd); r.nexam = vread(&ctl->nexam); r.degexam = vread(&ctl->degexam);
+            r.degx = degx; r.degm = degm;
+            r.nbnd = nbnd; r.nexam = nexam; r.degexam = degexam;
             L.trace[it] = r;
         }
         if (kind == MODE_LP) ctl->lp_epoch = it;
-        ctl->kcount[kind] += 1;
+        ctl->kcount[kind] = kc + 1;
         ctl->it = it + 1;
-        ctl->nX = ctl->nXb = ctl->nM = ctl->nMb = 0;
-        ctl->nW = ctl->nWb = 0;
-        ctl->ncand = 0;
-        ctl->degx = ctl->degm = 0;
-        ctl->nbnd = ctl->nexam = ctl->degexam = 0;
-        int32_t m = choose_mode(L, bal);
+        ctl->weak = weak;
+        ctl->hit_cap = hit_cap;
+        reset_counters(ctl);
         ctl->mode = m;
         next_mode = m;
         if (L.use_graph) {
@@ -319,22 +426,19 @@ __device__ inline void ph_ctl_init(const Level &L, const int64_t *cut2) {
         ctl->best_maxw = maxw;
         ctl->best_bal = maxw <= ctl->L;
         ctl->it = 0; ctl->noimp = 0; ctl->weak = 0; ctl->lp_epoch = -1;
-        ctl->copy_best = 0; ctl->hit_cap = 0;
+        ctl->copy_best = 0; ctl->hit_cap = 0; ctl->ticket = 0;
         ctl->kcount[0] = ctl->kcount[1] = ctl->kcount[2] = ctl->kcount[3] = 0;
-        ctl->nX = ctl->nXb = ctl->nM = ctl->nMb = 0;
-        ctl->nW = ctl->nWb = 0;
-        ctl->ncand = 0;
-        ctl->degx = ctl->degm = 0;
-        ctl->nbnd = ctl->nexam = ctl->degexam = 0;
+        reset_counters(ctl);
         ctl->mode = choose_mode(L, maxw <= ctl->L);
     }
     __syncthreads();
     if (ctl->mode == MODE_RW || ctl->mode == MODE_RS) compute_classes(L, sh);
 }
 
-// P_best <- P_iter when the controller asked for it.
+// P_best <- P_iter when the controller asked for it (first phase of the next
+// iteration, and once after the level's loop).
 __device__ inline void ph_copy_best(const Level &L, Grid G) {
-    if (!vread(&L.ctl->copy_best)) return;
+    if (!L.ctl->copy_best) return;
     const int64_t stride = (int64_t)G.nb * blockDim.x;
     if (((reinterpret_cast<uintptr_t>(L.part) | reinterpret_cast<uintptr_t>(L.best)) & 15) != 0) {
         for (int64_t i = (int64_t)G.bid * blockDim.x + threadIdx.x; i < L.g.n; i += stride) L.best[i] = L.part[i];
@@ -363,7 +467,7 @@ __device__ inline void ph_lp_scan(const Level &L, Grid G, char *arena) {
     __shared__ long long red[40];
     JET_APPENDER(wapp, reinterpret_cast<int32_t *>(arena), kScanCap);
     Ctl *ctl = L.ctl;
-    const int32_t epoch = vread(&ctl->lp_epoch);
+    const int32_t epoch = ctl->lp_epoch;
     const bool use_locks = !ablate_locks(L.abl);
     const int64_t n = L.g.n, nq = (n + 3) / 4;
     const bool vec = (reinterpret_cast<uintptr_t>(L.ext) & 15) == 0;
@@ -395,26 +499,78 @@ __device__ inline void ph_lp_scan(const Level &L, Grid G, char *arena) {
     flush_counter(&ctl->nbnd, nb, red);
 }
 
-// Step 1 (Alg. 4 first loop, Eq. for P_d, Eq. gainconn_filter) for the listed
-// vertices with rows of <= 16 entries: one thread per vertex, the row
-// preloaded into registers so all its loads are in flight together.  Longer
-// rows are passed on to the warp phase.  prio holds F only for members of X;
-// every other entry stays kNoneGain (reset after the afterburner).
+// One long row of step 1, by a whole warp: conn(v, .) in the warp's dense
+// table, which is all-zero between rows (the read pass takes every touched
+// entry with atomicExch(.., 0), which also meets each distinct part once).
 template <bool EW>
-__device__ inline void ph_lp_select_list(const Level &L, LpExport ex, Grid G, char *arena) {
+__device__ __forceinline__ void lp_select_row(const Level &L, LpExport ex, int32_t v, int32_t *tab, long long &nexam,
+                                              long long &degexam, long long &degx) {
+    const DGraph &g = L.g;
+    const unsigned lane = lane_id();
+    int32_t ps = L.part[v];
+    int32_t F = kNoneGain, pd = -1;
+    bool inX = false;
+    int64_t beg = ld_xadj(g.xadj, v), end = ld_xadj(g.xadj, (int64_t)v + 1);
+    for (int64_t j = beg + lane; j < end; j += 32) atomicAdd(&tab[L.part[__ldg(g.adj + j)]], edge_w<EW>(g, j));
+    __syncwarp();
+    int32_t conn_s = tab[ps];
+    __syncwarp();
+    unsigned long long best = 0;
+    for (int64_t j = beg + lane; j < end; j += 32) {
+        int32_t p = L.part[__ldg(g.adj + j)];
+        int32_t c = atomicExch(&tab[p], 0);
+        if (c > 0 && p != ps) {
+            unsigned long long key = part_key(c, p);
+            best = key > best ? key : best;
+        }
+    }
+    __syncwarp();
+    best = warp_max_u64(best);
+    if (best) {
+        pd = key_part(best);
+        F = key_conn(best) - conn_s;
+        inX = first_filter(F, conn_s, L.cq16, L.abl);
+    }
+    if (lane == 0) {
+        nexam += 1;
+        degexam += end - beg;
+        if (inX) {
+            L.prio[v] = F;
+            L.nxt[v] = nxt_pack(ps, pd);
+            L.listX[atomicAdd(&L.ctl->nX, 1)] = v;
+            degx += end - beg;
+        }
+        if (ex.pd) { ex.pd[v] = pd >= 0 ? pd : ps; ex.gain[v] = F; }
+    }
+}
+
+// Step 1 (Alg. 4 first loop, Eq. for P_d, Eq. gainconn_filter) over the work
+// list.  Rows of <= 16 entries: one thread per vertex, the row preloaded into
+// registers so all its loads are in flight together; longer rows are staged
+// for the block's warps.  prio holds F only for members of X; every other
+// entry stays kNoneGain (reset after the afterburner).
+template <bool EW>
+__device__ inline void ph_lp_select(const Level &L, LpExport ex, Grid G, char *arena) {
     __shared__ long long red[40];
     Ctl *ctl = L.ctl;
-    const int32_t nW = vread(&ctl->nW);
-    if ((int64_t)G.bid * blockDim.x >= nW) return;
-    JET_APPENDER(xapp, reinterpret_cast<int32_t *>(arena), kListCap);
-    JET_APPENDER(bapp, reinterpret_cast<int32_t *>(arena) + kListCap, kBigCap);
+    const Share sh = list_share(ctl->nW, G);
+    if (sh.beg >= sh.end) return;
+    int32_t *a32 = reinterpret_cast<int32_t *>(arena);
+    JET_APPENDER(xapp, a32, kListCap);
+    JET_APPENDER(bigs, a32 + kListCap, kBigCap);
+    int32_t *tab = a32 + kListCap + kBigCap + (threadIdx.x >> 5) * L.k;
+    if (L.nbig > 0) {
+        for (int i = threadIdx.x; i < (int)(blockDim.x >> 5) * L.k; i += blockDim.x) a32[kListCap + kBigCap + i] = 0;
+        __syncthreads();
+    }
     const DGraph g = L.g;
     long long nexam = 0, degexam = 0, degx = 0;
-    for (int64_t i0 = (int64_t)G.bid * blockDim.x; i0 < nW; i0 += (int64_t)G.nb * blockDim.x) {
+    auto big_row = [&](int32_t v) { lp_select_row<EW>(L, ex, v, tab, nexam, degexam, degx); };
+    for (int64_t i0 = sh.beg; i0 < sh.end; i0 += blockDim.x) {
         int64_t i = i0 + threadIdx.x;
         bool inX = false, big = false;
         int32_t v = -1;
-        if (i < nW) {
+        if (i < sh.end) {
             v = L.listW[i];
             int64_t beg = ld_xadj(g.xadj, v), end = ld_xadj(g.xadj, (int64_t)v + 1);
             int d = (int)(end - beg);
@@ -456,222 +612,218 @@ __device__ inline void ph_lp_select_list(const Level &L, LpExport ex, Grid G, ch
                 }
                 if (inX) {
                     L.prio[v] = F;
-                    L.nxt[v] = pd;
+                    L.nxt[v] = nxt_pack(ps, pd);
                     degx += d;
                 }
                 if (ex.pd) { ex.pd[v] = pd >= 0 ? pd : ps; ex.gain[v] = F; }
             }
         }
         xapp.add(inX, v);
-        bapp.add(big, v);
+        bigs.add(big, v);
         xapp.flush(&ctl->nX, L.listX, false);
-        bapp.flush(&ctl->nWb, L.listWb, false);
+        bigs.drain(false, big_row);
     }
     xapp.flush(&ctl->nX, L.listX, true);
-    bapp.flush(&ctl->nWb, L.listWb, true);
-    flush_counter(&ctl->nexam, nexam, red);
-    flush_counter(&ctl->degexam, degexam, red);
-    flush_counter(&ctl->degx, degx, red);
-}
-
-// Long rows: one warp per vertex, dense per-warp table in shared memory.
-// The table is all-zero between vertices: the read pass takes every touched
-// entry with atomicExch(.., 0), which also detects each distinct part once.
-template <bool EW>
-__device__ inline void ph_lp_select_big(const Level &L, LpExport ex, Grid G, char *arena) {
-    __shared__ long long red[40];
-    Ctl *ctl = L.ctl;
-    const int32_t nWb = vread(&ctl->nWb);
-    const int warps = blockDim.x >> 5;
-    if ((int64_t)G.bid * warps >= nWb) return;
-    int32_t *tab = reinterpret_cast<int32_t *>(arena) + (threadIdx.x >> 5) * L.k;
-    for (int i = threadIdx.x; i < warps * L.k; i += blockDim.x) reinterpret_cast<int32_t *>(arena)[i] = 0;
-    __syncthreads();
-    const DGraph g = L.g;
-    const unsigned lane = lane_id();
-    long long nexam = 0, degexam = 0, degx = 0;
-    for (int64_t w = (int64_t)G.bid * warps + (threadIdx.x >> 5); w < nWb; w += (int64_t)G.nb * warps) {
-        int32_t v = L.listWb[w];
-        int32_t ps = L.part[v];
-        int32_t F = kNoneGain, pd = -1;
-        bool inX = false;
-        int64_t beg = ld_xadj(g.xadj, v), end = ld_xadj(g.xadj, (int64_t)v + 1);
-        for (int64_t j = beg + lane; j < end; j += 32) atomicAdd(&tab[L.part[__ldg(g.adj + j)]], edge_w<EW>(g, j));
-        __syncwarp();
-        int32_t conn_s = tab[ps];
-        __syncwarp();
-        unsigned long long best = 0;
-        for (int64_t j = beg + lane; j < end; j += 32) {
-            int32_t p = L.part[__ldg(g.adj + j)];
-            int32_t c = atomicExch(&tab[p], 0);
-            if (c > 0 && p != ps) {
-                unsigned long long key = part_key(c, p);
-                best = key > best ? key : best;
-            }
-        }
-        __syncwarp();
-        best = warp_max_u64(best);
-        if (best) {
-            pd = key_part(best);
-            F = key_conn(best) - conn_s;
-            inX = first_filter(F, conn_s, L.cq16, L.abl);
-        }
-        if (lane == 0) {
-            nexam += 1;
-            degexam += end - beg;
-            if (inX) {
-                L.prio[v] = F;
-                L.nxt[v] = pd;
-                L.listXb[atomicAdd(&ctl->nXb, 1)] = v;
-                degx += end - beg;
-            }
-            if (ex.pd) { ex.pd[v] = pd >= 0 ? pd : ps; ex.gain[v] = F; }
-        }
-    }
-    __syncthreads();
+    bigs.drain(true, big_row);
     flush_counter(&ctl->nexam, nexam, red);
     flush_counter(&ctl->degexam, degexam, red);
     flush_counter(&ctl->degx, degx, red);
 }
 
 // Step 2: afterburner (Alg. 4 second loop, ord of Sec. 4.1.1) and the second
-// filter M = {v in X : F2 >= 0}.  Short rows: one thread per vertex, the row
-// preloaded so that the neighbours' gathers are all in flight together.
-template <bool EW>
-__device__ inline void ph_afterburn_small(const Level &L, LpExport ex, Grid G, char *arena) {
-    Ctl *ctl = L.ctl;
-    const int32_t nX = vread(&ctl->nX), it = vread(&ctl->it);
-    if ((int64_t)G.bid * blockDim.x >= nX) return;
-    JET_APPENDER(mapp, reinterpret_cast<int32_t *>(arena), kListCap);
-    const bool full = !(L.abl & (ABL_NO_AFTERBURN | ABL_BASELINE_LP));
-    for (int64_t i0 = (int64_t)G.bid * blockDim.x; i0 < nX; i0 += (int64_t)G.nb * blockDim.x) {
-        int64_t i = i0 + threadIdx.x;
-        bool inM = false;
-        int32_t v = -1;
-        if (i < nX) {
-            v = L.listX[i];
-            if (!full) {
-                inM = true;
-            } else {
-                int32_t Fv = L.prio[v], pd = L.nxt[v], ps = L.part[v];
-                int64_t beg = ld_xadj(L.g.xadj, v);
-                int d = (int)(ld_xadj(L.g.xadj, (int64_t)v + 1) - beg);
-                int32_t uu[kSmallDeg], ww[kSmallDeg];
-#pragma unroll
-                for (int t = 0; t < kSmallDeg; ++t) {
-                    uu[t] = t < d ? __ldg(L.g.adj + beg + t) : -1;
-                    ww[t] = t < d ? edge_w<EW>(L.g, beg + t) : 0;
-                }
-                int32_t f2 = 0;
-#pragma unroll
-                for (int t = 0; t < kSmallDeg; ++t) {
-                    if (t < d) {
-                        int32_t u = uu[t];
-                        int32_t pu = L.part[u];
-                        int32_t fu = L.prio[u];
-                        if (fu > Fv || (fu == Fv && u < v)) pu = L.nxt[u];
-                        f2 += pu == pd ? ww[t] : (pu == ps ? -ww[t] : 0);
-                    }
-                }
-                inM = f2 >= 0;
-                if (ex.f2) ex.f2[v] = f2;
-            }
-            if (inM) L.mstamp[v] = it;
-        }
-        mapp.add(inM, v);
-        mapp.flush(&ctl->nM, L.listM, false);
-    }
-    mapp.flush(&ctl->nM, L.listM, true);
-}
-
+// filter M = {v in X : F2 >= 0}.  A neighbour u counts in its destination
+// part when it precedes v in ord (higher F, ties to the lower id).
 template <bool EW>
 __device__ __forceinline__ int32_t afterburn_term(const Level &L, int32_t v, int32_t Fv, int32_t pd, int32_t ps,
                                                   int64_t j) {
     int32_t u = __ldg(L.g.adj + j);
     int32_t pu = L.part[u];
     int32_t fu = L.prio[u];
-    if (fu > Fv || (fu == Fv && u < v)) pu = L.nxt[u];
+    if (fu > Fv || (fu == Fv && u < v)) pu = nxt_to(L.nxt[u]);
     int32_t w = edge_w<EW>(L.g, j);
     return pu == pd ? w : (pu == ps ? -w : 0);
 }
 
 template <bool EW>
-__device__ inline void ph_afterburn_big(const Level &L, LpExport ex, Grid G) {
+__device__ inline void ph_afterburn(const Level &L, LpExport ex, Grid G, char *arena) {
     Ctl *ctl = L.ctl;
-    const int32_t nXb = vread(&ctl->nXb), it = vread(&ctl->it);
-    const int warps = blockDim.x >> 5;
+    const int32_t it = ctl->it;
+    const Share sh = list_share(ctl->nX, G);
+    if (sh.beg >= sh.end) return;
+    int32_t *a32 = reinterpret_cast<int32_t *>(arena);
+    JET_APPENDER(mapp, a32, kListCap);
+    JET_APPENDER(bigs, a32 + kListCap, kBigCap);
+    const bool full = !(L.abl & (ABL_NO_AFTERBURN | ABL_BASELINE_LP));
     const unsigned lane = lane_id();
-    for (int64_t w = (int64_t)G.bid * warps + (threadIdx.x >> 5); w < nXb; w += (int64_t)G.nb * warps) {
-        int32_t v = L.listXb[w];
-        bool inM;
+    auto big_row = [&](int32_t v) {
+        int32_t Fv = L.prio[v], pd = nxt_to(L.nxt[v]), ps = L.part[v];
+        int64_t beg = ld_xadj(L.g.xadj, v), end = ld_xadj(L.g.xadj, (int64_t)v + 1);
         int32_t f2 = 0;
-        if (L.abl & (ABL_NO_AFTERBURN | ABL_BASELINE_LP)) {
-            inM = true;
-        } else {
-            int32_t Fv = L.prio[v], pd = L.nxt[v], ps = L.part[v];
-            int64_t beg = ld_xadj(L.g.xadj, v), end = ld_xadj(L.g.xadj, (int64_t)v + 1);
-            for (int64_t j = beg + lane; j < end; j += 32) f2 += afterburn_term<EW>(L, v, Fv, pd, ps, j);
-            f2 = warp_sum_i32(f2);
-            inM = f2 >= 0;
-        }
+        for (int64_t j = beg + lane; j < end; j += 32) f2 += afterburn_term<EW>(L, v, Fv, pd, ps, j);
+        f2 = warp_sum_i32(f2);
         if (lane == 0) {
-            if (ex.f2 && !(L.abl & (ABL_NO_AFTERBURN | ABL_BASELINE_LP))) ex.f2[v] = f2;
-            if (inM) {
+            if (ex.f2) ex.f2[v] = f2;
+            if (f2 >= 0) {
                 L.mstamp[v] = it;
-                L.listMb[atomicAdd(&ctl->nMb, 1)] = v;
+                L.listM[atomicAdd(&ctl->nM, 1)] = v;
             }
         }
+    };
+    for (int64_t i0 = sh.beg; i0 < sh.end; i0 += blockDim.x) {
+        int64_t i = i0 + threadIdx.x;
+        bool inM = false, big = false;
+        int32_t v = -1;
+        if (i < sh.end) {
+            v = L.listX[i];
+            if (!full) {
+                inM = true;
+            } else {
+                int64_t beg = ld_xadj(L.g.xadj, v);
+                int d = (int)(ld_xadj(L.g.xadj, (int64_t)v + 1) - beg);
+                if (d > kSmallDeg) {
+                    big = true;
+                } else {
+                    int32_t Fv = L.prio[v], pd = nxt_to(L.nxt[v]), ps = L.part[v];
+                    int32_t uu[kSmallDeg], ww[kSmallDeg];
+#pragma unroll
+                    for (int t = 0; t < kSmallDeg; ++t) {
+                        uu[t] = t < d ? __ldg(L.g.adj + beg + t) : -1;
+                        ww[t] = t < d ? edge_w<EW>(L.g, beg + t) : 0;
+                    }
+                    int32_t f2 = 0;
+#pragma unroll
+                    for (int t = 0; t < kSmallDeg; ++t) {
+                        if (t < d) {
+                            int32_t u = uu[t];
+                            int32_t pu = L.part[u];
+                            int32_t fu = L.prio[u];
+                            if (fu > Fv || (fu == Fv && u < v)) pu = nxt_to(L.nxt[u]);
+                            f2 += pu == pd ? ww[t] : (pu == ps ? -ww[t] : 0);
+                        }
+                    }
+                    inM = f2 >= 0;
+                    if (ex.f2) ex.f2[v] = f2;
+                }
+            }
+            if (inM) L.mstamp[v] = it;
+        }
+        mapp.add(inM, v);
+        bigs.add(big, v);
+        mapp.flush(&ctl->nM, L.listM, false);
+        bigs.drain(false, big_row);
     }
+    mapp.flush(&ctl->nM, L.listM, true);
+    bigs.drain(true, big_row);
 }
 
 // ---------------------------------------------------------------------------
-// Apply M (Alg. 3 updatePartsAndDS): exact cut change, part weights, and the
-// neighbour counts ext.  For an edge with both ends moving, the smaller id
-// accounts for the cut.
+// Apply M (Alg. 3 updatePartsAndDS) and commit it: exact cut change, part
+// weights, neighbour counts ext, P_s[v] <- P_d[v]; Jetlp movers are locked
+// for the next Jetlp (Sec. 4.1.3) and the priorities of X go back to
+// kNoneGain.  A neighbour that moves too is recognised by its stamp and its
+// old part read from nxt, never from part[] (which the commit overwrites);
+// for an edge with both ends moving the smaller id accounts for the cut.
 // ---------------------------------------------------------------------------
 template <bool EW>
-__device__ inline void ph_apply_small(const Level &L, Grid G, char *arena) {
+__device__ __forceinline__ int64_t apply_edge(const Level &L, int32_t v, int32_t a, int32_t b, int32_t it, int32_t u,
+                                              int32_t w, int32_t *other) {
+    int32_t pu, pn;
+    bool mu = L.mstamp[u] == it;
+    if (mu) {
+        int32_t x = L.nxt[u];
+        pu = nxt_from(x);
+        pn = nxt_to(x);
+    } else {
+        pu = pn = L.part[u];
+    }
+    *other = pn != b;
+    int32_t diff = (int)(pn != b) - (int)(pu != a);
+    if (!mu) {
+        if (diff) atomicAdd(&L.ext[u], diff);
+    } else if (u < v) {
+        return 0;
+    }
+    return (int64_t)w * diff;
+}
+
+template <bool EW>
+__device__ inline void ph_apply(const Level &L, Grid G, char *arena) {
     __shared__ long long red[40];
     Ctl *ctl = L.ctl;
-    if (vread(&ctl->mode) == MODE_DONE) return;
-    const int32_t nM = vread(&ctl->nM), it = vread(&ctl->it);
-    if ((int64_t)G.bid * blockDim.x >= nM) return;
+    const int32_t kind = ctl->mode;
+    if (kind == MODE_DONE) return;
+    const int32_t nM = ctl->nM, nX = ctl->nX, it = ctl->it;
+    const bool lp = kind == MODE_LP;
     long long *shpw = reinterpret_cast<long long *>(arena);
+    int32_t *stage = reinterpret_cast<int32_t *>(arena + align16((size_t)L.k * 8));
     for (int i = threadIdx.x; i < L.k; i += blockDim.x) shpw[i] = 0;
-    __syncthreads();
+    JET_APPENDER(bigs, stage, kBigCap);
+    const unsigned lane = lane_id();
     long long dc = 0, dm = 0;
-    for (int64_t i = (int64_t)G.bid * blockDim.x + threadIdx.x; i < nM; i += (int64_t)G.nb * blockDim.x) {
-        int32_t v = L.listM[i];
-        int32_t a = L.part[v], b = L.nxt[v];
-        long long wv = L.g.vw[v];
-        atomicAdd(reinterpret_cast<unsigned long long *>(&shpw[a]), (unsigned long long)(-wv));
-        atomicAdd(reinterpret_cast<unsigned long long *>(&shpw[b]), (unsigned long long)wv);
-        int64_t beg = ld_xadj(L.g.xadj, v);
-        int d = (int)(ld_xadj(L.g.xadj, (int64_t)v + 1) - beg);
-        // rows in listM are short (long ones are in listMb): preload them
-        int32_t uu[kSmallDeg];
-#pragma unroll
-        for (int t = 0; t < kSmallDeg; ++t) uu[t] = t < d ? __ldg(L.g.adj + beg + t) : -1;
+    auto big_row = [&](int32_t v) {
+        int32_t x = L.nxt[v];
+        int32_t a = nxt_from(x), b = nxt_to(x);
+        int64_t beg = ld_xadj(L.g.xadj, v), end = ld_xadj(L.g.xadj, (int64_t)v + 1);
+        long long c = 0;
         int32_t ne = 0;
+        for (int64_t j = beg + lane; j < end; j += 32) {
+            int32_t o;
+            c += apply_edge<EW>(L, v, a, b, it, __ldg(L.g.adj + j), edge_w<EW>(L.g, j), &o);
+            ne += o;
+        }
+        c = warp_sum_i64(c);
+        ne = warp_sum_i32(ne);
+        if (lane == 0) {
+            dc += c;
+            dm += end - beg;
+            L.ext[v] = ne;
+            L.part[v] = b;
+            if (lp) L.lstamp[v] = it;
+        }
+    };
+    const Share sh = list_share(nM, G);
+    for (int64_t i0 = sh.beg; i0 < sh.end; i0 += blockDim.x) {
+        int64_t i = i0 + threadIdx.x;
+        bool big = false;
+        int32_t v = -1;
+        if (i < sh.end) {
+            v = L.listM[i];
+            int32_t x = L.nxt[v];
+            int32_t a = nxt_from(x), b = nxt_to(x);
+            long long wv = L.g.vw[v];
+            atomicAdd(reinterpret_cast<unsigned long long *>(&shpw[a]), (unsigned long long)(-wv));
+            atomicAdd(reinterpret_cast<unsigned long long *>(&shpw[b]), (unsigned long long)wv);
+            int64_t beg = ld_xadj(L.g.xadj, v);
+            int d = (int)(ld_xadj(L.g.xadj, (int64_t)v + 1) - beg);
+            if (d > kSmallDeg) {
+                big = true;
+            } else {
+                // short row: preloaded so that its gathers are in flight together
+                int32_t uu[kSmallDeg];
 #pragma unroll
-        for (int t = 0; t < kSmallDeg; ++t) {
-            if (t < d) {
-                int32_t u = uu[t];
-                int32_t pu = L.part[u];
-                bool mu = L.mstamp[u] == it;
-                int32_t pn = mu ? L.nxt[u] : pu;
-                int32_t diff = (int)(pn != b) - (int)(pu != a);
-                ne += pn != b;
-                if (!mu) {
-                    if (diff) atomicAdd(&L.ext[u], diff);
-                    dc += (long long)edge_w<EW>(L.g, beg + t) * diff;
-                } else if (u > v) {
-                    dc += (long long)edge_w<EW>(L.g, beg + t) * diff;
+                for (int t = 0; t < kSmallDeg; ++t) uu[t] = t < d ? __ldg(L.g.adj + beg + t) : -1;
+                int32_t ne = 0;
+#pragma unroll
+                for (int t = 0; t < kSmallDeg; ++t) {
+                    if (t < d) {
+                        int32_t o;
+                        dc += apply_edge<EW>(L, v, a, b, it, uu[t], edge_w<EW>(L.g, beg + t), &o);
+                        ne += o;
+                    }
                 }
+                L.ext[v] = ne;
+                L.part[v] = b;
+                if (lp) L.lstamp[v] = it;
+                dm += d;
             }
         }
-        L.ext[v] = ne;
-        dm += d;
+        bigs.add(big, v);
+        bigs.drain(false, big_row);
+    }
+    bigs.drain(true, big_row);
+    if (lp) {
+        const int64_t stride = (int64_t)G.nb * blockDim.x;
+        for (int64_t i = (int64_t)G.bid * blockDim.x + threadIdx.x; i < nX; i += stride) L.prio[L.listX[i]] = kNoneGain;
     }
     dc = block_sum_i64(dc, red);
     dm = block_sum_i64(dm, red);
@@ -682,88 +834,6 @@ __device__ inline void ph_apply_small(const Level &L, Grid G, char *arena) {
         if (shpw[i]) atomic_add_i64(&L.pw[i], shpw[i]);
     __syncthreads();
 }
-
-template <bool EW>
-__device__ __forceinline__ int64_t apply_edge(const Level &L, int32_t v, int32_t a, int32_t b, int32_t it, int64_t j,
-                                              int32_t *other) {
-    int32_t u = __ldg(L.g.adj + j);
-    int32_t pu = L.part[u];
-    bool mu = L.mstamp[u] == it;
-    int32_t pn = mu ? L.nxt[u] : pu;
-    *other = pn != b;
-    if (!mu) {
-        int32_t dx = (int)(pn != b) - (int)(pu != a);
-        if (dx) atomicAdd(&L.ext[u], dx);
-    } else if (u < v) {
-        return 0;
-    }
-    int32_t w = edge_w<EW>(L.g, j);
-    return (int64_t)w * ((int)(pn != b) - (int)(pu != a));
-}
-
-template <bool EW>
-__device__ inline void ph_apply_big(const Level &L, Grid G) {
-    Ctl *ctl = L.ctl;
-    if (vread(&ctl->mode) == MODE_DONE) return;
-    const int32_t nMb = vread(&ctl->nMb), it = vread(&ctl->it);
-    const int warps = blockDim.x >> 5;
-    const unsigned lane = lane_id();
-    for (int64_t w = (int64_t)G.bid * warps + (threadIdx.x >> 5); w < nMb; w += (int64_t)G.nb * warps) {
-        int32_t v = L.listMb[w];
-        int32_t a = L.part[v], b = L.nxt[v];
-        int64_t beg = ld_xadj(L.g.xadj, v), end = ld_xadj(L.g.xadj, (int64_t)v + 1);
-        long long dc = 0;
-        int32_t ne = 0;
-        for (int64_t j = beg + lane; j < end; j += 32) {
-            int32_t o;
-            dc += apply_edge<EW>(L, v, a, b, it, j, &o);
-            ne += o;
-        }
-        dc = warp_sum_i64(dc);
-        ne = warp_sum_i32(ne);
-        if (lane == 0) {
-            long long wv = L.g.vw[v];
-            atomic_add_i64(&L.pw[a], -wv);
-            atomic_add_i64(&L.pw[b], wv);
-            if (dc) atomic_add_i64(&ctl->dcut, dc);
-            atomic_add_i64(&ctl->degm, end - beg);
-            L.ext[v] = ne;
-        }
-    }
-}
-
-// Commit: P_s[v] <- P_d[v]; Jetlp movers are locked for the next Jetlp
-// (Sec. 4.1.3); rebalancing leaves the locks alone.  After a Jetlp the
-// priorities of X go back to kNoneGain.
-// The counters a commit needs, read once the move lists are final (before the
-// apply step): in the cluster loop the controller of block 0 resets them
-// while other blocks may still be committing.
-struct CommitSnap {
-    int32_t kind, nM, nMb, nX, nXb, it;
-};
-__device__ __forceinline__ CommitSnap commit_snapshot(const Level &L) {
-    const Ctl *ctl = L.ctl;
-    return CommitSnap{vread(&ctl->mode), vread(&ctl->nM), vread(&ctl->nMb),
-                      vread(&ctl->nX),   vread(&ctl->nXb), vread(&ctl->it)};
-}
-
-__device__ __forceinline__ void ph_commit_snap(const Level &L, Grid G, const CommitSnap &cs) {
-    if (cs.kind == MODE_DONE) return;
-    const int64_t stride = (int64_t)G.nb * blockDim.x;
-    int64_t total = (int64_t)cs.nM + cs.nMb;
-    for (int64_t i = (int64_t)G.bid * blockDim.x + threadIdx.x; i < total; i += stride) {
-        int32_t v = i < cs.nM ? L.listM[i] : L.listMb[i - cs.nM];
-        L.part[v] = L.nxt[v];
-        if (cs.kind == MODE_LP) L.lstamp[v] = cs.it;
-    }
-    if (cs.kind == MODE_LP) {
-        int64_t tx = (int64_t)cs.nX + cs.nXb;
-        for (int64_t i = (int64_t)G.bid * blockDim.x + threadIdx.x; i < tx; i += stride)
-            L.prio[i < cs.nX ? L.listX[i] : L.listXb[i - cs.nX]] = kNoneGain;
-    }
-}
-
-__device__ inline void ph_commit(const Level &L, Grid G) { ph_commit_snap(L, G, commit_snapshot(L)); }
 
 // ---------------------------------------------------------------------------
 // Rebalancing (Alg. 5 Jetrw, Sec. 4.2.2 Jetrs)
@@ -792,7 +862,7 @@ struct SmemBuckets {
     bool on;
     __device__ __forceinline__ void init(const Level &L, long long *buf) {
         b = buf;
-        nkeys = vread(&L.ctl->nA) * kSlots;
+        nkeys = L.ctl->nA * kSlots;
         on = nkeys <= kSmemBuckets;
         if (on)
             for (int i = threadIdx.x; i < nkeys; i += blockDim.x) b[i] = 0;
@@ -804,6 +874,10 @@ struct SmemBuckets {
         } else {
             bucket_add(L, key, w);
         }
+    }
+    __device__ __forceinline__ void add_one(const Level &L, int32_t key, long long w) {   // one thread
+        if (on) atomicAdd(reinterpret_cast<unsigned long long *>(&b[key]), (unsigned long long)w);
+        else atomic_add_i64(&L.bucketw[key], w);
     }
     __device__ __forceinline__ void flush(const Level &L) {
         if (!on) return;
@@ -820,7 +894,7 @@ struct SmemBuckets {
 // touches no part of B (its own part is oversized): conn(v, P_s) is its
 // weighted degree, Jetrw sends it to a random part of B and both losses
 // equal that degree — it is finished here without reading its row.  The
-// others are listed for the row phases.
+// others are listed for the row phase.
 template <bool STRONG>
 __device__ inline void ph_rb_scan(const Level &L, Grid G, char *arena) {
     disarm_loop(L, G);
@@ -829,9 +903,9 @@ __device__ inline void ph_rb_scan(const Level &L, Grid G, char *arena) {
     sb.init(L, reinterpret_cast<long long *>(arena));
     JET_APPENDER(wapp, reinterpret_cast<int32_t *>(arena + kSmemBuckets * 8), kScanCap);
     Ctl *ctl = L.ctl;
-    const int32_t it = vread(&ctl->it);
-    const int32_t nB = vread(&ctl->nB);
-    const int64_t opt = vread(&ctl->opt);
+    const int32_t it = ctl->it;
+    const int32_t nB = ctl->nB;
+    const int64_t opt = ctl->opt;
     const int64_t n = L.g.n, nq = (n + 3) / 4;
     const bool vec = (reinterpret_cast<uintptr_t>(L.part) & 15) == 0;
     long long ncand = 0, nlist = 0;
@@ -878,7 +952,7 @@ __device__ inline void ph_rb_scan(const Level &L, Grid G, char *arena) {
                 ncand += 1;
                 if (!listed) {
                     int32_t loss = wd[i];
-                    if constexpr (!STRONG) L.nxt[v] = random_B(L, v, it, nB);
+                    if constexpr (!STRONG) L.nxt[v] = nxt_pack(pp[i], random_B(L, v, it, nB));
                     key = aa[i] * kSlots + slot_of(loss);
                     wv = vwv[i];
                     if (L.rbloss) L.rbloss[v] = loss;
@@ -897,28 +971,89 @@ __device__ inline void ph_rb_scan(const Level &L, Grid G, char *arena) {
     flush_counter(&ctl->nbnd, nlist, red);
 }
 
-// Step 1 for listed candidates with rows of <= 16 entries: Jetrw destination
-// (best-connected part of B, lowest id on ties, else a random one) and loss,
-// or the Jetrs loss (Sec. 4.2.2), then the slot bucket.
+// One long candidate row of step 1, by a whole warp (dense per-warp table as
+// in the Jetlp select).
 template <bool EW, bool STRONG>
-__device__ inline void ph_rb_cand_list(const Level &L, Grid G, char *arena) {
+__device__ __forceinline__ void rb_cand_row(const Level &L, int32_t v, int32_t *tab, int32_t it, int32_t nB,
+                                            SmemBuckets &sb, long long &degrows) {
+    const DGraph &g = L.g;
+    const unsigned lane = lane_id();
+    int32_t ps = L.part[v];
+    int32_t a = L.aidx[ps];
+    int64_t beg = ld_xadj(g.xadj, v), end = ld_xadj(g.xadj, (int64_t)v + 1);
+    for (int64_t j = beg + lane; j < end; j += 32) atomicAdd(&tab[L.part[__ldg(g.adj + j)]], edge_w<EW>(g, j));
+    __syncwarp();
+    int32_t conn_s = tab[ps];
+    __syncwarp();
+    unsigned long long best = 0;
+    long long S = 0;
+    int32_t cnt = 0;
+    for (int64_t j = beg + lane; j < end; j += 32) {
+        int32_t p = L.part[__ldg(g.adj + j)];
+        int32_t c = atomicExch(&tab[p], 0);
+        if (c > 0 && L.inB[p]) {
+            if constexpr (!STRONG) {
+                unsigned long long k2 = part_key(c, p);
+                best = k2 > best ? k2 : best;
+            } else {
+                S += c; cnt += 1;
+            }
+        }
+    }
+    __syncwarp();
+    int32_t loss;
+    if constexpr (!STRONG) {
+        best = warp_max_u64(best);
+        int32_t dest, cd;
+        if (best) { dest = key_part(best); cd = key_conn(best); }
+        else { dest = random_B(L, v, it, nB); cd = 0; }
+        if (lane == 0) L.nxt[v] = nxt_pack(ps, dest);
+        loss = conn_s - cd;
+    } else {
+        S = warp_sum_i64(S);
+        cnt = warp_sum_i32(cnt);
+        loss = conn_s - (cnt > 0 ? (int32_t)(S / cnt) : 0);
+    }
+    if (lane == 0) {
+        int32_t key = a * kSlots + slot_of(loss);
+        L.key[v] = key;
+        if (L.rbloss) L.rbloss[v] = loss;
+        sb.add_one(L, key, (long long)g.vw[v]);
+        degrows += end - beg;
+    }
+}
+
+// Step 1 for the listed candidates: Jetrw destination (best-connected part of
+// B, lowest id on ties, else a random one) and loss, or the Jetrs loss
+// (Sec. 4.2.2), then the slot bucket.  Short rows one thread each, long rows
+// staged for the block's warps.
+template <bool EW, bool STRONG>
+__device__ inline void ph_rb_cand(const Level &L, Grid G, char *arena) {
     __shared__ long long red[40];
     Ctl *ctl = L.ctl;
-    const int32_t nW = vread(&ctl->nW), nB = vread(&ctl->nB);
-    if ((int64_t)G.bid * blockDim.x >= nW) return;
+    const int32_t nB = ctl->nB;
+    const Share sh = list_share(ctl->nW, G);
+    if (sh.beg >= sh.end) return;
     SmemBuckets sb;
     sb.init(L, reinterpret_cast<long long *>(arena));
-    JET_APPENDER(bapp, reinterpret_cast<int32_t *>(arena + kSmemBuckets * 8), kBigCap);
-    const int32_t it = vread(&ctl->it);
+    int32_t *a32 = reinterpret_cast<int32_t *>(arena + kSmemBuckets * 8);
+    JET_APPENDER(bigs, a32, kBigCap);
+    int32_t *tab = a32 + kBigCap + (threadIdx.x >> 5) * L.k;
+    if (L.nbig > 0) {
+        for (int i = threadIdx.x; i < (int)(blockDim.x >> 5) * L.k; i += blockDim.x) a32[kBigCap + i] = 0;
+        __syncthreads();
+    }
+    const int32_t it = ctl->it;
     const DGraph g = L.g;
     long long degrows = 0;
-    for (int64_t i0 = (int64_t)G.bid * blockDim.x; i0 < nW; i0 += (int64_t)G.nb * blockDim.x) {
+    auto big_row = [&](int32_t v) { rb_cand_row<EW, STRONG>(L, v, tab, it, nB, sb, degrows); };
+    for (int64_t i0 = sh.beg; i0 < sh.end; i0 += blockDim.x) {
         int64_t i = i0 + threadIdx.x;
         int32_t key = -1;
         long long wv = 0;
         bool big = false;
         int32_t v = -1;
-        if (i < nW) {
+        if (i < sh.end) {
             v = L.listW[i];
             int32_t ps = L.part[v];
             int32_t a = L.aidx[ps];
@@ -957,7 +1092,7 @@ __device__ inline void ph_rb_cand_list(const Level &L, Grid G, char *arena) {
                     int32_t dest, cd;
                     if (best) { dest = key_part(best); cd = key_conn(best); }
                     else { dest = random_B(L, v, it, nB); cd = 0; }
-                    L.nxt[v] = dest;
+                    L.nxt[v] = nxt_pack(ps, dest);
                     loss = conn_s - cd;
                 } else {
                     long long S = 0;
@@ -982,88 +1117,27 @@ __device__ inline void ph_rb_cand_list(const Level &L, Grid G, char *arena) {
             }
         }
         sb.add(L, key, wv);
-        bapp.add(big, v);
-        bapp.flush(&ctl->nWb, L.listWb, false);
+        bigs.add(big, v);
+        bigs.drain(false, big_row);
     }
-    bapp.flush(&ctl->nWb, L.listWb, true);
+    bigs.drain(true, big_row);
     sb.flush(L);
     flush_counter(&ctl->degexam, degrows, red);
 }
 
-// Listed candidates with long rows: one warp per vertex.
-template <bool EW, bool STRONG>
-__device__ inline void ph_rb_cand_big(const Level &L, Grid G, char *arena) {
-    Ctl *ctl = L.ctl;
-    const int32_t nWb = vread(&ctl->nWb);
-    const int warps = blockDim.x >> 5;
-    if ((int64_t)G.bid * warps >= nWb) return;
-    int32_t *tab = reinterpret_cast<int32_t *>(arena) + (threadIdx.x >> 5) * L.k;
-    for (int i = threadIdx.x; i < warps * L.k; i += blockDim.x) reinterpret_cast<int32_t *>(arena)[i] = 0;
-    __syncthreads();
-    const int32_t it = vread(&ctl->it), nB = vread(&ctl->nB);
-    const DGraph g = L.g;
-    const unsigned lane = lane_id();
-    for (int64_t w = (int64_t)G.bid * warps + (threadIdx.x >> 5); w < nWb; w += (int64_t)G.nb * warps) {
-        int32_t v = L.listWb[w];
-        int32_t ps = L.part[v];
-        int32_t a = L.aidx[ps];
-        int64_t beg = ld_xadj(g.xadj, v), end = ld_xadj(g.xadj, (int64_t)v + 1);
-        for (int64_t j = beg + lane; j < end; j += 32) atomicAdd(&tab[L.part[__ldg(g.adj + j)]], edge_w<EW>(g, j));
-        __syncwarp();
-        int32_t conn_s = tab[ps];
-        __syncwarp();
-        unsigned long long best = 0;
-        long long S = 0;
-        int32_t cnt = 0;
-        for (int64_t j = beg + lane; j < end; j += 32) {
-            int32_t p = L.part[__ldg(g.adj + j)];
-            int32_t c = atomicExch(&tab[p], 0);
-            if (c > 0 && L.inB[p]) {
-                if constexpr (!STRONG) {
-                    unsigned long long k2 = part_key(c, p);
-                    best = k2 > best ? k2 : best;
-                } else {
-                    S += c; cnt += 1;
-                }
-            }
-        }
-        __syncwarp();
-        int32_t loss;
-        if constexpr (!STRONG) {
-            best = warp_max_u64(best);
-            int32_t dest, cd;
-            if (best) { dest = key_part(best); cd = key_conn(best); }
-            else { dest = random_B(L, v, it, nB); cd = 0; }
-            if (lane == 0) L.nxt[v] = dest;
-            loss = conn_s - cd;
-        } else {
-            S = warp_sum_i64(S);
-            cnt = warp_sum_i32(cnt);
-            loss = conn_s - (cnt > 0 ? (int32_t)(S / cnt) : 0);
-        }
-        int32_t key = a * kSlots + slot_of(loss);
-        if (lane == 0) {
-            L.key[v] = key;
-            if (L.rbloss) L.rbloss[v] = loss;
-            atomic_add_i64(&L.bucketw[key], (long long)g.vw[v]);
-            atomic_add_i64(&ctl->degexam, end - beg);
-        }
-    }
-    __syncthreads();
-}
-
-// Step 2: per oversized part (one warp each), the boundary slot s* where the
-// weight taken so far reaches the excess (Alg. 5 scan: a candidate is taken
-// while the weight before it is below w_p - L) and the weight still to take
-// inside s*.  s* = kSlots means every candidate is taken.
-__device__ inline void ph_rb_plan(const Level &L, Grid G) {
+// Step 2 (tail of step 1, one block): per oversized part (one warp each), the
+// boundary slot s* where the weight taken so far reaches the excess (Alg. 5
+// scan: a candidate is taken while the weight before it is below w_p - L) and
+// the weight still to take inside s*.  s* = kSlots means every candidate is
+// taken.
+__device__ inline void ph_rb_plan(const Level &L) {
     const Ctl *ctl = L.ctl;
-    const int32_t nA = vread(&ctl->nA);
+    const int32_t nA = ctl->nA;
     const int warps = blockDim.x >> 5;
     const unsigned lane = lane_id();
-    for (int a = G.bid * warps + (threadIdx.x >> 5); a < nA; a += G.nb * warps) {
-        long long t = L.bucketw[a * kSlots + lane];          // slots 0..31 on the lanes
-        long long t32 = L.bucketw[a * kSlots + 32];
+    for (int a = threadIdx.x >> 5; a < nA; a += warps) {
+        long long t = ld_gpu(&L.bucketw[a * kSlots + lane]);          // slots 0..31 on the lanes
+        long long t32 = ld_gpu(&L.bucketw[a * kSlots + 32]);
         long long x = t;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -1095,7 +1169,7 @@ __device__ inline void ph_rb_plan(const Level &L, Grid G) {
 // boundary-slot members (they are taken in vertex order).
 __device__ inline void ph_rb_tilehist(const Level &L, Grid G, char *arena) {
     int32_t *h = reinterpret_cast<int32_t *>(arena);
-    const int32_t nA = vread(&L.ctl->nA);
+    const int32_t nA = L.ctl->nA;
     for (int64_t t = G.bid; t < L.ntiles; t += G.nb) {
         for (int i = threadIdx.x; i < nA; i += blockDim.x) h[i] = 0;
         __syncthreads();
@@ -1117,7 +1191,7 @@ __device__ inline void ph_rb_tilehist(const Level &L, Grid G, char *arena) {
 // eight consecutive tiles per thread).
 __device__ inline void ph_rb_tilescan(const Level &L, Grid G) {
     __shared__ long long sh[40];
-    const int32_t nA = vread(&L.ctl->nA);
+    const int32_t nA = L.ctl->nA;
     const int64_t nt = L.ntiles;
     constexpr int kItems = 8;
     for (int a = G.bid; a < nA; a += G.nb) {
@@ -1149,10 +1223,11 @@ __device__ inline void ph_rb_tilescan(const Level &L, Grid G) {
 template <bool STRONG>
 __device__ inline void ph_rb_take(const Level &L, Grid G, char *arena) {
     long long *run = reinterpret_cast<long long *>(arena);
-    int32_t *mbuf = reinterpret_cast<int32_t *>(arena + (((size_t)L.k * 8 + 15) & ~size_t(15)));
+    int32_t *mbuf = reinterpret_cast<int32_t *>(arena + align16((size_t)L.k * 8));
     JET_APPENDER(mapp, mbuf, 2 * (int)blockDim.x);
+    __shared__ long long red[40];
     Ctl *ctl = L.ctl;
-    const int32_t nA = vread(&ctl->nA), it = vread(&ctl->it);
+    const int32_t nA = ctl->nA, it = ctl->it;
     const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
     const unsigned lt_mask = (1u << lane) - 1u;
     for (int64_t tile = G.bid; tile < L.ntiles; tile += G.nb) {
@@ -1195,12 +1270,9 @@ __device__ inline void ph_rb_take(const Level &L, Grid G, char *arena) {
         bool taken = kv >= 0 && (s < ss || (member && mine < L.need[a]));
         if constexpr (!STRONG) {
             if (taken) L.mstamp[vv] = it;
-            bool big = taken && is_big_row(L.g, (int32_t)vv);
-            mapp.add(taken && !big, (int32_t)vv);
-            if (big) L.listMb[atomicAdd(&ctl->nMb, 1)] = (int32_t)vv;
+            mapp.add(taken, (int32_t)vv);
             mapp.flush(&ctl->nM, L.listM, true);
         } else {
-            __shared__ long long red[40];
             if (vv < L.g.n) L.etaken[vv] = taken ? w : 0;
             long long tt = block_sum_i64(taken ? w : 0, red);
             if (threadIdx.x == 0) L.tiletaken[tile] = tt;
@@ -1209,13 +1281,14 @@ __device__ inline void ph_rb_take(const Level &L, Grid G, char *arena) {
     }
 }
 
-// Jetrs: exclusive scan of the evicted weight over tiles (one block).
+// Jetrs (tail of step 4, one block): exclusive scan of the evicted weight
+// over the tiles.
 __device__ inline void ph_rb_tiletaken_scan(const Level &L) {
     __shared__ long long sh[40];
     long long carry = 0;
     for (int64_t t0 = 0; t0 < L.ntiles; t0 += blockDim.x) {
         int64_t t = t0 + threadIdx.x;
-        long long x = t < L.ntiles ? L.tiletaken[t] : 0;
+        long long x = t < L.ntiles ? ld_gpu(&L.tiletaken[t]) : 0;
         long long tot = 0;
         long long ex = block_exscan_i64(x, sh, &tot);
         if (t < L.ntiles) L.tiletaken[t] = carry + ex;
@@ -1230,7 +1303,7 @@ __device__ inline void ph_rb_cookie(const Level &L, Grid G, char *arena) {
     __shared__ long long sh[40];
     JET_APPENDER(mapp, reinterpret_cast<int32_t *>(arena), 2 * (int)blockDim.x);
     Ctl *ctl = L.ctl;
-    const int32_t it = vread(&ctl->it), nB = vread(&ctl->nB);
+    const int32_t it = ctl->it, nB = ctl->nB;
     const long long total2 = 2 * L.capC[nB];
     for (int64_t tile = G.bid; tile < L.ntiles; tile += G.nb) {
         int64_t v = tile * blockDim.x + threadIdx.x;
@@ -1250,10 +1323,8 @@ __device__ inline void ph_rb_cookie(const Level &L, Grid G, char *arena) {
             }
         }
         bool mv = dest >= 0;
-        if (mv) { L.nxt[v] = dest; L.mstamp[v] = it; }
-        bool big = mv && is_big_row(L.g, (int32_t)v);
-        mapp.add(mv && !big, (int32_t)v);
-        if (big) L.listMb[atomicAdd(&ctl->nMb, 1)] = (int32_t)v;
+        if (mv) { L.nxt[v] = nxt_pack(L.part[v], dest); L.mstamp[v] = it; }
+        mapp.add(mv, (int32_t)v);
         mapp.flush(&ctl->nM, L.listM, true);
     }
 }

@@ -77,47 +77,48 @@ __global__ void k_graph_start(Level L) {
     }
 }
 
-__global__ void __launch_bounds__(1024) k_controller(Level L) { ph_controller(L); }
 __global__ void __launch_bounds__(kTB) k_copy_best(Level L) { ph_copy_best(L, launch_grid()); }
-__global__ void __launch_bounds__(kTB) k_lp_scan(Level L) { ph_lp_scan(L, launch_grid(), JET_ARENA); }
-template <bool EW>
-__global__ void __launch_bounds__(kTB, 4) k_lp_select_list(Level L, LpExport ex) {
-    ph_lp_select_list<EW>(L, ex, launch_grid(), JET_ARENA);
+// Jetlp: P_best copy + work list, select, afterburner
+__global__ void __launch_bounds__(kTB) k_lp_scan(Level L) {
+    ph_copy_best(L, launch_grid());
+    ph_lp_scan(L, launch_grid(), JET_ARENA);
 }
 template <bool EW>
-__global__ void __launch_bounds__(kTB) k_lp_select_big(Level L, LpExport ex) {
-    ph_lp_select_big<EW>(L, ex, launch_grid(), JET_ARENA);
+__global__ void __launch_bounds__(kTB, 4) k_lp_select(Level L, LpExport ex) {
+    ph_lp_select<EW>(L, ex, launch_grid(), JET_ARENA);
 }
 template <bool EW>
-__global__ void __launch_bounds__(kTB, 4) k_afterburn_small(Level L, LpExport ex) {
-    ph_afterburn_small<EW>(L, ex, launch_grid(), JET_ARENA);
+__global__ void __launch_bounds__(kTB, 4) k_afterburn(Level L, LpExport ex) {
+    ph_afterburn<EW>(L, ex, launch_grid(), JET_ARENA);
 }
+// apply + commit; the last block runs the controller
 template <bool EW>
-__global__ void __launch_bounds__(kTB) k_afterburn_big(Level L, LpExport ex) { ph_afterburn_big<EW>(L, ex, launch_grid()); }
-template <bool EW>
-__global__ void __launch_bounds__(kTB, 4) k_apply_small(Level L) { ph_apply_small<EW>(L, launch_grid(), JET_ARENA); }
-template <bool EW>
-__global__ void __launch_bounds__(kTB) k_apply_big(Level L) { ph_apply_big<EW>(L, launch_grid()); }
-__global__ void __launch_bounds__(kTB) k_commit(Level L) { ph_commit(L, launch_grid()); }
+__global__ void __launch_bounds__(kTB, 4) k_apply(Level L) {
+    ph_apply<EW>(L, launch_grid(), JET_ARENA);
+    if (last_block(L.ctl)) ph_controller(L);
+}
+// rebalancing: P_best copy + candidates, rows (+ plan), tile sums, tile scan,
+// take (+ Jetrs eviction scan), cookie cutter
 template <bool STRONG>
-__global__ void __launch_bounds__(kTB) k_rb_scan(Level L) { ph_rb_scan<STRONG>(L, launch_grid(), JET_ARENA); }
-template <bool EW, bool STRONG>
-__global__ void __launch_bounds__(kTB, 4) k_rb_cand_list(Level L) {
-    ph_rb_cand_list<EW, STRONG>(L, launch_grid(), JET_ARENA);
+__global__ void __launch_bounds__(kTB) k_rb_scan(Level L) {
+    ph_copy_best(L, launch_grid());
+    ph_rb_scan<STRONG>(L, launch_grid(), JET_ARENA);
 }
 template <bool EW, bool STRONG>
-__global__ void __launch_bounds__(kTB) k_rb_cand_big(Level L) { ph_rb_cand_big<EW, STRONG>(L, launch_grid(), JET_ARENA); }
-__global__ void __launch_bounds__(kTB) k_rb_plan(Level L) { ph_rb_plan(L, launch_grid()); }
+__global__ void __launch_bounds__(kTB, 4) k_rb_cand(Level L) {
+    ph_rb_cand<EW, STRONG>(L, launch_grid(), JET_ARENA);
+    if (last_block(L.ctl)) ph_rb_plan(L);
+}
 __global__ void __launch_bounds__(kTB) k_rb_tilehist(Level L) { ph_rb_tilehist(L, launch_grid(), JET_ARENA); }
 __global__ void __launch_bounds__(1024) k_rb_tilescan(Level L) { ph_rb_tilescan(L, launch_grid()); }
 template <bool STRONG>
-__global__ void __launch_bounds__(kTB) k_rb_take(Level L) { ph_rb_take<STRONG>(L, launch_grid(), JET_ARENA); }
-__global__ void __launch_bounds__(1024) k_rb_tiletaken_scan(Level L) { ph_rb_tiletaken_scan(L); }
+__global__ void __launch_bounds__(kTB) k_rb_take(Level L) {
+    ph_rb_take<STRONG>(L, launch_grid(), JET_ARENA);
+    if constexpr (STRONG) {
+        if (last_block(L.ctl)) ph_rb_tiletaken_scan(L);
+    }
+}
 __global__ void __launch_bounds__(kTB) k_rb_cookie(Level L) { ph_rb_cookie(L, launch_grid(), JET_ARENA); }
-
-// dynamic shared memory of each per-phase kernel (blocks of kTB threads)
-inline size_t sm_table(int32_t k) { return arena_table(k, kTB); }
-inline size_t sm_take(int32_t k) { return (((size_t)k * 8 + 15) & ~size_t(15)) + (size_t)2 * kTB * 4; }
 
 // ---------------------------------------------------------------------------
 // one cluster per level: every iteration in a single launch
@@ -128,13 +129,9 @@ template <bool EW, bool STRONG>
 __device__ __forceinline__ void cluster_rebalance(const Level &L, Grid G, char *arena, cg::cluster_group &cl) {
     ph_rb_scan<STRONG>(L, G, arena);
     cl.sync();
-    ph_rb_cand_list<EW, STRONG>(L, G, arena);
+    ph_rb_cand<EW, STRONG>(L, G, arena);
     cl.sync();
-    if (L.nbig > 0) {
-        ph_rb_cand_big<EW, STRONG>(L, G, arena);
-        cl.sync();
-    }
-    ph_rb_plan(L, G);
+    if (G.bid == 0) ph_rb_plan(L);
     cl.sync();
     ph_rb_tilehist(L, G, arena);
     cl.sync();
@@ -152,8 +149,8 @@ __device__ __forceinline__ void cluster_rebalance(const Level &L, Grid G, char *
 
 // The whole loop of Alg. 3 on one level.  The blocks of the cluster take the
 // phases in lockstep (cluster barrier between phases; block 0 runs the
-// controller); the loop ends when the controller chooses DONE, which the
-// stop rule or the iteration cap guarantees.
+// tails); the loop ends when the controller chooses DONE, which the stop
+// rule or the iteration cap guarantees.
 template <bool EW>
 __global__ void __launch_bounds__(kClusterThreads, 1) k_refine_cluster(Level L) {
     cg::cluster_group cl = cg::this_cluster();
@@ -161,31 +158,23 @@ __global__ void __launch_bounds__(kClusterThreads, 1) k_refine_cluster(Level L) 
     char *arena = JET_ARENA;
     const LpExport none{nullptr, nullptr, nullptr};
     for (;;) {
-        const int32_t mode = *reinterpret_cast<volatile int32_t *>(&L.ctl->mode);
+        const int32_t mode = L.ctl->mode;
         if (mode == MODE_DONE) break;
         ph_copy_best(L, G);   // P_best <- P_iter asked for by the previous controller
         if (mode == MODE_LP) {
             ph_lp_scan(L, G, arena);
             cl.sync();
-            ph_lp_select_list<EW>(L, none, G, arena);
+            ph_lp_select<EW>(L, none, G, arena);
             cl.sync();
-            if (L.nbig > 0) {
-                ph_lp_select_big<EW>(L, none, G, arena);
-                cl.sync();
-            }
-            ph_afterburn_small<EW>(L, none, G, arena);
-            ph_afterburn_big<EW>(L, none, G);
+            ph_afterburn<EW>(L, none, G, arena);
             cl.sync();
         } else if (mode == MODE_RW) {
             cluster_rebalance<EW, false>(L, G, arena, cl);
         } else {
             cluster_rebalance<EW, true>(L, G, arena, cl);
         }
-        const CommitSnap cs = commit_snapshot(L);
-        ph_apply_small<EW>(L, G, arena);
-        ph_apply_big<EW>(L, G);
+        ph_apply<EW>(L, G, arena);
         cl.sync();
-        ph_commit_snap(L, G, cs);
         if (G.bid == 0) ph_controller(L);
         cl.sync();
     }
@@ -195,11 +184,12 @@ __global__ void __launch_bounds__(kClusterThreads, 1) k_refine_cluster(Level L) 
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
-__global__ void k_collect_big(DGraph g, int32_t *bigv, int32_t *count) {
+// Vertices with rows longer than kSmallDeg (only whether there are any matters).
+__global__ void k_count_big(DGraph g, int32_t *count) {
     int32_t v = blockIdx.x * blockDim.x + threadIdx.x;
     bool big = v < g.n && ld_xadj(g.xadj, (int64_t)v + 1) - ld_xadj(g.xadj, v) > kSmallDeg;
-    int slot = warp_append(count, big);
-    if (big) bigv[slot] = v;
+    unsigned m = __ballot_sync(0xffffffffu, big);
+    if (lane_id() == 0 && m) atomicAdd(count, __popc(m));
 }
 
 __global__ void k_fill_i32(int32_t *p, int64_t n, int32_t val) {
@@ -234,21 +224,18 @@ int setup_level(Ctx &c, const DGraph &g, int32_t k, LevelBufs &B) {
     int64_t n = g.n;
     size_t nn = (size_t)std::max<int64_t>(n, 1);
     int32_t ntiles = (int32_t)std::max<int64_t>((n + kRbTile - 1) / kRbTile, 1);
-    // per-vertex int32 arrays: best, nxt, prio, mstamp, lstamp, key, listX, listXb, listM, listMb, bigv,
-    // ext, wdeg, listW, listWb
-    const int nv32 = 15;
+    // per-vertex int32 arrays: best, nxt, prio, mstamp, lstamp, key, listX, listM, ext, wdeg, listW
+    const int nv32 = 11;
     size_t vbytes = nv32 * align256(nn * 4) + align256(nn * 8) /* etaken */;
     JET_TRY(dev_alloc(B.vert, vbytes, s));
     char *p = B.vert.as<char>();
     auto take32 = [&](void) { int32_t *r = reinterpret_cast<int32_t *>(p); p += align256(nn * 4); return r; };
     Level &L = B.L;
     L.best = take32(); L.nxt = take32(); L.prio = take32(); L.mstamp = take32(); L.lstamp = take32();
-    L.key = take32(); L.listX = take32(); L.listXb = take32(); L.listM = take32(); L.listMb = take32();
-    int32_t *bigv = take32();
+    L.key = take32(); L.listX = take32(); L.listM = take32();
     L.ext = take32();
     L.wdeg = take32();
     L.listW = take32();
-    L.listWb = take32();
     L.rbloss = nullptr;
     L.etaken = reinterpret_cast<int64_t *>(p);
     p += align256(nn * 8);
@@ -280,13 +267,12 @@ int setup_level(Ctx &c, const DGraph &g, int32_t k, LevelBufs &B) {
     L.ntiles = ntiles;
     L.g = g;
     L.k = k;
-    L.bigv = bigv;
     JET_CUDA_TRY(cudaMemsetAsync(L.ctl, 0, sizeof(Ctl), s));
     JET_CUDA_TRY(cudaMemsetAsync(L.pw, 0, kk * 8, s));
     JET_CUDA_TRY(cudaMemsetAsync(B.cut2, 0, 16, s));
     JET_CUDA_TRY(cudaMemsetAsync(B.nbig_dev, 0, 16, s));
     if (n > 0) {
-        k_collect_big<<<grid_for(n, kTB), kTB, 0, s>>>(g, bigv, B.nbig_dev);
+        k_count_big<<<grid_for(n, kTB), kTB, 0, s>>>(g, B.nbig_dev);
         k_fill_i32<<<grid_for(n, kTB, 4096), kTB, 0, s>>>(L.lstamp, n, -2);
         k_fill_i32<<<grid_for(n, kTB, 4096), kTB, 0, s>>>(L.mstamp, n, -2);
         k_fill_i32<<<grid_for(n, kTB, 4096), kTB, 0, s>>>(L.prio, n, kNoneGain);
@@ -300,8 +286,6 @@ int setup_level(Ctx &c, const DGraph &g, int32_t k, LevelBufs &B) {
 
 int list_grid() { return num_sms() * 4; }
 
-size_t table_smem(int32_t k) { return sm_table(k); }
-
 // grid of a kernel over a list of at most `items` entries (one per thread)
 int list_blocks(int64_t items) { return std::min(list_grid(), grid_for(items, kTB)); }
 
@@ -310,36 +294,20 @@ int list_blocks(int64_t items) { return std::min(list_grid(), grid_for(items, kT
 int enqueue_lp_select(const Level &L, cudaStream_t s, LpExport ex, int *nk) {
     int n = L.g.n;
     bool ew = L.g.ew != nullptr;
-    int lg = list_grid();
-    k_lp_scan<<<std::min(lg, grid_for((n + 3) / 4, kTB)), kTB, (size_t)kScanCap * 4, s>>>(L);
-    const size_t sm_list = (size_t)(kListCap + kBigCap) * 4;
-    if (ew) k_lp_select_list<true><<<list_blocks(n), kTB, sm_list, s>>>(L, ex);
-    else k_lp_select_list<false><<<list_blocks(n), kTB, sm_list, s>>>(L, ex);
+    k_lp_scan<<<std::min(list_grid(), grid_for((n + 3) / 4, kTB)), kTB, sm_lp_scan(), s>>>(L);
+    const size_t sm = sm_lp_select(L.k, kTB, L.nbig > 0);
+    if (ew) k_lp_select<true><<<list_blocks(n), kTB, sm, s>>>(L, ex);
+    else k_lp_select<false><<<list_blocks(n), kTB, sm, s>>>(L, ex);
     *nk = 2;
-    if (L.nbig > 0) {
-        int gb = std::min(lg, grid_for(L.nbig, kTB / 32));
-        if (ew) k_lp_select_big<true><<<gb, kTB, table_smem(L.k), s>>>(L, ex);
-        else k_lp_select_big<false><<<gb, kTB, table_smem(L.k), s>>>(L, ex);
-        *nk += 1;
-    }
     JET_CUDA_TRY(cudaGetLastError());
     return JET_OK;
 }
 
 int enqueue_lp_after(const Level &L, cudaStream_t s, LpExport ex, int *nk) {
     int n = L.g.n;
-    int lg = list_grid();
-    bool ew = L.g.ew != nullptr;
-    int ga = std::min(lg, grid_for(n, kTB));
-    if (ew) k_afterburn_small<true><<<ga, kTB, (size_t)kListCap * 4, s>>>(L, ex);
-    else k_afterburn_small<false><<<ga, kTB, (size_t)kListCap * 4, s>>>(L, ex);
+    if (L.g.ew) k_afterburn<true><<<list_blocks(n), kTB, sm_afterburn(), s>>>(L, ex);
+    else k_afterburn<false><<<list_blocks(n), kTB, sm_afterburn(), s>>>(L, ex);
     *nk = 1;
-    if (L.nbig > 0) {
-        int gb = std::min(lg, grid_for(L.nbig, kTB / 32));
-        if (ew) k_afterburn_big<true><<<gb, kTB, 0, s>>>(L, ex);
-        else k_afterburn_big<false><<<gb, kTB, 0, s>>>(L, ex);
-        *nk += 1;
-    }
     JET_CUDA_TRY(cudaGetLastError());
     return JET_OK;
 }
@@ -355,28 +323,18 @@ int enqueue_lp(const Level &L, cudaStream_t s, int *nk, LpExport ex = {nullptr, 
 template <bool STRONG>
 int enqueue_rb_t(const Level &L, cudaStream_t s, int *nk) {
     int n = L.g.n;
-    int lg = list_grid();
     bool ew = L.g.ew != nullptr;
-    k_rb_scan<STRONG><<<std::min(lg, grid_for((n + 3) / 4, kTB)), kTB, (size_t)kSmemBuckets * 8 + (size_t)kScanCap * 4, s>>>(L);
-    const size_t sm_list = (size_t)kSmemBuckets * 8 + (size_t)kBigCap * 4;
-    if (ew) k_rb_cand_list<true, STRONG><<<list_blocks(n), kTB, sm_list, s>>>(L);
-    else k_rb_cand_list<false, STRONG><<<list_blocks(n), kTB, sm_list, s>>>(L);
-    *nk = 2;
-    if (L.nbig > 0) {
-        int gb = std::min(lg, grid_for(L.nbig, kTB / 32));
-        if (ew) k_rb_cand_big<true, STRONG><<<gb, kTB, table_smem(L.k), s>>>(L);
-        else k_rb_cand_big<false, STRONG><<<gb, kTB, table_smem(L.k), s>>>(L);
-        *nk += 1;
-    }
-    k_rb_plan<<<std::max(1, (L.k + 7) / 8), kTB, 0, s>>>(L);
-    k_rb_tilehist<<<L.ntiles, kTB, (size_t)L.k * 4, s>>>(L);
+    k_rb_scan<STRONG><<<std::min(list_grid(), grid_for((n + 3) / 4, kTB)), kTB, sm_rb_scan(), s>>>(L);
+    const size_t sm = sm_rb_cand(L.k, kTB, L.nbig > 0);
+    if (ew) k_rb_cand<true, STRONG><<<list_blocks(n), kTB, sm, s>>>(L);
+    else k_rb_cand<false, STRONG><<<list_blocks(n), kTB, sm, s>>>(L);
+    k_rb_tilehist<<<L.ntiles, kTB, sm_rb_tilehist(L.k), s>>>(L);
     k_rb_tilescan<<<L.k, 1024, 0, s>>>(L);
-    k_rb_take<STRONG><<<L.ntiles, kTB, sm_take(L.k), s>>>(L);
-    *nk += 4;
+    k_rb_take<STRONG><<<L.ntiles, kTB, sm_rb_take(L.k, kTB), s>>>(L);
+    *nk = 5;
     if (STRONG) {
-        k_rb_tiletaken_scan<<<1, 1024, 0, s>>>(L);
-        k_rb_cookie<<<L.ntiles, kTB, (size_t)2 * kTB * 4, s>>>(L);
-        *nk += 2;
+        k_rb_cookie<<<L.ntiles, kTB, sm_rb_cookie(kTB), s>>>(L);
+        *nk += 1;
     }
     JET_CUDA_TRY(cudaGetLastError());
     return JET_OK;
@@ -386,25 +344,19 @@ int enqueue_rb(const Level &L, cudaStream_t s, bool strong, int *nk) {
     return strong ? enqueue_rb_t<true>(L, s, nk) : enqueue_rb_t<false>(L, s, nk);
 }
 
-// apply + commit + controller + best copy
+// apply + commit + controller
 int enqueue_tail(const Level &L, cudaStream_t s, int *nk) {
-    int lg = list_grid();
-    int n = L.g.n;
-    bool ew = L.g.ew != nullptr;
-    int ga = std::min(lg, grid_for(n, kTB));
-    if (ew) k_apply_small<true><<<ga, kTB, (size_t)L.k * 8, s>>>(L);
-    else k_apply_small<false><<<ga, kTB, (size_t)L.k * 8, s>>>(L);
+    int ga = std::min(list_grid(), grid_for(L.g.n, kTB));
+    if (L.g.ew) k_apply<true><<<ga, kTB, sm_apply(L.k), s>>>(L);
+    else k_apply<false><<<ga, kTB, sm_apply(L.k), s>>>(L);
     *nk = 1;
-    if (L.nbig > 0) {
-        int gb = std::min(lg, grid_for(L.nbig, kTB / 32));
-        if (ew) k_apply_big<true><<<gb, kTB, 0, s>>>(L);
-        else k_apply_big<false><<<gb, kTB, 0, s>>>(L);
-        *nk += 1;
-    }
-    k_commit<<<ga, kTB, 0, s>>>(L);
-    k_controller<<<1, 1024, 0, s>>>(L);
-    k_copy_best<<<std::min(lg, grid_for(n / 4 + 1, kTB)), kTB, 0, s>>>(L);
-    *nk += 3;
+    JET_CUDA_TRY(cudaGetLastError());
+    return JET_OK;
+}
+
+// P_best <- P_iter after the level's last iteration
+int enqueue_final_copy(const Level &L, cudaStream_t s) {
+    k_copy_best<<<std::min(list_grid(), grid_for(L.g.n / 4 + 1, kTB)), kTB, 0, s>>>(L);
     JET_CUDA_TRY(cudaGetLastError());
     return JET_OK;
 }
@@ -487,6 +439,8 @@ int run_hostloop(Ctx &c, const Level &L, bool profile, float *sel_ms) {
         JET_TRY(enqueue_tail(L, c.stream, &nk));
         c.launches += nk;
     }
+    JET_TRY(enqueue_final_copy(L, c.stream));
+    c.launches += 1;
     float tot = 0.f;
     for (auto &m : marks) {
         float t = 0.f;
@@ -498,7 +452,7 @@ int run_hostloop(Ctx &c, const Level &L, bool profile, float *sel_ms) {
 }
 
 // Device-resident loop: graph = start kernel -> WHILE(h_loop) { SWITCH(h_mode)
-// {Jetlp | Jetrw | Jetrs} -> apply, commit, controller, best copy }.
+// {Jetlp | Jetrw | Jetrs} -> apply + commit + controller } -> final best copy.
 // nk_branch[3] / *nk_tail receive the kernel counts of the captured pieces.
 int run_graph(Ctx &c, Level L, int *nk_branch, int *nk_tail) {
     cudaStream_t s = c.stream;
@@ -535,6 +489,16 @@ int run_graph(Ctx &c, Level L, int *nk_branch, int *nk_tail) {
         wp.conditional.size = 1;
         cudaGraphNode_t wnode;
         if ((e = cudaGraphAddNode(&wnode, g, &start, nullptr, 1, &wp)) != cudaSuccess) { fail(e, "while node"); break; }
+        {
+            cudaKernelNodeParams kp{};
+            void *args[] = {&L};
+            kp.func = (void *)k_copy_best;
+            kp.gridDim = dim3(std::min(list_grid(), grid_for(L.g.n / 4 + 1, kTB)));
+            kp.blockDim = dim3(kTB);
+            kp.kernelParams = args;
+            cudaGraphNode_t fin;
+            if ((e = cudaGraphAddKernelNode(&fin, g, &wnode, 1, &kp)) != cudaSuccess) { fail(e, "final copy node"); break; }
+        }
         cudaGraph_t body = wp.conditional.phGraph_out[0];
         cudaGraphNodeParams sp{};
         sp.type = cudaGraphNodeTypeConditional;
@@ -742,7 +706,7 @@ int refine_level(Ctx &c, const DGraph &g, int32_t k, double eps, int32_t is_fine
         if (csize > 0) {
             c.launches += 1;  // the cluster kernel
         } else {
-            c.launches += 1;  // start kernel
+            c.launches += 2;  // start kernel, final copy
             for (int kd = 0; kd < 3; ++kd) c.launches += (int64_t)h.kcount[kd] * (nk_branch[kd] + nk_tail);
         }
     }
@@ -777,9 +741,8 @@ __global__ void k_set_epoch(Ctl *ctl, int32_t epoch, int32_t mode) {
     ctl->lp_epoch = epoch;
     ctl->mode = mode;
     ctl->it = 0;
-    ctl->nW = ctl->nWb = 0;
-    ctl->nX = ctl->nXb = ctl->nM = ctl->nMb = 0;
-    ctl->ncand = 0;
+    ctl->ticket = 0;
+    reset_counters(ctl);
 }
 
 __global__ void k_export_lp(Level L, uint8_t *inx, uint8_t *inm) {
@@ -831,7 +794,7 @@ int lp_pass(Ctx &c, const DGraph &g, int32_t k, const int32_t *part, const uint8
 __global__ void k_export_rb(Level L, int32_t *dest, int32_t *loss) {
     const int32_t it = L.ctl->it;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < L.g.n; v += (int64_t)gridDim.x * blockDim.x) {
-        if (dest) dest[v] = L.mstamp[v] == it ? L.nxt[v] : -1;
+        if (dest) dest[v] = L.mstamp[v] == it ? nxt_to(L.nxt[v]) : -1;
         if (loss && L.key[v] < 0) loss[v] = kNoneGain;
     }
 }
@@ -842,9 +805,8 @@ __global__ void __launch_bounds__(1024) k_rb_pass_init(Level L, const int64_t *c
     if (threadIdx.x == 0) {
         ctl->cut = *cut2 / 2;
         ctl->it = 0; ctl->mode = mode;
-        ctl->nW = ctl->nWb = 0;
-        ctl->nX = ctl->nXb = ctl->nM = ctl->nMb = 0;
-        ctl->ncand = 0;
+        ctl->ticket = 0;
+        reset_counters(ctl);
     }
     __syncthreads();
     compute_classes(L, sh);
@@ -885,7 +847,7 @@ int rebalance_pass(Ctx &c, const DGraph &g, int32_t k, double eps, int32_t stron
     JET_TRY(enqueue_rb(L, s, strong != 0, &nk));
     Ctl h;
     JET_TRY(read_ctl(c, L, h));
-    if (nmoves) *nmoves = (int64_t)h.nM + h.nMb;
+    if (nmoves) *nmoves = (int64_t)h.nM;
     if (ncand) *ncand = h.ncand;
     k_export_rb<<<grid_for(g.n, kTB, 4096), kTB, 0, s>>>(L, dest_out, loss_out);
     JET_CUDA_TRY(cudaGetLastError());
@@ -930,12 +892,10 @@ int lp_pass_in_scratch(Ctx &c, const DGraph &g, int32_t k, const int32_t *part, 
     L.k = k;
     L.part = const_cast<int32_t *>(part);   // read only in this pass
     L.nxt = take32(); L.prio = take32(); L.mstamp = take32(); L.lstamp = take32();
-    L.listX = take32(); L.listXb = take32(); L.listM = take32(); L.listMb = take32();
-    int32_t *bigv = take32();
+    L.listX = take32(); L.listM = take32();
     int32_t *tmp_pd = take32(), *tmp_gain = take32();
     L.ext = take32();
     L.listW = take32();
-    L.listWb = take32();
     L.ctl = reinterpret_cast<Ctl *>(p);
     p += align256c(sizeof(Ctl));
     int32_t *nbig_dev = reinterpret_cast<int32_t *>(p);
@@ -943,7 +903,6 @@ int lp_pass_in_scratch(Ctx &c, const DGraph &g, int32_t k, const int32_t *part, 
     L.pw = reinterpret_cast<int64_t *>(p);
     p += align256c((size_t)JET_MAX_K * 8);
     int64_t *cut2 = reinterpret_cast<int64_t *>(p);
-    L.bigv = bigv;
     fill_level_params(c, L, 1, 0);
     L.cq16 = (int32_t)llround(cval * 65536.0);
     L.abl = flags & (ABL_NO_LOCKS | ABL_NO_AFTERBURN | ABL_WEAK_AFTERBURN | ABL_BASELINE_LP);
@@ -957,7 +916,7 @@ int lp_pass_in_scratch(Ctx &c, const DGraph &g, int32_t k, const int32_t *part, 
         if (g.ew) k_cut_pw<true><<<gcut, kTB, (size_t)k * 8, s>>>(g, k, L.part, L.pw, cut2, L.ext, nullptr);
         else k_cut_pw<false><<<gcut, kTB, (size_t)k * 8, s>>>(g, k, L.part, L.pw, cut2, L.ext, nullptr);
     }
-    k_collect_big<<<grid_for(g.n, kTB), kTB, 0, s>>>(g, bigv, nbig_dev);
+    k_count_big<<<grid_for(g.n, kTB), kTB, 0, s>>>(g, nbig_dev);
     k_fill_i32<<<grid_for(g.n, kTB, 4096), kTB, 0, s>>>(L.mstamp, g.n, -2);
     k_fill_i32<<<grid_for(g.n, kTB, 4096), kTB, 0, s>>>(L.prio, g.n, kNoneGain);
     k_locks_from_mask<<<grid_for(g.n, kTB, 4096), kTB, 0, s>>>(locked, L.lstamp, g.n);
