@@ -555,98 +555,4 @@ int project(Ctx &c, int32_t n_fine, const int32_t *cmap, const int32_t *coarse_p
     return JET_OK;
 }
 
-// ---------------------------------------------------------------------------
-// greedy initial partition: order by (component's lowest id, BFS level from
-// it, id); P(v) = floor(k S(v) / W) with S(v) the weight before v.  One block.
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) k_initial_partition(DGraph g, int32_t k, int32_t *root, int32_t *dist,
-                                                            ulonglong2 *keys, int64_t P, int32_t *part) {
-    __shared__ long long sh[40];
-    const int32_t n = g.n;
-    for (int32_t v = threadIdx.x; v < n; v += blockDim.x) root[v] = v;
-    __syncthreads();
-    // components: minimum id by relaxation and pointer jumping
-    for (;;) {
-        int changed = 0;
-        for (int32_t v = threadIdx.x; v < n; v += blockDim.x) {
-            int32_t r = root[v];
-            int64_t e = ld_xadj(g.xadj, (int64_t)v + 1);
-            for (int64_t j = ld_xadj(g.xadj, v); j < e; ++j) {
-                int32_t ru = root[__ldg(g.adj + j)];
-                r = ru < r ? ru : r;
-            }
-            int32_t rr = root[r];
-            r = rr < r ? rr : r;
-            if (r < root[v]) { root[v] = r; changed = 1; }
-        }
-        if (!__syncthreads_or(changed)) break;
-    }
-    // BFS levels from each component's lowest id
-    for (int32_t v = threadIdx.x; v < n; v += blockDim.x) dist[v] = root[v] == v ? 0 : INT32_MAX;
-    __syncthreads();
-    for (int32_t l = 0;; ++l) {
-        int any = 0;
-        for (int32_t v = threadIdx.x; v < n; v += blockDim.x) {
-            if (dist[v] != l) continue;
-            int64_t e = ld_xadj(g.xadj, (int64_t)v + 1);
-            for (int64_t j = ld_xadj(g.xadj, v); j < e; ++j) {
-                int32_t u = __ldg(g.adj + j);
-                if (dist[u] == INT32_MAX) { dist[u] = l + 1; any = 1; }
-            }
-        }
-        if (!__syncthreads_or(any)) break;
-    }
-    // sort (root, dist, id)
-    for (int64_t i = threadIdx.x; i < P; i += blockDim.x) {
-        ulonglong2 kv;
-        if (i < n) { kv.x = ((unsigned long long)(uint32_t)root[i] << 32) | (uint32_t)dist[i]; kv.y = (unsigned long long)i; }
-        else { kv.x = ~0ull; kv.y = ~0ull; }
-        keys[i] = kv;
-    }
-    __syncthreads();
-    for (int64_t kk = 2; kk <= P; kk <<= 1) {
-        for (int64_t j = kk >> 1; j > 0; j >>= 1) {
-            for (int64_t i = threadIdx.x; i < P; i += blockDim.x) {
-                int64_t ixj = i ^ j;
-                if (ixj > i) {
-                    ulonglong2 a = keys[i], b = keys[ixj];
-                    bool agt = a.x > b.x || (a.x == b.x && a.y > b.y);
-                    bool up = (i & kk) == 0;
-                    if (agt == up) { keys[i] = b; keys[ixj] = a; }
-                }
-            }
-            __syncthreads();
-        }
-    }
-    // total weight, then prefix in sorted order
-    long long W = 0;
-    for (int32_t v = threadIdx.x; v < n; v += blockDim.x) W += g.vw[v];
-    W = block_sum_i64(W, sh);
-    long long carry = 0;
-    for (int64_t i0 = 0; i0 < n; i0 += blockDim.x) {
-        int64_t i = i0 + threadIdx.x;
-        int32_t v = i < n ? (int32_t)keys[i].y : 0;
-        long long w = i < n ? (long long)g.vw[v] : 0;
-        long long tot = 0;
-        long long S = carry + block_exscan_i64(w, sh, &tot);
-        if (i < n) part[v] = (int32_t)(((long long)k * S) / W);
-        carry += tot;
-    }
-}
-
-int initial_partition(Ctx &c, const DGraph &g, int32_t k, int32_t *part) {
-    cudaStream_t s = c.stream;
-    if (g.n == 0) return JET_OK;
-    int64_t P = pow2ceil(g.n);
-    DevBuf b;
-    JET_TRY(dev_alloc(b, (size_t)g.n * 8 + (size_t)P * 16 + 512, s));
-    int32_t *root = b.as<int32_t>(), *dist = root + g.n;
-    ulonglong2 *keys = reinterpret_cast<ulonglong2 *>((reinterpret_cast<uintptr_t>(dist + g.n) + 255) & ~uintptr_t(255));
-    k_initial_partition<<<1, 1024, 0, s>>>(g, k, root, dist, keys, P, part);
-    c.launches += 1;
-    JET_CUDA_TRY(cudaGetLastError());
-    JET_CUDA_TRY(cudaStreamSynchronize(s));
-    return JET_OK;
-}
-
 }  // namespace jet

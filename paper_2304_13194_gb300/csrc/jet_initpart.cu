@@ -1,0 +1,356 @@
+// Greedy initial partition of the coarsest graph (Alg. 1 InitialPartition;
+// the paper calls Metis there, Sec. 3 — this build grows parts greedily).
+//
+// Order the vertices by (lowest vertex id of their connected component, hop
+// distance from that vertex, vertex id) and cut the sequence into k pieces by
+// weight: P(v) = floor(k S(v) / W), S(v) the weight of the vertices before v.
+//
+// Device-wide, for any graph size (a stalled coarsening can leave millions of
+// vertices here):
+//  1. components by union-find, the larger root always hooked under the
+//     smaller, so every tree ends at its component's lowest id whatever the
+//     order of the hooks; then double-buffered pointer jumping (a fixed
+//     number of rounds, each reading one array and writing the other) gives
+//     every vertex its root exactly — path compression done in place would
+//     let a late halving store overwrite a finished root with an ancestor;
+//  2. breadth-first levels from all those roots at once, one frontier per
+//     level (each kernel launch takes one level and exits at once when the
+//     frontier is empty, so the host enqueues levels in batches);
+//  3. a stable LSD radix sort of the vertices (in id order) by the key
+//     (root, distance): the id order inside a key is kept;
+//  4. an exclusive scan of the weights in that order, then P.
+#include "jet_internal.cuh"
+
+#include <algorithm>
+
+namespace jet {
+
+namespace {
+
+constexpr int32_t kInf = INT32_MAX;
+constexpr int kSortItems = 8;                     // elements per thread and tile
+constexpr int kSortTile = kTB * kSortItems;       // elements per tile
+constexpr int kRadixBits = 8;
+constexpr int kRadix = 1 << kRadixBits;
+constexpr int kBfsBatch = 16;                     // levels enqueued between host checks
+constexpr int kFindCap = 1 << 26;                 // bound of every union-find loop
+
+struct IpCtl {
+    int32_t size[2];     // frontier lengths, by level parity
+    int32_t level;       // level the next k_bfs_level launch expands
+    int32_t ticket;      // blocks of the current launch that finished
+    int32_t error;       // a union-find loop hit kFindCap
+    int32_t pad;
+    int64_t total;       // scan total (W)
+};
+
+// Root of x with path halving.  parent[] only ever decreases (parent[x] <= x),
+// so the walk is strictly decreasing and ends; the cap is a safety net.
+__device__ __forceinline__ int32_t uf_find(int32_t *parent, int32_t x, int32_t *err) {
+    for (int i = 0; i < kFindCap; ++i) {
+        int32_t p = parent[x];
+        if (p == x) return x;
+        int32_t gp = parent[p];
+        if (gp != p) parent[x] = gp;
+        x = gp;
+    }
+    *err = 1;
+    return x;
+}
+
+__global__ void k_uf_init(int32_t n, int32_t *parent) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+        parent[v] = (int32_t)v;
+}
+
+// One warp per vertex v; every edge {u, v} with u < v hooks the two roots,
+// the larger under the smaller (a failed CAS means another hook lowered the
+// root; retry from the new one).
+__global__ void __launch_bounds__(kTB) k_uf_hook(DGraph g, int32_t *parent, IpCtl *ctl) {
+    const int warps = blockDim.x >> 5;
+    const unsigned lane = lane_id();
+    int32_t err = 0;
+    for (int64_t v = (int64_t)blockIdx.x * warps + (threadIdx.x >> 5); v < g.n; v += (int64_t)gridDim.x * warps) {
+        int64_t beg = ld_xadj(g.xadj, v), end = ld_xadj(g.xadj, v + 1);
+        for (int64_t j = beg + lane; j < end; j += 32) {
+            int32_t u = __ldg(g.adj + j);
+            if (u >= v) continue;
+            int32_t ru = uf_find(parent, u, &err), rv = uf_find(parent, (int32_t)v, &err);
+            for (int i = 0; i < kFindCap && ru != rv; ++i) {
+                int32_t hi = ru > rv ? ru : rv, lo = ru > rv ? rv : ru;
+                int32_t old = atomicCAS(&parent[hi], hi, lo);
+                if (old == hi) break;
+                ru = uf_find(parent, old, &err);
+                rv = uf_find(parent, lo, &err);
+                if (i + 1 == kFindCap) err = 1;
+            }
+        }
+    }
+    if (err) ctl->error = 1;
+}
+
+// One round of pointer jumping: out[v] = in[in[v]] (ancestors only, so after
+// ceil(log2 n) rounds every entry is its tree's root).
+__global__ void k_uf_jump(int32_t n, const int32_t *in, int32_t *out) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+        out[v] = in[in[v]];
+}
+
+// Distance 0 at the roots, which form the first frontier.
+__global__ void k_uf_finish(int32_t n, const int32_t *root, int32_t *dist, int32_t *front0, IpCtl *ctl) {
+    for (int64_t v0 = (int64_t)blockIdx.x * blockDim.x; v0 < n; v0 += (int64_t)gridDim.x * blockDim.x) {
+        int64_t v = v0 + threadIdx.x;
+        bool is_root = false;
+        if (v < n) {
+            is_root = root[v] == v;
+            dist[v] = is_root ? 0 : kInf;
+        }
+        int slot = warp_append(&ctl->size[0], is_root);
+        if (is_root) front0[slot] = (int32_t)v;
+    }
+}
+
+// One breadth-first level: the frontier of level l (parity l & 1), one warp
+// per vertex; a neighbour is claimed for level l + 1 by a CAS on its
+// distance.  The last block to finish closes the level.
+__global__ void __launch_bounds__(kTB) k_bfs_level(DGraph g, int32_t *dist, int32_t *front0, int32_t *front1,
+                                                   IpCtl *ctl) {
+    const int32_t l = ctl->level;
+    const int32_t cur = ctl->size[l & 1];
+    if (cur == 0) return;                        // search finished: every block leaves
+    const int32_t *in = (l & 1) ? front1 : front0;
+    int32_t *out = (l & 1) ? front0 : front1;
+    int32_t *out_size = &ctl->size[(l + 1) & 1];
+    const int warps = blockDim.x >> 5;
+    const unsigned lane = lane_id();
+    for (int64_t w0 = (int64_t)blockIdx.x * warps; w0 < cur; w0 += (int64_t)gridDim.x * warps) {
+        int64_t w = w0 + (threadIdx.x >> 5);
+        int64_t beg = 0, end = 0;
+        if (w < cur) {
+            int32_t v = in[w];
+            beg = ld_xadj(g.xadj, v);
+            end = ld_xadj(g.xadj, (int64_t)v + 1);
+        }
+        for (int64_t j0 = beg; j0 < end; j0 += 32) {   // whole warp: same row
+            int64_t j = j0 + lane;
+            bool claim = false;
+            int32_t u = -1;
+            if (j < end) {
+                u = __ldg(g.adj + j);
+                claim = dist[u] == kInf && atomicCAS(&dist[u], kInf, l + 1) == kInf;
+            }
+            int slot = warp_append(out_size, claim);
+            if (claim) out[slot] = u;
+        }
+    }
+    __shared__ int s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int t = atomicAdd(&ctl->ticket, 1);
+        s_last = t == (int)gridDim.x - 1;
+        if (s_last) {
+            ctl->ticket = 0;
+            ctl->size[l & 1] = 0;
+            ctl->level = l + 1;
+        }
+    }
+}
+
+// ---- stable LSD radix sort of (key, vertex) -------------------------------
+__global__ void k_sort_init(int32_t n, const int32_t *root, const int32_t *dist, int dbits, uint64_t *key,
+                            int32_t *val) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        key[v] = ((uint64_t)(uint32_t)root[v] << dbits) | (uint64_t)(uint32_t)dist[v];
+        val[v] = (int32_t)v;
+    }
+}
+
+// Digit histogram of each tile, stored digit-major: hist[d * ntiles + tile].
+__global__ void __launch_bounds__(kTB) k_sort_hist(const uint64_t *key, int64_t n, int shift, int64_t ntiles,
+                                                   int64_t *hist) {
+    __shared__ int32_t h[kRadix];
+    for (int i = threadIdx.x; i < kRadix; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kSortTile;
+#pragma unroll
+    for (int i = 0; i < kSortItems; ++i) {
+        int64_t e = base + (int64_t)i * blockDim.x + threadIdx.x;
+        if (e < n) atomicAdd(&h[(int)((key[e] >> shift) & (kRadix - 1))], 1);
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < kRadix; d += blockDim.x) hist[(int64_t)d * ntiles + blockIdx.x] = h[d];
+}
+
+struct HistVal {
+    const int64_t *hist;
+    __device__ int64_t operator()(int64_t i) const { return hist[i]; }
+};
+
+// Scatter of one tile, chunk after chunk of blockDim elements in index order;
+// inside a chunk, warp after warp and lane after lane: the rank of an element
+// among the tile's equal digits keeps the input order (stable).
+__global__ void __launch_bounds__(kTB) k_sort_scatter(const uint64_t *key_in, const int32_t *val_in, uint64_t *key_out,
+                                                      int32_t *val_out, int64_t n, int shift, int64_t ntiles,
+                                                      const int64_t *off) {
+    __shared__ int32_t wcnt[kTB / 32][kRadix];    // per-warp digit counts, then warp prefixes
+    __shared__ int32_t ctot[kRadix];              // this chunk's count per digit
+    __shared__ int64_t run[kRadix];               // tile offset + elements placed so far, per digit
+    const int64_t base = (int64_t)blockIdx.x * kSortTile;
+    const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    const int nwarps = blockDim.x >> 5;
+    for (int d = threadIdx.x; d < kRadix; d += blockDim.x) run[d] = off[(int64_t)d * ntiles + blockIdx.x];
+    for (int i = 0; i < kSortItems; ++i) {
+        for (int t = threadIdx.x; t < nwarps * kRadix; t += blockDim.x) wcnt[t / kRadix][t % kRadix] = 0;
+        __syncthreads();
+        const int64_t e = base + (int64_t)i * blockDim.x + threadIdx.x;
+        const bool ok = e < n;
+        const uint64_t k = ok ? key_in[e] : 0;
+        const int32_t v = ok ? val_in[e] : 0;
+        const int d = ok ? (int)((k >> shift) & (kRadix - 1)) : -1;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const int rank = __popc(peers & lt);
+        if (ok && rank == 0) wcnt[warp][d] = __popc(peers);
+        __syncthreads();
+        for (int dd = threadIdx.x; dd < kRadix; dd += blockDim.x) {
+            int32_t acc = 0;
+            for (int w = 0; w < nwarps; ++w) {
+                int32_t c = wcnt[w][dd];
+                wcnt[w][dd] = acc;
+                acc += c;
+            }
+            ctot[dd] = acc;
+        }
+        __syncthreads();
+        if (ok) {
+            const int64_t pos = run[d] + wcnt[warp][d] + rank;
+            key_out[pos] = k;
+            val_out[pos] = v;
+        }
+        __syncthreads();
+        for (int dd = threadIdx.x; dd < kRadix; dd += blockDim.x) run[dd] += ctot[dd];
+        __syncthreads();
+    }
+}
+
+// Weight of the vertex at sorted position i (unit weights when vw is null).
+struct SortedWeight {
+    const int32_t *val;
+    const int32_t *vw;
+    __device__ int64_t operator()(int64_t i) const { return vw ? vw[val[i]] : 1; }
+};
+
+__global__ void k_assign(int32_t n, const int32_t *val, const int64_t *S, const IpCtl *ctl, int32_t k, int32_t *part) {
+    const long long W = ctl->total;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        part[val[i]] = (int32_t)(((long long)k * S[i]) / W);
+}
+
+int bits_for(int64_t x) {   // bits to hold 0..x
+    int b = 0;
+    while (b < 63 && (x >> b) != 0) ++b;
+    return b;
+}
+
+}  // namespace
+
+int initial_partition(Ctx &c, const DGraph &g, int32_t k, int32_t *part) {
+    cudaStream_t s = c.stream;
+    const int64_t n = g.n;
+    if (n == 0) return JET_OK;
+    const size_t nn = (size_t)n;
+    const int64_t ntiles = (n + kSortTile - 1) / kSortTile;
+    const int64_t nhist = ntiles * kRadix;
+    auto a256 = [](size_t x) { return (x + 255) & ~size_t(255); };
+    // parent, root, dist, front0, front1 | key x2 | val x2 | S | hist, off | scan tiles | ctl
+    const size_t bytes = 5 * a256(nn * 4) + 2 * a256(nn * 8) + 2 * a256(nn * 4) + a256(nn * 8) +
+                         2 * a256((size_t)nhist * 8) + a256((size_t)(scan_tiles_for(std::max(nhist, n)) + 1) * 8) +
+                         a256(sizeof(IpCtl));
+    DevBuf buf;
+    JET_TRY(dev_alloc(buf, bytes, s));
+    char *p = buf.as<char>();
+    auto take = [&](size_t b) { char *r = p; p += a256(b); return r; };
+    int32_t *parent = reinterpret_cast<int32_t *>(take(nn * 4));
+    int32_t *rootb = reinterpret_cast<int32_t *>(take(nn * 4));
+    int32_t *dist = reinterpret_cast<int32_t *>(take(nn * 4));
+    int32_t *front0 = reinterpret_cast<int32_t *>(take(nn * 4));
+    int32_t *front1 = reinterpret_cast<int32_t *>(take(nn * 4));
+    uint64_t *key0 = reinterpret_cast<uint64_t *>(take(nn * 8));
+    uint64_t *key1 = reinterpret_cast<uint64_t *>(take(nn * 8));
+    int32_t *val0 = reinterpret_cast<int32_t *>(take(nn * 4));
+    int32_t *val1 = reinterpret_cast<int32_t *>(take(nn * 4));
+    int64_t *S = reinterpret_cast<int64_t *>(take(nn * 8));
+    int64_t *hist = reinterpret_cast<int64_t *>(take((size_t)nhist * 8));
+    int64_t *off = reinterpret_cast<int64_t *>(take((size_t)nhist * 8));
+    int64_t *scan_scr = reinterpret_cast<int64_t *>(take((size_t)(scan_tiles_for(std::max(nhist, n)) + 1) * 8));
+    IpCtl *ctl = reinterpret_cast<IpCtl *>(take(sizeof(IpCtl)));
+    JET_CUDA_TRY(cudaMemsetAsync(ctl, 0, sizeof(IpCtl), s));
+    const int gv = std::min(num_sms() * 8, grid_for(n, kTB));
+    const int gw = std::min(num_sms() * 8, grid_for(n, kTB / 32));
+
+    // 1. components
+    k_uf_init<<<gv, kTB, 0, s>>>((int32_t)n, parent);
+    k_uf_hook<<<gw, kTB, 0, s>>>(g, parent, ctl);
+    int32_t *ra = parent, *rb = rootb;
+    const int rounds = bits_for(n);
+    for (int r = 0; r < rounds; ++r) {
+        k_uf_jump<<<gv, kTB, 0, s>>>((int32_t)n, ra, rb);
+        std::swap(ra, rb);
+    }
+    const int32_t *root = ra;
+    k_uf_finish<<<gv, kTB, 0, s>>>((int32_t)n, root, dist, front0, ctl);
+    c.launches += 3 + rounds;
+    JET_CUDA_TRY(cudaGetLastError());
+
+    // 2. breadth-first levels, kBfsBatch launches between checks
+    const int gb = num_sms() * 4;
+    for (int64_t batch = 0;; ++batch) {
+        for (int i = 0; i < kBfsBatch; ++i) k_bfs_level<<<gb, kTB, 0, s>>>(g, dist, front0, front1, ctl);
+        c.launches += kBfsBatch;
+        JET_CUDA_TRY(cudaGetLastError());
+        IpCtl h;
+        JET_CUDA_TRY(cudaMemcpyAsync(&h, ctl, sizeof(IpCtl), cudaMemcpyDeviceToHost, s));
+        JET_CUDA_TRY(cudaStreamSynchronize(s));
+        if (h.error) {
+            record_error("initial partition: union-find step limit reached");
+            return JET_ETIMEOUT;
+        }
+        if (h.size[0] == 0 && h.size[1] == 0) break;
+        if (batch * kBfsBatch > n + kBfsBatch) {     // more levels than vertices: impossible
+            record_error("initial partition: breadth-first search did not end");
+            return JET_ETIMEOUT;
+        }
+    }
+    IpCtl h;
+    JET_CUDA_TRY(cudaMemcpyAsync(&h, ctl, sizeof(IpCtl), cudaMemcpyDeviceToHost, s));
+    JET_CUDA_TRY(cudaStreamSynchronize(s));
+    const int32_t maxdist = std::max(h.level - 1, 0);   // deepest level reached
+
+    // 3. stable sort of the vertices (in id order) by (root, distance)
+    const int dbits = bits_for(maxdist);
+    const int kbits = bits_for(n - 1) + dbits;
+    k_sort_init<<<gv, kTB, 0, s>>>((int32_t)n, root, dist, dbits, key0, val0);
+    c.launches += 1;
+    uint64_t *kin = key0, *kout = key1;
+    int32_t *vin = val0, *vout = val1;
+    for (int shift = 0; shift < kbits; shift += kRadixBits) {
+        k_sort_hist<<<(unsigned)ntiles, kTB, 0, s>>>(kin, n, shift, ntiles, hist);
+        JET_TRY(device_exscan(HistVal{hist}, nhist, off, &ctl->total, scan_scr, s));
+        k_sort_scatter<<<(unsigned)ntiles, kTB, 0, s>>>(kin, vin, kout, vout, n, shift, ntiles, off);
+        c.launches += 5;
+        JET_CUDA_TRY(cudaGetLastError());
+        std::swap(kin, kout);
+        std::swap(vin, vout);
+    }
+
+    // 4. weights before each vertex in that order, then P
+    JET_TRY(device_exscan(SortedWeight{vin, g.vw}, n, S, &ctl->total, scan_scr, s));
+    k_assign<<<gv, kTB, 0, s>>>((int32_t)n, vin, S, ctl, k, part);
+    c.launches += 4;
+    JET_CUDA_TRY(cudaGetLastError());
+    JET_CUDA_TRY(cudaStreamSynchronize(s));
+    return JET_OK;
+}
+
+}  // namespace jet

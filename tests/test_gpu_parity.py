@@ -187,6 +187,34 @@ def test_initial_partition_matches_oracle(ctx, name, g, unit):
         assert (_np(ctx.initial_partition(g.xadj, g.adjncy, vw, k)) == oracle.initial_partition(og, k)).all()
 
 
+def _initpart_mix():
+    """Many components of every kind: isolated vertices, a long path (more
+    breadth-first levels than one batch of launches), a grid, an R-MAT graph
+    with its own isolated vertices; ids interleaved by a permutation so that
+    components are not contiguous; > 2 sort tiles and > 2 radix passes."""
+    path = graphgen.from_edges(3000, [(i, i + 1) for i in range(2999)], vw=(1, 3), seed=2)
+    iso = graphgen.Graph(500, np.zeros(501, np.int64), np.zeros(0, np.int32), np.full(500, 2, np.int32),
+                         np.zeros(0, np.int32))
+    u = graphgen.disjoint_union(path, iso, graphgen.grid2d(50, 40, vw=(1, 4)), graphgen.rmat(13, seed=3, vw=(1, 2)))
+    perm = np.random.default_rng(7).permutation(u.n).astype(np.int64)
+    src = np.repeat(np.arange(u.n, dtype=np.int64), np.diff(u.xadj))
+    edges = np.stack([perm[src], perm[u.adjncy.astype(np.int64)]], 1)
+    edges = edges[edges[:, 0] < edges[:, 1]]
+    g = graphgen.from_edges(u.n, edges, seed=4)
+    vw = np.empty(u.n, np.int32)
+    vw[perm] = u.vwgt
+    return graphgen.Graph(g.n, g.xadj, g.adjncy, vw, g.adjwgt, "initpart_mix")
+
+
+def test_initial_partition_many_components_and_levels(ctx):
+    g = _initpart_mix()
+    for k in (3, 64, 1000):
+        ref = oracle.initial_partition(g, k)
+        assert (_np(ctx.initial_partition(g.xadj, g.adjncy, g.vwgt, k)) == ref).all()
+    ref = oracle.initial_partition(graphgen.Graph(g.n, g.xadj, g.adjncy, None, None), 16)
+    assert (_np(ctx.initial_partition(g.xadj, g.adjncy, None, 16)) == ref).all()
+
+
 @pytest.mark.parametrize("name,g,unit", graphs_small(), ids=[x[0] for x in graphs_small()])
 def test_coarsen_hierarchy_matches_oracle(ctx, name, g, unit):
     vw, ew = _vw(g, unit), _ew(g, unit)
@@ -409,6 +437,16 @@ def test_partition_grid_128cube_k64_full_size(ctx):
     part, cut, st = _check_partition(ctx, g, False, 64, seed=1)
     L, _ = oracle.limit(int(g.vwgt.sum()), 64, 0.03)
     assert st.max_part_w <= L
+
+
+def test_initial_partition_rmat_s22_full_size(ctx):
+    """R-MAT scale 22 (the power-law workload, 4.2M vertices with its isolated
+    vertices kept): the greedy initial partition of the whole graph, as it runs
+    when coarsening stalls at the first level."""
+    g = graphgen.rmat(22, seed=1)
+    og = graphgen.Graph(g.n, g.xadj, g.adjncy, None, None)
+    for k in (2, 256):
+        assert (_np(ctx.initial_partition(g.xadj, g.adjncy, None, k)) == oracle.initial_partition(og, k)).all()
 
 
 def test_partition_rmat_s16_k64(ctx):
