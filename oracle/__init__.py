@@ -28,6 +28,8 @@ _lib = None
 
 KIND_LP, KIND_RW, KIND_RS = 0, 1, 2
 ABL_NO_LOCKS, ABL_NO_AFTERBURN, ABL_WEAK_AFTERBURN, ABL_BASELINE_LP = 1, 2, 4, 8
+NO_TWO_HOP = 16          # coarsening: heavy-edge matching only (Sec. 3.1)
+MATCHMAKER_MAX_DEG = 1024
 NONE = np.iinfo(np.int64).min  # the "negative infinity" gain
 
 
@@ -105,6 +107,8 @@ def _load():
                                     i32, vp, vp, vp, vp, vp, vp, vp]
             L.or_refine.restype = ctypes.c_int
             L.or_hem.argtypes = [G, u64, i32, i32, vp]; L.or_hem.restype = i64
+            L.or_two_hop.argtypes = [G, vp, vp]; L.or_two_hop.restype = i64
+            L.or_twin_key.argtypes = [G, i32]; L.or_twin_key.restype = u64
             L.or_coarse_map.argtypes = [i32, vp, vp]; L.or_coarse_map.restype = i32
             L.or_contract.argtypes = [G, vp, i32, vp, vp, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p)]
             L.or_initial_partition.argtypes = [G, i32, vp]
@@ -260,6 +264,21 @@ def hem(g, seed: int = 1, level: int = 0, rounds: int = 8) -> np.ndarray:
     gr = _GraphRef(g); mate = np.zeros(gr.n, np.int32)
     _load().or_hem(gr.p, seed, level, rounds, mate.ctypes.data)
     return mate
+
+
+def two_hop(g, mate) -> tuple[np.ndarray, list[int]]:
+    """Two-hop matching after heavy-edge matching (Sec. 3.1 reading): leaves,
+    twins, relatives, each stage while > 25% of vertices are unmatched.
+    Returns the new mate array and the vertices matched by each stage."""
+    gr = _GraphRef(g); m = _i32(mate).copy(); added = np.zeros(3, np.int64)
+    _load().or_two_hop(gr.p, m.ctypes.data, added.ctypes.data)
+    return m, [int(x) for x in added]
+
+
+def twin_key(g, v: int) -> int:
+    """Order-free neighbourhood hash that identifies twins."""
+    gr = _GraphRef(g)
+    return int(_load().or_twin_key(gr.p, int(v)))
 
 
 def coarse_map(mate) -> tuple[np.ndarray, int]:

@@ -58,6 +58,8 @@ typedef struct {
 #define OR_ABL_NO_AFTERBURN  2 /* M = X (no second filter) */
 #define OR_ABL_WEAK_AFTERBURN 4 /* first filter keeps only F >= 0 */
 #define OR_ABL_BASELINE_LP   8 /* baseline LP: move iff F > 0, no afterburner, no locks */
+/* Coarsening switch (Sec. 3.1): heavy-edge matching only, no two-hop matches */
+#define OR_NO_TWO_HOP       16
 
 typedef struct {
     int32_t levels;
@@ -561,6 +563,101 @@ int64_t or_hem(const or_graph *g, uint64_t seed, int32_t level, int32_t rounds, 
     return matched;
 }
 
+/*
+ * Two-hop matching (Sec. 3.1; details are in the paper's references, not in
+ * the paper).  Readings, all deterministic:
+ *  - it runs after heavy-edge matching, stage by stage (leaves, twins,
+ *    relatives), each stage only while more than 25% of the vertices are
+ *    unmatched (4 u > n);
+ *  - leaves: unmatched vertices of degree 1, grouped by their neighbour;
+ *  - twins: unmatched vertices grouped by their neighbourhood, identified by
+ *    the order-free hash  splitmix64(deg ^ TWIN_DEG) + sum_u splitmix64(u ^
+ *    TWIN_SALT)  (mod 2^64; the all-ones value is mapped to all-ones - 1),
+ *    degree 0 included (isolated vertices are twins of each other);
+ *  - relatives: unmatched vertices grouped by their matchmaker, the
+ *    lowest-id neighbour that is matched when the stage starts and has
+ *    degree <= OR_MATCHMAKER_MAX_DEG ("very high degree" vertices do not
+ *    act as matchmakers);
+ *  - inside a group, vertices are paired in ascending id: the 1st with the
+ *    2nd, the 3rd with the 4th, ...; an odd last one stays unmatched.
+ * added[s] (optional) receives the vertices matched by stage s.
+ */
+#define OR_MATCHMAKER_MAX_DEG 1024
+#define OR_TWIN_SALT 0x2545F4914F6CDD1DULL
+#define OR_TWIN_DEG 0x9FB21C651E98DF25ULL
+
+typedef struct { uint64_t key; int32_t v; } or_pk;
+
+static int pk_cmp(const void *a, const void *b)
+{
+    const or_pk *x = (const or_pk *)a, *y = (const or_pk *)b;
+    if (x->key != y->key) return x->key < y->key ? -1 : 1;
+    return (x->v > y->v) - (x->v < y->v);
+}
+
+static int64_t pair_groups(or_pk *c, int64_t nc, int32_t *mate)
+{
+    qsort(c, (size_t)nc, sizeof(or_pk), pk_cmp);
+    int64_t added = 0;
+    for (int64_t s = 0; s < nc;) {
+        int64_t e = s;
+        while (e < nc && c[e].key == c[s].key) ++e;
+        for (int64_t i = s; i + 1 < e; i += 2) {
+            mate[c[i].v] = c[i + 1].v;
+            mate[c[i + 1].v] = c[i].v;
+            added += 2;
+        }
+        s = e;
+    }
+    return added;
+}
+
+uint64_t or_twin_key(const or_graph *g, int32_t v)
+{
+    int64_t deg = g->xadj[v + 1] - g->xadj[v];
+    uint64_t h = or_splitmix64((uint64_t)deg ^ OR_TWIN_DEG);
+    for (int64_t j = g->xadj[v]; j < g->xadj[v + 1]; ++j) h += or_splitmix64((uint64_t)(uint32_t)g->adjncy[j] ^ OR_TWIN_SALT);
+    return h == ~0ULL ? ~0ULL - 1 : h;
+}
+
+int64_t or_two_hop(const or_graph *g, int32_t *mate, int64_t *added)
+{
+    int64_t n = g->n, total = 0;
+    or_pk *c = (or_pk *)malloc(sizeof(or_pk) * (size_t)(n > 0 ? n : 1));
+    for (int s = 0; s < 3; ++s) {
+        if (added) added[s] = 0;
+        int64_t un = 0;
+        for (int64_t v = 0; v < n; ++v) un += mate[v] < 0;
+        if (4 * un <= n) break;
+        int64_t nc = 0;
+        for (int64_t v = 0; v < n; ++v) {
+            if (mate[v] >= 0) continue;
+            int64_t deg = g->xadj[v + 1] - g->xadj[v];
+            if (s == 0) {
+                if (deg != 1) continue;
+                c[nc].key = (uint64_t)(uint32_t)g->adjncy[g->xadj[v]];
+            } else if (s == 1) {
+                c[nc].key = or_twin_key(g, (int32_t)v);
+            } else {
+                int32_t mm = -1;
+                for (int64_t j = g->xadj[v]; j < g->xadj[v + 1]; ++j) {
+                    int32_t u = g->adjncy[j];
+                    if (mate[u] >= 0 && g->xadj[u + 1] - g->xadj[u] <= OR_MATCHMAKER_MAX_DEG && (mm < 0 || u < mm)) mm = u;
+                }
+                if (mm < 0) continue;
+                c[nc].key = (uint64_t)(uint32_t)mm;
+            }
+            c[nc].v = (int32_t)v;
+            ++nc;
+        }
+        int64_t a = pair_groups(c, nc, mate);
+        if (added) added[s] = a;
+        total += a;
+    }
+    free(c);
+    return total;
+}
+
 /* Coarse mapping C (input of Alg. 2): each matched pair and each unmatched
  * vertex becomes one coarse vertex, numbered in the order of the smaller
  * fine id of the pair.  Returns n_c. */
@@ -714,7 +811,8 @@ int32_t or_coarsen_target(int32_t k, const or_opts *o)
 }
 
 /*
- * MLCoarsen (Alg. 1): repeat matching + contraction while the current graph
+ * MLCoarsen (Alg. 1): repeat matching (heavy-edge, then two-hop unless
+ * OR_NO_TWO_HOP) + contraction while the current graph
  * has more than T vertices (T = max(8k, 256), reading of Sec. 3's "between 4k
  * and 8k") and fewer than max_levels levels exist.  A level that would keep
  * more than 95% of the vertices is not added (coarsening stalled; reading).
@@ -738,6 +836,7 @@ or_hier *or_coarsen(const or_graph *g, int32_t k, uint64_t seed, const or_opts *
         int32_t *mate = (int32_t *)malloc(sizeof(int32_t) * (size_t)(gi.n > 0 ? gi.n : 1));
         int32_t *cmap = (int32_t *)malloc(sizeof(int32_t) * (size_t)(gi.n > 0 ? gi.n : 1));
         or_hem(&gi, seed, i, o->hem_rounds, mate);
+        if (!(o->flags & OR_NO_TWO_HOP)) or_two_hop(&gi, mate, NULL);
         int32_t nc = or_coarse_map(gi.n, mate, cmap);
         free(mate);
         if ((int64_t)100 * nc > (int64_t)95 * gi.n) { free(cmap); break; }
