@@ -71,6 +71,7 @@ extern "C" {
 #define JET_FLAG_NO_AFTERBURN 32u  /*   M = X (skip the second filter) */
 #define JET_FLAG_WEAK_AFTERBURN 64u/*   first filter keeps only F >= 0 */
 #define JET_FLAG_BASELINE_LP 128u  /*   baseline LP: move iff F > 0, no afterburner, no locks */
+#define JET_FLAG_NO_TWO_HOP 256u   /* coarsening: heavy-edge matching only (no two-hop matches, Sec. 3.1) */
 
 /* Hyper-parameters the paper names (defaults from jet_options_default):
  *   c_fine = 0.25, c_coarse = 0.75  first-filter ratio c (Sec. 4.1.2, Eq. gainconn_filter);
@@ -244,6 +245,19 @@ int jet_lp_pass_noalloc(jet_ctx *ctx, int32_t n, const int64_t *xadj, const int3
  * graph: mate_out device int32[n] (partner or -1).  level salts the hash. */
 int jet_hem(jet_ctx *ctx, int32_t n, const int64_t *xadj, const int32_t *adjncy,
             const int32_t *adjwgt, uint64_t seed, int32_t level, int32_t rounds, int32_t *mate_out);
+
+/* Two-hop matching of Sec. 3.1, applied to a matching (mate_inout: device
+ * int32[n], partner or -1, e.g. the output of jet_hem) the way jet_coarsen
+ * does after heavy-edge matching: leaves (degree-1 vertices with the same
+ * neighbour), then twins (same neighbourhood, identified by an order-free hash
+ * of the neighbour ids; isolated vertices included), then relatives (same
+ * matchmaker: the lowest-id neighbour that is matched when the stage starts
+ * and has degree <= 1024); each stage only while more than 25% of the
+ * vertices are unmatched; inside a group, pairs in ascending id.  added_out
+ * (host int64[3], may be NULL) receives the vertices each stage matched.
+ * Edge weights play no part.  JET_EINVAL for a bad argument. */
+int jet_two_hop(jet_ctx *ctx, int32_t n, const int64_t *xadj, const int32_t *adjncy, int32_t *mate_inout,
+                int64_t *added_out);
 
 /* InitialPartition of Alg. 1 (the greedy graph growing described at
  * jet_uncoarsen) on one graph: part_out device int32[n]. */

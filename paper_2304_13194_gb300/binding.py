@@ -19,6 +19,7 @@ JET_MAX_K = 1024
 JET_MAX_LEVELS = 64
 FLAG_VALIDATE, FLAG_HOSTLOOP, FLAG_PROFILE = 1, 2, 4
 FLAG_NO_LOCKS, FLAG_NO_AFTERBURN, FLAG_WEAK_AFTERBURN, FLAG_BASELINE_LP = 16, 32, 64, 128
+FLAG_NO_TWO_HOP = 256
 KIND_LP, KIND_RW, KIND_RS = 0, 1, 2
 NONE_GAIN = -(2 ** 31)
 
@@ -26,7 +27,7 @@ EXPORTED_SYMBOLS = [
     "jet_options_default", "jet_ctx_create", "jet_ctx_destroy", "jet_coarsen", "jet_hier_destroy",
     "jet_hier_info", "jet_hier_level", "jet_uncoarsen", "jet_refine", "jet_last_trace", "jet_partition",
     "jet_partition_host", "jet_cut", "jet_lp_pass", "jet_rebalance_pass", "jet_hem", "jet_initial_partition",
-    "jet_status_string", "jet_last_error", "jet_lp_pass_noalloc",
+    "jet_status_string", "jet_last_error", "jet_lp_pass_noalloc", "jet_two_hop",
 ]
 JET_NOALLOC_MAX_N = 262144
 
@@ -147,6 +148,7 @@ def load_library(path: str | None = None):
             "jet_rebalance_pass": (ctypes.c_int, [vp, i32, vp, vp, vp, vp, i32, f64, i32, u64, i32, vp, vp, vp,
                                                   P(i64), P(i64)]),
             "jet_hem": (ctypes.c_int, [vp, i32, vp, vp, vp, u64, i32, i32, vp]),
+            "jet_two_hop": (ctypes.c_int, [vp, i32, vp, vp, vp, vp]),
             "jet_initial_partition": (ctypes.c_int, [vp, i32, vp, vp, vp, i32, vp]),
             "jet_status_string": (ctypes.c_char_p, [ctypes.c_int]),
             "jet_last_error": (ctypes.c_char_p, []),
@@ -429,6 +431,15 @@ class Context:
         _check(load_library().jet_hem(self._h, n, _ptr(xadj), _ptr(adjncy), _ptr(adjwgt), int(seed), int(level),
                                       int(rounds), _ptr(mate)), "jet_hem")
         return mate
+
+    def two_hop(self, xadj, adjncy, mate):
+        """jet_two_hop on a copy of ``mate``: returns (mate, vertices matched per stage)."""
+        torch = _torch()
+        n, xadj, adjncy, _, _ = self._graph(xadj, adjncy, None, None)
+        m = self._dev(mate, torch.int32, "mate", n).clone()
+        added = (ctypes.c_int64 * 3)()
+        _check(load_library().jet_two_hop(self._h, n, _ptr(xadj), _ptr(adjncy), _ptr(m), added), "jet_two_hop")
+        return m, [int(x) for x in added]
 
     def initial_partition(self, xadj, adjncy, vwgt, k):
         n, xadj, adjncy, vwgt, _ = self._graph(xadj, adjncy, vwgt, None)

@@ -553,6 +553,20 @@ int jet_hem(jet_ctx *ctx, int32_t n, const int64_t *xadj, const int32_t *adjncy,
     return hem(c, g, seed, level, rounds, mate_out);
 }
 
+int jet_two_hop(jet_ctx *ctx, int32_t n, const int64_t *xadj, const int32_t *adjncy, int32_t *mate_inout,
+                int64_t *added_out) {
+    if (!ctx || (n > 0 && !mate_inout)) return JET_EINVAL;
+    Ctx &c = ctx->c;
+    JET_TRY(use_device(c));
+    DGraph g;
+    DevBuf ones;
+    JET_TRY(prepare_graph(c, n, xadj, adjncy, nullptr, nullptr, g, ones, false));
+    int64_t added[3] = {0, 0, 0};
+    JET_TRY(two_hop(c, g, mate_inout, added));
+    if (added_out) memcpy(added_out, added, sizeof(added));
+    return JET_OK;
+}
+
 int jet_initial_partition(jet_ctx *ctx, int32_t n, const int64_t *xadj, const int32_t *adjncy, const int32_t *vwgt,
                           int32_t k, int32_t *part_out) {
     if (!ctx || bad_k_eps(k, 0.0) || (n > 0 && !part_out)) return JET_EINVAL;

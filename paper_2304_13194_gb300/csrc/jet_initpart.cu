@@ -28,10 +28,6 @@ namespace jet {
 namespace {
 
 constexpr int32_t kInf = INT32_MAX;
-constexpr int kSortItems = 8;                     // elements per thread and tile
-constexpr int kSortTile = kTB * kSortItems;       // elements per tile
-constexpr int kRadixBits = 8;
-constexpr int kRadix = 1 << kRadixBits;
 constexpr int kBfsBatch = 16;                     // levels enqueued between host checks
 constexpr int kFindCap = 1 << 26;                 // bound of every union-find loop
 
@@ -157,80 +153,12 @@ __global__ void __launch_bounds__(kTB) k_bfs_level(DGraph g, int32_t *dist, int3
     }
 }
 
-// ---- stable LSD radix sort of (key, vertex) -------------------------------
+// ---- sort keys: (root, distance) over vertices in id order ----------------
 __global__ void k_sort_init(int32_t n, const int32_t *root, const int32_t *dist, int dbits, uint64_t *key,
                             int32_t *val) {
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
         key[v] = ((uint64_t)(uint32_t)root[v] << dbits) | (uint64_t)(uint32_t)dist[v];
         val[v] = (int32_t)v;
-    }
-}
-
-// Digit histogram of each tile, stored digit-major: hist[d * ntiles + tile].
-__global__ void __launch_bounds__(kTB) k_sort_hist(const uint64_t *key, int64_t n, int shift, int64_t ntiles,
-                                                   int64_t *hist) {
-    __shared__ int32_t h[kRadix];
-    for (int i = threadIdx.x; i < kRadix; i += blockDim.x) h[i] = 0;
-    __syncthreads();
-    const int64_t base = (int64_t)blockIdx.x * kSortTile;
-#pragma unroll
-    for (int i = 0; i < kSortItems; ++i) {
-        int64_t e = base + (int64_t)i * blockDim.x + threadIdx.x;
-        if (e < n) atomicAdd(&h[(int)((key[e] >> shift) & (kRadix - 1))], 1);
-    }
-    __syncthreads();
-    for (int d = threadIdx.x; d < kRadix; d += blockDim.x) hist[(int64_t)d * ntiles + blockIdx.x] = h[d];
-}
-
-struct HistVal {
-    const int64_t *hist;
-    __device__ int64_t operator()(int64_t i) const { return hist[i]; }
-};
-
-// Scatter of one tile, chunk after chunk of blockDim elements in index order;
-// inside a chunk, warp after warp and lane after lane: the rank of an element
-// among the tile's equal digits keeps the input order (stable).
-__global__ void __launch_bounds__(kTB) k_sort_scatter(const uint64_t *key_in, const int32_t *val_in, uint64_t *key_out,
-                                                      int32_t *val_out, int64_t n, int shift, int64_t ntiles,
-                                                      const int64_t *off) {
-    __shared__ int32_t wcnt[kTB / 32][kRadix];    // per-warp digit counts, then warp prefixes
-    __shared__ int32_t ctot[kRadix];              // this chunk's count per digit
-    __shared__ int64_t run[kRadix];               // tile offset + elements placed so far, per digit
-    const int64_t base = (int64_t)blockIdx.x * kSortTile;
-    const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
-    const unsigned lt = (1u << lane) - 1u;
-    const int nwarps = blockDim.x >> 5;
-    for (int d = threadIdx.x; d < kRadix; d += blockDim.x) run[d] = off[(int64_t)d * ntiles + blockIdx.x];
-    for (int i = 0; i < kSortItems; ++i) {
-        for (int t = threadIdx.x; t < nwarps * kRadix; t += blockDim.x) wcnt[t / kRadix][t % kRadix] = 0;
-        __syncthreads();
-        const int64_t e = base + (int64_t)i * blockDim.x + threadIdx.x;
-        const bool ok = e < n;
-        const uint64_t k = ok ? key_in[e] : 0;
-        const int32_t v = ok ? val_in[e] : 0;
-        const int d = ok ? (int)((k >> shift) & (kRadix - 1)) : -1;
-        const unsigned peers = __match_any_sync(0xffffffffu, d);
-        const int rank = __popc(peers & lt);
-        if (ok && rank == 0) wcnt[warp][d] = __popc(peers);
-        __syncthreads();
-        for (int dd = threadIdx.x; dd < kRadix; dd += blockDim.x) {
-            int32_t acc = 0;
-            for (int w = 0; w < nwarps; ++w) {
-                int32_t c = wcnt[w][dd];
-                wcnt[w][dd] = acc;
-                acc += c;
-            }
-            ctot[dd] = acc;
-        }
-        __syncthreads();
-        if (ok) {
-            const int64_t pos = run[d] + wcnt[warp][d] + rank;
-            key_out[pos] = k;
-            val_out[pos] = v;
-        }
-        __syncthreads();
-        for (int dd = threadIdx.x; dd < kRadix; dd += blockDim.x) run[dd] += ctot[dd];
-        __syncthreads();
     }
 }
 
@@ -247,11 +175,6 @@ __global__ void k_assign(int32_t n, const int32_t *val, const int64_t *S, const 
         part[val[i]] = (int32_t)(((long long)k * S[i]) / W);
 }
 
-int bits_for(int64_t x) {   // bits to hold 0..x
-    int b = 0;
-    while (b < 63 && (x >> b) != 0) ++b;
-    return b;
-}
 
 }  // namespace
 
@@ -260,13 +183,10 @@ int initial_partition(Ctx &c, const DGraph &g, int32_t k, int32_t *part) {
     const int64_t n = g.n;
     if (n == 0) return JET_OK;
     const size_t nn = (size_t)n;
-    const int64_t ntiles = (n + kSortTile - 1) / kSortTile;
-    const int64_t nhist = ntiles * kRadix;
     auto a256 = [](size_t x) { return (x + 255) & ~size_t(255); };
-    // parent, root, dist, front0, front1 | key x2 | val x2 | S | hist, off | scan tiles | ctl
-    const size_t bytes = 5 * a256(nn * 4) + 2 * a256(nn * 8) + 2 * a256(nn * 4) + a256(nn * 8) +
-                         2 * a256((size_t)nhist * 8) + a256((size_t)(scan_tiles_for(std::max(nhist, n)) + 1) * 8) +
-                         a256(sizeof(IpCtl));
+    // parent, root, dist, front0, front1 | S | scan tiles | ctl | sort scratch
+    const size_t bytes = 5 * a256(nn * 4) + a256(nn * 8) + a256((size_t)(scan_tiles_for(n) + 1) * 8) +
+                         a256(sizeof(IpCtl)) + sort_scratch_bytes(n);
     DevBuf buf;
     JET_TRY(dev_alloc(buf, bytes, s));
     char *p = buf.as<char>();
@@ -276,15 +196,11 @@ int initial_partition(Ctx &c, const DGraph &g, int32_t k, int32_t *part) {
     int32_t *dist = reinterpret_cast<int32_t *>(take(nn * 4));
     int32_t *front0 = reinterpret_cast<int32_t *>(take(nn * 4));
     int32_t *front1 = reinterpret_cast<int32_t *>(take(nn * 4));
-    uint64_t *key0 = reinterpret_cast<uint64_t *>(take(nn * 8));
-    uint64_t *key1 = reinterpret_cast<uint64_t *>(take(nn * 8));
-    int32_t *val0 = reinterpret_cast<int32_t *>(take(nn * 4));
-    int32_t *val1 = reinterpret_cast<int32_t *>(take(nn * 4));
     int64_t *S = reinterpret_cast<int64_t *>(take(nn * 8));
-    int64_t *hist = reinterpret_cast<int64_t *>(take((size_t)nhist * 8));
-    int64_t *off = reinterpret_cast<int64_t *>(take((size_t)nhist * 8));
-    int64_t *scan_scr = reinterpret_cast<int64_t *>(take((size_t)(scan_tiles_for(std::max(nhist, n)) + 1) * 8));
+    int64_t *scan_scr = reinterpret_cast<int64_t *>(take((size_t)(scan_tiles_for(n) + 1) * 8));
     IpCtl *ctl = reinterpret_cast<IpCtl *>(take(sizeof(IpCtl)));
+    SortScratch sc;
+    sort_scratch_carve(p, n, sc);
     JET_CUDA_TRY(cudaMemsetAsync(ctl, 0, sizeof(IpCtl), s));
     const int gv = std::min(num_sms() * 8, grid_for(n, kTB));
     const int gw = std::min(num_sms() * 8, grid_for(n, kTB / 32));
@@ -329,24 +245,15 @@ int initial_partition(Ctx &c, const DGraph &g, int32_t k, int32_t *part) {
 
     // 3. stable sort of the vertices (in id order) by (root, distance)
     const int dbits = bits_for(maxdist);
-    const int kbits = bits_for(n - 1) + dbits;
-    k_sort_init<<<gv, kTB, 0, s>>>((int32_t)n, root, dist, dbits, key0, val0);
+    k_sort_init<<<gv, kTB, 0, s>>>((int32_t)n, root, dist, dbits, sc.key[0], sc.val[0]);
     c.launches += 1;
-    uint64_t *kin = key0, *kout = key1;
-    int32_t *vin = val0, *vout = val1;
-    for (int shift = 0; shift < kbits; shift += kRadixBits) {
-        k_sort_hist<<<(unsigned)ntiles, kTB, 0, s>>>(kin, n, shift, ntiles, hist);
-        JET_TRY(device_exscan(HistVal{hist}, nhist, off, &ctl->total, scan_scr, s));
-        k_sort_scatter<<<(unsigned)ntiles, kTB, 0, s>>>(kin, vin, kout, vout, n, shift, ntiles, off);
-        c.launches += 5;
-        JET_CUDA_TRY(cudaGetLastError());
-        std::swap(kin, kout);
-        std::swap(vin, vout);
-    }
+    int which = 0;
+    JET_TRY(sort_pairs(c, sc, n, bits_for(n - 1) + dbits, &which));
+    const int32_t *order = sc.val[which];
 
     // 4. weights before each vertex in that order, then P
-    JET_TRY(device_exscan(SortedWeight{vin, g.vw}, n, S, &ctl->total, scan_scr, s));
-    k_assign<<<gv, kTB, 0, s>>>((int32_t)n, vin, S, ctl, k, part);
+    JET_TRY(device_exscan(SortedWeight{order, g.vw}, n, S, &ctl->total, scan_scr, s));
+    k_assign<<<gv, kTB, 0, s>>>((int32_t)n, order, S, ctl, k, part);
     c.launches += 4;
     JET_CUDA_TRY(cudaGetLastError());
     JET_CUDA_TRY(cudaStreamSynchronize(s));

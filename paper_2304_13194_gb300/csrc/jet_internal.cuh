@@ -471,6 +471,24 @@ int cut_and_weights(Ctx &c, const DGraph &g, int32_t k, const int32_t *part, int
 int hem(Ctx &c, const DGraph &g, uint64_t seed, int32_t level, int32_t rounds, int32_t *mate);
 int coarsen(Ctx &c, const DGraph &g0, int32_t k, uint64_t seed, jet_hier *h);
 int initial_partition(Ctx &c, const DGraph &g, int32_t k, int32_t *part);
+
+// jet_sort.cu: stable LSD radix sort of (key, value) pairs.
+struct SortScratch {
+    uint64_t *key[2];
+    int32_t *val[2];
+    int64_t *hist, *off, *scan, *total;
+};
+int bits_for(int64_t x);                         // bits that hold 0..x
+size_t sort_scratch_bytes(int64_t n);
+void sort_scratch_carve(char *p, int64_t n, SortScratch &s);
+// Sorts (key[0], val[0]) by the low kbits bits of the key, keeping the input
+// order among equal keys; *which = buffer index (0/1) that holds the result.
+int sort_pairs(Ctx &c, SortScratch &s, int64_t n, int kbits, int *which);
+
+// jet_twohop.cu: two-hop matching after heavy-edge matching (Sec. 3.1);
+// added[s] = vertices matched by stage s (leaves, twins, relatives).
+constexpr int32_t kMatchmakerMaxDeg = 1024;
+int two_hop(Ctx &c, const DGraph &g, int32_t *mate, int64_t added[3]);
 int project(Ctx &c, int32_t n_fine, const int32_t *cmap, const int32_t *coarse_part, int32_t *fine_part);
 
 // host helpers (jet_api.cu)

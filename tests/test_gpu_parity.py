@@ -215,6 +215,48 @@ def test_initial_partition_many_components_and_levels(ctx):
     assert (_np(ctx.initial_partition(g.xadj, g.adjncy, None, 16)) == ref).all()
 
 
+def _two_hop_graphs():
+    iso = graphgen.Graph(301, np.zeros(302, np.int64), np.zeros(0, np.int32), np.ones(301, np.int32),
+                         np.zeros(0, np.int32))
+    star = graph_from_triples(200, [[0, i, 1] for i in range(1, 200)])
+    return graphs_small() + [
+        ("rmat_s14", graphgen.rmat(14, seed=11), True),
+        ("isolated_301", iso, True),
+        ("star_199", star, True),
+        ("rmat_s12_plus_isolated", graphgen.disjoint_union(graphgen.rmat(12, seed=2), iso), True),
+    ]
+
+
+@pytest.mark.parametrize("name,g,unit", _two_hop_graphs(), ids=[x[0] for x in _two_hop_graphs()])
+def test_two_hop_matches_oracle(ctx, name, g, unit):
+    ew = _ew(g, unit)
+    mate0 = _np(ctx.hem(g.xadj, g.adjncy, ew, seed=3, level=1))
+    og = graphgen.Graph(g.n, g.xadj, g.adjncy, None, ew)
+    assert (mate0 == oracle.hem(og, 3, 1, 8)).all()
+    ref, ref_added = oracle.two_hop(og, mate0)
+    got, added = ctx.two_hop(g.xadj, g.adjncy, mate0)
+    assert added == ref_added
+    assert (_np(got) == ref).all()
+
+
+def test_coarsen_without_two_hop_matches_oracle():
+    c = jet.Context(0, flags=jet.FLAG_NO_TWO_HOP)
+    try:
+        g = graphgen.rmat(13, seed=4)
+        h = c.coarsen(g.xadj, g.adjncy, None, None, k=8, seed=2)
+        ref = oracle.coarsen(graphgen.Graph(g.n, g.xadj, g.adjncy, None, None), 8, 2,
+                             oracle.Options(flags=oracle.NO_TWO_HOP))
+        try:
+            lv, ns, ms = h.info()
+            assert lv == len(ref) and list(ns) == [r.graph.n for r in ref]
+            for i in range(lv - 1):
+                assert (_np(h.level(i)["cmap"]) == ref[i].cmap).all()
+        finally:
+            h.close()
+    finally:
+        c.close()
+
+
 @pytest.mark.parametrize("name,g,unit", graphs_small(), ids=[x[0] for x in graphs_small()])
 def test_coarsen_hierarchy_matches_oracle(ctx, name, g, unit):
     vw, ew = _vw(g, unit), _ew(g, unit)
