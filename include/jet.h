@@ -71,7 +71,8 @@ extern "C" {
 #define JET_FLAG_NO_AFTERBURN 32u  /*   M = X (skip the second filter) */
 #define JET_FLAG_WEAK_AFTERBURN 64u/*   first filter keeps only F >= 0 */
 #define JET_FLAG_BASELINE_LP 128u  /*   baseline LP: move iff F > 0, no afterburner, no locks */
-#define JET_FLAG_NO_TWO_HOP 256u   /* coarsening: heavy-edge matching only (no two-hop matches, Sec. 3.1) */
+#define JET_FLAG_TWO_HOP 256u      /* coarsening: add two-hop matches (Sec. 3.1) after heavy-edge matching;
+                                      the plain method coarsens by heavy-edge matching alone */
 
 /* Hyper-parameters the paper names (defaults from jet_options_default):
  *   c_fine = 0.25, c_coarse = 0.75  first-filter ratio c (Sec. 4.1.2, Eq. gainconn_filter);
@@ -248,7 +249,7 @@ int jet_hem(jet_ctx *ctx, int32_t n, const int64_t *xadj, const int32_t *adjncy,
 
 /* Two-hop matching of Sec. 3.1, applied to a matching (mate_inout: device
  * int32[n], partner or -1, e.g. the output of jet_hem) the way jet_coarsen
- * does after heavy-edge matching: leaves (degree-1 vertices with the same
+ * does after heavy-edge matching when JET_FLAG_TWO_HOP is set: leaves (degree-1 vertices with the same
  * neighbour), then twins (same neighbourhood, identified by an order-free hash
  * of the neighbour ids; isolated vertices included), then relatives (same
  * matchmaker: the lowest-id neighbour that is matched when the stage starts

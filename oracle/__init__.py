@@ -28,7 +28,7 @@ _lib = None
 
 KIND_LP, KIND_RW, KIND_RS = 0, 1, 2
 ABL_NO_LOCKS, ABL_NO_AFTERBURN, ABL_WEAK_AFTERBURN, ABL_BASELINE_LP = 1, 2, 4, 8
-NO_TWO_HOP = 16          # coarsening: heavy-edge matching only (Sec. 3.1)
+TWO_HOP = 16             # coarsening: add two-hop matches after heavy-edge matching (Sec. 3.1)
 MATCHMAKER_MAX_DEG = 1024
 NONE = np.iinfo(np.int64).min  # the "negative infinity" gain
 

@@ -58,8 +58,9 @@ typedef struct {
 #define OR_ABL_NO_AFTERBURN  2 /* M = X (no second filter) */
 #define OR_ABL_WEAK_AFTERBURN 4 /* first filter keeps only F >= 0 */
 #define OR_ABL_BASELINE_LP   8 /* baseline LP: move iff F > 0, no afterburner, no locks */
-/* Coarsening switch (Sec. 3.1): heavy-edge matching only, no two-hop matches */
-#define OR_NO_TWO_HOP       16
+/* Coarsening switch (Sec. 3.1): add two-hop matches after heavy-edge matching.
+ * Off in the plain method, whose coarsening is heavy-edge matching alone. */
+#define OR_TWO_HOP          16
 
 typedef struct {
     int32_t levels;
@@ -566,7 +567,7 @@ int64_t or_hem(const or_graph *g, uint64_t seed, int32_t level, int32_t rounds, 
 /*
  * Two-hop matching (Sec. 3.1; details are in the paper's references, not in
  * the paper).  Readings, all deterministic:
- *  - it runs after heavy-edge matching, stage by stage (leaves, twins,
+ *  - with OR_TWO_HOP set, it runs after heavy-edge matching, stage by stage (leaves, twins,
  *    relatives), each stage only while more than 25% of the vertices are
  *    unmatched (4 u > n);
  *  - leaves: unmatched vertices of degree 1, grouped by their neighbour;
@@ -811,8 +812,8 @@ int32_t or_coarsen_target(int32_t k, const or_opts *o)
 }
 
 /*
- * MLCoarsen (Alg. 1): repeat matching (heavy-edge, then two-hop unless
- * OR_NO_TWO_HOP) + contraction while the current graph
+ * MLCoarsen (Alg. 1): repeat matching (heavy-edge, then two-hop with
+ * OR_TWO_HOP) + contraction while the current graph
  * has more than T vertices (T = max(8k, 256), reading of Sec. 3's "between 4k
  * and 8k") and fewer than max_levels levels exist.  A level that would keep
  * more than 95% of the vertices is not added (coarsening stalled; reading).
@@ -836,7 +837,7 @@ or_hier *or_coarsen(const or_graph *g, int32_t k, uint64_t seed, const or_opts *
         int32_t *mate = (int32_t *)malloc(sizeof(int32_t) * (size_t)(gi.n > 0 ? gi.n : 1));
         int32_t *cmap = (int32_t *)malloc(sizeof(int32_t) * (size_t)(gi.n > 0 ? gi.n : 1));
         or_hem(&gi, seed, i, o->hem_rounds, mate);
-        if (!(o->flags & OR_NO_TWO_HOP)) or_two_hop(&gi, mate, NULL);
+        if (o->flags & OR_TWO_HOP) or_two_hop(&gi, mate, NULL);
         int32_t nc = or_coarse_map(gi.n, mate, cmap);
         free(mate);
         if ((int64_t)100 * nc > (int64_t)95 * gi.n) { free(cmap); break; }

@@ -19,11 +19,15 @@ void record_error(const char *msg) { snprintf(g_err, sizeof(g_err), "%s", msg); 
 
 const char *last_error_text() { return g_err; }
 
+// Pool of the context whose entry point runs on this thread (set by
+// use_device); null: the device's default pool.
+static thread_local cudaMemPool_t t_pool = nullptr;
+
 int dev_alloc(DevBuf &b, size_t bytes, cudaStream_t s) {
     b.release();
     b.s = s;
     bytes = std::max<size_t>(256, (bytes + 255) & ~size_t(255));
-    cudaError_t e = cudaMallocAsync(&b.p, bytes, s);
+    cudaError_t e = t_pool ? cudaMallocFromPoolAsync(&b.p, bytes, t_pool, s) : cudaMallocAsync(&b.p, bytes, s);
     if (e != cudaSuccess) {
         b.p = nullptr;
         record_cuda_error(e, "cudaMallocAsync", __FILE__, __LINE__);
@@ -178,6 +182,7 @@ static bool bad_k_eps(int32_t k, double eps) { return k < 1 || k > JET_MAX_K || 
 
 static int use_device(Ctx &c) {
     JET_CUDA_TRY(cudaSetDevice(c.device));
+    t_pool = c.pool;
     return JET_OK;
 }
 
@@ -331,6 +336,19 @@ int jet_ctx_create(int device, void *cuda_stream, const jet_options *opt, jet_ct
         delete c;
         return JET_ENOMEM;
     }
+    // a private pool that keeps its memory across synchronisations, so that
+    // repeated calls of the same size reuse it instead of mapping it again
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    if (cudaMemPoolCreate(&c->c.pool, &props) == cudaSuccess) {
+        uint64_t keep = ~0ULL;
+        cudaMemPoolSetAttribute(c->c.pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    } else {
+        cudaGetLastError();
+        c->c.pool = nullptr;
+    }
     *out = c;
     return JET_OK;
 }
@@ -340,6 +358,10 @@ void jet_ctx_destroy(jet_ctx *ctx) {
     cudaSetDevice(ctx->c.device);
     cudaStreamSynchronize(ctx->c.stream);
     if (ctx->c.pinned) cudaFreeHost(ctx->c.pinned);
+    if (t_pool == ctx->c.pool) t_pool = nullptr;
+    // memory still held by hierarchies of this context returns to the
+    // system when they are destroyed
+    if (ctx->c.pool) cudaMemPoolDestroy(ctx->c.pool);
     delete ctx;
 }
 

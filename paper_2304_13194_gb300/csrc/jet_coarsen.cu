@@ -410,7 +410,7 @@ static int coarsen_level(Ctx &c, const DGraph &g, uint64_t seed, int32_t level, 
     JET_TRY(dev_alloc(mbuf, (size_t)n * 4, s));
     int32_t *mate = mbuf.as<int32_t>();
     JET_TRY(hem(c, g, seed, level, c.opt.hem_rounds, mate));
-    if (!(c.opt.flags & JET_FLAG_NO_TWO_HOP)) {
+    if (c.opt.flags & JET_FLAG_TWO_HOP) {
         int64_t added[3];
         JET_TRY(two_hop(c, g, mate, added));
     }

@@ -416,6 +416,7 @@ struct Ctx {
     cudaStream_t stream = nullptr;
     jet_options opt{};
     int64_t *pinned = nullptr;   // small pinned host buffer for scalar readbacks
+    cudaMemPool_t pool = nullptr; // the context's stream-ordered pool (keeps its memory between calls)
     TraceHost last_trace;
 };
 

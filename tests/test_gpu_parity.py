@@ -239,22 +239,39 @@ def test_two_hop_matches_oracle(ctx, name, g, unit):
     assert (_np(got) == ref).all()
 
 
-def test_coarsen_without_two_hop_matches_oracle():
-    c = jet.Context(0, flags=jet.FLAG_NO_TWO_HOP)
+@pytest.fixture(scope="module")
+def ctx_two_hop():
+    """Coarsening with two-hop matches (Sec. 3.1)."""
+    c = jet.Context(0, flags=jet.FLAG_TWO_HOP)
+    yield c
+    c.close()
+
+
+def test_coarsen_with_two_hop_matches_oracle(ctx_two_hop):
+    g = graphgen.rmat(13, seed=4)
+    h = ctx_two_hop.coarsen(g.xadj, g.adjncy, None, None, k=8, seed=2)
+    ref = oracle.coarsen(graphgen.Graph(g.n, g.xadj, g.adjncy, None, None), 8, 2, oracle.Options(flags=oracle.TWO_HOP))
     try:
-        g = graphgen.rmat(13, seed=4)
-        h = c.coarsen(g.xadj, g.adjncy, None, None, k=8, seed=2)
-        ref = oracle.coarsen(graphgen.Graph(g.n, g.xadj, g.adjncy, None, None), 8, 2,
-                             oracle.Options(flags=oracle.NO_TWO_HOP))
-        try:
-            lv, ns, ms = h.info()
-            assert lv == len(ref) and list(ns) == [r.graph.n for r in ref]
-            for i in range(lv - 1):
-                assert (_np(h.level(i)["cmap"]) == ref[i].cmap).all()
-        finally:
-            h.close()
+        lv, ns, ms = h.info()
+        assert lv == len(ref) and list(ns) == [r.graph.n for r in ref]
+        for i in range(lv - 1):
+            assert (_np(h.level(i)["cmap"]) == ref[i].cmap).all()
     finally:
-        c.close()
+        h.close()
+
+
+@pytest.mark.parametrize("name,g,unit,k", [
+    ("rmat_s14", graphgen.rmat(14, seed=11), True, 64),
+    ("rmat_s12_w", graphgen.rmat(12, seed=6, vw=(1, 3), ew=(1, 5)), False, 8),
+    ("grid3d_24_w", graphgen.grid3d(24, 24, 24, vw=(1, 4), ew=(1, 10), seed=1), False, 64),
+])
+def test_partition_with_two_hop_matches_oracle(ctx_two_hop, name, g, unit, k):
+    vw, ew = _vw(g, unit), _ew(g, unit)
+    og = graphgen.Graph(g.n, g.xadj, g.adjncy, vw, ew)
+    ref = oracle.partition(og, k, 0.03, 2, oracle.Options(flags=oracle.TWO_HOP))
+    part, cut, st = ctx_two_hop.partition(g.xadj, g.adjncy, vw, ew, k=k, eps=0.03, seed=2, return_stats=True)
+    assert st.n == ref.stats["n"] and st.cut_level == ref.stats["cut_level"]
+    assert cut == ref.cut and (_np(part) == ref.part).all()
 
 
 @pytest.mark.parametrize("name,g,unit", graphs_small(), ids=[x[0] for x in graphs_small()])

@@ -153,9 +153,9 @@ def test_relatives_stage_pairs_share_their_matchmaker():
 
 def test_coarsening_of_power_law_graph_no_longer_stalls():
     g = graphgen.rmat(12, seed=5)
-    with_th = [lv.graph.n for lv in oracle.coarsen(g, 8, 1)]
-    without = [lv.graph.n for lv in oracle.coarsen(g, 8, 1, oracle.Options(flags=oracle.NO_TWO_HOP))]
+    with_th = [lv.graph.n for lv in oracle.coarsen(g, 8, 1, oracle.Options(flags=oracle.TWO_HOP))]
+    without = [lv.graph.n for lv in oracle.coarsen(g, 8, 1)]
     assert with_th[-1] <= max(8 * 8, 256) < without[-1]
     # two-hop pairs merge vertices only: weight is preserved level by level
-    lv = oracle.coarsen(g, 8, 1)
+    lv = oracle.coarsen(g, 8, 1, oracle.Options(flags=oracle.TWO_HOP))
     assert all(int(l.graph.vwgt.sum()) == g.n for l in lv)
