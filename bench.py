@@ -209,10 +209,16 @@ def run_reference(args):
 # --------------------------------------------------------------------------
 # our arm
 # --------------------------------------------------------------------------
+KERNEL_SOURCES = ("jet_refine.cu", "jet_phases.cuh", "jet_internal.cuh")
+
+
 def kernel_source_hash():
+    """Hash of the refinement kernels' sources (the profile summary is only
+    used for the source it was captured on)."""
     h = hashlib.sha256()
-    with open(os.path.join(ROOT, "paper_2304_13194_gb300", "csrc", "jet_refine.cu"), "rb") as f:
-        h.update(f.read())
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2304_13194_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
     return h.hexdigest()[:16]
 
 
