@@ -78,17 +78,17 @@ __global__ void k_graph_start(Level L) {
 }
 
 __global__ void __launch_bounds__(kTB) k_copy_best(Level L) { ph_copy_best(L, launch_grid()); }
-// Jetlp: P_best copy + work list, select, afterburner
-__global__ void __launch_bounds__(kTB) k_lp_scan(Level L) {
-    ph_copy_best(L, launch_grid());
-    ph_lp_scan(L, launch_grid(), JET_ARENA);
-}
+// Jetlp: work list, select; P_best copy + afterburner (the copy only reads
+// part, which the afterburner does not change, and stays out of the select
+// step)
+__global__ void __launch_bounds__(kTB) k_lp_scan(Level L) { ph_lp_scan(L, launch_grid(), JET_ARENA); }
 template <bool EW>
 __global__ void __launch_bounds__(kTB, 4) k_lp_select(Level L, LpExport ex) {
     ph_lp_select<EW>(L, ex, launch_grid(), JET_ARENA);
 }
 template <bool EW>
 __global__ void __launch_bounds__(kTB, 4) k_afterburn(Level L, LpExport ex) {
+    ph_copy_best(L, launch_grid());
     ph_afterburn<EW>(L, ex, launch_grid(), JET_ARENA);
 }
 // apply + commit; the last block runs the controller
@@ -219,7 +219,10 @@ struct LevelBufs {
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // Carves all per-level buffers out of two allocations.
+int allow_large_arenas(int device);
+
 int setup_level(Ctx &c, const DGraph &g, int32_t k, LevelBufs &B) {
+    JET_TRY(allow_large_arenas(c.device));
     cudaStream_t s = c.stream;
     int64_t n = g.n;
     size_t nn = (size_t)std::max<int64_t>(n, 1);
@@ -532,6 +535,25 @@ int run_graph(Ctx &c, Level L, int *nk_branch, int *nk_tail) {
     if (g) cudaGraphDestroy(g);
     if (cap) cudaStreamDestroy(cap);
     return rc;
+}
+
+// The row kernels whose arena can pass 48 KB (per-warp tables for k up to
+// JET_MAX_K) are allowed the larger dynamic shared memory once per device.
+int allow_large_arenas(int device) {
+    static std::mutex mu;
+    static bool done[256];
+    if (device < 0 || device >= 256) return JET_EINVAL;
+    std::lock_guard<std::mutex> lock(mu);
+    if (done[device]) return JET_OK;
+    const int sel = (int)sm_lp_select(JET_MAX_K, kTB, true), cand = (int)sm_rb_cand(JET_MAX_K, kTB, true);
+    JET_CUDA_TRY(cudaFuncSetAttribute(k_lp_select<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sel));
+    JET_CUDA_TRY(cudaFuncSetAttribute(k_lp_select<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sel));
+    JET_CUDA_TRY(cudaFuncSetAttribute(k_rb_cand<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, cand));
+    JET_CUDA_TRY(cudaFuncSetAttribute(k_rb_cand<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, cand));
+    JET_CUDA_TRY(cudaFuncSetAttribute(k_rb_cand<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, cand));
+    JET_CUDA_TRY(cudaFuncSetAttribute(k_rb_cand<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, cand));
+    done[device] = true;
+    return JET_OK;
 }
 
 // Cluster loop: the largest cluster (at most kMaxCluster blocks of
@@ -884,6 +906,7 @@ int lp_pass_in_scratch(Ctx &c, const DGraph &g, int32_t k, const int32_t *part, 
                        uint8_t *inm_out, char *scratch) {
     cudaStream_t s = c.stream;
     if (g.n == 0) return JET_OK;
+    JET_TRY(allow_large_arenas(c.device));
     size_t nn = (size_t)g.n;
     char *p = scratch;
     auto take32 = [&]() { int32_t *r = reinterpret_cast<int32_t *>(p); p += align256c(nn * 4); return r; };

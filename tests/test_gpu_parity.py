@@ -342,6 +342,7 @@ def test_refine_hostloop_equals_graph_loop(ctx, ctx_hostloop):
     ("rmat_s12", graphgen.rmat(12, seed=5), True, 64),                  # long rows: warp paths
     ("gnp_700_dense", graphgen.gnp(700, 0.06, seed=4, ew=(1, 9)), False, 8),
     ("rgg_30000", graphgen.rgg(30000, seed=3), True, 128),              # many 1024-vertex tiles
+    ("rmat_s12_k256", graphgen.rmat(12, seed=5), True, 256),            # one block meets > 2048 X members
 ])
 def test_refine_cluster_loop_equals_graph_loop(ctx_cluster, ctx_graph, name, g, unit, k):
     vw, ew = _vw(g, unit), _ew(g, unit)
