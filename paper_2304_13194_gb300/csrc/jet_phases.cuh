@@ -234,10 +234,12 @@ __host__ __device__ constexpr size_t arena_bytes(int32_t k, int T) {
 // ---------------------------------------------------------------------------
 // controller helpers (one block)
 // ---------------------------------------------------------------------------
-__device__ inline long long block_max_pw(const int64_t *pw, int32_t k, long long *sh) {
+// Max part weight; the weights are left in spw[0..k) for compute_classes.
+__device__ inline long long block_max_pw(const int64_t *pw, int32_t k, long long *sh, long long *spw) {
     long long m = 0;
     for (int i = threadIdx.x; i < k; i += blockDim.x) {
         long long w = ld_gpu(&pw[i]);
+        spw[i] = w;
         m = w > m ? w : m;
     }
 #pragma unroll
@@ -265,8 +267,9 @@ __device__ inline long long block_max_pw(const int64_t *pw, int32_t k, long long
 
 // Rebalancing classes (Alg. 5): A = {p : w_p > L} numbered in ascending id,
 // B = {p : w_p <= sigma} listed in ascending id, excess of each A part, the
-// capacity prefix of B (Jetrs) and zeroed slot buckets.  Any block size.
-__device__ inline void compute_classes(const Level &L, long long *sh) {
+// capacity prefix of B (Jetrs) and zeroed slot buckets.  Any block size;
+// spw holds the part weights (block_max_pw).
+__device__ inline void compute_classes(const Level &L, long long *sh, const long long *spw) {
     Ctl *ctl = L.ctl;
     long long ca = 0, cb = 0, cc = 0;
     for (int p0 = 0; p0 < L.k; p0 += blockDim.x) {
@@ -274,7 +277,7 @@ __device__ inline void compute_classes(const Level &L, long long *sh) {
         bool inA = false, inB = false;
         long long w = 0;
         if (p < L.k) {
-            w = ld_gpu(&L.pw[p]);
+            w = spw[p];
             inA = w > ctl->L;
             inB = w <= ctl->sigma;
         }
@@ -338,6 +341,7 @@ __device__ __forceinline__ void reset_counters(Ctl *ctl) {
 // (all threads).
 __device__ inline int32_t ph_controller(const Level &L) {
     __shared__ long long sh[40];
+    __shared__ long long spw[JET_MAX_K];
     __shared__ int32_t next_mode;
     Ctl *ctl = L.ctl;
     int32_t kind = ctl->mode;
@@ -351,16 +355,22 @@ __device__ inline int32_t ph_controller(const Level &L) {
         }
         return MODE_DONE;
     }
-    long long maxw = block_max_pw(L.pw, L.k, sh);
+    // thread 0 gathers: values of earlier kernels (plain loads) and of this
+    // one (ld_gpu), issued before the part-weight reduction so that the two
+    // round trips overlap
+    long long cut0 = 0, Llim = 0, best_cut0 = 0, best_maxw0 = 0, ncand = 0, degx = 0, nbnd = 0, nexam = 0,
+              degexam = 0, dcut = 0, degm = 0;
+    int32_t it = 0, noimp0 = 0, best_bal0 = 0, kc = 0, weak = 0, hit_cap = 0, nX = 0, nM = 0;
     if (threadIdx.x == 0) {
-        // gather: values of earlier kernels (plain loads) and of this one (ld_gpu)
-        const long long cut0 = ctl->cut, Llim = ctl->L, best_cut0 = ctl->best_cut, best_maxw0 = ctl->best_maxw;
-        const int32_t it = ctl->it, noimp0 = ctl->noimp, best_bal0 = ctl->best_bal, kc = ctl->kcount[kind];
-        int32_t weak = ctl->weak, hit_cap = ctl->hit_cap;
-        const int32_t nX = ctl->nX, nM = ctl->nM;
-        const long long ncand = ctl->ncand, degx = ctl->degx, nbnd = ctl->nbnd, nexam = ctl->nexam,
-                        degexam = ctl->degexam;
-        const long long dcut = ld_gpu(&ctl->dcut), degm = ld_gpu(&ctl->degm);
+        cut0 = ctl->cut; Llim = ctl->L; best_cut0 = ctl->best_cut; best_maxw0 = ctl->best_maxw;
+        it = ctl->it; noimp0 = ctl->noimp; best_bal0 = ctl->best_bal; kc = ctl->kcount[kind];
+        weak = ctl->weak; hit_cap = ctl->hit_cap;
+        nX = ctl->nX; nM = ctl->nM;
+        ncand = ctl->ncand; degx = ctl->degx; nbnd = ctl->nbnd; nexam = ctl->nexam; degexam = ctl->degexam;
+        dcut = ld_gpu(&ctl->dcut); degm = ld_gpu(&ctl->degm);
+    }
+    long long maxw = block_max_pw(L.pw, L.k, sh, spw);
+    if (threadIdx.x == 0) {
         // decide
         const long long cut = cut0 + dcut;
         const bool bal = maxw <= Llim;
@@ -409,15 +419,16 @@ __device__ inline int32_t ph_controller(const Level &L) {
     }
     __syncthreads();
     int32_t m = next_mode;
-    if (m == MODE_RW || m == MODE_RS) compute_classes(L, sh);
+    if (m == MODE_RW || m == MODE_RS) compute_classes(L, sh, spw);
     return m;
 }
 
 // Level start, one block: control block from the initial cut and weights.
 __device__ inline void ph_ctl_init(const Level &L, const int64_t *cut2) {
     __shared__ long long sh[40];
+    __shared__ long long spw[JET_MAX_K];
     Ctl *ctl = L.ctl;
-    long long maxw = block_max_pw(L.pw, L.k, sh);
+    long long maxw = block_max_pw(L.pw, L.k, sh, spw);
     if (threadIdx.x == 0) {
         ctl->cut = *cut2 / 2;
         ctl->dcut = 0;
@@ -432,7 +443,7 @@ __device__ inline void ph_ctl_init(const Level &L, const int64_t *cut2) {
         ctl->mode = choose_mode(L, maxw <= ctl->L);
     }
     __syncthreads();
-    if (ctl->mode == MODE_RW || ctl->mode == MODE_RS) compute_classes(L, sh);
+    if (ctl->mode == MODE_RW || ctl->mode == MODE_RS) compute_classes(L, sh, spw);
 }
 
 // P_best <- P_iter when the controller asked for it (first phase of the next
@@ -637,9 +648,11 @@ template <bool EW>
 __device__ __forceinline__ int32_t afterburn_term(const Level &L, int32_t v, int32_t Fv, int32_t pd, int32_t ps,
                                                   int64_t j) {
     int32_t u = __ldg(L.g.adj + j);
+    // the three loads are independent: one round trip, not two
     int32_t pu = L.part[u];
-    int32_t fu = L.prio[u];
-    if (fu > Fv || (fu == Fv && u < v)) pu = nxt_to(L.nxt[u]);
+    const int32_t fu = L.prio[u];
+    const int32_t nu = L.nxt[u];
+    if (fu > Fv || (fu == Fv && u < v)) pu = nxt_to(nu);
     int32_t w = edge_w<EW>(L.g, j);
     return pu == pd ? w : (pu == ps ? -w : 0);
 }
@@ -696,8 +709,9 @@ __device__ inline void ph_afterburn(const Level &L, LpExport ex, Grid G, char *a
                         if (t < d) {
                             int32_t u = uu[t];
                             int32_t pu = L.part[u];
-                            int32_t fu = L.prio[u];
-                            if (fu > Fv || (fu == Fv && u < v)) pu = nxt_to(L.nxt[u]);
+                            const int32_t fu = L.prio[u];
+                            const int32_t nu = L.nxt[u];
+                            if (fu > Fv || (fu == Fv && u < v)) pu = nxt_to(nu);
                             f2 += pu == pd ? ww[t] : (pu == ps ? -ww[t] : 0);
                         }
                     }
@@ -727,15 +741,12 @@ __device__ inline void ph_afterburn(const Level &L, LpExport ex, Grid G, char *a
 template <bool EW>
 __device__ __forceinline__ int64_t apply_edge(const Level &L, int32_t v, int32_t a, int32_t b, int32_t it, int32_t u,
                                               int32_t w, int32_t *other) {
-    int32_t pu, pn;
-    bool mu = L.mstamp[u] == it;
-    if (mu) {
-        int32_t x = L.nxt[u];
-        pu = nxt_from(x);
-        pn = nxt_to(x);
-    } else {
-        pu = pn = L.part[u];
-    }
+    // stamp, packed move and part loaded together (one round trip)
+    const bool mu = L.mstamp[u] == it;
+    const int32_t x = L.nxt[u];
+    const int32_t p = L.part[u];
+    const int32_t pu = mu ? nxt_from(x) : p;
+    const int32_t pn = mu ? nxt_to(x) : p;
     *other = pn != b;
     int32_t diff = (int)(pn != b) - (int)(pu != a);
     if (!mu) {
@@ -1135,16 +1146,28 @@ __device__ inline void ph_rb_plan(const Level &L) {
     const int32_t nA = ctl->nA;
     const int warps = blockDim.x >> 5;
     const unsigned lane = lane_id();
-    for (int a = threadIdx.x >> 5; a < nA; a += warps) {
-        long long t = ld_gpu(&L.bucketw[a * kSlots + lane]);          // slots 0..31 on the lanes
-        long long t32 = ld_gpu(&L.bucketw[a * kSlots + 32]);
+    constexpr int kBatch = 4;                      // parts per warp whose loads are in flight together
+    for (int a0 = threadIdx.x >> 5; a0 < nA; a0 += warps * kBatch) {
+        long long tb[kBatch], t32b[kBatch], exb[kBatch];
+#pragma unroll
+        for (int b = 0; b < kBatch; ++b) {
+            const int a = a0 + b * warps;
+            tb[b] = a < nA ? ld_gpu(&L.bucketw[a * kSlots + lane]) : 0;    // slots 0..31 on the lanes
+            t32b[b] = a < nA ? ld_gpu(&L.bucketw[a * kSlots + 32]) : 0;
+            exb[b] = a < nA ? L.excess[a] : 0;
+        }
+#pragma unroll
+        for (int b = 0; b < kBatch; ++b) {
+        const int a = a0 + b * warps;
+        if (a >= nA) break;
+        const long long t = tb[b], t32 = t32b[b];
         long long x = t;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             long long y = __shfl_up_sync(0xffffffffu, x, o);
             if ((int)lane >= o) x += y;
         }
-        long long ex = L.excess[a];
+        const long long ex = exb[b];
         unsigned m = __ballot_sync(0xffffffffu, x >= ex);
         long long tot31 = __shfl_sync(0xffffffffu, x, 31);
         int32_t ss;
@@ -1162,6 +1185,7 @@ __device__ inline void ph_rb_plan(const Level &L) {
             need = 0;
         }
         if (lane == 0) { L.sstar[a] = ss; L.need[a] = need; }
+        }
     }
 }
 

@@ -823,6 +823,7 @@ __global__ void k_export_rb(Level L, int32_t *dest, int32_t *loss) {
 
 __global__ void __launch_bounds__(1024) k_rb_pass_init(Level L, const int64_t *cut2, int32_t mode) {
     __shared__ long long sh[40];
+    __shared__ long long spw[JET_MAX_K];
     Ctl *ctl = L.ctl;
     if (threadIdx.x == 0) {
         ctl->cut = *cut2 / 2;
@@ -830,8 +831,8 @@ __global__ void __launch_bounds__(1024) k_rb_pass_init(Level L, const int64_t *c
         ctl->ticket = 0;
         reset_counters(ctl);
     }
-    __syncthreads();
-    compute_classes(L, sh);
+    block_max_pw(L.pw, L.k, sh, spw);   // part weights into shared memory
+    compute_classes(L, sh, spw);
 }
 
 __global__ void k_clear_keys(Level L) {
