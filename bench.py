@@ -56,6 +56,9 @@ def parse_args(argv=None):
                    help="largest level refined by the one-cluster loop (library default if omitted; 0 = never)")
     p.add_argument("--kernel-probe", action="store_true",
                    help="run one profiled partition and report per-level select launches (profiler target)")
+    p.add_argument("--sweep", choices=["lp_versions"], default=None,
+                   help="the Jetlp versions of the paper's component study and the phi trade-off, on the "
+                        "mesh, power-law and large-grid workloads (one JSON line per run and a summary)")
     return p.parse_args(argv)
 
 
@@ -387,12 +390,67 @@ def run_ours(args):
     return 0
 
 
+# Jetlp versions of the component study (Sec. 6.1.4, Table 2) as library flags
+LP_VERSIONS = [("baseline", "BASELINE_LP"), ("baseline+locks", "STRICT_GAIN|NO_AFTERBURN"),
+               ("baseline+weak_afterburner", "WEAK_AFTERBURN|NO_LOCKS"), ("baseline+full_afterburner", "NO_LOCKS"),
+               ("full_jetlp", "")]
+
+
+def sweep_graphs():
+    """Meshes, a power-law graph and the paper's two large synthetic grids."""
+    import graphgen
+    return [
+        ("grid2d_64x64", lambda: graphgen.grid2d(64, 64), 8),
+        ("grid3d_128", lambda: graphgen.grid3d(128, 128, 128, vw=(1, 4), ew=(1, 10), seed=SEED), 64),
+        ("rmat_s22", lambda: graphgen.rmat(22, seed=SEED), 64),
+        ("grid2d_2000x4000", lambda: graphgen.grid2d(2000, 4000), 64),
+        ("grid3d_200", lambda: graphgen.grid3d(200, 200, 200), 64),
+    ]
+
+
+def run_sweep(args):
+    import math
+    import torch
+    import paper_2304_13194_gb300 as jet
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    flag = lambda spec: sum(getattr(jet, "FLAG_" + f) for f in spec.split("|") if f)
+    runs = [(name, flag(spec), 0.999) for name, spec in LP_VERSIONS] + [("phi_0.99", 0, 0.99), ("phi_0.9999", 0, 0.9999)]
+    results = {}
+    for gname, make, k in sweep_graphs():
+        g = make()
+        t = [torch.from_numpy(a).to(dev) if a is not None else None for a in (g.xadj, g.adjncy, g.vwgt, g.adjwgt)]
+        for rname, flags, phi in runs:
+            with jet.Context(0, flags=flags, phi=phi) as ctx:
+                ctx.partition(*t, k=k, eps=EPS, seed=SEED)                       # warm-up
+                _, cut, st = ctx.partition(*t, k=k, eps=EPS, seed=SEED, return_stats=True)
+            results[(gname, rname)] = (cut, st.ms_refine, st.ms_total, st.max_part_w)
+            print(json.dumps({"sweep": "lp_versions", "graph": gname, "n": g.n, "m": g.m, "k": k, "version": rname,
+                              "phi": phi, "cut": cut, "uncoarsen_ms": round(st.ms_refine, 3),
+                              "total_ms": round(st.ms_total, 3), "max_part_w": st.max_part_w}), flush=True)
+        del t
+    gnames = [x[0] for x in sweep_graphs()]
+
+    def geo(rname, idx):
+        return math.exp(sum(math.log(results[(gn, rname)][idx]) for gn in gnames) / len(gnames))
+    base = geo("baseline", 0)
+    summary = {"sweep": "lp_versions", "summary": "geomean(baseline cut) / geomean(version cut)",
+               "ratios": {rname: round(base / geo(rname, 0), 4) for rname, _, _ in runs},
+               "phi_vs_default": {r: {"uncoarsen_time": round(geo(r, 1) / geo("full_jetlp", 1), 3),
+                                      "cut": round(geo(r, 0) / geo("full_jetlp", 0), 4)}
+                                  for r in ("phi_0.99", "phi_0.9999")}}
+    print(json.dumps(summary), flush=True)
+    return 0
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
     if args.kernel_probe:
         return run_probe(args)
+    if args.sweep:
+        return run_sweep(args)
     return run_ours(args)
 
 

@@ -71,6 +71,8 @@ extern "C" {
 #define JET_FLAG_NO_AFTERBURN 32u  /*   M = X (skip the second filter) */
 #define JET_FLAG_WEAK_AFTERBURN 64u/*   first filter keeps only F >= 0 */
 #define JET_FLAG_BASELINE_LP 128u  /*   baseline LP: move iff F > 0, no afterburner, no locks */
+#define JET_FLAG_STRICT_GAIN 512u  /* Jetlp ablation: first filter keeps only F > 0 (with
+                                      JET_FLAG_NO_AFTERBURN: the baseline LP plus locks) */
 #define JET_FLAG_TWO_HOP 256u      /* coarsening: add two-hop matches (Sec. 3.1) after heavy-edge matching;
                                       the plain method coarsens by heavy-edge matching alone */
 

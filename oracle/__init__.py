@@ -28,6 +28,7 @@ _lib = None
 
 KIND_LP, KIND_RW, KIND_RS = 0, 1, 2
 ABL_NO_LOCKS, ABL_NO_AFTERBURN, ABL_WEAK_AFTERBURN, ABL_BASELINE_LP = 1, 2, 4, 8
+ABL_STRICT_GAIN = 32     # first filter keeps only F > 0
 TWO_HOP = 16             # coarsening: add two-hop matches after heavy-edge matching (Sec. 3.1)
 MATCHMAKER_MAX_DEG = 1024
 NONE = np.iinfo(np.int64).min  # the "negative infinity" gain

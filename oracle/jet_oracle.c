@@ -58,6 +58,7 @@ typedef struct {
 #define OR_ABL_NO_AFTERBURN  2 /* M = X (no second filter) */
 #define OR_ABL_WEAK_AFTERBURN 4 /* first filter keeps only F >= 0 */
 #define OR_ABL_BASELINE_LP   8 /* baseline LP: move iff F > 0, no afterburner, no locks */
+#define OR_ABL_STRICT_GAIN  32 /* first filter keeps only F > 0 (with NO_AFTERBURN: the baseline plus locks) */
 /* Coarsening switch (Sec. 3.1): add two-hop matches after heavy-edge matching.
  * Off in the plain method, whose coarsening is heavy-edge matching alone. */
 #define OR_TWO_HOP          16
@@ -214,7 +215,7 @@ void or_jetlp(const or_graph *g, int32_t k, const int32_t *P, const uint8_t *loc
         int64_t f = F[v];
         int x = 0;
         if (f != OR_NONE) {
-            if (abl & OR_ABL_BASELINE_LP) x = f > 0;
+            if (abl & (OR_ABL_BASELINE_LP | OR_ABL_STRICT_GAIN)) x = f > 0;
             else if (abl & OR_ABL_WEAK_AFTERBURN) x = f >= 0;
             else x = (f >= 0) || (-f < (c_q16 * conn_s[v]) / 65536);
         }

@@ -29,6 +29,8 @@ constexpr uint32_t ABL_NO_LOCKS = JET_FLAG_NO_LOCKS;
 constexpr uint32_t ABL_NO_AFTERBURN = JET_FLAG_NO_AFTERBURN;
 constexpr uint32_t ABL_WEAK_AFTERBURN = JET_FLAG_WEAK_AFTERBURN;
 constexpr uint32_t ABL_BASELINE_LP = JET_FLAG_BASELINE_LP;
+constexpr uint32_t ABL_STRICT_GAIN = JET_FLAG_STRICT_GAIN;
+constexpr uint32_t ABL_ALL = ABL_NO_LOCKS | ABL_NO_AFTERBURN | ABL_WEAK_AFTERBURN | ABL_BASELINE_LP | ABL_STRICT_GAIN;
 
 // ---------------------------------------------------------------------------
 // error handling

@@ -88,9 +88,10 @@ __device__ __forceinline__ int32_t edge_w(const DGraph &g, int64_t j) {
 __device__ __forceinline__ bool ablate_locks(uint32_t abl) { return (abl & (ABL_NO_LOCKS | ABL_BASELINE_LP)) != 0; }
 
 // First filter, Eq. gainconn_filter: -F < floor(c * conn(v,P_s)) or F >= 0
-// (ablations: weak afterburner keeps F >= 0, baseline LP keeps F > 0).
+// (ablations: weak afterburner keeps F >= 0, baseline LP and strict gain keep
+// F > 0).
 __device__ __forceinline__ bool first_filter(int32_t F, int32_t conn_s, int32_t cq16, uint32_t abl) {
-    if (abl & ABL_BASELINE_LP) return F > 0;
+    if (abl & (ABL_BASELINE_LP | ABL_STRICT_GAIN)) return F > 0;
     if (abl & ABL_WEAK_AFTERBURN) return F >= 0;
     if (F >= 0) return true;
     long long lim = ((long long)cq16 * (long long)conn_s) >> 16;

@@ -660,7 +660,7 @@ static void fill_level_params(Ctx &c, Level &L, int32_t is_finest, uint64_t seed
     L.max_no_improve = o.max_no_improve;
     L.weak_limit = o.weak_limit;
     L.max_iters = o.max_iters_per_level;
-    L.abl = o.flags & (ABL_NO_LOCKS | ABL_NO_AFTERBURN | ABL_WEAK_AFTERBURN | ABL_BASELINE_LP);
+    L.abl = o.flags & ABL_ALL;
     L.seed = seed;
     L.use_graph = 0;
     L.h_loop = L.h_mode = 0;
@@ -785,7 +785,7 @@ int lp_pass(Ctx &c, const DGraph &g, int32_t k, const int32_t *part, const uint8
     L.part = const_cast<int32_t *>(part);   // read only in this pass
     fill_level_params(c, L, 1, 0);
     L.cq16 = (int32_t)llround(cval * 65536.0);
-    L.abl = flags & (ABL_NO_LOCKS | ABL_NO_AFTERBURN | ABL_WEAK_AFTERBURN | ABL_BASELINE_LP);
+    L.abl = flags & ABL_ALL;
     {
         int gcut = std::min(list_grid(), grid_for(g.n, kTB));
         if (g.ew) k_cut_pw<true><<<gcut, kTB, (size_t)k * 8, s>>>(g, k, L.part, L.pw, B.cut2, L.ext, nullptr);
@@ -929,7 +929,7 @@ int lp_pass_in_scratch(Ctx &c, const DGraph &g, int32_t k, const int32_t *part, 
     int64_t *cut2 = reinterpret_cast<int64_t *>(p);
     fill_level_params(c, L, 1, 0);
     L.cq16 = (int32_t)llround(cval * 65536.0);
-    L.abl = flags & (ABL_NO_LOCKS | ABL_NO_AFTERBURN | ABL_WEAK_AFTERBURN | ABL_BASELINE_LP);
+    L.abl = flags & ABL_ALL;
     // the array keeps the previous call's contents: clear what must start at zero
     JET_CUDA_TRY(cudaMemsetAsync(L.ctl, 0, sizeof(Ctl), s));
     JET_CUDA_TRY(cudaMemsetAsync(nbig_dev, 0, 16, s));

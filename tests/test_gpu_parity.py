@@ -55,6 +55,14 @@ def _np(t):
     return t.cpu().numpy()
 
 
+def _oracle_ablation(flags):
+    """The oracle's switches for the library's Jetlp ablation flags."""
+    return sum(o for f, o in [(jet.FLAG_NO_LOCKS, oracle.ABL_NO_LOCKS), (jet.FLAG_NO_AFTERBURN, oracle.ABL_NO_AFTERBURN),
+                              (jet.FLAG_WEAK_AFTERBURN, oracle.ABL_WEAK_AFTERBURN),
+                              (jet.FLAG_BASELINE_LP, oracle.ABL_BASELINE_LP),
+                              (jet.FLAG_STRICT_GAIN, oracle.ABL_STRICT_GAIN)] if flags & f)
+
+
 def _vw(g, unit):
     return None if unit else g.vwgt
 
@@ -99,7 +107,8 @@ def test_lp_pass_hand_cases(ctx, golden_dir):
 
 @pytest.mark.parametrize("name,g,unit", graphs_small(), ids=[x[0] for x in graphs_small()])
 @pytest.mark.parametrize("k,c,abl", [(8, 0.25, 0), (64, 0.75, 0), (5, 0.25, jet.FLAG_NO_AFTERBURN),
-                                     (16, 0.25, jet.FLAG_WEAK_AFTERBURN), (16, 0.25, jet.FLAG_BASELINE_LP)])
+                                     (16, 0.25, jet.FLAG_WEAK_AFTERBURN), (16, 0.25, jet.FLAG_BASELINE_LP),
+                                     (16, 0.75, jet.FLAG_STRICT_GAIN | jet.FLAG_NO_AFTERBURN)])
 def test_lp_pass_random(ctx, name, g, unit, k, c, abl):
     rng = np.random.default_rng(k + abl)
     part = oracle.initial_partition(g, k)
@@ -108,9 +117,7 @@ def test_lp_pass_random(ctx, name, g, unit, k, c, abl):
     locked = (rng.random(g.n) < 0.15).astype(np.uint8)
     vw, ew = _vw(g, unit), _ew(g, unit)
     og = graphgen.Graph(g.n, g.xadj, g.adjncy, vw, ew)
-    oabl = sum(o for f, o in [(jet.FLAG_NO_LOCKS, oracle.ABL_NO_LOCKS), (jet.FLAG_NO_AFTERBURN, oracle.ABL_NO_AFTERBURN),
-                              (jet.FLAG_WEAK_AFTERBURN, oracle.ABL_WEAK_AFTERBURN),
-                              (jet.FLAG_BASELINE_LP, oracle.ABL_BASELINE_LP)] if abl & f)
+    oabl = _oracle_ablation(abl)
     ref = oracle.jetlp(og, k, part, locked, c=c, ablation=oabl)
     r = ctx.lp_pass(g.xadj, g.adjncy, vw, ew, k, part, locked, c=c, flags=abl)
     F = _np(r["F"]).astype(np.int64)
@@ -398,6 +405,25 @@ def test_partition_grid_64x64_k8(ctx):
 @pytest.mark.parametrize("k", [2, 8, 64])
 def test_partition_matches_oracle(ctx, name, g, unit, k):
     _check_partition(ctx, g, unit, k, seed=k)
+
+
+# the Jetlp versions of Table 2 (Sec. 6.1.4): whole partitions, bit-exact
+LP_VERSIONS = [("baseline", jet.FLAG_BASELINE_LP), ("baseline+locks", jet.FLAG_STRICT_GAIN | jet.FLAG_NO_AFTERBURN),
+               ("baseline+weak_afterburner", jet.FLAG_WEAK_AFTERBURN | jet.FLAG_NO_LOCKS),
+               ("baseline+full_afterburner", jet.FLAG_NO_LOCKS), ("full_jetlp", 0)]
+
+
+@pytest.mark.parametrize("version,flags", LP_VERSIONS, ids=[v[0] for v in LP_VERSIONS])
+def test_partition_lp_versions_match_oracle(version, flags):
+    g = graphgen.grid3d(20, 20, 20, vw=(1, 4), ew=(1, 10), seed=3)
+    c = jet.Context(0, flags=flags)
+    try:
+        ref = oracle.partition(g, 32, 0.03, 1, oracle.Options(flags=_oracle_ablation(flags)))
+        part, cut, st = c.partition(g.xadj, g.adjncy, g.vwgt, g.adjwgt, k=32, eps=0.03, seed=1, return_stats=True)
+        assert st.cut_level == ref.stats["cut_level"]
+        assert cut == ref.cut and (_np(part) == ref.part).all()
+    finally:
+        c.close()
 
 
 def test_partition_hostloop(ctx_hostloop):
