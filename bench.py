@@ -56,7 +56,7 @@ def parse_args(argv=None):
                    help="largest level refined by the one-cluster loop (library default if omitted; 0 = never)")
     p.add_argument("--kernel-probe", action="store_true",
                    help="run one profiled partition and report per-level select launches (profiler target)")
-    p.add_argument("--sweep", choices=["lp_versions"], default=None,
+    p.add_argument("--sweep", choices=["lp_versions", "batched"], default=None,
                    help="the Jetlp versions of the paper's component study and the phi trade-off, on the "
                         "mesh, power-law and large-grid workloads (one JSON line per run and a summary)")
     return p.parse_args(argv)
@@ -443,8 +443,59 @@ def run_sweep(args):
     return 0
 
 
+def batched_graphs(count=512):
+    """The batched workload: random geometric graphs in the unit square, n
+    log-uniform in [1k, 200k], mean degree 8, unit weights, each with its own
+    k uniform in {2, 4, ..., 64}; seeded."""
+    import numpy as np
+    import graphgen
+    rng = np.random.default_rng(SEED)
+    ns = np.exp(rng.uniform(np.log(1000), np.log(200000), count)).astype(np.int64)
+    ks = rng.choice(np.arange(2, 65, 2), count)
+    return [(graphgen.rgg(int(n), seed=i + 1), int(k)) for i, (n, k) in enumerate(zip(ns, ks))]
+
+
+def run_batched(args):
+    """Sequential plain partitions vs the batched form on the same graphs
+    (cuts must agree); wall time around each whole set."""
+    import time
+    import torch
+    import paper_2304_13194_gb300 as jet
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    gks = batched_graphs()
+    items = [dict(xadj=torch.from_numpy(g.xadj).to(dev), adjncy=torch.from_numpy(g.adjncy).to(dev), k=k, eps=EPS,
+                  seed=SEED + i) for i, (g, k) in enumerate(gks)]
+    n_tot = sum(g.n for g, _ in gks)
+    m_tot = sum(g.m for g, _ in gks)
+    with jet.Context(0) as ctx:
+        for it in items[:8]:                                          # warm-up
+            ctx.partition(it["xadj"], it["adjncy"], k=it["k"], eps=EPS, seed=it["seed"])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        seq = [ctx.partition(it["xadj"], it["adjncy"], k=it["k"], eps=EPS, seed=it["seed"])[1] for it in items]
+        torch.cuda.synchronize()
+        t_seq = time.perf_counter() - t0
+        print(json.dumps({"sweep": "batched", "mode": "sequential", "graphs": len(items), "n_total": n_tot,
+                          "m_total": m_tot, "seconds": round(t_seq, 4)}), flush=True)
+        for workers in (4, 8, 16):
+            ctx.partition_batch(items[:16], workers=workers)          # warm-up
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            out = ctx.partition_batch(items, workers=workers)
+            torch.cuda.synchronize()
+            t_b = time.perf_counter() - t0
+            same = all(o[1] == c for o, c in zip(out, seq))
+            print(json.dumps({"sweep": "batched", "mode": "batched", "workers": workers, "graphs": len(items),
+                              "seconds": round(t_b, 4), "speedup_vs_sequential": round(t_seq / t_b, 3),
+                              "cuts_equal_to_sequential": same}), flush=True)
+    return 0
+
+
 def main(argv=None):
     args = parse_args(argv)
+    if args.sweep == "batched":
+        return run_batched(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.kernel_probe:

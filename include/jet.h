@@ -191,6 +191,30 @@ int jet_partition_host(jet_ctx *ctx, int32_t n, const int64_t *xadj, const int32
                        const int32_t *vwgt, const int32_t *adjwgt, int32_t k, double eps,
                        uint64_t seed, int32_t *part_out, int64_t *cut_out, jet_stats *stats);
 
+/* Batched form: many independent graphs partitioned concurrently.  Each item
+ * is one jet_partition (device arrays, its own k, eps and seed; results
+ * bit-identical to a jet_partition call with the same arguments); `workers`
+ * host threads (<= 0: 8) each drive their own stream and memory pool on the
+ * context's device, so small graphs, whose refinement is latency-bound, fill
+ * the GPU together.  The work starts after what is already enqueued on the
+ * context's stream and is complete when the call returns.  Returns JET_OK
+ * when every item succeeded or returned a warning, else the status of the
+ * first failed item (each item's own status is in its `status`). */
+typedef struct {
+    int32_t n;                        /* vertices */
+    const int64_t *xadj;              /* device int64[n+1] */
+    const int32_t *adjncy;            /* device int32[xadj[n]] */
+    const int32_t *vwgt, *adjwgt;     /* device, NULL = unit */
+    int32_t k;
+    double eps;
+    uint64_t seed;
+    int32_t *part_out;                /* device int32[n] */
+    int64_t cut;                      /* out: cut of part_out */
+    int32_t status;                   /* out: the item's jet_partition status */
+    float ms;                         /* out: host wall time of the item on its worker */
+} jet_batch_item;
+int jet_partition_batch(jet_ctx *ctx, int32_t count, jet_batch_item *items, int32_t workers);
+
 /* --- single passes (for composition and per-pass checks) ---------------- */
 
 /* Cost (Sec. 2.1) and part weights of `part`.  pw_out: device int64[k] or

@@ -28,7 +28,7 @@ EXPORTED_SYMBOLS = [
     "jet_options_default", "jet_ctx_create", "jet_ctx_destroy", "jet_coarsen", "jet_hier_destroy",
     "jet_hier_info", "jet_hier_level", "jet_uncoarsen", "jet_refine", "jet_last_trace", "jet_partition",
     "jet_partition_host", "jet_cut", "jet_lp_pass", "jet_rebalance_pass", "jet_hem", "jet_initial_partition",
-    "jet_status_string", "jet_last_error", "jet_lp_pass_noalloc", "jet_two_hop",
+    "jet_status_string", "jet_last_error", "jet_lp_pass_noalloc", "jet_two_hop", "jet_partition_batch",
 ]
 JET_NOALLOC_MAX_N = 262144
 
@@ -150,6 +150,7 @@ def load_library(path: str | None = None):
                                                   P(i64), P(i64)]),
             "jet_hem": (ctypes.c_int, [vp, i32, vp, vp, vp, u64, i32, i32, vp]),
             "jet_two_hop": (ctypes.c_int, [vp, i32, vp, vp, vp, vp]),
+            "jet_partition_batch": (ctypes.c_int, [vp, i32, vp, i32]),
             "jet_initial_partition": (ctypes.c_int, [vp, i32, vp, vp, vp, i32, vp]),
             "jet_status_string": (ctypes.c_char_p, [ctypes.c_int]),
             "jet_last_error": (ctypes.c_char_p, []),
@@ -190,6 +191,14 @@ class _DevArray:
     def __init__(self, ptr: int, n: int, typestr: str):
         self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (ptr, False), "version": 3,
                                          "strides": None}
+
+
+class _BatchItem(ctypes.Structure):
+    """jet_batch_item."""
+    _fields_ = [("n", ctypes.c_int32), ("xadj", ctypes.c_void_p), ("adjncy", ctypes.c_void_p),
+                ("vwgt", ctypes.c_void_p), ("adjwgt", ctypes.c_void_p), ("k", ctypes.c_int32), ("eps", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("part_out", ctypes.c_void_p), ("cut", ctypes.c_int64),
+                ("status", ctypes.c_int32), ("ms", ctypes.c_float)]
 
 
 class Hierarchy:
@@ -314,6 +323,25 @@ class Context:
             self._h, n, _ptr(xadj), _ptr(adjncy), _ptr(vwgt), _ptr(adjwgt), int(k), float(eps), int(seed),
             _ptr(part), ctypes.byref(cut), ctypes.byref(st)), "jet_partition")
         return (part, cut.value, Stats.from_c(st)) if return_stats else (part, cut.value)
+
+    def partition_batch(self, graphs, workers=8):
+        """jet_partition_batch: ``graphs`` is a list of dicts with keys xadj,
+        adjncy and optionally vwgt, adjwgt, k, eps, seed.  Returns a list of
+        (part int32 tensor, cut, status, ms) in the same order."""
+        items = (_BatchItem * max(len(graphs), 1))()
+        keep = []
+        for i, gd in enumerate(graphs):
+            n, xadj, adjncy, vwgt, adjwgt = self._graph(gd["xadj"], gd["adjncy"], gd.get("vwgt"), gd.get("adjwgt"))
+            part = self._out(n)
+            keep.append((xadj, adjncy, vwgt, adjwgt, part))
+            it = items[i]
+            it.n = n
+            it.xadj, it.adjncy, it.vwgt, it.adjwgt = _ptr(xadj), _ptr(adjncy), _ptr(vwgt), _ptr(adjwgt)
+            it.k = int(gd.get("k", 2)); it.eps = float(gd.get("eps", 0.03)); it.seed = int(gd.get("seed", 1))
+            it.part_out = _ptr(part)
+        self.last_status = _check(load_library().jet_partition_batch(self._h, len(graphs), items, int(workers)),
+                                  "jet_partition_batch")
+        return [(keep[i][4], items[i].cut, items[i].status, items[i].ms) for i in range(len(graphs))]
 
     def partition_host(self, xadj, adjncy, vwgt=None, adjwgt=None, k=2, eps=0.03, seed=1, part_out=None,
                        return_stats=False):

@@ -66,7 +66,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
             list(ex.map(run, jobs))
     if force or jobs or _stale(LIB, objs):
         tmp = LIB + f".{os.getpid()}.tmp"
-        run([nvcc(), "-shared", *ARCH, "-o", tmp, *objs])
+        run([nvcc(), "-shared", *ARCH, "-o", tmp, *objs, "-lpthread"])
         os.replace(tmp, LIB)
     return LIB
 

@@ -3,9 +3,13 @@
 #include "jet_internal.cuh"
 
 #include <algorithm>
+#include <atomic>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <new>
+#include <thread>
+#include <vector>
 
 namespace jet {
 
@@ -491,6 +495,65 @@ int jet_partition(jet_ctx *ctx, int32_t n, const int64_t *xadj, const int32_t *a
     r = jet_uncoarsen(ctx, h, k, eps, seed, part_out, cut_out, stats);
     jet_hier_destroy(h);
     return r;
+}
+
+int jet_partition_batch(jet_ctx *ctx, int32_t count, jet_batch_item *items, int32_t workers) {
+    if (!ctx || count < 0 || (count > 0 && !items)) return JET_EINVAL;
+    if (count == 0) return JET_OK;
+    Ctx &c = ctx->c;
+    JET_TRY(use_device(c));
+    if (workers <= 0) workers = 8;
+    workers = std::min(workers, count);
+    // the workers' streams start after the work already on the caller's stream
+    cudaEvent_t start = nullptr;
+    JET_CUDA_TRY(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
+    cudaError_t e = cudaEventRecord(start, c.stream);
+    if (e != cudaSuccess) {
+        cudaEventDestroy(start);
+        record_cuda_error(e, "cudaEventRecord", __FILE__, __LINE__);
+        return JET_ECUDA;
+    }
+    std::atomic<int32_t> next{0};
+    std::vector<int> wstat((size_t)workers, JET_OK);
+    auto worker = [&](int w) {
+        cudaSetDevice(c.device);
+        cudaStream_t s = nullptr;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            wstat[(size_t)w] = JET_ECUDA;
+            return;
+        }
+        cudaStreamWaitEvent(s, start, 0);
+        jet_ctx *wc = nullptr;
+        int r = jet_ctx_create(c.device, s, &c.opt, &wc);
+        if (r != JET_OK) {
+            wstat[(size_t)w] = r;
+            cudaStreamDestroy(s);
+            return;
+        }
+        for (;;) {
+            int32_t i = next.fetch_add(1);
+            if (i >= count) break;
+            jet_batch_item &it = items[i];
+            auto t0 = std::chrono::steady_clock::now();
+            it.cut = 0;
+            it.status = jet_partition(wc, it.n, it.xadj, it.adjncy, it.vwgt, it.adjwgt, it.k, it.eps, it.seed,
+                                      it.part_out, &it.cut, nullptr);
+            it.ms = std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        }
+        jet_ctx_destroy(wc);
+        cudaStreamDestroy(s);
+    };
+    std::vector<std::thread> pool;
+    pool.reserve((size_t)workers);
+    for (int w = 0; w < workers; ++w) pool.emplace_back(worker, w);
+    for (auto &t : pool) t.join();
+    cudaEventDestroy(start);
+    for (int w = 0; w < workers; ++w)
+        if (wstat[(size_t)w] != JET_OK) return wstat[(size_t)w];
+    for (int32_t i = 0; i < count; ++i)
+        if (items[i].status < 0) return items[i].status;
+    return JET_OK;
 }
 
 int jet_partition_host(jet_ctx *ctx, int32_t n, const int64_t *xadj, const int32_t *adjncy, const int32_t *vwgt,

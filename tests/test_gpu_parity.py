@@ -436,6 +436,22 @@ def test_partition_graph_loop_matches_oracle(ctx_graph, name, g, unit):
     _check_partition(ctx_graph, g, unit, 64, seed=3)
 
 
+def test_partition_batch_matches_oracle(ctx):
+    """The batched form: graphs of uneven size (RGGs as in the batched
+    workload, a mesh, an R-MAT graph), each with its own k and seed, on
+    4 workers; every graph bit-exact with the oracle."""
+    rng = np.random.default_rng(3)
+    gs = [graphgen.rgg(int(n), seed=i + 1) for i, n in enumerate(np.exp(rng.uniform(np.log(1000), np.log(60000), 10)))]
+    gs += [graphgen.grid3d(16, 16, 16, vw=(1, 4), ew=(1, 10), seed=2), graphgen.rmat(12, seed=4)]
+    ks = [int(x) for x in rng.choice(np.arange(2, 65, 2), len(gs))]
+    items = [dict(xadj=g.xadj, adjncy=g.adjncy, vwgt=g.vwgt, adjwgt=g.adjwgt, k=k, eps=0.03, seed=i + 7)
+             for i, (g, k) in enumerate(zip(gs, ks))]
+    out = ctx.partition_batch(items, workers=4)
+    for (part, cut, status, ms), g, k, it in zip(out, gs, ks, items):
+        ref = oracle.partition(g, k, 0.03, it["seed"])
+        assert status == ref.status and cut == ref.cut and (_np(part) == ref.part).all()
+
+
 def test_partition_host_entry_point(ctx):
     g = graphgen.grid3d(16, 16, 16, vw=(1, 4), ew=(1, 10), seed=4)
     ref = oracle.partition(g, 32, 0.03, 3)
