@@ -649,11 +649,11 @@ template <bool EW>
 __device__ __forceinline__ int32_t afterburn_term(const Level &L, int32_t v, int32_t Fv, int32_t pd, int32_t ps,
                                                   int64_t j) {
     int32_t u = __ldg(L.g.adj + j);
-    // the three loads are independent: one round trip, not two
+    // long rows (one warp each) are bandwidth-bound: the move is loaded only
+    // for the neighbours that take it
     int32_t pu = L.part[u];
     const int32_t fu = L.prio[u];
-    const int32_t nu = L.nxt[u];
-    if (fu > Fv || (fu == Fv && u < v)) pu = nxt_to(nu);
+    if (fu > Fv || (fu == Fv && u < v)) pu = nxt_to(L.nxt[u]);
     int32_t w = edge_w<EW>(L.g, j);
     return pu == pd ? w : (pu == ps ? -w : 0);
 }
@@ -739,15 +739,26 @@ __device__ inline void ph_afterburn(const Level &L, LpExport ex, Grid G, char *a
 // old part read from nxt, never from part[] (which the commit overwrites);
 // for an edge with both ends moving the smaller id accounts for the cut.
 // ---------------------------------------------------------------------------
-template <bool EW>
+// FLAT (short rows, one thread each, latency-bound): stamp, packed move and
+// part loaded together, one round trip; otherwise (long rows, bandwidth-bound)
+// the move or the part is loaded after the stamp, whichever is needed.
+template <bool EW, bool FLAT>
 __device__ __forceinline__ int64_t apply_edge(const Level &L, int32_t v, int32_t a, int32_t b, int32_t it, int32_t u,
                                               int32_t w, int32_t *other) {
-    // stamp, packed move and part loaded together (one round trip)
     const bool mu = L.mstamp[u] == it;
-    const int32_t x = L.nxt[u];
-    const int32_t p = L.part[u];
-    const int32_t pu = mu ? nxt_from(x) : p;
-    const int32_t pn = mu ? nxt_to(x) : p;
+    int32_t pu, pn;
+    if constexpr (FLAT) {
+        const int32_t x = L.nxt[u];
+        const int32_t p = L.part[u];
+        pu = mu ? nxt_from(x) : p;
+        pn = mu ? nxt_to(x) : p;
+    } else if (mu) {
+        const int32_t x = L.nxt[u];
+        pu = nxt_from(x);
+        pn = nxt_to(x);
+    } else {
+        pu = pn = L.part[u];
+    }
     *other = pn != b;
     int32_t diff = (int)(pn != b) - (int)(pu != a);
     if (!mu) {
@@ -780,7 +791,7 @@ __device__ inline void ph_apply(const Level &L, Grid G, char *arena) {
         int32_t ne = 0;
         for (int64_t j = beg + lane; j < end; j += 32) {
             int32_t o;
-            c += apply_edge<EW>(L, v, a, b, it, __ldg(L.g.adj + j), edge_w<EW>(L.g, j), &o);
+            c += apply_edge<EW, false>(L, v, a, b, it, __ldg(L.g.adj + j), edge_w<EW>(L.g, j), &o);
             ne += o;
         }
         c = warp_sum_i64(c);
@@ -819,7 +830,7 @@ __device__ inline void ph_apply(const Level &L, Grid G, char *arena) {
                 for (int t = 0; t < kSmallDeg; ++t) {
                     if (t < d) {
                         int32_t o;
-                        dc += apply_edge<EW>(L, v, a, b, it, uu[t], edge_w<EW>(L.g, beg + t), &o);
+                        dc += apply_edge<EW, true>(L, v, a, b, it, uu[t], edge_w<EW>(L.g, beg + t), &o);
                         ne += o;
                     }
                 }
