@@ -291,6 +291,117 @@ int jet_two_hop(jet_ctx *ctx, int32_t n, const int64_t *xadj, const int32_t *adj
 int jet_initial_partition(jet_ctx *ctx, int32_t n, const int64_t *xadj, const int32_t *adjncy,
                           const int32_t *vwgt, int32_t k, int32_t *part_out);
 
+/* Plain pipeline's partition of the coarsest level of `h`: the greedy initial
+ * partition refined by Alg. 3 exactly as jet_uncoarsen refines that level
+ * (same c, same level seed), without the finer levels.  part_out: device
+ * int32[n of the coarsest level].  These are the training labels of the
+ * learned initial partition. */
+int jet_coarsest_refined(jet_ctx *ctx, const jet_hier *h, int32_t k, double eps, uint64_t seed, int32_t *part_out,
+                         int64_t *cut_out);
+
+/* --- learned initial partition (an extension: the paper uses Metis for the
+ * initial partition of the coarsest graph, Sec. 3) ----------------------
+ *
+ * A message-passing network proposes the k-way partition of the coarsest
+ * graph; the plain greedy initial partition stays its fallback and its judge.
+ *
+ * Features (JET_LIP_FEATURES float32 per vertex, each ratio one IEEE float32
+ * division of float32-converted integers, the divisor taken as 1 when 0):
+ *   1, deg/max deg, vw/max vw, s = S/W, dist/max dist, wdeg/max wdeg,
+ *   tri(2^j s) and tri(2^j s + 1/4) for j = 0..4, tri(y) = |2 (y - floor y) - 1|,
+ * with S(v) the weight before v and dist(v) the BFS distance in the greedy
+ * order of jet_initial_partition, wdeg the sum of v's edge weights.
+ * Network (rows are vertices; H0 = features, d0 = 16, d1 = d2 = 64):
+ *   A_l = mean of H_{l-1} over the neighbours (0 without neighbours),
+ *   H_l = relu([H_{l-1}, A_l] W_l + b_l), l = 1..3, W_l: (2 d_{l-1}) x 64;
+ *   logits = H_3 Wo + bo, Wo: 64 x k;  loss = mean cross-entropy of softmax.
+ * The dense products run on the tensor cores with bf16 operands (rounded to
+ * nearest even from the float32 values) and float32 accumulation; everything
+ * else is float32.  Parameters are one float32 vector in the order W1, b1,
+ * W2, b2, W3, b3, Wo, bo, matrices row-major (input index first):
+ * jet_lip_num_params(k) entries.  Training uses Adam (beta1 0.9, beta2
+ * 0.999, epsilon 1e-8) on float32 master parameters. */
+#define JET_LIP_FEATURES 16
+#define JET_LIP_HIDDEN 64
+#define JET_LIP_MAX_K 256
+#define JET_LIP_MAX_N (1 << 20)   /* largest coarsest graph the learned proposal is tried on */
+typedef struct jet_lip jet_lip;
+
+/* Parameter count for k parts, or -1 for k outside [2, JET_LIP_MAX_K]. */
+int64_t jet_lip_num_params(int32_t k);
+
+/* A model for k parts on the context's device, initialised from the HOST
+ * array params (jet_lip_num_params(k) floats; the caller draws them).
+ * Adam's moments start at zero.  Destroy with jet_lip_destroy. */
+int jet_lip_create(jet_ctx *ctx, int32_t k, const float *params, jet_lip **out);
+void jet_lip_destroy(jet_lip *m);
+/* Copy the parameters to / from a HOST array; setting resets Adam. */
+int jet_lip_get_params(jet_ctx *ctx, const jet_lip *m, float *params_out);
+int jet_lip_set_params(jet_ctx *ctx, jet_lip *m, const float *params);
+
+/* Input features of one graph: x_out device float32[n * JET_LIP_FEATURES]
+ * (row-major).  Edge weights enter wdeg only; vwgt NULL = unit. */
+int jet_lip_features(jet_ctx *ctx, int32_t n, const int64_t *xadj, const int32_t *adjncy, const int32_t *vwgt,
+                     const int32_t *adjwgt, float *x_out);
+
+/* Canonical labels of a partition: parts renumbered 0, 1, ... by first
+ * occurrence when the vertices are visited in the greedy order (component,
+ * BFS distance, id) — the order the features describe.  part: device
+ * int32[n] in [0, k); labels_out: device int32[n]. */
+int jet_lip_labels(jet_ctx *ctx, int32_t n, const int64_t *xadj, const int32_t *adjncy, int32_t k,
+                   const int32_t *part, int32_t *labels_out);
+
+/* Forward pass on a graph (or a block-diagonal union of graphs, each row
+ * aggregating its own neighbours): x device float32[n * 16], logits_out
+ * device float32[n * k] (row-major). */
+int jet_lip_forward(jet_ctx *ctx, const jet_lip *m, int32_t n, const int64_t *xadj, const int32_t *adjncy,
+                    const float *x, float *logits_out);
+
+/* Mean cross-entropy against labels (device int32[n] in [0, k); JET_EINVAL
+ * otherwise) and its gradient: *loss_out host, grad_out device
+ * float32[jet_lip_num_params(k)] in parameter order.  Weight gradients are
+ * reduced over fixed row blocks in a fixed order: results are bit-identical
+ * between runs. */
+int jet_lip_loss_grad(jet_ctx *ctx, const jet_lip *m, int32_t n, const int64_t *xadj, const int32_t *adjncy,
+                      const float *x, const int32_t *labels, float *loss_out, float *grad_out);
+
+/* One Adam step with learning rate lr on that loss; *loss_out (host, may be
+ * NULL) = the loss before the step. */
+int jet_lip_train_step(jet_ctx *ctx, jet_lip *m, int32_t n, const int64_t *xadj, const int32_t *adjncy,
+                       const float *x, const int32_t *labels, float lr, float *loss_out);
+
+/* Balanced decode of logits (device float32[n * k]): a(v) = argmax (lowest
+ * part on ties); margin = largest minus second largest logit (float32);
+ * vertices visited by margin descending, then id ascending; a vertex takes
+ * a(v) while that part's weight plus its own stays <= cap, else the lightest
+ * part (lowest id on ties).  Logits must be finite.  part_out device int32[n]. */
+int jet_lip_decode(jet_ctx *ctx, int32_t n, const float *logits, const int32_t *vwgt, int32_t k, int64_t cap,
+                   int32_t *part_out);
+
+/* The network's proposal for one graph: features, forward, decode with cap =
+ * the balance limit of jet_refine for the model's k and eps. */
+int jet_lip_initial_partition(jet_ctx *ctx, const jet_lip *m, int32_t n, const int64_t *xadj, const int32_t *adjncy,
+                              const int32_t *vwgt, const int32_t *adjwgt, double eps, int32_t *part_out);
+
+/* Learned form of Alg. 1 for the model's k: one jet_coarsen, then
+ * jet_uncoarsen twice on that hierarchy, from the greedy initial partition
+ * (the plain result, identical to jet_partition's) and from the network's
+ * proposal.  The proposal's result is kept iff it is balanced while the plain
+ * one is not, or both are alike in balance and its exactly computed cut is
+ * <= the plain cut.  The proposal is skipped (plain kept) when the coarsest
+ * level has more than JET_LIP_MAX_N vertices.  stats (may be NULL) describe
+ * the kept run, with ms_total = the whole call; info (may be NULL) both. */
+typedef struct {
+    int64_t cut_plain, cut_learned;     /* cut_learned = -1 when the proposal was skipped */
+    int32_t status_plain, status_learned;
+    int32_t chosen;                     /* 1 learned kept, 0 plain kept */
+    int32_t n_coarsest;
+    float ms_coarsen, ms_plain, ms_proposal, ms_learned; /* CUDA-event times of the phases */
+} jet_learned_info;
+int jet_partition_learned(jet_ctx *ctx, const jet_lip *m, int32_t n, const int64_t *xadj, const int32_t *adjncy,
+                          const int32_t *vwgt, const int32_t *adjwgt, double eps, uint64_t seed, int32_t *part_out,
+                          int64_t *cut_out, jet_stats *stats, jet_learned_info *info);
+
 /* Human-readable name of a status code (static storage). */
 const char *jet_status_string(int status);
 

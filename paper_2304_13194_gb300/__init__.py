@@ -21,7 +21,8 @@ from .binding import (  # noqa: F401
     FLAG_VALIDATE, FLAG_HOSTLOOP, FLAG_PROFILE, FLAG_NO_LOCKS, FLAG_NO_AFTERBURN, FLAG_WEAK_AFTERBURN, FLAG_BASELINE_LP,
     FLAG_TWO_HOP, FLAG_STRICT_GAIN,
     KIND_LP, KIND_RW, KIND_RS, NONE_GAIN, EXPORTED_SYMBOLS,
+    LearnedPartitioner, num_lip_params, LIP_FEATURES, LIP_HIDDEN, LIP_MAX_K, LIP_MAX_N,
 )
 
 __all__ = ["Context", "Options", "Stats", "JetError", "load_library", "status_string", "JET_MAX_K",
-           "EXPORTED_SYMBOLS"]
+           "EXPORTED_SYMBOLS", "LearnedPartitioner", "num_lip_params"]

@@ -29,7 +29,11 @@ EXPORTED_SYMBOLS = [
     "jet_hier_info", "jet_hier_level", "jet_uncoarsen", "jet_refine", "jet_last_trace", "jet_partition",
     "jet_partition_host", "jet_cut", "jet_lp_pass", "jet_rebalance_pass", "jet_hem", "jet_initial_partition",
     "jet_status_string", "jet_last_error", "jet_lp_pass_noalloc", "jet_two_hop", "jet_partition_batch",
+    "jet_coarsest_refined", "jet_lip_num_params", "jet_lip_create", "jet_lip_destroy", "jet_lip_get_params",
+    "jet_lip_set_params", "jet_lip_features", "jet_lip_labels", "jet_lip_forward", "jet_lip_loss_grad",
+    "jet_lip_train_step", "jet_lip_decode", "jet_lip_initial_partition", "jet_partition_learned",
 ]
+LIP_FEATURES, LIP_HIDDEN, LIP_MAX_K, LIP_MAX_N = 16, 64, 256, 1 << 20
 JET_NOALLOC_MAX_N = 262144
 
 _STATUS = {0: "JET_OK", 1: "JET_WUNBALANCED", 2: "JET_WITERLIMIT", -1: "JET_EINVAL", -2: "JET_EGRAPH",
@@ -152,6 +156,21 @@ def load_library(path: str | None = None):
             "jet_two_hop": (ctypes.c_int, [vp, i32, vp, vp, vp, vp]),
             "jet_partition_batch": (ctypes.c_int, [vp, i32, vp, i32]),
             "jet_initial_partition": (ctypes.c_int, [vp, i32, vp, vp, vp, i32, vp]),
+            "jet_coarsest_refined": (ctypes.c_int, [vp, vp, i32, f64, u64, vp, P(i64)]),
+            "jet_lip_num_params": (i64, [i32]),
+            "jet_lip_create": (ctypes.c_int, [vp, i32, vp, P(vp)]),
+            "jet_lip_destroy": (None, [vp]),
+            "jet_lip_get_params": (ctypes.c_int, [vp, vp, vp]),
+            "jet_lip_set_params": (ctypes.c_int, [vp, vp, vp]),
+            "jet_lip_features": (ctypes.c_int, [vp, i32, vp, vp, vp, vp, vp]),
+            "jet_lip_labels": (ctypes.c_int, [vp, i32, vp, vp, i32, vp, vp]),
+            "jet_lip_forward": (ctypes.c_int, [vp, vp, i32, vp, vp, vp, vp]),
+            "jet_lip_loss_grad": (ctypes.c_int, [vp, vp, i32, vp, vp, vp, vp, P(ctypes.c_float), vp]),
+            "jet_lip_train_step": (ctypes.c_int, [vp, vp, i32, vp, vp, vp, vp, ctypes.c_float, P(ctypes.c_float)]),
+            "jet_lip_decode": (ctypes.c_int, [vp, i32, vp, vp, i32, i64, vp]),
+            "jet_lip_initial_partition": (ctypes.c_int, [vp, vp, i32, vp, vp, vp, vp, f64, vp]),
+            "jet_partition_learned": (ctypes.c_int, [vp, vp, i32, vp, vp, vp, vp, f64, u64, vp, P(i64), P(_CStats),
+                                                     P(_LearnedInfo)]),
             "jet_status_string": (ctypes.c_char_p, [ctypes.c_int]),
             "jet_last_error": (ctypes.c_char_p, []),
         }
@@ -199,6 +218,125 @@ class _BatchItem(ctypes.Structure):
                 ("vwgt", ctypes.c_void_p), ("adjwgt", ctypes.c_void_p), ("k", ctypes.c_int32), ("eps", ctypes.c_double),
                 ("seed", ctypes.c_uint64), ("part_out", ctypes.c_void_p), ("cut", ctypes.c_int64),
                 ("status", ctypes.c_int32), ("ms", ctypes.c_float)]
+
+
+class _LearnedInfo(ctypes.Structure):
+    """jet_learned_info."""
+    _fields_ = [("cut_plain", ctypes.c_int64), ("cut_learned", ctypes.c_int64), ("status_plain", ctypes.c_int32),
+                ("status_learned", ctypes.c_int32), ("chosen", ctypes.c_int32), ("n_coarsest", ctypes.c_int32),
+                ("ms_coarsen", ctypes.c_float), ("ms_plain", ctypes.c_float), ("ms_proposal", ctypes.c_float),
+                ("ms_learned", ctypes.c_float)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class LearnedPartitioner:
+    """A jet_lip model (the learned initial partition's network) for k parts
+    on a context's device.  ``params`` is the initial parameter vector
+    (float32, jet_lip_num_params(k) entries, drawn by the caller)."""
+
+    def __init__(self, ctx: "Context", k: int, params):
+        self._ctx, self.k = ctx, int(k)
+        self.num_params = num_lip_params(k)
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        if p.size != self.num_params:
+            raise ValueError(f"params: expected {self.num_params} entries, got {p.size}")
+        h = ctypes.c_void_p()
+        _check(load_library().jet_lip_create(ctx._h, self.k, ctypes.c_void_p(p.ctypes.data), ctypes.byref(h)),
+               "jet_lip_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load_library().jet_lip_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self) -> np.ndarray:
+        out = np.zeros(self.num_params, np.float32)
+        _check(load_library().jet_lip_get_params(self._ctx._h, self._h, ctypes.c_void_p(out.ctypes.data)),
+               "jet_lip_get_params")
+        return out
+
+    def set_params(self, params):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        if p.size != self.num_params:
+            raise ValueError("params size")
+        _check(load_library().jet_lip_set_params(self._ctx._h, self._h, ctypes.c_void_p(p.ctypes.data)),
+               "jet_lip_set_params")
+
+    def forward(self, xadj, adjncy, x):
+        """Logits (float32 tensor n x k) of graph (xadj, adjncy) with features x (n x 16)."""
+        torch = _torch()
+        c = self._ctx
+        n, xadj, adjncy, _, _ = c._graph(xadj, adjncy, None, None)
+        x = c._dev(x, torch.float32, "x", n * LIP_FEATURES)
+        out = c._out(n * self.k, torch.float32)
+        _check(load_library().jet_lip_forward(c._h, self._h, n, _ptr(xadj), _ptr(adjncy), _ptr(x), _ptr(out)),
+               "jet_lip_forward")
+        return out.view(n, self.k)
+
+    def loss_grad(self, xadj, adjncy, x, labels):
+        """(mean cross-entropy, gradient float32 tensor in parameter order)."""
+        torch = _torch()
+        c = self._ctx
+        n, xadj, adjncy, _, _ = c._graph(xadj, adjncy, None, None)
+        x = c._dev(x, torch.float32, "x", n * LIP_FEATURES)
+        y = c._dev(labels, torch.int32, "labels", n)
+        grad = c._out(self.num_params, torch.float32)
+        loss = ctypes.c_float()
+        _check(load_library().jet_lip_loss_grad(c._h, self._h, n, _ptr(xadj), _ptr(adjncy), _ptr(x), _ptr(y),
+                                                ctypes.byref(loss), _ptr(grad)), "jet_lip_loss_grad")
+        return loss.value, grad
+
+    def train_step(self, xadj, adjncy, x, labels, lr=1e-3) -> float:
+        """One Adam step; returns the loss before it."""
+        torch = _torch()
+        c = self._ctx
+        n, xadj, adjncy, _, _ = c._graph(xadj, adjncy, None, None)
+        x = c._dev(x, torch.float32, "x", n * LIP_FEATURES)
+        y = c._dev(labels, torch.int32, "labels", n)
+        loss = ctypes.c_float()
+        _check(load_library().jet_lip_train_step(c._h, self._h, n, _ptr(xadj), _ptr(adjncy), _ptr(x), _ptr(y),
+                                                 float(lr), ctypes.byref(loss)), "jet_lip_train_step")
+        return loss.value
+
+    def initial_partition(self, xadj, adjncy, vwgt=None, adjwgt=None, eps=0.03):
+        """The network's proposal (features, forward, balanced decode)."""
+        c = self._ctx
+        n, xadj, adjncy, vwgt, adjwgt = c._graph(xadj, adjncy, vwgt, adjwgt)
+        part = c._out(n)
+        _check(load_library().jet_lip_initial_partition(c._h, self._h, n, _ptr(xadj), _ptr(adjncy), _ptr(vwgt),
+                                                        _ptr(adjwgt), float(eps), _ptr(part)),
+               "jet_lip_initial_partition")
+        return part
+
+    def partition(self, xadj, adjncy, vwgt=None, adjwgt=None, eps=0.03, seed=1, return_stats=False):
+        """jet_partition_learned: (part, cut, info dict[, Stats])."""
+        c = self._ctx
+        n, xadj, adjncy, vwgt, adjwgt = c._graph(xadj, adjncy, vwgt, adjwgt)
+        part = c._out(n)
+        cut = ctypes.c_int64()
+        st = _CStats()
+        info = _LearnedInfo()
+        c.last_status = _check(load_library().jet_partition_learned(
+            c._h, self._h, n, _ptr(xadj), _ptr(adjncy), _ptr(vwgt), _ptr(adjwgt), float(eps), int(seed), _ptr(part),
+            ctypes.byref(cut), ctypes.byref(st), ctypes.byref(info)), "jet_partition_learned")
+        out = (part, cut.value, info.as_dict())
+        return out + (Stats.from_c(st),) if return_stats else out
+
+
+def num_lip_params(k: int) -> int:
+    v = load_library().jet_lip_num_params(int(k))
+    if v < 0:
+        raise ValueError(f"k = {k} outside [2, {LIP_MAX_K}]")
+    return int(v)
 
 
 class Hierarchy:
@@ -475,4 +613,44 @@ class Context:
         part = self._out(n)
         _check(load_library().jet_initial_partition(self._h, n, _ptr(xadj), _ptr(adjncy), _ptr(vwgt), int(k),
                                                     _ptr(part)), "jet_initial_partition")
+        return part
+
+    def coarsest_refined(self, hier: Hierarchy, k=2, eps=0.03, seed=1):
+        """jet_coarsest_refined: the plain pipeline's refined partition of the
+        coarsest level (part tensor, cut)."""
+        n = hier.info()[1][-1]
+        part = self._out(n)
+        cut = ctypes.c_int64()
+        _check(load_library().jet_coarsest_refined(self._h, hier._h, int(k), float(eps), int(seed), _ptr(part),
+                                                   ctypes.byref(cut)), "jet_coarsest_refined")
+        return part, cut.value
+
+    def lip_features(self, xadj, adjncy, vwgt=None, adjwgt=None):
+        """jet_lip_features: float32 tensor n x 16."""
+        torch = _torch()
+        n, xadj, adjncy, vwgt, adjwgt = self._graph(xadj, adjncy, vwgt, adjwgt)
+        x = self._out(n * LIP_FEATURES, torch.float32)
+        _check(load_library().jet_lip_features(self._h, n, _ptr(xadj), _ptr(adjncy), _ptr(vwgt), _ptr(adjwgt),
+                                               _ptr(x)), "jet_lip_features")
+        return x.view(n, LIP_FEATURES)
+
+    def lip_labels(self, xadj, adjncy, k, part):
+        """jet_lip_labels: canonical labels of ``part``."""
+        torch = _torch()
+        n, xadj, adjncy, _, _ = self._graph(xadj, adjncy, None, None)
+        p = self._dev(part, torch.int32, "part", n)
+        out = self._out(n)
+        _check(load_library().jet_lip_labels(self._h, n, _ptr(xadj), _ptr(adjncy), int(k), _ptr(p), _ptr(out)),
+               "jet_lip_labels")
+        return out
+
+    def lip_decode(self, logits, k, cap, vwgt=None):
+        """jet_lip_decode of float32 logits (n x k)."""
+        torch = _torch()
+        lg = self._dev(logits, torch.float32, "logits")
+        n = lg.numel() // int(k)
+        vw = self._dev(vwgt, torch.int32, "vwgt", n, allow_none=True)
+        part = self._out(n)
+        _check(load_library().jet_lip_decode(self._h, n, _ptr(lg), _ptr(vw), int(k), int(cap), _ptr(part)),
+               "jet_lip_decode")
         return part

@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libjet.so")
 SOURCES = ["jet_api.cu", "jet_refine.cu", "jet_coarsen.cu", "jet_initpart.cu", "jet_sort.cu", "jet_twohop.cu",
-           "jet_noalloc.cu"]
+           "jet_noalloc.cu", "jet_learn.cu"]
 HEADERS = [os.path.join(CSRC, "jet_internal.cuh"), os.path.join(CSRC, "jet_phases.cuh"), os.path.join(INCLUDE, "jet.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

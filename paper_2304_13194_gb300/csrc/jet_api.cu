@@ -130,8 +130,8 @@ __global__ void k_check_part(int32_t n, const int32_t *part, int32_t k, int *bad
 // Argument checks plus the overflow limits of jet.h (and the full graph
 // check with JET_FLAG_VALIDATE).  Fills g; materialises unit vertex weights
 // into `ones` when vwgt is NULL.
-static int prepare_graph(Ctx &c, int32_t n, const int64_t *xadj, const int32_t *adjncy, const int32_t *vwgt,
-                         const int32_t *adjwgt, DGraph &g, DevBuf &ones, bool need_vw) {
+int prepare_graph(Ctx &c, int32_t n, const int64_t *xadj, const int32_t *adjncy, const int32_t *vwgt,
+                  const int32_t *adjwgt, DGraph &g, DevBuf &ones, bool need_vw) {
     if (n < 0 || !xadj) return JET_EINVAL;
     cudaStream_t s = c.stream;
     int64_t nnz = 0;
@@ -169,7 +169,7 @@ static int prepare_graph(Ctx &c, int32_t n, const int64_t *xadj, const int32_t *
     return JET_OK;
 }
 
-static int check_part(Ctx &c, int32_t n, const int32_t *part, int32_t k) {
+int check_part(Ctx &c, int32_t n, const int32_t *part, int32_t k) {
     if (n == 0) return JET_OK;
     if (!part) return JET_EINVAL;
     DevBuf b;
@@ -182,9 +182,9 @@ static int check_part(Ctx &c, int32_t n, const int32_t *part, int32_t k) {
     return (c.pinned[0] & 0xFFFFFFFF) ? JET_EINVAL : JET_OK;
 }
 
-static bool bad_k_eps(int32_t k, double eps) { return k < 1 || k > JET_MAX_K || !(eps >= 0.0) || !std::isfinite(eps); }
+bool bad_k_eps(int32_t k, double eps) { return k < 1 || k > JET_MAX_K || !(eps >= 0.0) || !std::isfinite(eps); }
 
-static int use_device(Ctx &c) {
+int use_device(Ctx &c) {
     JET_CUDA_TRY(cudaSetDevice(c.device));
     t_pool = c.pool;
     return JET_OK;
@@ -211,8 +211,8 @@ struct EventTimer {
     }
 };
 
-static int uncoarsen(Ctx &c, const jet_hier *h, int32_t k, double eps, uint64_t seed, int32_t *part_out, int64_t *cut_out,
-                     jet_stats *st) {
+int uncoarsen(Ctx &c, const jet_hier *h, int32_t k, double eps, uint64_t seed, const int32_t *init_coarsest,
+              int32_t *part_out, int64_t *cut_out, jet_stats *st) {
     cudaStream_t s = c.stream;
     int32_t l = h->levels - 1;
     int32_t nmax = 1;
@@ -231,8 +231,12 @@ static int uncoarsen(Ctx &c, const jet_hier *h, int32_t k, double eps, uint64_t 
         g.n = h->n[i]; g.nnz = h->nnz[i]; g.xadj = h->xadj[i]; g.adj = h->adj[i]; g.vw = h->vw[i]; g.ew = h->ew[i];
         return g;
     };
-    JET_TRY(initial_partition(c, level_graph(l), k, cur));
-    c.launches += 1;
+    if (init_coarsest) {
+        JET_CUDA_TRY(cudaMemcpyAsync(cur, init_coarsest, (size_t)h->n[l] * 4, cudaMemcpyDeviceToDevice, s));
+    } else {
+        JET_TRY(initial_partition(c, level_graph(l), k, cur));
+        c.launches += 1;
+    }
     cudaEventRecord(ev.e[1], s);
     int status = JET_OK;
     int64_t cut = 0, maxw = 0;
@@ -441,11 +445,34 @@ int jet_uncoarsen(jet_ctx *ctx, const jet_hier *h, int32_t k, double eps, uint64
         return JET_OK;
     }
     int64_t l0 = c.launches;
-    int r = uncoarsen(c, h, k, eps, seed, part_out, cut_out, stats);
+    int r = uncoarsen(c, h, k, eps, seed, nullptr, part_out, cut_out, stats);
     if (stats) {
         stats->ms_total = stats->ms_coarsen + stats->ms_init + stats->ms_refine;
         stats->kernel_launches = h->launches + (c.launches - l0);
     }
+    return r;
+}
+
+int jet_coarsest_refined(jet_ctx *ctx, const jet_hier *h, int32_t k, double eps, uint64_t seed, int32_t *part_out,
+                         int64_t *cut_out) {
+    if (!ctx || !h || bad_k_eps(k, eps)) return JET_EINVAL;
+    const int32_t l = h->levels - 1;
+    if (h->n[l] > 0 && !part_out) return JET_EINVAL;
+    Ctx &c = ctx->c;
+    JET_TRY(use_device(c));
+    if (h->n[l] == 0) {
+        if (cut_out) *cut_out = 0;
+        return JET_OK;
+    }
+    DGraph g;
+    g.n = h->n[l]; g.nnz = h->nnz[l]; g.xadj = h->xadj[l]; g.adj = h->adj[l]; g.vw = h->vw[l]; g.ew = h->ew[l];
+    JET_TRY(initial_partition(c, g, k, part_out));
+    int64_t cut = 0, maxw = 0;
+    LevelReport rep;
+    int r = refine_level(c, g, k, eps, l == 0, level_seed(seed, l), part_out, &cut, &maxw, &rep);
+    if (r < 0) return r;
+    JET_TRY(sync_stream(c));
+    if (cut_out) *cut_out = cut;
     return r;
 }
 

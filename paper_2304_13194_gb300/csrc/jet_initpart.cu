@@ -175,10 +175,21 @@ __global__ void k_assign(int32_t n, const int32_t *val, const int64_t *S, const 
         part[val[i]] = (int32_t)(((long long)k * S[i]) / W);
 }
 
+// The order itself, by vertex: S(v), position and distance.
+__global__ void k_order_out(int32_t n, const int32_t *val, const int64_t *S, const int32_t *dist, int64_t *S_out,
+                            int32_t *rank_out, int32_t *dist_out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = val[i];
+        if (S_out) S_out[v] = S[i];
+        if (rank_out) rank_out[v] = (int32_t)i;
+        if (dist_out) dist_out[v] = dist[v];
+    }
+}
+
 
 }  // namespace
 
-int initial_partition(Ctx &c, const DGraph &g, int32_t k, int32_t *part) {
+int initial_partition(Ctx &c, const DGraph &g, int32_t k, int32_t *part, GreedyOut *go) {
     cudaStream_t s = c.stream;
     const int64_t n = g.n;
     if (n == 0) return JET_OK;
@@ -253,8 +264,17 @@ int initial_partition(Ctx &c, const DGraph &g, int32_t k, int32_t *part) {
 
     // 4. weights before each vertex in that order, then P
     JET_TRY(device_exscan(SortedWeight{order, g.vw}, n, S, &ctl->total, scan_scr, s));
-    k_assign<<<gv, kTB, 0, s>>>((int32_t)n, order, S, ctl, k, part);
-    c.launches += 4;
+    c.launches += 3;
+    if (part) {
+        k_assign<<<gv, kTB, 0, s>>>((int32_t)n, order, S, ctl, k, part);
+        c.launches += 1;
+    }
+    if (go) {
+        k_order_out<<<gv, kTB, 0, s>>>((int32_t)n, order, S, dist, go->S, go->rank, go->dist);
+        c.launches += 1;
+        JET_CUDA_TRY(cudaMemcpyAsync(&go->W, &ctl->total, 8, cudaMemcpyDeviceToHost, s));
+        go->maxdist = maxdist;
+    }
     JET_CUDA_TRY(cudaGetLastError());
     JET_CUDA_TRY(cudaStreamSynchronize(s));
     return JET_OK;

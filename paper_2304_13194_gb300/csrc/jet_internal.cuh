@@ -473,7 +473,18 @@ int cut_and_weights(Ctx &c, const DGraph &g, int32_t k, const int32_t *part, int
 // jet_coarsen.cu
 int hem(Ctx &c, const DGraph &g, uint64_t seed, int32_t level, int32_t rounds, int32_t *mate);
 int coarsen(Ctx &c, const DGraph &g0, int32_t k, uint64_t seed, jet_hier *h);
-int initial_partition(Ctx &c, const DGraph &g, int32_t k, int32_t *part);
+// The greedy order behind the initial partition (component, BFS distance,
+// id), for the learned initial partition's features and labels.  Device
+// arrays are the caller's (any may be null); the scalars are filled on return.
+struct GreedyOut {
+    int32_t *dist = nullptr;   // int32[n]: BFS distance from the component's lowest id
+    int64_t *S = nullptr;      // int64[n]: weight of the vertices before v in the order
+    int32_t *rank = nullptr;   // int32[n]: position of v in the order
+    int32_t maxdist = 0;       // deepest BFS level
+    int64_t W = 0;             // total vertex weight
+};
+// part may be null when only the order is wanted.
+int initial_partition(Ctx &c, const DGraph &g, int32_t k, int32_t *part, GreedyOut *go = nullptr);
 
 // jet_sort.cu: stable LSD radix sort of (key, value) pairs.
 struct SortScratch {
@@ -497,5 +508,14 @@ int project(Ctx &c, int32_t n_fine, const int32_t *cmap, const int32_t *coarse_p
 // host helpers (jet_api.cu)
 int64_t balance_limit(int64_t W, int32_t k, double eps, int64_t *opt);
 int sync_stream(Ctx &c);
+int use_device(Ctx &c);
+bool bad_k_eps(int32_t k, double eps);
+int check_part(Ctx &c, int32_t n, const int32_t *part, int32_t k);   // JET_EINVAL unless every part is in [0, k)
+int prepare_graph(Ctx &c, int32_t n, const int64_t *xadj, const int32_t *adjncy, const int32_t *vwgt,
+                  const int32_t *adjwgt, DGraph &g, DevBuf &ones, bool need_vw);
+// Alg. 1 after coarsening; init_coarsest (device, n of the coarsest level)
+// replaces the greedy initial partition when not null.
+int uncoarsen(Ctx &c, const jet_hier *h, int32_t k, double eps, uint64_t seed, const int32_t *init_coarsest,
+              int32_t *part_out, int64_t *cut_out, jet_stats *st);
 
 }  // namespace jet

@@ -52,5 +52,6 @@ def test_options_struct_layout_matches_header():
     assert ctypes.sizeof(binding.Options) == 56
     # jet_batch_item: int32, 4 pointers, int32, double, uint64, pointer, int64, int32, float
     assert ctypes.sizeof(binding._BatchItem) == 88
+    assert ctypes.sizeof(binding._LearnedInfo) == 48
     # jet_stats: int32 + 2*64 int64 + 3*64 int32 + 64 int64 + 2 int64 + 5 float + 2 int64
     assert ctypes.sizeof(binding._CStats) % 8 == 0

@@ -1,0 +1,262 @@
+"""GPU checks of the learned initial partition (jet_lip_*): features, labels
+and decode bit-exact against the oracle (oracle/mpnn.py); forward, loss and
+gradient against the oracle's float64 evaluation with the same bf16 operand
+rounding; Adam's first step against its closed form; the keep-or-fall-back
+rule of jet_partition_learned; and a small training run that reports what
+the trained network gains over the plain initial partition."""
+import json
+
+import numpy as np
+import pytest
+import torch
+
+import graphgen
+import oracle
+from helpers import graph_from_triples
+from oracle import mpnn
+
+pytestmark = pytest.mark.gpu
+
+jet = pytest.importorskip("paper_2304_13194_gb300")
+from paper_2304_13194_gb300 import train_lip  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    c = jet.Context(0)
+    yield c
+    c.close()
+
+
+def _d(a, dt):
+    return None if a is None else torch.as_tensor(np.asarray(a)).cuda().to(dt)
+
+
+def _args(g):
+    return (_d(g.xadj, torch.int64), _d(g.adjncy, torch.int32), _d(g.vwgt, torch.int32), _d(g.adjwgt, torch.int32))
+
+
+def _graphs():
+    iso = graphgen.Graph(5, np.zeros(6, np.int64), np.zeros(0, np.int32), np.ones(5, np.int32),
+                         np.zeros(0, np.int32))
+    return [
+        ("grid2d_23x17", graphgen.grid2d(23, 17)),
+        ("grid3d_15x12x9_w", graphgen.grid3d(15, 12, 9, vw=(1, 4), ew=(1, 10), seed=3)),
+        ("rmat11_w", graphgen.rmat(11, seed=4, vw=(1, 5), ew=(1, 7))),
+        ("union_iso", graphgen.disjoint_union(graphgen.grid2d(9, 9), graphgen.gnp(300, 0.004, seed=2), iso)),
+        ("path", graph_from_triples(7, [[i, i + 1, i + 1] for i in range(6)])),
+    ]
+
+
+GRAPHS = _graphs()
+
+
+def _theta(k, seed):
+    """Seeded parameters scaled by 1/sqrt(fan-in), biases small."""
+    r = np.random.default_rng(seed)
+    parts = []
+    for shape in mpnn.param_shapes(k):
+        if len(shape) == 2:
+            parts.append(r.normal(0, 1.0 / np.sqrt(shape[0]), shape))
+        else:
+            parts.append(r.normal(0, 0.1, shape))
+    return mpnn.flatten(parts).astype(np.float32)
+
+
+@pytest.mark.parametrize("name,g", GRAPHS, ids=[n for n, _ in GRAPHS])
+def test_features_bit_exact(ctx, name, g):
+    x = ctx.lip_features(*_args(g)).cpu().numpy()
+    want = mpnn.features(g)
+    assert np.array_equal(x.view(np.uint32), want.view(np.uint32))
+
+
+@pytest.mark.parametrize("name,g", GRAPHS, ids=[n for n, _ in GRAPHS])
+def test_labels_bit_exact(ctx, name, g):
+    k = 13
+    part = np.random.default_rng(g.n).integers(0, k - 3, g.n).astype(np.int32)   # some parts empty
+    lab = ctx.lip_labels(_d(g.xadj, torch.int64), _d(g.adjncy, torch.int32), k, _d(part, torch.int32))
+    assert np.array_equal(lab.cpu().numpy(), mpnn.canonical(part, mpnn.greedy_sequence(g)))
+
+
+# Tolerance of the float paths.  Both sides round the same operands to bf16;
+# the GPU accumulates in float32 (K <= 256 terms: relative error ~1e-5) and
+# aggregates in float32, so an operand whose float32 and float64 values fall
+# on opposite sides of a bf16 rounding boundary (probability ~K 2^-16 per
+# element) moves by one bf16 ulp (2^-8 relative).  Relative Frobenius errors
+# therefore sit near 1e-4; the bounds below leave a factor of ten.
+FWD_RTOL = 2e-3
+GRAD_RTOL = 1e-2
+
+
+def _learn_graph():
+    return graphgen.disjoint_union(graphgen.grid3d(14, 13, 11, vw=(1, 4), ew=(1, 10), seed=5),
+                                   graphgen.rmat(10, seed=6))
+
+
+@pytest.mark.parametrize("k", [5, 64, 200])
+def test_forward_matches_oracle(ctx, k):
+    g = _learn_graph()             # 2002 + 1024 rows: many 64-row tiles, ragged tail
+    theta = _theta(k, k)
+    X = mpnn.features(g)
+    m = jet.LearnedPartitioner(ctx, k, theta)
+    lg = m.forward(_d(g.xadj, torch.int64), _d(g.adjncy, torch.int32), _d(X, torch.float32)).cpu().numpy()
+    ref, _, _ = mpnn.forward(g, X, theta.astype(np.float64), k, emulate_bf16=True)
+    err = np.linalg.norm(lg - ref) / np.linalg.norm(ref)
+    assert err < FWD_RTOL, err
+    m.close()
+
+
+@pytest.mark.parametrize("k", [5, 64, 200])
+def test_loss_and_gradient_match_oracle(ctx, k):
+    g = _learn_graph()
+    theta = _theta(k, 100 + k)
+    X = mpnn.features(g)
+    y = np.random.default_rng(k).integers(0, k, g.n).astype(np.int32)
+    m = jet.LearnedPartitioner(ctx, k, theta)
+    loss, grad = m.loss_grad(_d(g.xadj, torch.int64), _d(g.adjncy, torch.int32), _d(X, torch.float32),
+                             _d(y, torch.int32))
+    grad = grad.cpu().numpy().astype(np.float64)
+    l_ref, g_ref = mpnn.loss_and_grad(g, X, theta.astype(np.float64), k, y, emulate_bf16=True)
+    assert abs(loss - l_ref) <= 1e-4 * abs(l_ref)
+    o = 0
+    for shape in mpnn.param_shapes(k):
+        c = int(np.prod(shape))
+        a, b = grad[o:o + c], g_ref[o:o + c]
+        assert np.linalg.norm(a - b) <= GRAD_RTOL * np.linalg.norm(b) + 1e-7, (shape, np.linalg.norm(a - b),
+                                                                               np.linalg.norm(b))
+        o += c
+    # against the unrounded float64 network: bf16's own error only
+    _, g64 = mpnn.loss_and_grad(g, X, theta.astype(np.float64), k, y)
+    assert np.linalg.norm(grad - g64) <= 0.05 * np.linalg.norm(g64)
+    # deterministic: a second call gives the same bits
+    _, grad2 = m.loss_grad(_d(g.xadj, torch.int64), _d(g.adjncy, torch.int32), _d(X, torch.float32),
+                           _d(y, torch.int32))
+    assert np.array_equal(grad2.cpu().numpy(), grad.astype(np.float32))
+    m.close()
+
+
+def test_bad_label_is_rejected(ctx):
+    g = graphgen.grid2d(8, 8)
+    m = jet.LearnedPartitioner(ctx, 4, _theta(4, 1))
+    y = np.zeros(g.n, np.int32)
+    y[7] = 4
+    with pytest.raises(jet.JetError):
+        m.loss_grad(_d(g.xadj, torch.int64), _d(g.adjncy, torch.int32), _d(mpnn.features(g), torch.float32),
+                    _d(y, torch.int32))
+    m.close()
+
+
+def test_first_adam_step_is_lr_times_sign(ctx):
+    # at step 1 Adam's bias-corrected moments are g and g^2: the update is
+    # -lr g / (|g| + 1e-8), i.e. -lr sign(g) wherever |g| >> 1e-8
+    k = 16
+    g = _learn_graph()
+    theta = _theta(k, 7)
+    X = mpnn.features(g)
+    y = np.random.default_rng(3).integers(0, k, g.n).astype(np.int32)
+    m = jet.LearnedPartitioner(ctx, k, theta)
+    lr = 1e-3
+    m.train_step(_d(g.xadj, torch.int64), _d(g.adjncy, torch.int32), _d(X, torch.float32), _d(y, torch.int32), lr=lr)
+    delta = m.get_params().astype(np.float64) - theta.astype(np.float64)
+    _, g_ref = mpnn.loss_and_grad(g, X, theta.astype(np.float64), k, y, emulate_bf16=True)
+    sure = np.abs(g_ref) > 1e-3 * np.abs(g_ref).max()
+    assert sure.sum() > 1000
+    assert np.abs(delta[sure] + lr * np.sign(g_ref[sure])).max() <= 1e-2 * lr
+    assert np.abs(delta).max() <= lr * 1.001
+    m.close()
+
+
+def test_training_reduces_loss_on_fixed_batch(ctx):
+    k = 8
+    g = graphgen.grid2d(30, 30)
+    X = mpnn.features(g)
+    y = np.minimum((mpnn.greedy_order(g)[2] * k) // g.n, k - 1).astype(np.int32)   # greedy parts as labels
+    m = jet.LearnedPartitioner(ctx, k, train_lip.init_params(k, 0))
+    args = (_d(g.xadj, torch.int64), _d(g.adjncy, torch.int32), _d(X, torch.float32), _d(y, torch.int32))
+    first = m.train_step(*args, lr=1e-2)
+    for _ in range(150):
+        last = m.train_step(*args, lr=1e-2)
+    assert last < 0.5 * first, (first, last)
+    m.close()
+
+
+@pytest.mark.parametrize("k,ties", [(37, False), (64, True), (1, False), (3, True)])
+def test_decode_bit_exact(ctx, k, ties):
+    r = np.random.default_rng(k)
+    n = 5003
+    if ties:
+        L = r.integers(0, 3, (n, k)).astype(np.float32)           # equal logits and equal margins
+    else:
+        L = (r.normal(size=(n, k)) + np.linspace(0, 2, k)).astype(np.float32)
+    vw = r.integers(1, 6, n).astype(np.int32)
+    cap, _ = oracle.limit(int(vw.sum()), k, 0.03)
+    part = ctx.lip_decode(_d(L, torch.float32), k, cap, _d(vw, torch.int32)).cpu().numpy()
+    assert np.array_equal(part, mpnn.decode(L, vw, k, cap))
+
+
+def test_decode_empty(ctx):
+    part = ctx.lip_decode(torch.zeros(0, device="cuda"), 4, 10)
+    assert part.numel() == 0
+
+
+def test_proposal_is_valid_and_balanced(ctx):
+    k = 64
+    g = graphgen.grid3d(20, 20, 20)
+    m = jet.LearnedPartitioner(ctx, k, train_lip.init_params(k, 3))
+    part = m.initial_partition(*_args(g), eps=0.03).cpu().numpy()
+    L, _ = oracle.limit(g.n, k, 0.03)
+    assert part.min() >= 0 and part.max() < k
+    assert np.bincount(part, minlength=k).max() <= L    # unit weights: the fill never exceeds the cap
+    m.close()
+
+
+@pytest.mark.parametrize("g", [graphgen.grid3d(24, 24, 24, vw=(1, 4), ew=(1, 10), seed=9), graphgen.rmat(13, seed=3)],
+                         ids=["grid24w", "rmat13"])
+def test_partition_learned_keeps_the_better_result(ctx, g):
+    k = 64
+    m = jet.LearnedPartitioner(ctx, k, train_lip.init_params(k, 5))
+    args = _args(g)
+    part, cut, info = m.partition(*args, eps=0.03, seed=3)
+    p_plain, c_plain = ctx.partition(*args, k=k, eps=0.03, seed=3)
+    assert info["cut_plain"] == c_plain
+    assert ctx.cut(*args, k, part)[0] == cut
+    if info["chosen"]:
+        assert cut == info["cut_learned"] <= c_plain
+    else:
+        assert cut == c_plain and torch.equal(part, p_plain)
+    m.close()
+
+
+def test_training_gain_on_held_out_seeds(ctx):
+    """Train on pairs from small seeded graphs, then compare on graphs from
+    seeds training never saw: the final cut of the learned form (never worse
+    by construction) against the plain form, and the network's label accuracy
+    against chance."""
+    k, eps = 64, 0.03
+    train_graphs = [graphgen.grid3d(d, d, d, vw=(1, 4), ew=(1, 10), seed=s) for d in (16, 20, 24) for s in (1, 2)]
+    train_graphs += [graphgen.rmat(sc, seed=s) for sc in (12, 13) for s in (1, 2)]
+    pairs = []
+    for g in train_graphs:
+        for cs in range(12):
+            p = train_lip.make_pair(ctx, g, k, eps, seed=1000 + cs)
+            if p is not None:
+                pairs.append(p)
+    assert len(pairs) >= 80
+    held = pairs[-10:]
+    pairs = pairs[:-10]
+    m = jet.LearnedPartitioner(ctx, k, train_lip.init_params(k, 0))
+    acc0 = train_lip.accuracy(m, held)
+    hist = train_lip.train(m, pairs, epochs=25, batch_graphs=16, lr=3e-3)
+    acc = train_lip.accuracy(m, held)
+    assert hist[-1] < 0.7 * hist[0]
+    assert acc > max(3.0 / k, 2 * acc0)
+    ev = train_lip.evaluate(ctx, m, [(f"grid22w_s{s}", graphgen.grid3d(22, 22, 22, vw=(1, 4), ew=(1, 10), seed=s))
+                                     for s in (101, 102)] +
+                            [(f"rmat13_s{s}", graphgen.rmat(13, seed=s)) for s in (101, 102)], eps, seed=7)
+    for e in ev:
+        assert e["cut"] <= e["cut_plain"]
+    gain = float(np.mean([1 - e["cut"] / e["cut_plain"] for e in ev]))
+    print(json.dumps(dict(loss_first=hist[0], loss_last=hist[-1], acc_before=acc0, acc_after=acc,
+                          mean_cut_gain=gain, kept=sum(e["chosen"] for e in ev), eval=ev)))
