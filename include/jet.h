@@ -344,10 +344,10 @@ int jet_lip_set_params(jet_ctx *ctx, jet_lip *m, const float *params);
 int jet_lip_features(jet_ctx *ctx, int32_t n, const int64_t *xadj, const int32_t *adjncy, const int32_t *vwgt,
                      const int32_t *adjwgt, float *x_out);
 
-/* Canonical labels of a partition: parts renumbered 0, 1, ... by first
- * occurrence when the vertices are visited in the greedy order (component,
- * BFS distance, id) — the order the features describe.  part: device
- * int32[n] in [0, k); labels_out: device int32[n]. */
+/* Canonical labels of a partition: parts renumbered 0, 1, ... by the mean
+ * position of their vertices in the greedy order (component, BFS distance,
+ * id) — the order the features describe — compared exactly, equal means by
+ * part id.  part: device int32[n] in [0, k); labels_out: device int32[n]. */
 int jet_lip_labels(jet_ctx *ctx, int32_t n, const int64_t *xadj, const int32_t *adjncy, int32_t k,
                    const int32_t *part, int32_t *labels_out);
 

@@ -201,18 +201,26 @@ def loss_and_grad(g, X, theta, k, y, emulate_bf16=False):
 
 
 def canonical(part, order=None) -> np.ndarray:
-    """Relabel parts 0, 1, 2, ... by first occurrence when the vertices are
-    visited in `order` (default: id order)."""
+    """Relabel parts 0, 1, 2, ... by the mean position of their vertices when
+    the vertices are visited in `order` (default: id order); equal means by
+    part id; parts without vertices take no label.  Means are compared
+    exactly (sum_p * count_q against sum_q * count_p)."""
     part = np.asarray(part)
     order = np.arange(len(part)) if order is None else np.asarray(order)
-    mp, out = {}, np.empty_like(part)
-    for v in order:
-        p = int(part[v])
-        if p not in mp:
-            mp[p] = len(mp)
+    pos = np.empty(len(part), np.int64)
+    pos[order] = np.arange(len(part))
+    parts = sorted(set(int(p) for p in part))
+    tot = {p: 0 for p in parts}
+    cnt = {p: 0 for p in parts}
     for v in range(len(part)):
-        out[v] = mp[int(part[v])]
-    return out
+        tot[int(part[v])] += int(pos[v])
+        cnt[int(part[v])] += 1
+
+    def before(q, p):
+        a, b = tot[q] * cnt[p], tot[p] * cnt[q]
+        return a < b or (a == b and q < p)
+    label = {p: sum(before(q, p) for q in parts if q != p) for p in parts}
+    return np.array([label[int(p)] for p in part], dtype=part.dtype)
 
 
 def greedy_sequence(g) -> np.ndarray:

@@ -410,18 +410,34 @@ __global__ void k_feat(DGraph g, const int64_t *wdeg, const FeatStats *st, const
 }
 
 // ---- canonical labels ----------------------------------------------------------
-__global__ void k_lab_first(int32_t n, const int32_t *part, const int32_t *rank, int32_t *first) {
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
-        atomicMin(&first[part[v]], rank[v]);
+// Parts renumbered by the mean position of their vertices in the greedy
+// order: per part the sum of positions and the count (integer atomics, so the
+// result does not depend on their order), then each part's rank.
+__global__ void k_lab_sum(int32_t n, const int32_t *part, const int32_t *rank, unsigned long long *sum,
+                          unsigned long long *cnt) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        atomicAdd(&sum[part[v]], (unsigned long long)rank[v]);
+        atomicAdd(&cnt[part[v]], 1ULL);
+    }
 }
 
-// newlab[p] = number of parts whose first position comes before p's (empty
-// parts, first = INT_MAX, after all others, by id).  One block.
-__global__ void k_lab_rank(int k, const int32_t *first, int32_t *newlab) {
+// newlab[p] = number of parts before p: nonempty parts by mean position
+// (compared exactly as sum_q cnt_p < sum_p cnt_q), equal means by id, empty
+// parts after all others.  One block.
+__global__ void k_lab_rank(int k, const unsigned long long *sum, const unsigned long long *cnt, int32_t *newlab) {
     for (int p = threadIdx.x; p < k; p += blockDim.x) {
         int c = 0;
-        const int32_t fp = first[p];
-        for (int q = 0; q < k; ++q) c += first[q] < fp || (first[q] == fp && q < p);
+        for (int q = 0; q < k; ++q) {
+            if (q == p) continue;
+            bool before;
+            if (cnt[q] == 0 || cnt[p] == 0) {
+                before = cnt[q] != 0 && cnt[p] == 0 ? true : (cnt[q] == 0 && cnt[p] != 0 ? false : q < p);
+            } else {
+                const unsigned __int128 a = (unsigned __int128)sum[q] * cnt[p], b = (unsigned __int128)sum[p] * cnt[q];
+                before = a < b || (a == b && q < p);
+            }
+            c += before;
+        }
         newlab[p] = c;
     }
 }
@@ -837,18 +853,20 @@ int jet_lip_labels(jet_ctx *ctx, int32_t n, const int64_t *xadj, const int32_t *
     JET_TRY(check_part(c, n, part, k));
     if (n == 0) return JET_OK;
     DevBuf buf;
-    JET_TRY(dev_alloc(buf, align256c((size_t)n * 4) + 2 * align256c((size_t)k * 4), c.stream));
+    const size_t kb = align256c((size_t)k * 8);
+    JET_TRY(dev_alloc(buf, align256c((size_t)n * 4) + 2 * kb + align256c((size_t)k * 4), c.stream));
     int32_t *rank = buf.as<int32_t>();
-    int32_t *first = reinterpret_cast<int32_t *>(buf.as<char>() + align256c((size_t)n * 4));
-    int32_t *newlab = reinterpret_cast<int32_t *>(reinterpret_cast<char *>(first) + align256c((size_t)k * 4));
+    unsigned long long *sum = reinterpret_cast<unsigned long long *>(buf.as<char>() + align256c((size_t)n * 4));
+    unsigned long long *cnt = reinterpret_cast<unsigned long long *>(reinterpret_cast<char *>(sum) + kb);
+    int32_t *newlab = reinterpret_cast<int32_t *>(reinterpret_cast<char *>(cnt) + kb);
     GreedyOut go;
     go.rank = rank;
     JET_TRY(initial_partition(c, g, 1, nullptr, &go));
-    k_fill_i32<<<grid_elems(k), kTB, 0, c.stream>>>(first, k, INT32_MAX);
-    k_lab_first<<<grid_elems(n), kTB, 0, c.stream>>>(n, part, rank, first);
-    k_lab_rank<<<1, kTB, 0, c.stream>>>(k, first, newlab);
+    JET_CUDA_TRY(cudaMemsetAsync(sum, 0, 2 * kb, c.stream));
+    k_lab_sum<<<grid_elems(n), kTB, 0, c.stream>>>(n, part, rank, sum, cnt);
+    k_lab_rank<<<1, kTB, 0, c.stream>>>(k, sum, cnt, newlab);
     k_lab_apply<<<grid_elems(n), kTB, 0, c.stream>>>(n, part, newlab, labels_out);
-    c.launches += 4;
+    c.launches += 3;
     JET_CUDA_TRY(cudaGetLastError());
     return sync_stream(c);
 }

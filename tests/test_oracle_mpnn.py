@@ -170,9 +170,18 @@ def test_bf16_emulation_stays_within_bf16_error():
 
 
 def test_canonical_relabelling():
+    # mean positions: part 3 -> 0.5, parts 0 and 1 -> 3 (tie: lower id first), part 2 -> 5
     part = np.array([3, 3, 1, 0, 1, 2])
-    assert list(mpnn.canonical(part)) == [0, 0, 1, 2, 1, 3]
-    assert list(mpnn.canonical(part, order=[5, 4, 3, 2, 1, 0])) == [3, 3, 1, 2, 1, 0]
+    assert list(mpnn.canonical(part)) == [0, 0, 2, 1, 2, 3]
+    # reversed visit order: part 2 -> 0, parts 0 and 1 -> 2, part 3 -> 4.5
+    assert list(mpnn.canonical(part, order=[5, 4, 3, 2, 1, 0])) == [3, 3, 2, 1, 2, 0]
+    # a partition into consecutive pieces of the order keeps its numbering
+    r = np.random.default_rng(1)
+    order = r.permutation(40)
+    seq = np.repeat(np.arange(8), 5)
+    p = np.empty(40, np.int64)
+    p[order] = r.permutation(8)[seq]
+    assert np.array_equal(mpnn.canonical(p, order)[order], seq)
 
 
 def test_decode_keeps_argmax_when_every_part_has_room():
