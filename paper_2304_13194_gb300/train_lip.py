@@ -14,7 +14,9 @@ only generates inputs, concatenates arrays and loops.
 Default recipe (``python -m paper_2304_13194_gb300.train_lip``): 20,000
 pairs from seeded R-MAT graphs of scale 16-20 (edge factor 16, unit weights)
 and 3D grids 32^3-96^3 (vertex weights 1-4, edge weights 1-10), k = 64,
-eps = 0.03; evaluation on graphs from seeds that training never saw.
+eps = 0.03, coarsening with two-hop matches (Sec. 3.1) so that the power-law
+graphs reach coarsest levels of a few hundred vertices; evaluation on graphs
+from seeds that training never saw, through the same context options.
 """
 from __future__ import annotations
 
@@ -49,24 +51,28 @@ def _dev(ctx, a, dtype):
                                                                      dtype=dtype)
 
 
-def make_pair(ctx, g, k: int, eps: float, seed: int, max_n: int = 16384):
-    """One training example from graph g (graphgen.Graph) and coarsening
-    seed: dict(n, xadj, adjncy, x, y) of the coarsest level, or None when it
-    has more than max_n vertices."""
+def make_pairs(ctx, g, k: int, eps: float, seeds, max_n: int = 16384):
+    """Training examples from graph g (graphgen.Graph), one per coarsening
+    seed: dicts (n, xadj, adjncy, x, y) of the coarsest level; seeds whose
+    coarsest level has more than max_n vertices give none."""
     import torch
-    hier = ctx.coarsen(_dev(ctx, g.xadj, torch.int64), _dev(ctx, g.adjncy, torch.int32),
-                       _dev(ctx, g.vwgt, torch.int32), _dev(ctx, g.adjwgt, torch.int32), k=k, seed=seed)
-    try:
-        levels, ns, _ = hier.info()
-        if ns[-1] > max_n:
-            return None
-        lv = hier.level(levels - 1)
-        part, _ = ctx.coarsest_refined(hier, k=k, eps=eps, seed=seed)
-    finally:
-        hier.close()
-    x = ctx.lip_features(lv["xadj"], lv["adjncy"], lv["vwgt"], lv["adjwgt"])
-    y = ctx.lip_labels(lv["xadj"], lv["adjncy"], k, part)
-    return dict(n=lv["n"], xadj=lv["xadj"], adjncy=lv["adjncy"], x=x, y=y)
+    args = (_dev(ctx, g.xadj, torch.int64), _dev(ctx, g.adjncy, torch.int32), _dev(ctx, g.vwgt, torch.int32),
+            _dev(ctx, g.adjwgt, torch.int32))
+    out = []
+    for seed in seeds:
+        hier = ctx.coarsen(*args, k=k, seed=seed)
+        try:
+            levels, ns, _ = hier.info()
+            if ns[-1] > max_n:
+                continue
+            lv = hier.level(levels - 1)
+            part, _ = ctx.coarsest_refined(hier, k=k, eps=eps, seed=seed)
+        finally:
+            hier.close()
+        x = ctx.lip_features(lv["xadj"], lv["adjncy"], lv["vwgt"], lv["adjwgt"])
+        y = ctx.lip_labels(lv["xadj"], lv["adjncy"], k, part)
+        out.append(dict(n=lv["n"], xadj=lv["xadj"], adjncy=lv["adjncy"], x=x, y=y))
+    return out
 
 
 def collate(pairs):
@@ -162,18 +168,15 @@ def main(argv=None):
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--eval-seeds", default="101,102")
     ap.add_argument("--save", default="")
+    ap.add_argument("--no-two-hop", action="store_true")
     a = ap.parse_args(argv)
-    ctx = _b.Context(0)
+    ctx = _b.Context(0, flags=0 if a.no_two_hop else _b.FLAG_TWO_HOP)
     facts, per = recipe(tuple(int(x) for x in a.scales.split(",") if x),
                         tuple(int(x) for x in a.grids.split(",") if x), pairs=a.pairs)
     t0 = time.time()
     data = []
     for name, f in facts:
-        g = f()
-        for s in range(per):
-            p = make_pair(ctx, g, a.k, a.eps, seed=1000 + s)
-            if p is not None:
-                data.append(p)
+        data += make_pairs(ctx, f(), a.k, a.eps, seeds=range(1000, 1000 + per))
         print(f"{name}: {len(data)} pairs so far ({time.time() - t0:.1f} s)", flush=True)
     model = _b.LearnedPartitioner(ctx, a.k, init_params(a.k, a.seed))
     t1 = time.time()

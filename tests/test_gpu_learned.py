@@ -239,10 +239,7 @@ def test_training_gain_on_held_out_seeds(ctx):
     train_graphs += [graphgen.rmat(sc, seed=s) for sc in (12, 13) for s in (1, 2)]
     pairs = []
     for g in train_graphs:
-        for cs in range(12):
-            p = train_lip.make_pair(ctx, g, k, eps, seed=1000 + cs)
-            if p is not None:
-                pairs.append(p)
+        pairs += train_lip.make_pairs(ctx, g, k, eps, seeds=range(1000, 1012))
     assert len(pairs) >= 80
     held = pairs[-10:]
     pairs = pairs[:-10]
