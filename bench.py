@@ -489,6 +489,22 @@ def run_batched(args):
             print(json.dumps({"sweep": "batched", "mode": "batched", "workers": workers, "graphs": len(items),
                               "seconds": round(t_b, 4), "speedup_vs_sequential": round(t_seq / t_b, 3),
                               "cuts_equal_to_sequential": same}), flush=True)
+        # autotuned: execution choices timed on a sample of 64 graphs, then the whole set
+        t0 = time.perf_counter()
+        rep = ctx.autotune(items[::8], reps=1)
+        t_tune = time.perf_counter() - t0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = ctx.partition_batch(items, workers=rep["workers"])
+        torch.cuda.synchronize()
+        t_b = time.perf_counter() - t0
+        same = all(o[1] == c for o, c in zip(out, seq))
+        print(json.dumps({"sweep": "batched", "mode": "autotuned", "cluster_max_n": rep["cluster_max_n"],
+                          "workers": rep["workers"], "tune_seconds": round(t_tune, 3), "graphs": len(items),
+                          "seconds": round(t_b, 4), "speedup_vs_sequential": round(t_seq / t_b, 3),
+                          "cuts_equal_to_sequential": same,
+                          "candidates": [[c["cluster_max_n"], c["workers"], round(c["ms"], 2)]
+                                         for c in rep["candidates"]]}), flush=True)
     return 0
 
 

@@ -215,6 +215,25 @@ typedef struct {
 } jet_batch_item;
 int jet_partition_batch(jet_ctx *ctx, int32_t count, jet_batch_item *items, int32_t workers);
 
+/* Autotuner of the execution choices (no counterpart in the paper; results
+ * are bit-identical under every choice).  Times `items` (a batch, or one
+ * graph with count = 1) with jet_partition_batch under each candidate —
+ * first cluster_max_n in {0, 1024, 2048, 4096, 8192, 16384} (the largest level
+ * that runs its whole refinement loop in one thread-block-cluster launch),
+ * then, for count > 1, workers in {1, 2, 4, 8, 16} — taking the median of
+ * `reps` timed runs (reps <= 0: 3) after one untimed run, and writes the
+ * fastest cluster_max_n into the context's options.  The items' outputs
+ * hold the last run's results.  report (may be NULL) lists every candidate. */
+#define JET_TUNE_MAX_CAND 16
+typedef struct {
+    int32_t cluster_max_n;                  /* chosen (now in the context's options) */
+    int32_t workers;                        /* chosen worker count for jet_partition_batch */
+    int32_t ncand;                          /* candidates timed */
+    int32_t cand_cluster_max_n[JET_TUNE_MAX_CAND], cand_workers[JET_TUNE_MAX_CAND];
+    float cand_ms[JET_TUNE_MAX_CAND];       /* median host wall time of the whole batch */
+} jet_tune_report;
+int jet_autotune(jet_ctx *ctx, int32_t count, jet_batch_item *items, int32_t reps, jet_tune_report *report);
+
 /* --- single passes (for composition and per-pass checks) ---------------- */
 
 /* Cost (Sec. 2.1) and part weights of `part`.  pw_out: device int64[k] or

@@ -31,7 +31,7 @@ EXPORTED_SYMBOLS = [
     "jet_status_string", "jet_last_error", "jet_lp_pass_noalloc", "jet_two_hop", "jet_partition_batch",
     "jet_coarsest_refined", "jet_lip_num_params", "jet_lip_create", "jet_lip_destroy", "jet_lip_get_params",
     "jet_lip_set_params", "jet_lip_features", "jet_lip_labels", "jet_lip_forward", "jet_lip_loss_grad",
-    "jet_lip_train_step", "jet_lip_decode", "jet_lip_initial_partition", "jet_partition_learned",
+    "jet_lip_train_step", "jet_lip_decode", "jet_lip_initial_partition", "jet_partition_learned", "jet_autotune",
 ]
 LIP_FEATURES, LIP_HIDDEN, LIP_MAX_K, LIP_MAX_N = 16, 64, 256, 1 << 20
 JET_NOALLOC_MAX_N = 262144
@@ -171,6 +171,7 @@ def load_library(path: str | None = None):
             "jet_lip_initial_partition": (ctypes.c_int, [vp, vp, i32, vp, vp, vp, vp, f64, vp]),
             "jet_partition_learned": (ctypes.c_int, [vp, vp, i32, vp, vp, vp, vp, f64, u64, vp, P(i64), P(_CStats),
                                                      P(_LearnedInfo)]),
+            "jet_autotune": (ctypes.c_int, [vp, i32, vp, i32, P(_TuneReport)]),
             "jet_status_string": (ctypes.c_char_p, [ctypes.c_int]),
             "jet_last_error": (ctypes.c_char_p, []),
         }
@@ -218,6 +219,13 @@ class _BatchItem(ctypes.Structure):
                 ("vwgt", ctypes.c_void_p), ("adjwgt", ctypes.c_void_p), ("k", ctypes.c_int32), ("eps", ctypes.c_double),
                 ("seed", ctypes.c_uint64), ("part_out", ctypes.c_void_p), ("cut", ctypes.c_int64),
                 ("status", ctypes.c_int32), ("ms", ctypes.c_float)]
+
+
+class _TuneReport(ctypes.Structure):
+    """jet_tune_report."""
+    _fields_ = [("cluster_max_n", ctypes.c_int32), ("workers", ctypes.c_int32), ("ncand", ctypes.c_int32),
+                ("cand_cluster_max_n", ctypes.c_int32 * 16), ("cand_workers", ctypes.c_int32 * 16),
+                ("cand_ms", ctypes.c_float * 16)]
 
 
 class _LearnedInfo(ctypes.Structure):
@@ -480,6 +488,31 @@ class Context:
         self.last_status = _check(load_library().jet_partition_batch(self._h, len(graphs), items, int(workers)),
                                   "jet_partition_batch")
         return [(keep[i][4], items[i].cut, items[i].status, items[i].ms) for i in range(len(graphs))]
+
+    def autotune(self, graphs, reps=3):
+        """jet_autotune over a batch (list of dicts as in partition_batch):
+        times each candidate execution choice, keeps the fastest
+        cluster_max_n in this context's options and returns the report
+        (chosen cluster_max_n and workers, every candidate's median ms)."""
+        items = (_BatchItem * max(len(graphs), 1))()
+        keep = []
+        for i, gd in enumerate(graphs):
+            n, xadj, adjncy, vwgt, adjwgt = self._graph(gd["xadj"], gd["adjncy"], gd.get("vwgt"), gd.get("adjwgt"))
+            part = self._out(n)
+            keep.append((xadj, adjncy, vwgt, adjwgt, part))
+            it = items[i]
+            it.n = n
+            it.xadj, it.adjncy, it.vwgt, it.adjwgt = _ptr(xadj), _ptr(adjncy), _ptr(vwgt), _ptr(adjwgt)
+            it.k = int(gd.get("k", 2)); it.eps = float(gd.get("eps", 0.03)); it.seed = int(gd.get("seed", 1))
+            it.part_out = _ptr(part)
+        rep = _TuneReport()
+        _check(load_library().jet_autotune(self._h, len(graphs), items, int(reps), ctypes.byref(rep)), "jet_autotune")
+        self.options.cluster_max_n = rep.cluster_max_n
+        m = rep.ncand
+        return dict(cluster_max_n=rep.cluster_max_n, workers=rep.workers,
+                    candidates=[dict(cluster_max_n=rep.cand_cluster_max_n[i], workers=rep.cand_workers[i],
+                                     ms=rep.cand_ms[i]) for i in range(m)],
+                    parts=[(keep[i][4], items[i].cut) for i in range(len(graphs))])
 
     def partition_host(self, xadj, adjncy, vwgt=None, adjwgt=None, k=2, eps=0.03, seed=1, part_out=None,
                        return_stats=False):

@@ -583,6 +583,71 @@ int jet_partition_batch(jet_ctx *ctx, int32_t count, jet_batch_item *items, int3
     return JET_OK;
 }
 
+int jet_autotune(jet_ctx *ctx, int32_t count, jet_batch_item *items, int32_t reps, jet_tune_report *report) {
+    if (!ctx || count <= 0 || !items) return JET_EINVAL;
+    if (reps <= 0) reps = 3;
+    Ctx &c = ctx->c;
+    JET_TRY(use_device(c));
+    jet_tune_report rep;
+    memset(&rep, 0, sizeof(rep));
+    // median wall time of `reps` runs of the batch after one untimed run
+    auto time_batch = [&](int32_t workers, float *ms) -> int {
+        std::vector<float> t;
+        for (int r = 0; r <= reps; ++r) {
+            auto t0 = std::chrono::steady_clock::now();
+            int st = jet_partition_batch(ctx, count, items, workers);
+            if (st < 0) return st;
+            float dt = std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - t0).count();
+            if (r > 0) t.push_back(dt);
+        }
+        std::sort(t.begin(), t.end());
+        *ms = t[t.size() / 2];
+        return JET_OK;
+    };
+    auto record = [&](int32_t cm, int32_t w, float ms) {
+        if (rep.ncand < JET_TUNE_MAX_CAND) {
+            rep.cand_cluster_max_n[rep.ncand] = cm;
+            rep.cand_workers[rep.ncand] = w;
+            rep.cand_ms[rep.ncand] = ms;
+            rep.ncand += 1;
+        }
+    };
+    const int32_t saved = c.opt.cluster_max_n;
+    const int32_t w0 = count > 1 ? 8 : 1;
+    static const int32_t cands[] = {0, 1024, 2048, 4096, 8192, 16384};
+    int32_t best_cm = saved;
+    float best = 0.f;
+    bool have = false;
+    for (int32_t cm : cands) {
+        c.opt.cluster_max_n = cm;
+        float ms = 0.f;
+        int st = time_batch(w0, &ms);
+        if (st < 0) {
+            c.opt.cluster_max_n = saved;
+            return st;
+        }
+        record(cm, w0, ms);
+        if (!have || ms < best) { best = ms; best_cm = cm; have = true; }
+    }
+    c.opt.cluster_max_n = best_cm;
+    int32_t best_w = w0;
+    if (count > 1) {
+        static const int32_t wc[] = {1, 2, 4, 8, 16};
+        float bw = 0.f;
+        bool hw = false;
+        for (int32_t w : wc) {
+            float ms = 0.f;
+            JET_TRY(time_batch(w, &ms));
+            record(best_cm, w, ms);
+            if (!hw || ms < bw) { bw = ms; best_w = w; hw = true; }
+        }
+    }
+    rep.cluster_max_n = best_cm;
+    rep.workers = best_w;
+    if (report) *report = rep;
+    return JET_OK;
+}
+
 int jet_partition_host(jet_ctx *ctx, int32_t n, const int64_t *xadj, const int32_t *adjncy, const int32_t *vwgt,
                        const int32_t *adjwgt, int32_t k, double eps, uint64_t seed, int32_t *part_out, int64_t *cut_out,
                        jet_stats *stats) {

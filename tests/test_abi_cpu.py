@@ -53,5 +53,6 @@ def test_options_struct_layout_matches_header():
     # jet_batch_item: int32, 4 pointers, int32, double, uint64, pointer, int64, int32, float
     assert ctypes.sizeof(binding._BatchItem) == 88
     assert ctypes.sizeof(binding._LearnedInfo) == 48
+    assert ctypes.sizeof(binding._TuneReport) == 12 + 3 * 64
     # jet_stats: int32 + 2*64 int64 + 3*64 int32 + 64 int64 + 2 int64 + 5 float + 2 int64
     assert ctypes.sizeof(binding._CStats) % 8 == 0

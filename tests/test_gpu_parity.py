@@ -452,6 +452,30 @@ def test_partition_batch_matches_oracle(ctx):
         assert status == ref.status and cut == ref.cut and (_np(part) == ref.part).all()
 
 
+def test_autotune_picks_fastest_and_keeps_results():
+    """jet_autotune: every candidate timed, the fastest cluster threshold
+    kept in the context, and every graph still bit-exact with the oracle
+    (execution choices never change results)."""
+    rng = np.random.default_rng(5)
+    gs = [graphgen.rgg(int(n), seed=i + 3) for i, n in enumerate(np.exp(rng.uniform(np.log(1000), np.log(20000), 6)))]
+    ks = [int(x) for x in rng.choice(np.arange(2, 33, 2), len(gs))]
+    items = [dict(xadj=g.xadj, adjncy=g.adjncy, k=k, eps=0.03, seed=i + 1) for i, (g, k) in enumerate(zip(gs, ks))]
+    c = jet.Context(0)
+    rep = c.autotune(items, reps=1)
+    cands = rep["candidates"]
+    assert len(cands) == 6 + 5
+    first = cands[:6]
+    assert rep["cluster_max_n"] == min(first, key=lambda x: x["ms"])["cluster_max_n"]
+    assert rep["workers"] == min(cands[6:], key=lambda x: x["ms"])["workers"]
+    assert c.options.cluster_max_n == rep["cluster_max_n"]
+    for (part, cut), g, k, it in zip(rep["parts"], gs, ks, items):
+        ref = oracle.partition(g, k, 0.03, it["seed"])
+        assert cut == ref.cut and (_np(part) == ref.part).all()
+    part, cut = c.partition(gs[0].xadj, gs[0].adjncy, None, None, k=ks[0], seed=1)
+    assert cut == oracle.partition(gs[0], ks[0], 0.03, 1).cut
+    c.close()
+
+
 def test_partition_host_entry_point(ctx):
     g = graphgen.grid3d(16, 16, 16, vw=(1, 4), ew=(1, 10), seed=4)
     ref = oracle.partition(g, 32, 0.03, 3)
