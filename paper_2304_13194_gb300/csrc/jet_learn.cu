@@ -44,7 +44,7 @@ constexpr int kHd = JET_LIP_HIDDEN;
 constexpr int kLayers = 3;
 constexpr int kGemmBM = 64;        // rows per block of k_gemm_rows (4 warps x 16 rows)
 constexpr int kTnRows = 64;        // rows staged per step of k_gemm_tn
-constexpr int kTnChunk = 512;      // rows per block of k_gemm_tn
+constexpr int kTnChunk = 256;      // rows per block of k_gemm_tn (a constant: the summation order is fixed)
 constexpr int kTnWarps = 8;
 constexpr int kTnMaxTiles = 16;    // 16x8 output tiles per warp of k_gemm_tn
 constexpr int kGemmSmemMax = 100 * 1024;
@@ -160,7 +160,10 @@ __global__ void __launch_bounds__(128) k_gemm_rows(int32_t M, int Kp, int Kv, in
 // P[blk][i*Np + c] = sum_r A(r, i) B(r, c) with bf16 operands and float32
 // accumulation (i < Kp, c < Np; A(r, i) = A[r*lda + i] for i < Kv, B(r, c) =
 // B[r*ldb + c] for c < Nv, zero beyond), and CS[blk][c] = sum_r B(r, c) in
-// float32, rows in order.  Requires (Kp/16) (Np/8) <= kTnWarps * kTnMaxTiles.
+// float32: thread t stages the columns t % 64 + 64 g of the rows t / 64 + 4 j
+// and keeps their running sums, which the four row classes then add in a
+// fixed order.  Requires (Kp/16) (Np/8) <= kTnWarps * kTnMaxTiles, Np <= 256
+// and 256 threads.
 __global__ void __launch_bounds__(256) k_gemm_tn(int32_t M, int Kp, int Kv, int Np, int Nv, const float *A, int lda,
                                                  const float *B, int ldb, float *P, float *CS) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -174,6 +177,8 @@ __global__ void __launch_bounds__(256) k_gemm_tn(int32_t M, int Kp, int Kv, int 
     for (int q = 0; q < kTnMaxTiles; ++q) acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = 0.f;
     const int64_t c0 = (int64_t)blockIdx.x * kTnChunk;
     const int64_t c1 = min((int64_t)M, c0 + kTnChunk);
+    const int tc = threadIdx.x & 63, tr = threadIdx.x >> 6;   // column lane, row class (0..3)
+    float cs[4] = {0.f, 0.f, 0.f, 0.f};
     for (int64_t r0 = c0; r0 < c1; r0 += kTnRows) {
         __syncthreads();
         for (int i = threadIdx.x; i < kTnRows * Kp; i += blockDim.x) {
@@ -181,10 +186,16 @@ __global__ void __launch_bounds__(256) k_gemm_tn(int32_t M, int Kp, int Kv, int 
             const float x = (r0 + r < c1 && kk < Kv) ? A[(r0 + r) * lda + kk] : 0.f;
             At[kk * sr + r] = __float2bfloat16_rn(x);
         }
-        for (int i = threadIdx.x; i < kTnRows * Np; i += blockDim.x) {
-            const int r = i / Np, c = i - r * Np;
-            const float x = (r0 + r < c1 && c < Nv) ? B[(r0 + r) * ldb + c] : 0.f;
-            Bt[c * sr + r] = __float2bfloat16_rn(x);
+#pragma unroll
+        for (int gcol = 0; gcol < 4; ++gcol) {
+            const int c = tc + 64 * gcol;
+            if (c < Np) {
+                for (int r = tr; r < kTnRows; r += 4) {
+                    const float x = (r0 + r < c1 && c < Nv) ? B[(r0 + r) * ldb + c] : 0.f;
+                    cs[gcol] += x;
+                    Bt[c * sr + r] = __float2bfloat16_rn(x);
+                }
+            }
         }
         __syncthreads();
 #pragma unroll
@@ -215,12 +226,14 @@ __global__ void __launch_bounds__(256) k_gemm_tn(int32_t M, int Kp, int Kv, int 
             for (int h = 0; h < 4; ++h) Pb[(i0 + g + (h >> 1) * 8) * Np + n0 + 2 * t + (h & 1)] = acc[q][h];
         }
     }
-    for (int c = threadIdx.x; c < Np; c += blockDim.x) {
-        float s = 0.f;
-        if (c < Nv)
-            for (int64_t r = c0; r < c1; ++r) s += B[r * ldb + c];
-        CS[(int64_t)blockIdx.x * Np + c] = s;
-    }
+    // column sums: the four row classes in order
+    __syncthreads();
+    float *red = reinterpret_cast<float *>(smem_raw);   // [4][256], the staging tiles are no longer read
+#pragma unroll
+    for (int gcol = 0; gcol < 4; ++gcol) red[tr * 256 + tc + 64 * gcol] = cs[gcol];
+    __syncthreads();
+    for (int c = threadIdx.x; c < Np; c += blockDim.x)
+        CS[(int64_t)blockIdx.x * Np + c] = ((red[c] + red[256 + c]) + red[512 + c]) + red[768 + c];
 }
 
 // gW[i*Nv + c] = sum over blocks b (in order) of P[b][i*Np + c] (i < Kv,
@@ -326,12 +339,19 @@ __global__ void __launch_bounds__(kTB) k_softmax_ce(int32_t n, int k, const floa
     }
 }
 
-__global__ void k_loss_total(int nb, const double *part, int32_t n, float *loss) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        double t = 0.0;
-        for (int b = 0; b < nb; ++b) t += part[b];
-        *loss = (float)(t / (double)(n > 0 ? n : 1));
+// Sum of the per-block losses over a fixed tree (thread t takes the blocks
+// t, t + 256, ... in order, then pairwise halving): one block of 256 threads.
+__global__ void __launch_bounds__(256) k_loss_total(int nb, const double *part, int32_t n, float *loss) {
+    __shared__ double sh[256];
+    double t = 0.0;
+    for (int b = threadIdx.x; b < nb; b += 256) t += part[b];
+    sh[threadIdx.x] = t;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
     }
+    if (threadIdx.x == 0) *loss = (float)(sh[0] / (double)(n > 0 ? n : 1));
 }
 
 __global__ void k_adam(int64_t count, float *p, const float *gr, float *m, float *v, float lr, float b1, float b2,
@@ -666,7 +686,7 @@ int backward(Ctx &c, const Lip &m, const DGraph &g, const int32_t *labels, Work 
     const int k = m.k, kp = pad16(k);
     JET_CUDA_TRY(cudaMemsetAsync(w.bad, 0, 4, c.stream));
     k_softmax_ce<<<w.ce_blocks, kTB, 0, c.stream>>>(n, k, w.logits, labels, w.dlog, w.lpart, w.bad);
-    k_loss_total<<<1, 32, 0, c.stream>>>(w.ce_blocks, w.lpart, n, w.loss);
+    k_loss_total<<<1, 256, 0, c.stream>>>(w.ce_blocks, w.lpart, n, w.loss);
     c.launches += 2;
     JET_CUDA_TRY(cudaGetLastError());
     // output layer: dWo = H3^T dlog, dbo = colsum dlog, dH3 = dlog Wo^T

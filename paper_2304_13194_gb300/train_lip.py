@@ -155,6 +155,35 @@ def recipe(scales=(16, 17, 18, 19, 20), grid_sides=(32, 48, 64, 80, 96), graph_s
     return facts, per
 
 
+def step_benchmark(ctx, k: int = 64, graphs: int = 64, side: int = 24, steps: int = 50, seed: int = 0):
+    """Times training steps (forward, backward, Adam) with CUDA events on a
+    block-diagonal batch of `graphs` coarsest levels of seeded weighted
+    meshes side^3; returns dict(vertices, ms_per_step, vertices_per_s)."""
+    import torch
+    import graphgen
+    pairs = []
+    s = 0
+    while len(pairs) < graphs:
+        g = graphgen.grid3d(side, side, side, vw=(1, 4), ew=(1, 10), seed=1 + s)
+        pairs += make_pairs(ctx, g, k, 0.03, seeds=range(1000, 1000 + min(8, graphs - len(pairs))))
+        s += 1
+    b = collate(pairs[:graphs])
+    model = _b.LearnedPartitioner(ctx, k, init_params(k, seed))
+    for _ in range(3):
+        model.train_step(b["xadj"], b["adjncy"], b["x"], b["y"], lr=1e-3)
+    stream = torch.cuda.current_stream(ctx.device)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        model.train_step(b["xadj"], b["adjncy"], b["x"], b["y"], lr=1e-3)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    model.close()
+    return dict(vertices=b["n"], graphs=graphs, ms_per_step=ms, vertices_per_s=b["n"] / ms * 1e3)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--k", type=int, default=64)
@@ -169,8 +198,13 @@ def main(argv=None):
     ap.add_argument("--eval-seeds", default="101,102")
     ap.add_argument("--save", default="")
     ap.add_argument("--no-two-hop", action="store_true")
+    ap.add_argument("--step-benchmark", action="store_true",
+                    help="only time training steps on a batch of 64 coarsest mesh levels")
     a = ap.parse_args(argv)
     ctx = _b.Context(0, flags=0 if a.no_two_hop else _b.FLAG_TWO_HOP)
+    if a.step_benchmark:
+        print(json.dumps(step_benchmark(ctx, a.k)))
+        return
     facts, per = recipe(tuple(int(x) for x in a.scales.split(",") if x),
                         tuple(int(x) for x in a.grids.split(",") if x), pairs=a.pairs)
     t0 = time.time()
