@@ -52,6 +52,9 @@ def parse_args(argv=None):
     p.add_argument("--hostloop", action="store_true",
                    help="drive refinement iterations from the host (same kernels and launch configuration; "
                         "used for profiler launch lists)")
+    p.add_argument("--no-pdl", action="store_true",
+                   help="launch every refinement kernel after the previous one finishes (no programmatic "
+                        "dependent launch); results are identical")
     p.add_argument("--cluster-max-n", type=int, default=None,
                    help="largest level refined by the one-cluster loop (library default if omitted; 0 = never)")
     p.add_argument("--kernel-probe", action="store_true",
@@ -277,7 +280,8 @@ def run_ours(args):
     ew = torch.from_numpy(g.adjwgt).to(device)
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=device)
     copts = {} if args.cluster_max_n is None else {"cluster_max_n": args.cluster_max_n}
-    ctx = jet.Context(local, flags=jet.FLAG_HOSTLOOP if args.hostloop else 0, **copts)
+    pdl_off = jet.FLAG_NO_PDL if args.no_pdl else 0
+    ctx = jet.Context(local, flags=(jet.FLAG_HOSTLOOP if args.hostloop else 0) | pdl_off, **copts)
     stream = torch.cuda.current_stream(device)
 
     def step():
@@ -336,7 +340,7 @@ def run_ours(args):
 
     # ---- roofline of the dominant kernel: CUDA events around each select
     # launch (profiling mode drives the same kernels from the host) ----------
-    pctx = jet.Context(local, flags=jet.FLAG_PROFILE)
+    pctx = jet.Context(local, flags=jet.FLAG_PROFILE | pdl_off)
     flush.zero_()
     _, pcut, pst = pctx.partition(xadj, adj, vw, ew, k=K_PARTS, eps=EPS, seed=SEED, return_stats=True)
     pctx.close()

@@ -75,6 +75,10 @@ extern "C" {
                                       JET_FLAG_NO_AFTERBURN: the baseline LP plus locks) */
 #define JET_FLAG_TWO_HOP 256u      /* coarsening: add two-hop matches (Sec. 3.1) after heavy-edge matching;
                                       the plain method coarsens by heavy-edge matching alone */
+#define JET_FLAG_NO_PDL 1024u      /* execution choice (results do not depend on it): launch every
+                                      refinement kernel only after the previous one has finished,
+                                      instead of letting it start early and wait on the device
+                                      (programmatic dependent launch) */
 
 /* Hyper-parameters the paper names (defaults from jet_options_default):
  *   c_fine = 0.25, c_coarse = 0.75  first-filter ratio c (Sec. 4.1.2, Eq. gainconn_filter);

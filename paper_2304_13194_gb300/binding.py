@@ -21,6 +21,7 @@ FLAG_VALIDATE, FLAG_HOSTLOOP, FLAG_PROFILE = 1, 2, 4
 FLAG_NO_LOCKS, FLAG_NO_AFTERBURN, FLAG_WEAK_AFTERBURN, FLAG_BASELINE_LP = 16, 32, 64, 128
 FLAG_TWO_HOP = 256
 FLAG_STRICT_GAIN = 512
+FLAG_NO_PDL = 1024
 KIND_LP, KIND_RW, KIND_RS = 0, 1, 2
 NONE_GAIN = -(2 ** 31)
 

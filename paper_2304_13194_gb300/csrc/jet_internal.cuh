@@ -172,6 +172,7 @@ struct Level {
     // CUDA-graph loop control (0 when driven from the host)
     unsigned long long h_loop, h_mode;
     int32_t use_graph;
+    int32_t pdl;             // launch the row and tile kernels with programmatic dependent launch
 };
 
 // ---------------------------------------------------------------------------

@@ -66,6 +66,15 @@ __global__ void __launch_bounds__(kTB) k_cut_pw(DGraph g, int32_t k, const int32
 // ---------------------------------------------------------------------------
 #define JET_ARENA reinterpret_cast<char *>(jet_arena)
 
+// Programmatic dependent launch: a kernel lets the next one in the stream be
+// scheduled as soon as all its own blocks have started, and waits for the
+// previous kernel to complete (memory visible) before it touches any data.
+// Both are no-ops for a kernel launched without the attribute.
+__device__ __forceinline__ void pdl_enter() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 __global__ void __launch_bounds__(1024) k_ctl_init(Level L, const int64_t *cut2) { ph_ctl_init(L, cut2); }
 
 // Sets the CUDA-graph conditionals for the first iteration.
@@ -81,19 +90,25 @@ __global__ void __launch_bounds__(kTB) k_copy_best(Level L) { ph_copy_best(L, la
 // Jetlp: work list, select; P_best copy + afterburner (the copy only reads
 // part, which the afterburner does not change, and stays out of the select
 // step)
-__global__ void __launch_bounds__(kTB) k_lp_scan(Level L) { ph_lp_scan(L, launch_grid(), JET_ARENA); }
+__global__ void __launch_bounds__(kTB) k_lp_scan(Level L) {
+    pdl_enter();
+    ph_lp_scan(L, launch_grid(), JET_ARENA);
+}
 template <bool EW>
 __global__ void __launch_bounds__(kTB, 4) k_lp_select(Level L, LpExport ex) {
+    pdl_enter();
     ph_lp_select<EW>(L, ex, launch_grid(), JET_ARENA);
 }
 template <bool EW>
 __global__ void __launch_bounds__(kTB, 4) k_afterburn(Level L, LpExport ex) {
+    pdl_enter();
     ph_copy_best(L, launch_grid());
     ph_afterburn<EW>(L, ex, launch_grid(), JET_ARENA);
 }
 // apply + commit; the last block runs the controller
 template <bool EW>
 __global__ void __launch_bounds__(kTB, 4) k_apply(Level L) {
+    pdl_enter();
     ph_apply<EW>(L, launch_grid(), JET_ARENA);
     if (last_block(L.ctl)) ph_controller(L);
 }
@@ -101,24 +116,36 @@ __global__ void __launch_bounds__(kTB, 4) k_apply(Level L) {
 // take (+ Jetrs eviction scan), cookie cutter
 template <bool STRONG>
 __global__ void __launch_bounds__(kTB) k_rb_scan(Level L) {
+    pdl_enter();
     ph_copy_best(L, launch_grid());
     ph_rb_scan<STRONG>(L, launch_grid(), JET_ARENA);
 }
 template <bool EW, bool STRONG>
 __global__ void __launch_bounds__(kTB, 4) k_rb_cand(Level L) {
+    pdl_enter();
     ph_rb_cand<EW, STRONG>(L, launch_grid(), JET_ARENA);
     if (last_block(L.ctl)) ph_rb_plan(L);
 }
-__global__ void __launch_bounds__(kTB) k_rb_tilehist(Level L) { ph_rb_tilehist(L, launch_grid(), JET_ARENA); }
-__global__ void __launch_bounds__(1024) k_rb_tilescan(Level L) { ph_rb_tilescan(L, launch_grid()); }
+__global__ void __launch_bounds__(kTB) k_rb_tilehist(Level L) {
+    pdl_enter();
+    ph_rb_tilehist(L, launch_grid(), JET_ARENA);
+}
+__global__ void __launch_bounds__(1024) k_rb_tilescan(Level L) {
+    pdl_enter();
+    ph_rb_tilescan(L, launch_grid());
+}
 template <bool STRONG>
 __global__ void __launch_bounds__(kTB) k_rb_take(Level L) {
+    pdl_enter();
     ph_rb_take<STRONG>(L, launch_grid(), JET_ARENA);
     if constexpr (STRONG) {
         if (last_block(L.ctl)) ph_rb_tiletaken_scan(L);
     }
 }
-__global__ void __launch_bounds__(kTB) k_rb_cookie(Level L) { ph_rb_cookie(L, launch_grid(), JET_ARENA); }
+__global__ void __launch_bounds__(kTB) k_rb_cookie(Level L) {
+    pdl_enter();
+    ph_rb_cookie(L, launch_grid(), JET_ARENA);
+}
 
 // ---------------------------------------------------------------------------
 // one cluster per level: every iteration in a single launch
@@ -292,6 +319,24 @@ int list_grid() { return num_sms() * 4; }
 // grid of a kernel over a list of at most `items` entries (one per thread)
 int list_blocks(int64_t items) { return std::min(list_grid(), grid_for(items, kTB)); }
 
+// Launch of a kernel that follows another one of the same pass: with
+// L.pdl it may be scheduled early and waits on the device (pdl_enter).
+template <class... Args>
+cudaError_t launch_dep(const Level &L, void (*kern)(Args...), int grid, int block, size_t smem, cudaStream_t s,
+                       Args... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at{};
+    at.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at.val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = &at;
+    cfg.numAttrs = L.pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 // Kernel sequences of one iteration, by kind.  Each returns, through *nk,
 // the number of kernels it enqueued.
 int enqueue_lp_select(const Level &L, cudaStream_t s, LpExport ex, int *nk) {
@@ -299,8 +344,7 @@ int enqueue_lp_select(const Level &L, cudaStream_t s, LpExport ex, int *nk) {
     bool ew = L.g.ew != nullptr;
     k_lp_scan<<<std::min(list_grid(), grid_for((n + 3) / 4, kTB)), kTB, sm_lp_scan(), s>>>(L);
     const size_t sm = sm_lp_select(L.k, kTB, L.nbig > 0);
-    if (ew) k_lp_select<true><<<list_blocks(n), kTB, sm, s>>>(L, ex);
-    else k_lp_select<false><<<list_blocks(n), kTB, sm, s>>>(L, ex);
+    JET_CUDA_TRY(launch_dep(L, ew ? k_lp_select<true> : k_lp_select<false>, list_blocks(n), kTB, sm, s, L, ex));
     *nk = 2;
     JET_CUDA_TRY(cudaGetLastError());
     return JET_OK;
@@ -308,8 +352,8 @@ int enqueue_lp_select(const Level &L, cudaStream_t s, LpExport ex, int *nk) {
 
 int enqueue_lp_after(const Level &L, cudaStream_t s, LpExport ex, int *nk) {
     int n = L.g.n;
-    if (L.g.ew) k_afterburn<true><<<list_blocks(n), kTB, sm_afterburn(), s>>>(L, ex);
-    else k_afterburn<false><<<list_blocks(n), kTB, sm_afterburn(), s>>>(L, ex);
+    JET_CUDA_TRY(launch_dep(L, L.g.ew ? k_afterburn<true> : k_afterburn<false>, list_blocks(n), kTB, sm_afterburn(), s,
+                            L, ex));
     *nk = 1;
     JET_CUDA_TRY(cudaGetLastError());
     return JET_OK;
@@ -329,14 +373,13 @@ int enqueue_rb_t(const Level &L, cudaStream_t s, int *nk) {
     bool ew = L.g.ew != nullptr;
     k_rb_scan<STRONG><<<std::min(list_grid(), grid_for((n + 3) / 4, kTB)), kTB, sm_rb_scan(), s>>>(L);
     const size_t sm = sm_rb_cand(L.k, kTB, L.nbig > 0);
-    if (ew) k_rb_cand<true, STRONG><<<list_blocks(n), kTB, sm, s>>>(L);
-    else k_rb_cand<false, STRONG><<<list_blocks(n), kTB, sm, s>>>(L);
-    k_rb_tilehist<<<L.ntiles, kTB, sm_rb_tilehist(L.k), s>>>(L);
-    k_rb_tilescan<<<L.k, 1024, 0, s>>>(L);
-    k_rb_take<STRONG><<<L.ntiles, kTB, sm_rb_take(L.k, kTB), s>>>(L);
+    JET_CUDA_TRY(launch_dep(L, ew ? k_rb_cand<true, STRONG> : k_rb_cand<false, STRONG>, list_blocks(n), kTB, sm, s, L));
+    JET_CUDA_TRY(launch_dep(L, k_rb_tilehist, L.ntiles, kTB, sm_rb_tilehist(L.k), s, L));
+    JET_CUDA_TRY(launch_dep(L, k_rb_tilescan, L.k, 1024, 0, s, L));
+    JET_CUDA_TRY(launch_dep(L, k_rb_take<STRONG>, L.ntiles, kTB, sm_rb_take(L.k, kTB), s, L));
     *nk = 5;
     if (STRONG) {
-        k_rb_cookie<<<L.ntiles, kTB, sm_rb_cookie(kTB), s>>>(L);
+        JET_CUDA_TRY(launch_dep(L, k_rb_cookie, L.ntiles, kTB, sm_rb_cookie(kTB), s, L));
         *nk += 1;
     }
     JET_CUDA_TRY(cudaGetLastError());
@@ -664,6 +707,7 @@ static void fill_level_params(Ctx &c, Level &L, int32_t is_finest, uint64_t seed
     L.seed = seed;
     L.use_graph = 0;
     L.h_loop = L.h_mode = 0;
+    L.pdl = (o.flags & JET_FLAG_NO_PDL) ? 0 : 1;
 }
 
 // Algorithmic DRAM bytes of each pass, from the per-iteration trace (neighbour
