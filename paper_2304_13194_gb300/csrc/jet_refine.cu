@@ -66,6 +66,12 @@ __global__ void __launch_bounds__(kTB) k_cut_pw(DGraph g, int32_t k, const int32
 // ---------------------------------------------------------------------------
 #define JET_ARENA reinterpret_cast<char *>(jet_arena)
 
+// Resident blocks of 256 threads per SM that the row kernels are compiled for
+// (register budget 65536 / (256 x blocks)).
+#ifndef JET_ROW_MINB
+#define JET_ROW_MINB 4
+#endif
+
 // Programmatic dependent launch: a kernel lets the next one in the stream be
 // scheduled as soon as all its own blocks have started, and waits for the
 // previous kernel to complete (memory visible) before it touches any data.
@@ -95,19 +101,19 @@ __global__ void __launch_bounds__(kTB) k_lp_scan(Level L) {
     ph_lp_scan(L, launch_grid(), JET_ARENA);
 }
 template <bool EW>
-__global__ void __launch_bounds__(kTB, 4) k_lp_select(Level L, LpExport ex) {
+__global__ void __launch_bounds__(kTB, JET_ROW_MINB) k_lp_select(Level L, LpExport ex) {
     pdl_enter();
     ph_lp_select<EW>(L, ex, launch_grid(), JET_ARENA);
 }
 template <bool EW>
-__global__ void __launch_bounds__(kTB, 4) k_afterburn(Level L, LpExport ex) {
+__global__ void __launch_bounds__(kTB, JET_ROW_MINB) k_afterburn(Level L, LpExport ex) {
     pdl_enter();
     ph_copy_best(L, launch_grid());
     ph_afterburn<EW>(L, ex, launch_grid(), JET_ARENA);
 }
 // apply + commit; the last block runs the controller
 template <bool EW>
-__global__ void __launch_bounds__(kTB, 4) k_apply(Level L) {
+__global__ void __launch_bounds__(kTB, JET_ROW_MINB) k_apply(Level L) {
     pdl_enter();
     ph_apply<EW>(L, launch_grid(), JET_ARENA);
     if (last_block(L.ctl)) ph_controller(L);
@@ -121,7 +127,7 @@ __global__ void __launch_bounds__(kTB) k_rb_scan(Level L) {
     ph_rb_scan<STRONG>(L, launch_grid(), JET_ARENA);
 }
 template <bool EW, bool STRONG>
-__global__ void __launch_bounds__(kTB, 4) k_rb_cand(Level L) {
+__global__ void __launch_bounds__(kTB, JET_ROW_MINB) k_rb_cand(Level L) {
     pdl_enter();
     ph_rb_cand<EW, STRONG>(L, launch_grid(), JET_ARENA);
     if (last_block(L.ctl)) ph_rb_plan(L);
