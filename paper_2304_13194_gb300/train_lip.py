@@ -205,12 +205,23 @@ def main(argv=None):
     if a.step_benchmark:
         print(json.dumps(step_benchmark(ctx, a.k)))
         return
-    facts, per = recipe(tuple(int(x) for x in a.scales.split(",") if x),
-                        tuple(int(x) for x in a.grids.split(",") if x), pairs=a.pairs)
+    facts, _ = recipe(tuple(int(x) for x in a.scales.split(",") if x),
+                      tuple(int(x) for x in a.grids.split(",") if x), pairs=a.pairs)
     t0 = time.time()
     data = []
+    # graphs whose coarsest level stays above 16,384 vertices for the first
+    # three seeds give no pairs; the others share the requested count
+    graphs = []
     for name, f in facts:
-        data += make_pairs(ctx, f(), a.k, a.eps, seeds=range(1000, 1000 + per))
+        g = f()
+        first = make_pairs(ctx, g, a.k, a.eps, seeds=range(1000, 1003))
+        if first:
+            graphs.append((name, g, first))
+        else:
+            print(f"{name}: coarsest level above 16,384 vertices, skipped ({time.time() - t0:.1f} s)", flush=True)
+    per = max(3, -(-a.pairs // max(len(graphs), 1)))
+    for name, g, first in graphs:
+        data += first + make_pairs(ctx, g, a.k, a.eps, seeds=range(1003, 1000 + per))
         print(f"{name}: {len(data)} pairs so far ({time.time() - t0:.1f} s)", flush=True)
     model = _b.LearnedPartitioner(ctx, a.k, init_params(a.k, a.seed))
     t1 = time.time()
