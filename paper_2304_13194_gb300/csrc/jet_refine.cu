@@ -322,6 +322,13 @@ int setup_level(Ctx &c, const DGraph &g, int32_t k, LevelBufs &B) {
 
 int list_grid() { return num_sms() * 4; }
 
+// Blocks per SM of the two scan kernels (grid-stride over vertices in
+// groups of four), a launch-shape choice.
+#ifndef JET_SCAN_BLOCKS_PER_SM
+#define JET_SCAN_BLOCKS_PER_SM 8
+#endif
+int scan_grid(int64_t n) { return std::min(num_sms() * JET_SCAN_BLOCKS_PER_SM, grid_for((n + 3) / 4, kTB)); }
+
 // grid of a kernel over a list of at most `items` entries (one per thread)
 int list_blocks(int64_t items) { return std::min(list_grid(), grid_for(items, kTB)); }
 
@@ -348,7 +355,7 @@ cudaError_t launch_dep(const Level &L, void (*kern)(Args...), int grid, int bloc
 int enqueue_lp_select(const Level &L, cudaStream_t s, LpExport ex, int *nk) {
     int n = L.g.n;
     bool ew = L.g.ew != nullptr;
-    k_lp_scan<<<std::min(list_grid(), grid_for((n + 3) / 4, kTB)), kTB, sm_lp_scan(), s>>>(L);
+    k_lp_scan<<<scan_grid(n), kTB, sm_lp_scan(), s>>>(L);
     const size_t sm = sm_lp_select(L.k, kTB, L.nbig > 0);
     JET_CUDA_TRY(launch_dep(L, ew ? k_lp_select<true> : k_lp_select<false>, list_blocks(n), kTB, sm, s, L, ex));
     *nk = 2;
@@ -377,7 +384,7 @@ template <bool STRONG>
 int enqueue_rb_t(const Level &L, cudaStream_t s, int *nk) {
     int n = L.g.n;
     bool ew = L.g.ew != nullptr;
-    k_rb_scan<STRONG><<<std::min(list_grid(), grid_for((n + 3) / 4, kTB)), kTB, sm_rb_scan(), s>>>(L);
+    k_rb_scan<STRONG><<<scan_grid(n), kTB, sm_rb_scan(), s>>>(L);
     const size_t sm = sm_rb_cand(L.k, kTB, L.nbig > 0);
     JET_CUDA_TRY(launch_dep(L, ew ? k_rb_cand<true, STRONG> : k_rb_cand<false, STRONG>, list_blocks(n), kTB, sm, s, L));
     JET_CUDA_TRY(launch_dep(L, k_rb_tilehist, L.ntiles, kTB, sm_rb_tilehist(L.k), s, L));
