@@ -19,7 +19,10 @@ constexpr int32_t kNoneGain = INT32_MIN;   // "negative infinity" gain (Alg. 4)
 constexpr int kSlots = 33;                 // slot() values 0..32 for 32-bit losses (Sec. 4.2.1)
 constexpr int kSmallDeg = 16;              // rows up to this length: one thread per vertex
 constexpr int kTB = 256;                   // default block size
-constexpr int kRbTile = 256;               // vertices per rebalancing tile (ordered prefixes)
+#ifndef JET_RB_TILE
+#define JET_RB_TILE 256
+#endif
+constexpr int kRbTile = JET_RB_TILE;       // vertices per rebalancing tile (ordered prefixes; one block each)
 constexpr int kTrace = 4096;               // per-level trace records kept on the device
 
 enum Mode : int32_t { MODE_LP = 0, MODE_RW = 1, MODE_RS = 2, MODE_DONE = 3 };

@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(kTB, JET_ROW_MINB) k_rb_cand(Level L) {
     ph_rb_cand<EW, STRONG>(L, launch_grid(), JET_ARENA);
     if (last_block(L.ctl)) ph_rb_plan(L);
 }
-__global__ void __launch_bounds__(kTB) k_rb_tilehist(Level L) {
+__global__ void __launch_bounds__(kRbTile) k_rb_tilehist(Level L) {
     pdl_enter();
     ph_rb_tilehist(L, launch_grid(), JET_ARENA);
 }
@@ -141,14 +141,14 @@ __global__ void __launch_bounds__(1024) k_rb_tilescan(Level L) {
     ph_rb_tilescan(L, launch_grid());
 }
 template <bool STRONG>
-__global__ void __launch_bounds__(kTB) k_rb_take(Level L) {
+__global__ void __launch_bounds__(kRbTile) k_rb_take(Level L) {
     pdl_enter();
     ph_rb_take<STRONG>(L, launch_grid(), JET_ARENA);
     if constexpr (STRONG) {
         if (last_block(L.ctl)) ph_rb_tiletaken_scan(L);
     }
 }
-__global__ void __launch_bounds__(kTB) k_rb_cookie(Level L) {
+__global__ void __launch_bounds__(kRbTile) k_rb_cookie(Level L) {
     pdl_enter();
     ph_rb_cookie(L, launch_grid(), JET_ARENA);
 }
@@ -387,12 +387,12 @@ int enqueue_rb_t(const Level &L, cudaStream_t s, int *nk) {
     k_rb_scan<STRONG><<<scan_grid(n), kTB, sm_rb_scan(), s>>>(L);
     const size_t sm = sm_rb_cand(L.k, kTB, L.nbig > 0);
     JET_CUDA_TRY(launch_dep(L, ew ? k_rb_cand<true, STRONG> : k_rb_cand<false, STRONG>, list_blocks(n), kTB, sm, s, L));
-    JET_CUDA_TRY(launch_dep(L, k_rb_tilehist, L.ntiles, kTB, sm_rb_tilehist(L.k), s, L));
+    JET_CUDA_TRY(launch_dep(L, k_rb_tilehist, L.ntiles, kRbTile, sm_rb_tilehist(L.k), s, L));
     JET_CUDA_TRY(launch_dep(L, k_rb_tilescan, L.k, 1024, 0, s, L));
-    JET_CUDA_TRY(launch_dep(L, k_rb_take<STRONG>, L.ntiles, kTB, sm_rb_take(L.k, kTB), s, L));
+    JET_CUDA_TRY(launch_dep(L, k_rb_take<STRONG>, L.ntiles, kRbTile, sm_rb_take(L.k, kRbTile), s, L));
     *nk = 5;
     if (STRONG) {
-        JET_CUDA_TRY(launch_dep(L, k_rb_cookie, L.ntiles, kTB, sm_rb_cookie(kTB), s, L));
+        JET_CUDA_TRY(launch_dep(L, k_rb_cookie, L.ntiles, kRbTile, sm_rb_cookie(kRbTile), s, L));
         *nk += 1;
     }
     JET_CUDA_TRY(cudaGetLastError());
