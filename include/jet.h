@@ -406,10 +406,11 @@ int jet_lip_decode(jet_ctx *ctx, int32_t n, const float *logits, const int32_t *
 int jet_lip_initial_partition(jet_ctx *ctx, const jet_lip *m, int32_t n, const int64_t *xadj, const int32_t *adjncy,
                               const int32_t *vwgt, const int32_t *adjwgt, double eps, int32_t *part_out);
 
-/* Learned form of Alg. 1 for the model's k: one jet_coarsen, then
- * jet_uncoarsen twice on that hierarchy, from the greedy initial partition
- * (the plain result, identical to jet_partition's) and from the network's
- * proposal.  The proposal's result is kept iff it is balanced while the plain
+/* Learned form of Alg. 1 for the model's k: one jet_coarsen, the network's
+ * proposal for the coarsest level, then jet_uncoarsen twice on that
+ * hierarchy, concurrently (the second on a context and stream of its own):
+ * from the greedy initial partition (the plain result, identical to
+ * jet_partition's) and from the proposal.  The proposal's result is kept iff it is balanced while the plain
  * one is not, or both are alike in balance and its exactly computed cut is
  * <= the plain cut.  The proposal is skipped (plain kept) when the coarsest
  * level has more than JET_LIP_MAX_N vertices.  stats (may be NULL) describe
@@ -419,7 +420,8 @@ typedef struct {
     int32_t status_plain, status_learned;
     int32_t chosen;                     /* 1 learned kept, 0 plain kept */
     int32_t n_coarsest;
-    float ms_coarsen, ms_plain, ms_proposal, ms_learned; /* CUDA-event times of the phases */
+    float ms_coarsen, ms_plain, ms_proposal, ms_learned; /* CUDA-event times of the phases (the plain and
+                                                          the learned uncoarsening overlap) */
 } jet_learned_info;
 int jet_partition_learned(jet_ctx *ctx, const jet_lip *m, int32_t n, const int64_t *xadj, const int32_t *adjncy,
                           const int32_t *vwgt, const int32_t *adjwgt, double eps, uint64_t seed, int32_t *part_out,

@@ -34,6 +34,7 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <thread>
 
 namespace jet {
 
@@ -999,19 +1000,24 @@ int jet_partition_learned(jet_ctx *ctx, const jet_lip *h, int32_t n, const int64
     jet_learned_info inf;
     memset(&inf, 0, sizeof(inf));
     inf.cut_learned = -1;
-    cudaEvent_t ev[5] = {};
+    // ev: start, coarsened, proposal ready, plain done, all done; wv: the
+    // learned uncoarsening on the second stream
+    cudaEvent_t ev[5] = {}, wv[2] = {};
     struct EvGuard {
-        cudaEvent_t *e;
+        cudaEvent_t *e, *w;
         ~EvGuard() {
             for (int i = 0; i < 5; ++i)
                 if (e[i]) cudaEventDestroy(e[i]);
+            for (int i = 0; i < 2; ++i)
+                if (w[i]) cudaEventDestroy(w[i]);
         }
-    } guard{ev};
+    } guard{ev, wv};
     for (auto &e : ev) JET_CUDA_TRY(cudaEventCreate(&e));
+    for (auto &e : wv) JET_CUDA_TRY(cudaEventCreate(&e));
     const int64_t l0 = c.launches;
-    auto ms = [&](int a, int b) {
+    auto ms = [](cudaEvent_t a, cudaEvent_t b) {
         float t = 0.f;
-        if (cudaEventElapsedTime(&t, ev[a], ev[b]) != cudaSuccess) { cudaGetLastError(); return 0.f; }
+        if (cudaEventElapsedTime(&t, a, b) != cudaSuccess) { cudaGetLastError(); return 0.f; }
         return t;
     };
     JET_CUDA_TRY(cudaEventRecord(ev[0], c.stream));
@@ -1023,52 +1029,90 @@ int jet_partition_learned(jet_ctx *ctx, const jet_lip *h, int32_t n, const int64
         ~HierGuard() { jet_hier_destroy(h); }
     } hg{hier};
     JET_CUDA_TRY(cudaEventRecord(ev[1], c.stream));
-    jet_stats st_plain, st_learned;
-    memset(&st_plain, 0, sizeof(st_plain));
-    memset(&st_learned, 0, sizeof(st_learned));
-    int64_t cut_plain = 0;
-    int r_plain = n > 0 ? uncoarsen(c, hier, k, eps, seed, nullptr, part_out, &cut_plain, &st_plain) : JET_OK;
-    if (r_plain < 0) return r_plain;
-    JET_CUDA_TRY(cudaEventRecord(ev[2], c.stream));
     const int32_t l = hier->levels - 1;
     inf.n_coarsest = hier->n[l];
-    inf.cut_plain = cut_plain;
-    inf.status_plain = r_plain;
-    bool keep_learned = false;
-    int r_learned = JET_OK;
-    int64_t cut_learned = -1;
+    const bool learned = n > 0 && hier->n[l] <= JET_LIP_MAX_N;
     DevBuf init, tmp;
-    if (n > 0 && hier->n[l] <= JET_LIP_MAX_N) {
+    if (learned) {
         DGraph gc;
         gc.n = hier->n[l]; gc.nnz = hier->nnz[l]; gc.xadj = hier->xadj[l]; gc.adj = hier->adj[l];
         gc.vw = hier->vw[l]; gc.ew = hier->ew[l];
         JET_TRY(dev_alloc(init, (size_t)gc.n * 4, c.stream));
         JET_TRY(dev_alloc(tmp, (size_t)n * 4, c.stream));
         JET_TRY(proposal(c, h->m, gc, eps, init.as<int32_t>()));
-        JET_CUDA_TRY(cudaEventRecord(ev[3], c.stream));
-        r_learned = uncoarsen(c, hier, k, eps, seed, init.as<int32_t>(), tmp.as<int32_t>(), &cut_learned, &st_learned);
-        if (r_learned < 0) return r_learned;
-        JET_CUDA_TRY(cudaEventRecord(ev[4], c.stream));
+    }
+    JET_CUDA_TRY(cudaEventRecord(ev[2], c.stream));
+    jet_stats st_plain, st_learned;
+    memset(&st_plain, 0, sizeof(st_plain));
+    memset(&st_learned, 0, sizeof(st_learned));
+    // The two uncoarsenings of the hierarchy run concurrently: the plain one
+    // on the caller's stream, the learned one on a second context and stream
+    // (both latency-bound, so they share the GPU well).  The hierarchy is
+    // only read.
+    int r_learned = JET_OK;
+    int64_t cut_learned = -1;
+    cudaStream_t ws = nullptr;
+    jet_ctx *wc = nullptr;
+    if (learned) {
+        JET_CUDA_TRY(cudaStreamCreateWithFlags(&ws, cudaStreamNonBlocking));
+        int rc = jet_ctx_create(c.device, ws, &c.opt, &wc);
+        if (rc != JET_OK || cudaStreamWaitEvent(ws, ev[2], 0) != cudaSuccess) {
+            if (wc) jet_ctx_destroy(wc);
+            cudaStreamDestroy(ws);
+            record_error("jet_partition_learned: second context");
+            return rc != JET_OK ? rc : JET_ECUDA;
+        }
+    }
+    std::thread worker;
+    if (learned) {
+        worker = std::thread([&] {
+            Ctx &w = wc->c;
+            if (use_device(w) != JET_OK) { r_learned = JET_ECUDA; return; }
+            cudaEventRecord(wv[0], ws);
+            r_learned = uncoarsen(w, hier, k, eps, seed, init.as<int32_t>(), tmp.as<int32_t>(), &cut_learned,
+                                  &st_learned);
+            cudaEventRecord(wv[1], ws);
+        });
+    }
+    int64_t cut_plain = 0;
+    int r_plain = n > 0 ? uncoarsen(c, hier, k, eps, seed, nullptr, part_out, &cut_plain, &st_plain) : JET_OK;
+    cudaEventRecord(ev[3], c.stream);
+    if (learned) {
+        worker.join();
+        cudaStreamWaitEvent(c.stream, wv[1], 0);
+        c.launches += wc->c.launches;
+    }
+    cudaEventRecord(ev[4], c.stream);
+    const int sync = sync_stream(c);
+    if (learned) {
+        jet_ctx_destroy(wc);
+        cudaStreamDestroy(ws);
+    }
+    if (r_plain < 0) return r_plain;
+    if (r_learned < 0) return r_learned;
+    JET_TRY(sync);
+    inf.cut_plain = cut_plain;
+    inf.status_plain = r_plain;
+    bool keep_learned = false;
+    if (learned) {
         const bool bal_l = r_learned != JET_WUNBALANCED, bal_p = r_plain != JET_WUNBALANCED;
         keep_learned = (bal_l && !bal_p) || (bal_l == bal_p && cut_learned <= cut_plain);
-        if (keep_learned)
+        if (keep_learned) {
             JET_CUDA_TRY(cudaMemcpyAsync(part_out, tmp.as<int32_t>(), (size_t)n * 4, cudaMemcpyDeviceToDevice, c.stream));
-    } else {
-        JET_CUDA_TRY(cudaEventRecord(ev[3], c.stream));
-        JET_CUDA_TRY(cudaEventRecord(ev[4], c.stream));
+            JET_TRY(sync_stream(c));
+        }
     }
-    JET_TRY(sync_stream(c));
     inf.cut_learned = cut_learned;
     inf.status_learned = r_learned;
     inf.chosen = keep_learned ? 1 : 0;
-    inf.ms_coarsen = ms(0, 1);
-    inf.ms_plain = ms(1, 2);
-    inf.ms_proposal = ms(2, 3);
-    inf.ms_learned = ms(3, 4);
+    inf.ms_coarsen = ms(ev[0], ev[1]);
+    inf.ms_proposal = ms(ev[1], ev[2]);
+    inf.ms_plain = ms(ev[2], ev[3]);
+    inf.ms_learned = learned ? ms(wv[0], wv[1]) : 0.f;
     if (stats) {
         *stats = keep_learned ? st_learned : st_plain;
         stats->ms_coarsen = inf.ms_coarsen;
-        stats->ms_total = ms(0, 4);
+        stats->ms_total = ms(ev[0], ev[4]);
         stats->kernel_launches = c.launches - l0;
     }
     if (info) *info = inf;
