@@ -452,6 +452,35 @@ def test_partition_batch_matches_oracle(ctx):
         assert status == ref.status and cut == ref.cut and (_np(part) == ref.part).all()
 
 
+@pytest.mark.parametrize("g,k", [(graphgen.grid3d(24, 24, 24, vw=(1, 4), ew=(1, 10), seed=9), 64),
+                                 (graphgen.rmat(12, seed=5), 16)], ids=["grid24w_k64", "rmat12_k16"])
+def test_coarsest_refined_matches_oracle(ctx, g, k):
+    """jet_coarsest_refined (the learned form's training labels): the greedy
+    initial partition of the coarsest level refined by Alg. 3 with that
+    level's seed and c_coarse, bit for bit."""
+    seed = 3
+    h = ctx.coarsen(g.xadj, g.adjncy, g.vwgt, g.adjwgt, k=k, seed=seed)
+    part, cut = ctx.coarsest_refined(h, k=k, eps=0.03, seed=seed)
+    h.close()
+    lv = oracle.coarsen(g, k, seed)
+    gc = lv[-1].graph
+    ref = oracle.refine(gc, k, oracle.initial_partition(gc, k), 0.03, is_finest=len(lv) == 1,
+                        seed=oracle.level_seed(seed, len(lv) - 1))
+    assert cut == ref.cut and (_np(part) == ref.part).all()
+    assert cut == oracle.partition(g, k, 0.03, seed).stats["cut_level"][len(lv) - 1]
+
+
+def test_partition_without_pdl_is_identical(ctx):
+    """Programmatic dependent launch is an execution choice: the same
+    partition with JET_FLAG_NO_PDL, on the CUDA-graph and the host loop."""
+    g = graphgen.grid3d(40, 40, 40, vw=(1, 4), ew=(1, 10), seed=6)
+    ref = ctx.partition(g.xadj, g.adjncy, g.vwgt, g.adjwgt, k=32, seed=2)
+    for flags in (jet.FLAG_NO_PDL, jet.FLAG_NO_PDL | jet.FLAG_HOSTLOOP, jet.FLAG_HOSTLOOP):
+        with jet.Context(0, flags=flags, cluster_max_n=0) as c:
+            part, cut = c.partition(g.xadj, g.adjncy, g.vwgt, g.adjwgt, k=32, seed=2)
+        assert cut == ref[1] and torch.equal(part, ref[0])
+
+
 def test_autotune_picks_fastest_and_keeps_results():
     """jet_autotune: every candidate timed, the fastest cluster threshold
     kept in the context, and every graph still bit-exact with the oracle
