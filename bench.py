@@ -504,10 +504,11 @@ def run_batched(args):
         t_b = time.perf_counter() - t0
         same = all(o[1] == c for o, c in zip(out, seq))
         print(json.dumps({"sweep": "batched", "mode": "autotuned", "cluster_max_n": rep["cluster_max_n"],
+                          "cluster_blocks": rep["cluster_blocks"],
                           "workers": rep["workers"], "tune_seconds": round(t_tune, 3), "graphs": len(items),
                           "seconds": round(t_b, 4), "speedup_vs_sequential": round(t_seq / t_b, 3),
                           "cuts_equal_to_sequential": same,
-                          "candidates": [[c["cluster_max_n"], c["workers"], round(c["ms"], 2)]
+                          "candidates": [[c["cluster_blocks"], c["cluster_max_n"], c["workers"], round(c["ms"], 2)]
                                          for c in rep["candidates"]]}), flush=True)
     return 0
 

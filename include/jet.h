@@ -91,12 +91,15 @@ extern "C" {
  * Execution choice (no counterpart in the paper; results do not depend on it):
  *   cluster_max_n = 4096            levels with at most this many vertices run their whole
  *                                   refinement loop in one thread-block-cluster launch; larger
- *                                   levels use the CUDA-graph loop; 0 = never */
+ *                                   levels use the CUDA-graph loop; 0 = never
+ *   cluster_blocks = 0              blocks (of 1024 threads) of that cluster: 0 = the largest the
+ *                                   device runs (up to 16), else a power of two in [2, 16] */
 typedef struct {
     double c_fine, c_coarse, phi;
     int32_t max_no_improve, weak_limit, coarsen_target, max_levels, max_iters_per_level, hem_rounds;
     uint32_t flags;
     int32_t cluster_max_n;
+    int32_t cluster_blocks;
 } jet_options;
 
 /* Per-call statistics (jet_partition / jet_uncoarsen).  Times are CUDA-event
@@ -221,19 +224,23 @@ int jet_partition_batch(jet_ctx *ctx, int32_t count, jet_batch_item *items, int3
 
 /* Autotuner of the execution choices (no counterpart in the paper; results
  * are bit-identical under every choice).  Times `items` (a batch, or one
- * graph with count = 1) with jet_partition_batch under each candidate —
- * first cluster_max_n in {0, 1024, 2048, 4096, 8192, 16384} (the largest level
- * that runs its whole refinement loop in one thread-block-cluster launch),
- * then, for count > 1, workers in {1, 2, 4, 8, 16} — taking the median of
- * `reps` timed runs (reps <= 0: 3) after one untimed run, and writes the
- * fastest cluster_max_n into the context's options.  The items' outputs
+ * graph with count = 1) with jet_partition_batch under each candidate, one
+ * choice at a time, each stage keeping the best of the earlier ones:
+ * cluster_blocks in {16, 8, 4, 2} (at cluster_max_n 4096), then
+ * cluster_max_n in {0, 1024, 2048, 4096, 8192, 16384} (the largest level that
+ * runs its whole refinement loop in one thread-block-cluster launch), then,
+ * for count > 1, workers in {1, 2, 4, 8, 16} — taking the median of `reps`
+ * timed runs (reps <= 0: 3) after one untimed run, and writes the fastest
+ * cluster_blocks and cluster_max_n into the context's options.  The items' outputs
  * hold the last run's results.  report (may be NULL) lists every candidate. */
 #define JET_TUNE_MAX_CAND 16
 typedef struct {
     int32_t cluster_max_n;                  /* chosen (now in the context's options) */
+    int32_t cluster_blocks;                 /* chosen (now in the context's options) */
     int32_t workers;                        /* chosen worker count for jet_partition_batch */
     int32_t ncand;                          /* candidates timed */
-    int32_t cand_cluster_max_n[JET_TUNE_MAX_CAND], cand_workers[JET_TUNE_MAX_CAND];
+    int32_t cand_cluster_max_n[JET_TUNE_MAX_CAND], cand_cluster_blocks[JET_TUNE_MAX_CAND],
+        cand_workers[JET_TUNE_MAX_CAND];
     float cand_ms[JET_TUNE_MAX_CAND];       /* median host wall time of the whole batch */
 } jet_tune_report;
 int jet_autotune(jet_ctx *ctx, int32_t count, jet_batch_item *items, int32_t reps, jet_tune_report *report);

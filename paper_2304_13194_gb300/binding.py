@@ -53,7 +53,7 @@ class Options(ctypes.Structure):
                 ("max_no_improve", ctypes.c_int32), ("weak_limit", ctypes.c_int32),
                 ("coarsen_target", ctypes.c_int32), ("max_levels", ctypes.c_int32),
                 ("max_iters_per_level", ctypes.c_int32), ("hem_rounds", ctypes.c_int32),
-                ("flags", ctypes.c_uint32), ("cluster_max_n", ctypes.c_int32)]
+                ("flags", ctypes.c_uint32), ("cluster_max_n", ctypes.c_int32), ("cluster_blocks", ctypes.c_int32)]
 
     @classmethod
     def default(cls, **kw) -> "Options":
@@ -224,8 +224,9 @@ class _BatchItem(ctypes.Structure):
 
 class _TuneReport(ctypes.Structure):
     """jet_tune_report."""
-    _fields_ = [("cluster_max_n", ctypes.c_int32), ("workers", ctypes.c_int32), ("ncand", ctypes.c_int32),
-                ("cand_cluster_max_n", ctypes.c_int32 * 16), ("cand_workers", ctypes.c_int32 * 16),
+    _fields_ = [("cluster_max_n", ctypes.c_int32), ("cluster_blocks", ctypes.c_int32), ("workers", ctypes.c_int32),
+                ("ncand", ctypes.c_int32), ("cand_cluster_max_n", ctypes.c_int32 * 16),
+                ("cand_cluster_blocks", ctypes.c_int32 * 16), ("cand_workers", ctypes.c_int32 * 16),
                 ("cand_ms", ctypes.c_float * 16)]
 
 
@@ -509,9 +510,11 @@ class Context:
         rep = _TuneReport()
         _check(load_library().jet_autotune(self._h, len(graphs), items, int(reps), ctypes.byref(rep)), "jet_autotune")
         self.options.cluster_max_n = rep.cluster_max_n
+        self.options.cluster_blocks = rep.cluster_blocks
         m = rep.ncand
-        return dict(cluster_max_n=rep.cluster_max_n, workers=rep.workers,
-                    candidates=[dict(cluster_max_n=rep.cand_cluster_max_n[i], workers=rep.cand_workers[i],
+        return dict(cluster_max_n=rep.cluster_max_n, cluster_blocks=rep.cluster_blocks, workers=rep.workers,
+                    candidates=[dict(cluster_max_n=rep.cand_cluster_max_n[i],
+                                     cluster_blocks=rep.cand_cluster_blocks[i], workers=rep.cand_workers[i],
                                      ms=rep.cand_ms[i]) for i in range(m)],
                     parts=[(keep[i][4], items[i].cut) for i in range(len(graphs))])
 

@@ -318,6 +318,7 @@ void jet_options_default(jet_options *o) {
     o->hem_rounds = 8;
     o->flags = 0;
     o->cluster_max_n = 4096;
+    o->cluster_blocks = 0;
 }
 
 int jet_ctx_create(int device, void *cuda_stream, const jet_options *opt, jet_ctx **out) {
@@ -328,7 +329,9 @@ int jet_ctx_create(int device, void *cuda_stream, const jet_options *opt, jet_ct
     if (opt) o = *opt;
     if (!(o.c_fine >= 0 && o.c_fine <= 1 && o.c_coarse >= 0 && o.c_coarse <= 1 && o.phi > 0 && o.phi <= 1) ||
         o.max_no_improve < 0 || o.weak_limit < 0 || o.coarsen_target < 0 || o.max_levels < 1 ||
-        o.max_iters_per_level < 0 || o.hem_rounds < 0 || o.hem_rounds > 64 || o.cluster_max_n < 0)
+        o.max_iters_per_level < 0 || o.hem_rounds < 0 || o.hem_rounds > 64 || o.cluster_max_n < 0 ||
+        !(o.cluster_blocks == 0 || o.cluster_blocks == 2 || o.cluster_blocks == 4 || o.cluster_blocks == 8 ||
+          o.cluster_blocks == 16))
         return JET_EINVAL;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess) { cudaGetLastError(); return JET_ECUDA; }
@@ -604,46 +607,43 @@ int jet_autotune(jet_ctx *ctx, int32_t count, jet_batch_item *items, int32_t rep
         *ms = t[t.size() / 2];
         return JET_OK;
     };
-    auto record = [&](int32_t cm, int32_t w, float ms) {
-        if (rep.ncand < JET_TUNE_MAX_CAND) {
-            rep.cand_cluster_max_n[rep.ncand] = cm;
-            rep.cand_workers[rep.ncand] = w;
-            rep.cand_ms[rep.ncand] = ms;
-            rep.ncand += 1;
-        }
-    };
-    const int32_t saved = c.opt.cluster_max_n;
-    const int32_t w0 = count > 1 ? 8 : 1;
-    static const int32_t cands[] = {0, 1024, 2048, 4096, 8192, 16384};
-    int32_t best_cm = saved;
-    float best = 0.f;
-    bool have = false;
-    for (int32_t cm : cands) {
-        c.opt.cluster_max_n = cm;
-        float ms = 0.f;
-        int st = time_batch(w0, &ms);
-        if (st < 0) {
-            c.opt.cluster_max_n = saved;
-            return st;
-        }
-        record(cm, w0, ms);
-        if (!have || ms < best) { best = ms; best_cm = cm; have = true; }
-    }
-    c.opt.cluster_max_n = best_cm;
-    int32_t best_w = w0;
-    if (count > 1) {
-        static const int32_t wc[] = {1, 2, 4, 8, 16};
-        float bw = 0.f;
-        bool hw = false;
-        for (int32_t w : wc) {
+    int32_t workers = count > 1 ? 8 : 1;
+    // One stage: each value of one choice (*target) timed with the others
+    // fixed; the fastest stays.
+    auto stage = [&](const int32_t *vals, int nv, int32_t *target) -> int {
+        int32_t best_v = *target;
+        float best = 0.f;
+        for (int i = 0; i < nv; ++i) {
+            *target = vals[i];
             float ms = 0.f;
-            JET_TRY(time_batch(w, &ms));
-            record(best_cm, w, ms);
-            if (!hw || ms < bw) { bw = ms; best_w = w; hw = true; }
+            JET_TRY(time_batch(workers, &ms));
+            if (rep.ncand < JET_TUNE_MAX_CAND) {
+                rep.cand_cluster_max_n[rep.ncand] = c.opt.cluster_max_n;
+                rep.cand_cluster_blocks[rep.ncand] = c.opt.cluster_blocks;
+                rep.cand_workers[rep.ncand] = workers;
+                rep.cand_ms[rep.ncand] = ms;
+                rep.ncand += 1;
+            }
+            if (i == 0 || ms < best) { best = ms; best_v = vals[i]; }
         }
+        *target = best_v;
+        return JET_OK;
+    };
+    static const int32_t blocks[] = {16, 8, 4, 2};
+    static const int32_t thresholds[] = {0, 1024, 2048, 4096, 8192, 16384};
+    static const int32_t wcands[] = {1, 2, 4, 8, 16};
+    const jet_options saved = c.opt;
+    c.opt.cluster_max_n = 4096;
+    int st = stage(blocks, 4, &c.opt.cluster_blocks);
+    if (st >= 0) st = stage(thresholds, 6, &c.opt.cluster_max_n);
+    if (st >= 0 && count > 1) st = stage(wcands, 5, &workers);
+    if (st < 0) {
+        c.opt = saved;
+        return st;
     }
-    rep.cluster_max_n = best_cm;
-    rep.workers = best_w;
+    rep.cluster_max_n = c.opt.cluster_max_n;
+    rep.cluster_blocks = c.opt.cluster_blocks;
+    rep.workers = workers;
     if (report) *report = rep;
     return JET_OK;
 }

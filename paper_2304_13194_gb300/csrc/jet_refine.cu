@@ -682,8 +682,10 @@ size_t cluster_smem(int32_t k) { return (arena_bytes(k, kClusterThreads) + 255) 
 int pick_cluster(Ctx &c, const Level &L, int *cs) {
     *cs = 0;
     if (L.g.n <= 0 || L.g.n > c.opt.cluster_max_n) return JET_OK;
-    if (L.g.ew) return cluster_size<true>(c.device, cluster_smem(L.k), cs);
-    return cluster_size<false>(c.device, cluster_smem(L.k), cs);
+    if (L.g.ew) JET_TRY(cluster_size<true>(c.device, cluster_smem(L.k), cs));
+    else JET_TRY(cluster_size<false>(c.device, cluster_smem(L.k), cs));
+    if (c.opt.cluster_blocks > 0 && *cs > c.opt.cluster_blocks) *cs = c.opt.cluster_blocks;
+    return JET_OK;
 }
 
 int run_cluster(Ctx &c, const Level &L, int cs) {

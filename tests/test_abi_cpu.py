@@ -49,10 +49,10 @@ def test_library_is_sm103a_only(lib_path):
 
 def test_options_struct_layout_matches_header():
     # 3 doubles, 6 int32, 1 uint32, 1 int32 -> 56 bytes
-    assert ctypes.sizeof(binding.Options) == 56
+    assert ctypes.sizeof(binding.Options) == 64
     # jet_batch_item: int32, 4 pointers, int32, double, uint64, pointer, int64, int32, float
     assert ctypes.sizeof(binding._BatchItem) == 88
     assert ctypes.sizeof(binding._LearnedInfo) == 48
-    assert ctypes.sizeof(binding._TuneReport) == 12 + 3 * 64
+    assert ctypes.sizeof(binding._TuneReport) == 16 + 4 * 64
     # jet_stats: int32 + 2*64 int64 + 3*64 int32 + 64 int64 + 2 int64 + 5 float + 2 int64
     assert ctypes.sizeof(binding._CStats) % 8 == 0

@@ -364,6 +364,24 @@ def test_refine_cluster_loop_equals_graph_loop(ctx_cluster, ctx_graph, name, g, 
         assert all((ta[key] == tb[key]).all() for key in ("kind", "nx", "nm", "cut", "maxw"))
 
 
+@pytest.mark.parametrize("blocks", [2, 4])
+def test_small_clusters_equal_graph_loop(ctx_graph, blocks):
+    """cluster_blocks caps the cluster (execution choice): fewer blocks take
+    more 1024-vertex tiles each, with the same result."""
+    with jet.Context(0, cluster_max_n=1 << 30, cluster_blocks=blocks) as c:
+        for g, unit, k in ((graphgen.rgg(30000, seed=3), True, 128),
+                           (graphgen.grid3d(20, 20, 20, vw=(1, 4), ew=(1, 10), seed=9), False, 16)):
+            vw, ew = _vw(g, unit), _ew(g, unit)
+            part0 = oracle.initial_partition(graphgen.Graph(g.n, g.xadj, g.adjncy, vw, None), k)
+            a = c.refine(g.xadj, g.adjncy, vw, ew, k, part0, seed=2)
+            b = ctx_graph.refine(g.xadj, g.adjncy, vw, ew, k, part0, seed=2)
+            assert a[1] == b[1] and (_np(a[0]) == _np(b[0])).all()
+        g = graphgen.grid3d(24, 24, 24, vw=(1, 4), ew=(1, 10), seed=1)
+        _, cut, st = c.partition(g.xadj, g.adjncy, g.vwgt, g.adjwgt, k=64, seed=1, return_stats=True)
+        assert all(b == blocks for b in st.cluster_blocks)
+        assert cut == oracle.partition(g, 64, 0.03, 1).cut
+
+
 def test_cluster_loop_is_used_on_small_levels(ctx, ctx_cluster, ctx_graph):
     g = graphgen.grid3d(24, 24, 24, vw=(1, 4), ew=(1, 10), seed=1)
     _, c1, st = ctx_cluster.partition(g.xadj, g.adjncy, g.vwgt, g.adjwgt, k=64, seed=1, return_stats=True)
@@ -492,11 +510,12 @@ def test_autotune_picks_fastest_and_keeps_results():
     c = jet.Context(0)
     rep = c.autotune(items, reps=1)
     cands = rep["candidates"]
-    assert len(cands) == 6 + 5
-    first = cands[:6]
-    assert rep["cluster_max_n"] == min(first, key=lambda x: x["ms"])["cluster_max_n"]
-    assert rep["workers"] == min(cands[6:], key=lambda x: x["ms"])["workers"]
-    assert c.options.cluster_max_n == rep["cluster_max_n"]
+    assert len(cands) == 4 + 6 + 5
+    assert rep["cluster_blocks"] == min(cands[:4], key=lambda x: x["ms"])["cluster_blocks"]
+    assert rep["cluster_max_n"] == min(cands[4:10], key=lambda x: x["ms"])["cluster_max_n"]
+    assert rep["workers"] == min(cands[10:], key=lambda x: x["ms"])["workers"]
+    assert all(x["cluster_blocks"] == rep["cluster_blocks"] for x in cands[4:])
+    assert c.options.cluster_max_n == rep["cluster_max_n"] and c.options.cluster_blocks == rep["cluster_blocks"]
     for (part, cut), g, k, it in zip(rep["parts"], gs, ks, items):
         ref = oracle.partition(g, k, 0.03, it["seed"])
         assert cut == ref.cut and (_np(part) == ref.part).all()
