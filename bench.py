@@ -59,7 +59,7 @@ def parse_args(argv=None):
                    help="largest level refined by the one-cluster loop (library default if omitted; 0 = never)")
     p.add_argument("--kernel-probe", action="store_true",
                    help="run one profiled partition and report per-level select launches (profiler target)")
-    p.add_argument("--sweep", choices=["lp_versions", "batched"], default=None,
+    p.add_argument("--sweep", choices=["lp_versions", "batched", "rmat"], default=None,
                    help="the Jetlp versions of the paper's component study and the phi trade-off, on the "
                         "mesh, power-law and large-grid workloads (one JSON line per run and a summary)")
     return p.parse_args(argv)
@@ -513,10 +513,43 @@ def run_batched(args):
     return 0
 
 
+def run_rmat(args):
+    """The power-law configuration: R-MAT scale 22 (edge factor 16, a=.57,
+    b=c=.19, d=.05, symmetrised, unit weights), k in {2, 8, 64, 256}: partition
+    time (CUDA events, median of 3 after one warm-up), refinement throughput,
+    cut (checked against jet_cut) and balance."""
+    import torch
+    import graphgen
+    import paper_2304_13194_gb300 as jet
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    g = graphgen.rmat(22, seed=SEED)
+    xadj, adj = torch.from_numpy(g.xadj).to(dev), torch.from_numpy(g.adjncy).to(dev)
+    with jet.Context(0) as ctx:
+        for k in (2, 8, 64, 256):
+            ctx.partition(xadj, adj, k=k, eps=EPS, seed=SEED)                    # warm-up
+            runs = [ctx.partition(xadj, adj, k=k, eps=EPS, seed=SEED, return_stats=True) for _ in range(3)]
+            part, cut, st = runs[0]
+            assert all(r[1] == cut for r in runs)
+            c2, pw = ctx.cut(xadj, adj, None, None, k, part)
+            ms = sorted(r[2].ms_total for r in runs)[1]
+            L = (-(-g.n // k)) * (1000000 + round(EPS * 1e6)) // 1000000
+            print(json.dumps({"sweep": "rmat", "graph": "rmat22", "n": g.n, "m": g.m, "k": k, "levels": st.levels,
+                              "coarsest_n": st.n[-1], "partition_ms": round(ms, 2),
+                              "coarsen_ms": round(st.ms_coarsen, 2), "init_ms": round(st.ms_init, 2),
+                              "refine_ms": round(st.ms_refine, 2),
+                              "refine_medges_per_s": round(st.edge_iters / st.ms_refine / 1e3, 1),
+                              "cut": cut, "cut_recomputed": c2, "max_part_w": int(pw.max().item()), "limit": L}),
+                  flush=True)
+    return 0
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.sweep == "batched":
         return run_batched(args)
+    if args.sweep == "rmat":
+        return run_rmat(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.kernel_probe:
