@@ -18,6 +18,8 @@ namespace jet {
 constexpr int32_t kNoneGain = INT32_MIN;   // "negative infinity" gain (Alg. 4)
 constexpr int kSlots = 33;                 // slot() values 0..32 for 32-bit losses (Sec. 4.2.1)
 constexpr int kSmallDeg = 16;              // rows up to this length: one thread per vertex
+constexpr int kHugeDeg = 1024;             // rows longer than this: one whole block per row
+constexpr int kHugeCap = 128;              // block-schedule rows set aside per drain of a block
 constexpr int kTB = 256;                   // default block size
 #ifndef JET_RB_TILE
 #define JET_RB_TILE 256

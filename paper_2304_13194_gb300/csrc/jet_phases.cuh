@@ -176,16 +176,39 @@ struct Appender {
             __syncthreads();
         }
     }
-    // Long rows staged for the block's warps: when another round could
-    // overflow the buffer (or with force), every warp takes staged rows in
-    // turn, `row(v)` being called by all 32 lanes.  All threads call it.
-    template <class Row>
-    __device__ __forceinline__ void drain(bool force, Row &&row) {
+    // Long rows staged for the block: when another round could overflow the
+    // buffer (or with force), the block's warps take the staged rows in turn
+    // (`row(v)`, all 32 lanes), except rows longer than kHugeDeg, which are
+    // set aside (up to kHugeCap of them; more stay with the warps) and then
+    // taken by the whole block one after another (`block_row(v)`, every
+    // thread): a hub row no longer serialises one warp for the whole pass.
+    // All threads call it.
+    template <class Row, class BlockRow>
+    __device__ __forceinline__ void drain(bool force, const int64_t *xadj, Row &&row, BlockRow &&block_row) {
+        __shared__ int32_t huge[kHugeCap];
+        __shared__ int nhuge;
         __syncthreads();
         int c = *cnt;
         if (c > 0 && (force || c > cap - (int)blockDim.x)) {
+            if (threadIdx.x == 0) nhuge = 0;
+            __syncthreads();
             const int warps = blockDim.x >> 5;
-            for (int s = threadIdx.x >> 5; s < c; s += warps) row(buf[s]);
+            for (int s = threadIdx.x >> 5; s < c; s += warps) {
+                const int32_t v = buf[s];
+                int defer = 0;
+                if (lane_id() == 0 && ld_xadj(xadj, (int64_t)v + 1) - ld_xadj(xadj, v) > kHugeDeg) {
+                    const int slot = atomicAdd(&nhuge, 1);
+                    if (slot < kHugeCap) {
+                        huge[slot] = v;
+                        defer = 1;
+                    }
+                }
+                defer = __shfl_sync(0xffffffffu, defer, 0);
+                if (!defer) row(v);
+            }
+            __syncthreads();
+            const int nh = nhuge < kHugeCap ? nhuge : kHugeCap;
+            for (int s = 0; s < nh; ++s) block_row(huge[s]);
             __syncthreads();
             if (threadIdx.x == 0) *cnt = 0;
             __syncthreads();
@@ -511,6 +534,66 @@ __device__ inline void ph_lp_scan(const Level &L, Grid G, char *arena) {
     flush_counter(&ctl->nbnd, nb, red);
 }
 
+// Block-wide maximum, returned to every thread; sh holds >= 32 values.
+__device__ __forceinline__ unsigned long long block_max_u64(unsigned long long v, unsigned long long *sh) {
+    v = warp_max_u64(v);
+    __syncthreads();
+    if (lane_id() == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    const unsigned nw = (blockDim.x + 31) >> 5;
+    unsigned long long t = threadIdx.x < nw ? sh[threadIdx.x] : 0ULL;
+    if (threadIdx.x < 32) t = warp_max_u64(t);
+    if (threadIdx.x == 0) sh[0] = t;
+    __syncthreads();
+    const unsigned long long r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+// One hub row of step 1 (longer than kHugeDeg) by the whole block: conn(v, .)
+// in one k-entry table, zero between rows and cleared by a scan over the k
+// parts after the read; the same result as the warp version.
+template <bool EW>
+__device__ __forceinline__ void lp_select_block_row(const Level &L, LpExport ex, int32_t v, int32_t *tab, long long *red,
+                                                    long long &nexam, long long &degexam, long long &degx) {
+    const DGraph &g = L.g;
+    const int32_t ps = L.part[v];
+    const int64_t beg = ld_xadj(g.xadj, v), end = ld_xadj(g.xadj, (int64_t)v + 1);
+    for (int64_t j = beg + threadIdx.x; j < end; j += blockDim.x)
+        atomicAdd(&tab[L.part[__ldg(g.adj + j)]], edge_w<EW>(g, j));
+    __syncthreads();
+    const int32_t conn_s = tab[ps];
+    unsigned long long best = 0;
+    for (int p = threadIdx.x; p < L.k; p += blockDim.x) {
+        const int32_t c = tab[p];
+        if (c > 0 && p != ps) {
+            const unsigned long long key = part_key(c, p);
+            best = key > best ? key : best;
+        }
+    }
+    __syncthreads();
+    for (int p = threadIdx.x; p < L.k; p += blockDim.x) tab[p] = 0;
+    best = block_max_u64(best, reinterpret_cast<unsigned long long *>(red));
+    if (threadIdx.x == 0) {
+        int32_t F = kNoneGain, pd = -1;
+        bool inX = false;
+        if (best) {
+            pd = key_part(best);
+            F = key_conn(best) - conn_s;
+            inX = first_filter(F, conn_s, L.cq16, L.abl);
+        }
+        nexam += 1;
+        degexam += end - beg;
+        if (inX) {
+            L.prio[v] = F;
+            L.nxt[v] = nxt_pack(ps, pd);
+            L.listX[atomicAdd(&L.ctl->nX, 1)] = v;
+            degx += end - beg;
+        }
+        if (ex.pd) { ex.pd[v] = pd >= 0 ? pd : ps; ex.gain[v] = F; }
+    }
+}
+
 // One long row of step 1, by a whole warp: conn(v, .) in the warp's dense
 // table, which is all-zero between rows (the read pass takes every touched
 // entry with atomicExch(.., 0), which also meets each distinct part once).
@@ -578,6 +661,9 @@ __device__ inline void ph_lp_select(const Level &L, LpExport ex, Grid G, char *a
     const DGraph g = L.g;
     long long nexam = 0, degexam = 0, degx = 0;
     auto big_row = [&](int32_t v) { lp_select_row<EW>(L, ex, v, tab, nexam, degexam, degx); };
+    auto hub_row = [&](int32_t v) {
+        lp_select_block_row<EW>(L, ex, v, a32 + kListCap + kBigCap, red, nexam, degexam, degx);
+    };
     for (int64_t i0 = sh.beg; i0 < sh.end; i0 += blockDim.x) {
         int64_t i = i0 + threadIdx.x;
         bool inX = false, big = false;
@@ -633,10 +719,10 @@ __device__ inline void ph_lp_select(const Level &L, LpExport ex, Grid G, char *a
         xapp.add(inX, v);
         bigs.add(big, v);
         xapp.flush(&ctl->nX, L.listX, false);
-        bigs.drain(false, big_row);
+        bigs.drain(false, g.xadj, big_row, hub_row);
     }
     xapp.flush(&ctl->nX, L.listX, true);
-    bigs.drain(true, big_row);
+    bigs.drain(true, g.xadj, big_row, hub_row);
     flush_counter(&ctl->nexam, nexam, red);
     flush_counter(&ctl->degexam, degexam, red);
     flush_counter(&ctl->degx, degx, red);
@@ -658,8 +744,26 @@ __device__ __forceinline__ int32_t afterburn_term(const Level &L, int32_t v, int
     return pu == pd ? w : (pu == ps ? -w : 0);
 }
 
+// One hub row of step 2 by the whole block.
+template <bool EW>
+__device__ __forceinline__ void afterburn_block_row(const Level &L, LpExport ex, int32_t v, int32_t it, long long *red) {
+    const int32_t Fv = L.prio[v], pd = nxt_to(L.nxt[v]), ps = L.part[v];
+    const int64_t beg = ld_xadj(L.g.xadj, v), end = ld_xadj(L.g.xadj, (int64_t)v + 1);
+    long long f2 = 0;
+    for (int64_t j = beg + threadIdx.x; j < end; j += blockDim.x) f2 += afterburn_term<EW>(L, v, Fv, pd, ps, j);
+    f2 = block_sum_i64(f2, red);
+    if (threadIdx.x == 0) {
+        if (ex.f2) ex.f2[v] = (int32_t)f2;
+        if (f2 >= 0) {
+            L.mstamp[v] = it;
+            L.listM[atomicAdd(&L.ctl->nM, 1)] = v;
+        }
+    }
+}
+
 template <bool EW>
 __device__ inline void ph_afterburn(const Level &L, LpExport ex, Grid G, char *arena) {
+    __shared__ long long red[40];
     Ctl *ctl = L.ctl;
     const int32_t it = ctl->it;
     const Share sh = list_share(ctl->nX, G);
@@ -683,6 +787,7 @@ __device__ inline void ph_afterburn(const Level &L, LpExport ex, Grid G, char *a
             }
         }
     };
+    auto hub_row = [&](int32_t v) { afterburn_block_row<EW>(L, ex, v, it, red); };
     for (int64_t i0 = sh.beg; i0 < sh.end; i0 += blockDim.x) {
         int64_t i = i0 + threadIdx.x;
         bool inM = false, big = false;
@@ -725,10 +830,10 @@ __device__ inline void ph_afterburn(const Level &L, LpExport ex, Grid G, char *a
         mapp.add(inM, v);
         bigs.add(big, v);
         mapp.flush(&ctl->nM, L.listM, false);
-        bigs.drain(false, big_row);
+        bigs.drain(false, L.g.xadj, big_row, hub_row);
     }
     mapp.flush(&ctl->nM, L.listM, true);
-    bigs.drain(true, big_row);
+    bigs.drain(true, L.g.xadj, big_row, hub_row);
 }
 
 // ---------------------------------------------------------------------------
@@ -769,6 +874,30 @@ __device__ __forceinline__ int64_t apply_edge(const Level &L, int32_t v, int32_t
     return (int64_t)w * diff;
 }
 
+// One hub row of the apply phase by the whole block.
+template <bool EW>
+__device__ __forceinline__ void apply_block_row(const Level &L, int32_t v, int32_t it, bool lp, long long *red,
+                                                long long &dc, long long &dm) {
+    const int32_t x = L.nxt[v];
+    const int32_t a = nxt_from(x), b = nxt_to(x);
+    const int64_t beg = ld_xadj(L.g.xadj, v), end = ld_xadj(L.g.xadj, (int64_t)v + 1);
+    long long c = 0, ne = 0;
+    for (int64_t j = beg + threadIdx.x; j < end; j += blockDim.x) {
+        int32_t o;
+        c += apply_edge<EW, false>(L, v, a, b, it, __ldg(L.g.adj + j), edge_w<EW>(L.g, j), &o);
+        ne += o;
+    }
+    c = block_sum_i64(c, red);
+    ne = block_sum_i64(ne, red);
+    if (threadIdx.x == 0) {
+        dc += c;
+        dm += end - beg;
+        L.ext[v] = (int32_t)ne;
+        L.part[v] = b;
+        if (lp) L.lstamp[v] = it;
+    }
+}
+
 template <bool EW>
 __device__ inline void ph_apply(const Level &L, Grid G, char *arena) {
     __shared__ long long red[40];
@@ -804,6 +933,7 @@ __device__ inline void ph_apply(const Level &L, Grid G, char *arena) {
             if (lp) L.lstamp[v] = it;
         }
     };
+    auto hub_row = [&](int32_t v) { apply_block_row<EW>(L, v, it, lp, red, dc, dm); };
     const Share sh = list_share(nM, G);
     for (int64_t i0 = sh.beg; i0 < sh.end; i0 += blockDim.x) {
         int64_t i = i0 + threadIdx.x;
@@ -841,9 +971,9 @@ __device__ inline void ph_apply(const Level &L, Grid G, char *arena) {
             }
         }
         bigs.add(big, v);
-        bigs.drain(false, big_row);
+        bigs.drain(false, L.g.xadj, big_row, hub_row);
     }
-    bigs.drain(true, big_row);
+    bigs.drain(true, L.g.xadj, big_row, hub_row);
     if (lp) {
         const int64_t stride = (int64_t)G.nb * blockDim.x;
         for (int64_t i = (int64_t)G.bid * blockDim.x + threadIdx.x; i < nX; i += stride) L.prio[L.listX[i]] = kNoneGain;
@@ -1046,6 +1176,58 @@ __device__ __forceinline__ void rb_cand_row(const Level &L, int32_t v, int32_t *
     }
 }
 
+// One hub row of the rebalancing candidates by the whole block.
+template <bool EW, bool STRONG>
+__device__ __forceinline__ void rb_cand_block_row(const Level &L, int32_t v, int32_t *tab, long long *red, int32_t it,
+                                                  int32_t nB, SmemBuckets &sb, long long &degrows) {
+    const DGraph &g = L.g;
+    const int32_t ps = L.part[v];
+    const int32_t a = L.aidx[ps];
+    const int64_t beg = ld_xadj(g.xadj, v), end = ld_xadj(g.xadj, (int64_t)v + 1);
+    for (int64_t j = beg + threadIdx.x; j < end; j += blockDim.x)
+        atomicAdd(&tab[L.part[__ldg(g.adj + j)]], edge_w<EW>(g, j));
+    __syncthreads();
+    const int32_t conn_s = tab[ps];
+    unsigned long long best = 0;
+    long long S = 0, cnt = 0;
+    for (int p = threadIdx.x; p < L.k; p += blockDim.x) {
+        const int32_t c = tab[p];
+        if (c > 0 && L.inB[p]) {
+            if constexpr (!STRONG) {
+                const unsigned long long k2 = part_key(c, p);
+                best = k2 > best ? k2 : best;
+            } else {
+                S += c;
+                cnt += 1;
+            }
+        }
+    }
+    __syncthreads();
+    for (int p = threadIdx.x; p < L.k; p += blockDim.x) tab[p] = 0;
+    int32_t loss = 0;
+    if constexpr (!STRONG) {
+        best = block_max_u64(best, reinterpret_cast<unsigned long long *>(red));
+        if (threadIdx.x == 0) {
+            int32_t dest, cd;
+            if (best) { dest = key_part(best); cd = key_conn(best); }
+            else { dest = random_B(L, v, it, nB); cd = 0; }
+            L.nxt[v] = nxt_pack(ps, dest);
+            loss = conn_s - cd;
+        }
+    } else {
+        S = block_sum_i64(S, red);
+        cnt = block_sum_i64(cnt, red);
+        loss = conn_s - (cnt > 0 ? (int32_t)(S / cnt) : 0);
+    }
+    if (threadIdx.x == 0) {
+        const int32_t key = a * kSlots + slot_of(loss);
+        L.key[v] = key;
+        if (L.rbloss) L.rbloss[v] = loss;
+        sb.add_one(L, key, (long long)g.vw[v]);
+        degrows += end - beg;
+    }
+}
+
 // Step 1 for the listed candidates: Jetrw destination (best-connected part of
 // B, lowest id on ties, else a random one) and loss, or the Jetrs loss
 // (Sec. 4.2.2), then the slot bucket.  Short rows one thread each, long rows
@@ -1070,6 +1252,7 @@ __device__ inline void ph_rb_cand(const Level &L, Grid G, char *arena) {
     const DGraph g = L.g;
     long long degrows = 0;
     auto big_row = [&](int32_t v) { rb_cand_row<EW, STRONG>(L, v, tab, it, nB, sb, degrows); };
+    auto hub_row = [&](int32_t v) { rb_cand_block_row<EW, STRONG>(L, v, a32 + kBigCap, red, it, nB, sb, degrows); };
     for (int64_t i0 = sh.beg; i0 < sh.end; i0 += blockDim.x) {
         int64_t i = i0 + threadIdx.x;
         int32_t key = -1;
@@ -1141,9 +1324,9 @@ __device__ inline void ph_rb_cand(const Level &L, Grid G, char *arena) {
         }
         sb.add(L, key, wv);
         bigs.add(big, v);
-        bigs.drain(false, big_row);
+        bigs.drain(false, g.xadj, big_row, hub_row);
     }
-    bigs.drain(true, big_row);
+    bigs.drain(true, g.xadj, big_row, hub_row);
     sb.flush(L);
     flush_counter(&ctl->degexam, degrows, red);
 }
