@@ -59,6 +59,7 @@ def parse_args(argv=None):
                    help="largest level refined by the one-cluster loop (library default if omitted; 0 = never)")
     p.add_argument("--kernel-probe", action="store_true",
                    help="run one profiled partition and report per-level select launches (profiler target)")
+    p.add_argument("--rmat-k", type=int, default=None, help="with --sweep rmat: only this k")
     p.add_argument("--sweep", choices=["lp_versions", "batched", "rmat"], default=None,
                    help="the Jetlp versions of the paper's component study and the phi trade-off, on the "
                         "mesh, power-law and large-grid workloads (one JSON line per run and a summary)")
@@ -526,7 +527,7 @@ def run_rmat(args):
     g = graphgen.rmat(22, seed=SEED)
     xadj, adj = torch.from_numpy(g.xadj).to(dev), torch.from_numpy(g.adjncy).to(dev)
     with jet.Context(0) as ctx:
-        for k in (2, 8, 64, 256):
+        for k in ((args.rmat_k,) if args.rmat_k else (2, 8, 64, 256)):
             ctx.partition(xadj, adj, k=k, eps=EPS, seed=SEED)                    # warm-up
             runs = [ctx.partition(xadj, adj, k=k, eps=EPS, seed=SEED, return_stats=True) for _ in range(3)]
             part, cut, st = runs[0]

@@ -12,6 +12,7 @@
 #include "jet_internal.cuh"
 
 #include <algorithm>
+#include <cstring>
 
 namespace jet {
 
@@ -115,6 +116,47 @@ __global__ void __launch_bounds__(kTB) k_hem_propose_big(DGraph g, const int32_t
     }
 }
 
+// Hub rows (longer than kHugeDeg): one block per row, the same choice.
+template <bool EW>
+__global__ void __launch_bounds__(kTB) k_hem_propose_huge(DGraph g, const int32_t *hugev, int32_t nhuge,
+                                                          const int32_t *mate, int32_t *prop, uint64_t seed,
+                                                          uint64_t salt, int r, HemCtl *hc) {
+    if (hem_skip(hc, r)) return;
+    __shared__ int32_t su[32], sw[32];
+    __shared__ uint64_t shh[32];
+    const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
+    for (int64_t t = blockIdx.x; t < nhuge; t += gridDim.x) {
+        const int32_t v = hugev[t];
+        int32_t bu = -1, bw = 0;
+        uint64_t bh = 0;
+        if (mate[v] < 0) {
+            const int64_t beg = ld_xadj(g.xadj, v), end = ld_xadj(g.xadj, (int64_t)v + 1);
+            for (int64_t j = beg + threadIdx.x; j < end; j += blockDim.x) {
+                const int32_t u = __ldg(g.adj + j);
+                if (mate[u] >= 0) continue;
+                const int32_t ww = cw<EW>(g, j);
+                const uint64_t h = hem_hash(seed, salt, u);
+                if (hem_better(ww, h, u, bw, bh, bu)) { bu = u; bw = ww; bh = h; }
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const int32_t ou = __shfl_xor_sync(0xffffffffu, bu, o);
+            const int32_t ow = __shfl_xor_sync(0xffffffffu, bw, o);
+            const uint64_t oh = __shfl_xor_sync(0xffffffffu, bh, o);
+            if (hem_better(ow, oh, ou, bw, bh, bu)) { bu = ou; bw = ow; bh = oh; }
+        }
+        if (lane == 0) { su[warp] = bu; sw[warp] = bw; shh[warp] = bh; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (unsigned i = 1; i < (blockDim.x >> 5); ++i)
+                if (hem_better(sw[i], shh[i], su[i], bw, bh, bu)) { bu = su[i]; bw = sw[i]; bh = shh[i]; }
+            prop[v] = bu;
+        }
+        __syncthreads();
+    }
+}
+
 // Mutual proposals match (synchronous: every proposal of the round is read
 // before any mate changes matter, since proposals only name unmatched ones).
 __global__ void __launch_bounds__(kTB) k_hem_match(int32_t n, int32_t *mate, const int32_t *prop, int r, HemCtl *hc) {
@@ -129,29 +171,40 @@ __global__ void __launch_bounds__(kTB) k_hem_match(int32_t n, int32_t *mate, con
     if (threadIdx.x == 0 && c) atomic_add_i64(&hc->added[r], c);
 }
 
-__global__ void k_collect_rows(DGraph g, int32_t *list, int32_t *count) {
+// Rows longer than kSmallDeg: warp rows (up to kHugeDeg entries) into list,
+// hub rows into hlist.
+__global__ void k_collect_rows(DGraph g, int32_t *list, int32_t *count, int32_t *hlist, int32_t *hcount) {
     int32_t v = blockIdx.x * blockDim.x + threadIdx.x;
-    bool big = v < g.n && ld_xadj(g.xadj, (int64_t)v + 1) - ld_xadj(g.xadj, v) > kSmallDeg;
+    const int64_t d = v < g.n ? ld_xadj(g.xadj, (int64_t)v + 1) - ld_xadj(g.xadj, v) : 0;
+    const bool big = d > kSmallDeg && d <= kHugeDeg, huge = d > kHugeDeg;
     int slot = warp_append(count, big);
     if (big) list[slot] = v;
+    slot = warp_append(hcount, huge);
+    if (huge) hlist[slot] = v;
 }
 
 __global__ void k_fill(int32_t *p, int64_t n, int32_t val) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) p[i] = val;
 }
 
-static int big_rows(Ctx &c, const DGraph &g, DevBuf &buf, int32_t &nbig) {
+// The warp rows (list at buf) and the hub rows (list at *huge) of g.
+static int big_rows(Ctx &c, const DGraph &g, DevBuf &buf, int32_t &nbig, int32_t **huge, int32_t &nhuge) {
     cudaStream_t s = c.stream;
-    JET_TRY(dev_alloc(buf, (size_t)std::max<int64_t>(g.n, 1) * 4 + 256, s));
-    int32_t *cnt = reinterpret_cast<int32_t *>(buf.as<char>() + (size_t)std::max<int64_t>(g.n, 1) * 4);
-    cnt = reinterpret_cast<int32_t *>((reinterpret_cast<uintptr_t>(cnt) + 15) & ~uintptr_t(15));
-    JET_CUDA_TRY(cudaMemsetAsync(cnt, 0, 4, s));
-    if (g.n > 0) k_collect_rows<<<grid_for(g.n, kTB), kTB, 0, s>>>(g, buf.as<int32_t>(), cnt);
+    const size_t nb = ((size_t)std::max<int64_t>(g.n, 1) * 4 + 255) & ~size_t(255);
+    JET_TRY(dev_alloc(buf, 2 * nb + 256, s));
+    int32_t *list = buf.as<int32_t>();
+    *huge = reinterpret_cast<int32_t *>(buf.as<char>() + nb);
+    int32_t *cnt = reinterpret_cast<int32_t *>(buf.as<char>() + 2 * nb);
+    JET_CUDA_TRY(cudaMemsetAsync(cnt, 0, 8, s));
+    if (g.n > 0) k_collect_rows<<<grid_for(g.n, kTB), kTB, 0, s>>>(g, list, cnt, *huge, cnt + 1);
     if (g.n > 0) c.launches += 1;
     JET_CUDA_TRY(cudaGetLastError());
-    JET_CUDA_TRY(cudaMemcpyAsync(c.pinned, cnt, 4, cudaMemcpyDeviceToHost, s));
+    JET_CUDA_TRY(cudaMemcpyAsync(c.pinned, cnt, 8, cudaMemcpyDeviceToHost, s));
     JET_CUDA_TRY(cudaStreamSynchronize(s));
-    nbig = (int32_t)(c.pinned[0] & 0xFFFFFFFF);
+    int32_t h[2];
+    memcpy(h, c.pinned, 8);
+    nbig = h[0];
+    nhuge = h[1];
     return JET_OK;
 }
 
@@ -159,8 +212,9 @@ int hem(Ctx &c, const DGraph &g, uint64_t seed, int32_t level, int32_t rounds, i
     cudaStream_t s = c.stream;
     if (g.n == 0) return JET_OK;
     DevBuf bigbuf, pbuf, hbuf;
-    int32_t nbig = 0;
-    JET_TRY(big_rows(c, g, bigbuf, nbig));
+    int32_t nbig = 0, nhuge = 0;
+    int32_t *hugev = nullptr;
+    JET_TRY(big_rows(c, g, bigbuf, nbig, &hugev, nhuge));
     JET_TRY(dev_alloc(pbuf, (size_t)g.n * 4, s));
     JET_TRY(dev_alloc(hbuf, sizeof(HemCtl), s));
     HemCtl *hc = hbuf.as<HemCtl>();
@@ -178,6 +232,12 @@ int hem(Ctx &c, const DGraph &g, uint64_t seed, int32_t level, int32_t rounds, i
             int gb = std::min(gl, grid_for(nbig, kTB / 32));
             if (g.ew) k_hem_propose_big<true><<<gb, kTB, 0, s>>>(g, bigbuf.as<int32_t>(), nbig, mate, pbuf.as<int32_t>(), seed, salt, r, hc);
             else k_hem_propose_big<false><<<gb, kTB, 0, s>>>(g, bigbuf.as<int32_t>(), nbig, mate, pbuf.as<int32_t>(), seed, salt, r, hc);
+            c.launches += 1;
+        }
+        if (nhuge > 0) {
+            int gh = std::min(gl, nhuge);
+            if (g.ew) k_hem_propose_huge<true><<<gh, kTB, 0, s>>>(g, hugev, nhuge, mate, pbuf.as<int32_t>(), seed, salt, r, hc);
+            else k_hem_propose_huge<false><<<gh, kTB, 0, s>>>(g, hugev, nhuge, mate, pbuf.as<int32_t>(), seed, salt, r, hc);
             c.launches += 1;
         }
         k_hem_match<<<std::min(gl, grid_for(g.n, kTB)), kTB, 0, s>>>(g.n, mate, pbuf.as<int32_t>(), r, hc);

@@ -59,27 +59,55 @@ __global__ void k_uf_init(int32_t n, int32_t *parent) {
         parent[v] = (int32_t)v;
 }
 
-// One warp per vertex v; every edge {u, v} with u < v hooks the two roots,
-// the larger under the smaller (a failed CAS means another hook lowered the
-// root; retry from the new one).
+// The edge {u, v}, u < v, hooks the two roots, the larger under the smaller
+// (a failed CAS means another hook lowered the root; retry from the new one).
+__device__ __forceinline__ void uf_hook_edge(int32_t *parent, int32_t u, int32_t v, int32_t *err) {
+    int32_t ru = uf_find(parent, u, err), rv = uf_find(parent, v, err);
+    for (int i = 0; i < kFindCap && ru != rv; ++i) {
+        int32_t hi = ru > rv ? ru : rv, lo = ru > rv ? rv : ru;
+        int32_t old = atomicCAS(&parent[hi], hi, lo);
+        if (old == hi) break;
+        ru = uf_find(parent, old, err);
+        rv = uf_find(parent, lo, err);
+        if (i + 1 == kFindCap) *err = 1;
+    }
+}
+
+// One warp per vertex v hooks the edges {u, v} with u < v; rows longer than
+// kHugeDeg are set aside (up to kHugeCap per block) and taken by the whole
+// block at the end.
 __global__ void __launch_bounds__(kTB) k_uf_hook(DGraph g, int32_t *parent, IpCtl *ctl) {
+    __shared__ int32_t huge[kHugeCap];
+    __shared__ int nhuge;
+    if (threadIdx.x == 0) nhuge = 0;
+    __syncthreads();
     const int warps = blockDim.x >> 5;
     const unsigned lane = lane_id();
     int32_t err = 0;
     for (int64_t v = (int64_t)blockIdx.x * warps + (threadIdx.x >> 5); v < g.n; v += (int64_t)gridDim.x * warps) {
         int64_t beg = ld_xadj(g.xadj, v), end = ld_xadj(g.xadj, v + 1);
+        if (end - beg > kHugeDeg) {
+            int slot = 0;
+            if (lane == 0) slot = atomicAdd(&nhuge, 1);
+            slot = __shfl_sync(0xffffffffu, slot, 0);
+            if (slot < kHugeCap) {
+                if (lane == 0) huge[slot] = (int32_t)v;
+                continue;
+            }
+        }
         for (int64_t j = beg + lane; j < end; j += 32) {
             int32_t u = __ldg(g.adj + j);
-            if (u >= v) continue;
-            int32_t ru = uf_find(parent, u, &err), rv = uf_find(parent, (int32_t)v, &err);
-            for (int i = 0; i < kFindCap && ru != rv; ++i) {
-                int32_t hi = ru > rv ? ru : rv, lo = ru > rv ? rv : ru;
-                int32_t old = atomicCAS(&parent[hi], hi, lo);
-                if (old == hi) break;
-                ru = uf_find(parent, old, &err);
-                rv = uf_find(parent, lo, &err);
-                if (i + 1 == kFindCap) err = 1;
-            }
+            if (u < v) uf_hook_edge(parent, u, (int32_t)v, &err);
+        }
+    }
+    __syncthreads();
+    const int nh = nhuge < kHugeCap ? nhuge : kHugeCap;
+    for (int s = 0; s < nh; ++s) {
+        const int32_t v = huge[s];
+        const int64_t beg = ld_xadj(g.xadj, v), end = ld_xadj(g.xadj, (int64_t)v + 1);
+        for (int64_t j = beg + threadIdx.x; j < end; j += blockDim.x) {
+            int32_t u = __ldg(g.adj + j);
+            if (u < v) uf_hook_edge(parent, u, v, &err);
         }
     }
     if (err) ctl->error = 1;
@@ -119,15 +147,46 @@ __global__ void __launch_bounds__(kTB) k_bfs_level(DGraph g, int32_t *dist, int3
     int32_t *out_size = &ctl->size[(l + 1) & 1];
     const int warps = blockDim.x >> 5;
     const unsigned lane = lane_id();
+    __shared__ int32_t huge[kHugeCap];
+    __shared__ int nhuge;
+    if (threadIdx.x == 0) nhuge = 0;
+    __syncthreads();
     for (int64_t w0 = (int64_t)blockIdx.x * warps; w0 < cur; w0 += (int64_t)gridDim.x * warps) {
         int64_t w = w0 + (threadIdx.x >> 5);
         int64_t beg = 0, end = 0;
+        int32_t v = -1;
         if (w < cur) {
-            int32_t v = in[w];
+            v = in[w];
             beg = ld_xadj(g.xadj, v);
             end = ld_xadj(g.xadj, (int64_t)v + 1);
         }
+        if (end - beg > kHugeDeg) {              // hub row: the whole block, below
+            int slot = 0;
+            if (lane == 0) slot = atomicAdd(&nhuge, 1);
+            slot = __shfl_sync(0xffffffffu, slot, 0);
+            if (slot < kHugeCap) {
+                if (lane == 0) huge[slot] = v;
+                end = beg;
+            }
+        }
         for (int64_t j0 = beg; j0 < end; j0 += 32) {   // whole warp: same row
+            int64_t j = j0 + lane;
+            bool claim = false;
+            int32_t u = -1;
+            if (j < end) {
+                u = __ldg(g.adj + j);
+                claim = dist[u] == kInf && atomicCAS(&dist[u], kInf, l + 1) == kInf;
+            }
+            int slot = warp_append(out_size, claim);
+            if (claim) out[slot] = u;
+        }
+    }
+    __syncthreads();
+    const int nh = nhuge < kHugeCap ? nhuge : kHugeCap;
+    for (int s = 0; s < nh; ++s) {
+        const int32_t v = huge[s];
+        const int64_t beg = ld_xadj(g.xadj, v), end = ld_xadj(g.xadj, (int64_t)v + 1);
+        for (int64_t j0 = beg + (int64_t)(threadIdx.x >> 5) * 32; j0 < end; j0 += blockDim.x) {
             int64_t j = j0 + lane;
             bool claim = false;
             int32_t u = -1;

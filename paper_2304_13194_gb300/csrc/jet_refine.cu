@@ -29,37 +29,96 @@ extern __shared__ __align__(16) unsigned char jet_arena[];
 // cut and part weights of a partition (Sec. 2.1), used at level start; also
 // the neighbour counts in other parts (ext) and the weighted degrees
 // ---------------------------------------------------------------------------
+// Short rows (up to 2 kSmallDeg entries) one thread each; longer rows staged
+// for the block's warps, hub rows (over kHugeDeg) for the whole block.
 template <bool EW>
 __global__ void __launch_bounds__(kTB) k_cut_pw(DGraph g, int32_t k, const int32_t *__restrict__ part,
                                                  int64_t *__restrict__ pw, int64_t *__restrict__ cut2,
                                                  int32_t *__restrict__ ext, int32_t *__restrict__ wdeg) {
     long long *shpw = reinterpret_cast<long long *>(jet_arena);
+    int32_t *stage = reinterpret_cast<int32_t *>(jet_arena + align16((size_t)k * 8));
     __shared__ long long red[40];
     for (int i = threadIdx.x; i < k; i += blockDim.x) shpw[i] = 0;
-    __syncthreads();
+    JET_APPENDER(bigs, stage, kBigCap);
     long long c = 0;
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < g.n; v += (int64_t)gridDim.x * blockDim.x) {
-        int32_t p = part[v];
-        atomicAdd(reinterpret_cast<unsigned long long *>(&shpw[p]), (unsigned long long)(long long)(g.vw ? g.vw[v] : 1));
-        int64_t e = ld_xadj(g.xadj, v + 1);
-        int32_t nx = 0, wd = 0, cv = 0;
-        for (int64_t j = ld_xadj(g.xadj, v); j < e; ++j) {
-            int32_t w = edge_w<EW>(g, j);
-            bool other = part[g.adj[j]] != p;
+    const unsigned lane = lane_id();
+    // one row's cut share, ext and weighted degree; `part_v` is v's part
+    auto warp_row = [&](int32_t v) {
+        const int32_t p = part[v];
+        const int64_t b = ld_xadj(g.xadj, v), e = ld_xadj(g.xadj, (int64_t)v + 1);
+        long long cv = 0, nx = 0, wd = 0;
+        for (int64_t j = b + lane; j < e; j += 32) {
+            const int32_t w = edge_w<EW>(g, j);
+            const bool other = part[g.adj[j]] != p;
             cv += other ? w : 0;
             nx += other ? 1 : 0;
             wd += w;
         }
-        c += cv;
-        if (ext) ext[v] = nx;
-        if (wdeg) wdeg[v] = wd;
+        cv = warp_sum_i64(cv);
+        nx = warp_sum_i64(nx);
+        wd = warp_sum_i64(wd);
+        if (lane == 0) {
+            c += cv;
+            if (ext) ext[v] = (int32_t)nx;
+            if (wdeg) wdeg[v] = (int32_t)wd;
+        }
+    };
+    auto block_row = [&](int32_t v) {
+        const int32_t p = part[v];
+        const int64_t b = ld_xadj(g.xadj, v), e = ld_xadj(g.xadj, (int64_t)v + 1);
+        long long cv = 0, nx = 0, wd = 0;
+        for (int64_t j = b + threadIdx.x; j < e; j += blockDim.x) {
+            const int32_t w = edge_w<EW>(g, j);
+            const bool other = part[g.adj[j]] != p;
+            cv += other ? w : 0;
+            nx += other ? 1 : 0;
+            wd += w;
+        }
+        cv = block_sum_i64(cv, red);
+        nx = block_sum_i64(nx, red);
+        wd = block_sum_i64(wd, red);
+        if (threadIdx.x == 0) {
+            c += cv;
+            if (ext) ext[v] = (int32_t)nx;
+            if (wdeg) wdeg[v] = (int32_t)wd;
+        }
+    };
+    for (int64_t v0 = (int64_t)blockIdx.x * blockDim.x; v0 < g.n; v0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t v = v0 + threadIdx.x;
+        bool big = false;
+        if (v < g.n) {
+            const int32_t p = part[v];
+            atomicAdd(reinterpret_cast<unsigned long long *>(&shpw[p]), (unsigned long long)(long long)(g.vw ? g.vw[v] : 1));
+            const int64_t b = ld_xadj(g.xadj, v), e = ld_xadj(g.xadj, v + 1);
+            if (e - b > 2 * kSmallDeg) {
+                big = true;
+            } else {
+                int32_t nx = 0, wd = 0, cv = 0;
+                for (int64_t j = b; j < e; ++j) {
+                    const int32_t w = edge_w<EW>(g, j);
+                    const bool other = part[g.adj[j]] != p;
+                    cv += other ? w : 0;
+                    nx += other ? 1 : 0;
+                    wd += w;
+                }
+                c += cv;
+                if (ext) ext[v] = nx;
+                if (wdeg) wdeg[v] = wd;
+            }
+        }
+        bigs.add(big, (int32_t)v);
+        bigs.drain(false, g.xadj, warp_row, block_row);
     }
+    bigs.drain(true, g.xadj, warp_row, block_row);
     c = block_sum_i64(c, red);
     if (threadIdx.x == 0 && c) atomic_add_i64(cut2, c);
     __syncthreads();
     for (int i = threadIdx.x; i < k; i += blockDim.x)
         if (shpw[i]) atomic_add_i64(&pw[i], shpw[i]);
 }
+
+// dynamic shared memory of k_cut_pw
+size_t sm_cut_pw(int32_t k) { return align16((size_t)k * 8) + (size_t)kBigCap * 4; }
 
 // ---------------------------------------------------------------------------
 // one kernel per phase (large levels and the single-pass entry points)
@@ -431,8 +490,8 @@ int enqueue_init(Ctx &c, LevelBufs &B, int64_t L_lim, int64_t opt, int64_t sigma
     JET_CUDA_TRY(cudaMemcpyAsync(&L.ctl->L, consts, sizeof(consts), cudaMemcpyHostToDevice, s));
     if (n > 0) {
         int gcut = std::min(list_grid(), grid_for(n, kTB));
-        if (L.g.ew) k_cut_pw<true><<<gcut, kTB, (size_t)L.k * 8, s>>>(L.g, L.k, L.part, L.pw, B.cut2, L.ext, L.wdeg);
-        else k_cut_pw<false><<<gcut, kTB, (size_t)L.k * 8, s>>>(L.g, L.k, L.part, L.pw, B.cut2, L.ext, L.wdeg);
+        if (L.g.ew) k_cut_pw<true><<<gcut, kTB, sm_cut_pw(L.k), s>>>(L.g, L.k, L.part, L.pw, B.cut2, L.ext, L.wdeg);
+        else k_cut_pw<false><<<gcut, kTB, sm_cut_pw(L.k), s>>>(L.g, L.k, L.part, L.pw, B.cut2, L.ext, L.wdeg);
         c.launches += 1;
     }
     k_ctl_init<<<1, 1024, 0, s>>>(L, B.cut2);
@@ -847,8 +906,8 @@ int lp_pass(Ctx &c, const DGraph &g, int32_t k, const int32_t *part, const uint8
     L.abl = flags & ABL_ALL;
     {
         int gcut = std::min(list_grid(), grid_for(g.n, kTB));
-        if (g.ew) k_cut_pw<true><<<gcut, kTB, (size_t)k * 8, s>>>(g, k, L.part, L.pw, B.cut2, L.ext, nullptr);
-        else k_cut_pw<false><<<gcut, kTB, (size_t)k * 8, s>>>(g, k, L.part, L.pw, B.cut2, L.ext, nullptr);
+        if (g.ew) k_cut_pw<true><<<gcut, kTB, sm_cut_pw(k), s>>>(g, k, L.part, L.pw, B.cut2, L.ext, nullptr);
+        else k_cut_pw<false><<<gcut, kTB, sm_cut_pw(k), s>>>(g, k, L.part, L.pw, B.cut2, L.ext, nullptr);
     }
     k_locks_from_mask<<<grid_for(g.n, kTB, 4096), kTB, 0, s>>>(locked, L.lstamp, g.n);
     k_set_epoch<<<1, 1, 0, s>>>(L.ctl, 0, MODE_LP);
@@ -918,8 +977,8 @@ int rebalance_pass(Ctx &c, const DGraph &g, int32_t k, double eps, int32_t stron
     int64_t consts[3] = {L_lim, opt, sigma};
     JET_CUDA_TRY(cudaMemcpyAsync(&L.ctl->L, consts, sizeof(consts), cudaMemcpyHostToDevice, s));
     int gcut = std::min(list_grid(), grid_for(g.n, kTB));
-    if (g.ew) k_cut_pw<true><<<gcut, kTB, (size_t)k * 8, s>>>(g, k, L.part, L.pw, B.cut2, L.ext, L.wdeg);
-    else k_cut_pw<false><<<gcut, kTB, (size_t)k * 8, s>>>(g, k, L.part, L.pw, B.cut2, L.ext, L.wdeg);
+    if (g.ew) k_cut_pw<true><<<gcut, kTB, sm_cut_pw(k), s>>>(g, k, L.part, L.pw, B.cut2, L.ext, L.wdeg);
+    else k_cut_pw<false><<<gcut, kTB, sm_cut_pw(k), s>>>(g, k, L.part, L.pw, B.cut2, L.ext, L.wdeg);
     L.rbloss = loss_out;
     k_rb_pass_init<<<1, 1024, 0, s>>>(L, B.cut2, strong ? MODE_RS : MODE_RW);
     // the pass API takes the iteration index as a parameter: set ctl->it
@@ -947,8 +1006,8 @@ int cut_and_weights(Ctx &c, const DGraph &g, int32_t k, const int32_t *part, int
     JET_CUDA_TRY(cudaMemsetAsync(pw, 0, (size_t)k * 8, s));
     if (g.n > 0) {
         int gcut = std::min(list_grid(), grid_for(g.n, kTB));
-        if (g.ew) k_cut_pw<true><<<gcut, kTB, (size_t)k * 8, s>>>(g, k, part, pw, cut2, nullptr, nullptr);
-        else k_cut_pw<false><<<gcut, kTB, (size_t)k * 8, s>>>(g, k, part, pw, cut2, nullptr, nullptr);
+        if (g.ew) k_cut_pw<true><<<gcut, kTB, sm_cut_pw(k), s>>>(g, k, part, pw, cut2, nullptr, nullptr);
+        else k_cut_pw<false><<<gcut, kTB, sm_cut_pw(k), s>>>(g, k, part, pw, cut2, nullptr, nullptr);
     }
     JET_CUDA_TRY(cudaGetLastError());
     JET_CUDA_TRY(cudaMemcpyAsync(c.pinned, cut2, 8, cudaMemcpyDeviceToHost, s));
@@ -996,8 +1055,8 @@ int lp_pass_in_scratch(Ctx &c, const DGraph &g, int32_t k, const int32_t *part, 
     JET_CUDA_TRY(cudaMemsetAsync(cut2, 0, 16, s));
     {
         int gcut = std::min(list_grid(), grid_for(g.n, kTB));
-        if (g.ew) k_cut_pw<true><<<gcut, kTB, (size_t)k * 8, s>>>(g, k, L.part, L.pw, cut2, L.ext, nullptr);
-        else k_cut_pw<false><<<gcut, kTB, (size_t)k * 8, s>>>(g, k, L.part, L.pw, cut2, L.ext, nullptr);
+        if (g.ew) k_cut_pw<true><<<gcut, kTB, sm_cut_pw(k), s>>>(g, k, L.part, L.pw, cut2, L.ext, nullptr);
+        else k_cut_pw<false><<<gcut, kTB, sm_cut_pw(k), s>>>(g, k, L.part, L.pw, cut2, L.ext, nullptr);
     }
     k_count_big<<<grid_for(g.n, kTB), kTB, 0, s>>>(g, nbig_dev);
     k_fill_i32<<<grid_for(g.n, kTB, 4096), kTB, 0, s>>>(L.mstamp, g.n, -2);
