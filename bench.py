@@ -60,6 +60,7 @@ def parse_args(argv=None):
     p.add_argument("--kernel-probe", action="store_true",
                    help="run one profiled partition and report per-level select launches (profiler target)")
     p.add_argument("--rmat-k", type=int, default=None, help="with --sweep rmat: only this k")
+    p.add_argument("--two-hop", action="store_true", help="with --sweep rmat: coarsen with two-hop matches")
     p.add_argument("--sweep", choices=["lp_versions", "batched", "rmat"], default=None,
                    help="the Jetlp versions of the paper's component study and the phi trade-off, on the "
                         "mesh, power-law and large-grid workloads (one JSON line per run and a summary)")
@@ -526,7 +527,7 @@ def run_rmat(args):
     dev = torch.device("cuda", 0)
     g = graphgen.rmat(22, seed=SEED)
     xadj, adj = torch.from_numpy(g.xadj).to(dev), torch.from_numpy(g.adjncy).to(dev)
-    with jet.Context(0) as ctx:
+    with jet.Context(0, flags=jet.FLAG_TWO_HOP if args.two_hop else 0) as ctx:
         for k in ((args.rmat_k,) if args.rmat_k else (2, 8, 64, 256)):
             ctx.partition(xadj, adj, k=k, eps=EPS, seed=SEED)                    # warm-up
             runs = [ctx.partition(xadj, adj, k=k, eps=EPS, seed=SEED, return_stats=True) for _ in range(3)]
@@ -535,7 +536,8 @@ def run_rmat(args):
             c2, pw = ctx.cut(xadj, adj, None, None, k, part)
             ms = sorted(r[2].ms_total for r in runs)[1]
             L = (-(-g.n // k)) * (1000000 + round(EPS * 1e6)) // 1000000
-            print(json.dumps({"sweep": "rmat", "graph": "rmat22", "n": g.n, "m": g.m, "k": k, "levels": st.levels,
+            print(json.dumps({"sweep": "rmat", "graph": "rmat22", "two_hop": bool(args.two_hop), "n": g.n, "m": g.m,
+                              "k": k, "levels": st.levels,
                               "coarsest_n": st.n[-1], "partition_ms": round(ms, 2),
                               "coarsen_ms": round(st.ms_coarsen, 2), "init_ms": round(st.ms_init, 2),
                               "refine_ms": round(st.ms_refine, 2),
