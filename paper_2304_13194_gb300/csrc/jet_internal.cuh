@@ -123,7 +123,7 @@ struct Ctl {
     int32_t nM;          // M list length
     int32_t ticket;      // blocks of the current kernel that finished (last-block tails)
     int32_t hit_cap;     // stopped by max_iters
-    int32_t pad0;
+    int32_t nXh, nMh;    // hub rows of X / M, stored from the end of listX / listM downwards
     int32_t kcount[4];   // iterations run per kind (Jetlp, Jetrw, Jetrs)
     int64_t ncand;       // rebalancing candidates (trace)
     int64_t degx, degm;  // row-length sums over X / candidates and over M (byte model)

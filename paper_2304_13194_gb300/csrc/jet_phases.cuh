@@ -352,6 +352,7 @@ __device__ inline int32_t choose_mode(const Level &L, bool balanced) {
 
 __device__ __forceinline__ void reset_counters(Ctl *ctl) {
     ctl->nW = ctl->nX = ctl->nM = 0;
+    ctl->nXh = ctl->nMh = 0;
     ctl->ncand = 0;
     ctl->degx = ctl->degm = 0;
     ctl->nbnd = ctl->nexam = ctl->degexam = 0;
@@ -389,7 +390,7 @@ __device__ inline int32_t ph_controller(const Level &L) {
         cut0 = ctl->cut; Llim = ctl->L; best_cut0 = ctl->best_cut; best_maxw0 = ctl->best_maxw;
         it = ctl->it; noimp0 = ctl->noimp; best_bal0 = ctl->best_bal; kc = ctl->kcount[kind];
         weak = ctl->weak; hit_cap = ctl->hit_cap;
-        nX = ctl->nX; nM = ctl->nM;
+        nX = ctl->nX + ctl->nXh; nM = ctl->nM + ctl->nMh;
         ncand = ctl->ncand; degx = ctl->degx; nbnd = ctl->nbnd; nexam = ctl->nexam; degexam = ctl->degexam;
         dcut = ld_gpu(&ctl->dcut); degm = ld_gpu(&ctl->degm);
     }
@@ -587,7 +588,7 @@ __device__ __forceinline__ void lp_select_block_row(const Level &L, LpExport ex,
         if (inX) {
             L.prio[v] = F;
             L.nxt[v] = nxt_pack(ps, pd);
-            L.listX[atomicAdd(&L.ctl->nX, 1)] = v;
+            L.listX[L.g.n - 1 - atomicAdd(&L.ctl->nXh, 1)] = v;   // hub region, spread over the next phase's blocks
             degx += end - beg;
         }
         if (ex.pd) { ex.pd[v] = pd >= 0 ? pd : ps; ex.gain[v] = F; }
@@ -756,7 +757,7 @@ __device__ __forceinline__ void afterburn_block_row(const Level &L, LpExport ex,
         if (ex.f2) ex.f2[v] = (int32_t)f2;
         if (f2 >= 0) {
             L.mstamp[v] = it;
-            L.listM[atomicAdd(&L.ctl->nM, 1)] = v;
+            L.listM[L.g.n - 1 - atomicAdd(&L.ctl->nMh, 1)] = v;   // hub region
         }
     }
 }
@@ -766,6 +767,18 @@ __device__ inline void ph_afterburn(const Level &L, LpExport ex, Grid G, char *a
     __shared__ long long red[40];
     Ctl *ctl = L.ctl;
     const int32_t it = ctl->it;
+    const bool full_ab = !(L.abl & (ABL_NO_AFTERBURN | ABL_BASELINE_LP));
+    // hub rows of X, one block each, dealt round-robin over the blocks
+    const int32_t nXh = ctl->nXh;
+    for (int32_t h = G.bid; h < nXh; h += G.nb) {
+        const int32_t v = L.listX[L.g.n - 1 - h];
+        if (full_ab) {
+            afterburn_block_row<EW>(L, ex, v, it, red);
+        } else if (threadIdx.x == 0) {
+            L.mstamp[v] = it;
+            L.listM[L.g.n - 1 - atomicAdd(&ctl->nMh, 1)] = v;
+        }
+    }
     const Share sh = list_share(ctl->nX, G);
     if (sh.beg >= sh.end) return;
     int32_t *a32 = reinterpret_cast<int32_t *>(arena);
@@ -904,7 +917,7 @@ __device__ inline void ph_apply(const Level &L, Grid G, char *arena) {
     Ctl *ctl = L.ctl;
     const int32_t kind = ctl->mode;
     if (kind == MODE_DONE) return;
-    const int32_t nM = ctl->nM, nX = ctl->nX, it = ctl->it;
+    const int32_t nM = ctl->nM, nX = ctl->nX, it = ctl->it, nMh = ctl->nMh, nXh = ctl->nXh;
     const bool lp = kind == MODE_LP;
     long long *shpw = reinterpret_cast<long long *>(arena);
     int32_t *stage = reinterpret_cast<int32_t *>(arena + align16((size_t)L.k * 8));
@@ -974,9 +987,22 @@ __device__ inline void ph_apply(const Level &L, Grid G, char *arena) {
         bigs.drain(false, L.g.xadj, big_row, hub_row);
     }
     bigs.drain(true, L.g.xadj, big_row, hub_row);
+    // hub rows of M, one block each, dealt round-robin over the blocks
+    for (int32_t h = G.bid; h < nMh; h += G.nb) {
+        const int32_t v = L.listM[L.g.n - 1 - h];
+        if (threadIdx.x == 0) {
+            const int32_t x = L.nxt[v];
+            const long long wv = L.g.vw[v];
+            atomicAdd(reinterpret_cast<unsigned long long *>(&shpw[nxt_from(x)]), (unsigned long long)(-wv));
+            atomicAdd(reinterpret_cast<unsigned long long *>(&shpw[nxt_to(x)]), (unsigned long long)wv);
+        }
+        apply_block_row<EW>(L, v, it, lp, red, dc, dm);
+    }
     if (lp) {
         const int64_t stride = (int64_t)G.nb * blockDim.x;
         for (int64_t i = (int64_t)G.bid * blockDim.x + threadIdx.x; i < nX; i += stride) L.prio[L.listX[i]] = kNoneGain;
+        for (int64_t i = (int64_t)G.bid * blockDim.x + threadIdx.x; i < nXh; i += stride)
+            L.prio[L.listX[L.g.n - 1 - i]] = kNoneGain;
     }
     dc = block_sum_i64(dc, red);
     dm = block_sum_i64(dm, red);

@@ -988,7 +988,7 @@ int rebalance_pass(Ctx &c, const DGraph &g, int32_t k, double eps, int32_t stron
     JET_TRY(enqueue_rb(L, s, strong != 0, &nk));
     Ctl h;
     JET_TRY(read_ctl(c, L, h));
-    if (nmoves) *nmoves = (int64_t)h.nM;
+    if (nmoves) *nmoves = (int64_t)h.nM + h.nMh;
     if (ncand) *ncand = h.ncand;
     k_export_rb<<<grid_for(g.n, kTB, 4096), kTB, 0, s>>>(L, dest_out, loss_out);
     JET_CUDA_TRY(cudaGetLastError());
