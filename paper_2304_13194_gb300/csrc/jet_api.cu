@@ -575,8 +575,16 @@ int jet_partition_batch(jet_ctx *ctx, int32_t count, jet_batch_item *items, int3
         cudaStreamDestroy(s);
     };
     std::vector<std::thread> pool;
-    pool.reserve((size_t)workers);
-    for (int w = 0; w < workers; ++w) pool.emplace_back(worker, w);
+    int started = 0;
+    try {
+        pool.reserve((size_t)workers);
+        for (int w = 0; w < workers; ++w) {
+            pool.emplace_back(worker, w);
+            ++started;
+        }
+    } catch (...) {   // no exception crosses the C ABI: the workers that started take every item
+        if (started == 0) worker(0);   // none did: the calling thread takes the whole batch
+    }
     for (auto &t : pool) t.join();
     cudaEventDestroy(start);
     for (int w = 0; w < workers; ++w)

@@ -1063,22 +1063,30 @@ int jet_partition_learned(jet_ctx *ctx, const jet_lip *h, int32_t n, const int64
             return rc != JET_OK ? rc : JET_ECUDA;
         }
     }
+    auto learned_run = [&] {
+        Ctx &w = wc->c;
+        if (use_device(w) != JET_OK) { r_learned = JET_ECUDA; return; }
+        cudaEventRecord(wv[0], ws);
+        r_learned = uncoarsen(w, hier, k, eps, seed, init.as<int32_t>(), tmp.as<int32_t>(), &cut_learned,
+                              &st_learned);
+        cudaEventRecord(wv[1], ws);
+    };
     std::thread worker;
+    bool threaded = false;
     if (learned) {
-        worker = std::thread([&] {
-            Ctx &w = wc->c;
-            if (use_device(w) != JET_OK) { r_learned = JET_ECUDA; return; }
-            cudaEventRecord(wv[0], ws);
-            r_learned = uncoarsen(w, hier, k, eps, seed, init.as<int32_t>(), tmp.as<int32_t>(), &cut_learned,
-                                  &st_learned);
-            cudaEventRecord(wv[1], ws);
-        });
+        try {
+            worker = std::thread(learned_run);
+            threaded = true;
+        } catch (...) {   // no thread: the learned uncoarsening runs after the plain one
+        }
     }
     int64_t cut_plain = 0;
     int r_plain = n > 0 ? uncoarsen(c, hier, k, eps, seed, nullptr, part_out, &cut_plain, &st_plain) : JET_OK;
     cudaEventRecord(ev[3], c.stream);
     if (learned) {
-        worker.join();
+        if (threaded) worker.join();
+        else learned_run();
+        use_device(c);
         cudaStreamWaitEvent(c.stream, wv[1], 0);
         c.launches += wc->c.launches;
     }
