@@ -551,29 +551,45 @@ __device__ __forceinline__ unsigned long long block_max_u64(unsigned long long v
     return r;
 }
 
-// One hub row of step 1 (longer than kHugeDeg) by the whole block: conn(v, .)
-// in one k-entry table, zero between rows and cleared by a scan over the k
-// parts after the read; the same result as the warp version.
+// Sum over the block's per-warp tables of part p's connectivity.
+__device__ __forceinline__ int32_t tables_sum(const int32_t *tabs, int32_t k, int32_t p) {
+    int32_t c = 0;
+    const int warps = blockDim.x >> 5;
+    for (int w = 0; w < warps; ++w) c += tabs[w * k + p];
+    return c;
+}
+
+// Clears the block's per-warp tables (all threads).
+__device__ __forceinline__ void tables_clear(int32_t *tabs, int32_t k) {
+    const int n = (int)(blockDim.x >> 5) * k;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) tabs[i] = 0;
+}
+
+// One hub row of step 1 (longer than kHugeDeg) by the whole block: each warp
+// adds its share of conn(v, .) into its own k-entry table (tabs, zero
+// between rows), the parts then sum the warps' entries; the same result as
+// the warp version.
 template <bool EW>
-__device__ __forceinline__ void lp_select_block_row(const Level &L, LpExport ex, int32_t v, int32_t *tab, long long *red,
+__device__ __forceinline__ void lp_select_block_row(const Level &L, LpExport ex, int32_t v, int32_t *tabs, long long *red,
                                                     long long &nexam, long long &degexam, long long &degx) {
     const DGraph &g = L.g;
     const int32_t ps = L.part[v];
     const int64_t beg = ld_xadj(g.xadj, v), end = ld_xadj(g.xadj, (int64_t)v + 1);
+    int32_t *tab = tabs + (threadIdx.x >> 5) * L.k;
     for (int64_t j = beg + threadIdx.x; j < end; j += blockDim.x)
         atomicAdd(&tab[L.part[__ldg(g.adj + j)]], edge_w<EW>(g, j));
     __syncthreads();
-    const int32_t conn_s = tab[ps];
+    const int32_t conn_s = tables_sum(tabs, L.k, ps);
     unsigned long long best = 0;
     for (int p = threadIdx.x; p < L.k; p += blockDim.x) {
-        const int32_t c = tab[p];
+        const int32_t c = tables_sum(tabs, L.k, p);
         if (c > 0 && p != ps) {
             const unsigned long long key = part_key(c, p);
             best = key > best ? key : best;
         }
     }
     __syncthreads();
-    for (int p = threadIdx.x; p < L.k; p += blockDim.x) tab[p] = 0;
+    tables_clear(tabs, L.k);
     best = block_max_u64(best, reinterpret_cast<unsigned long long *>(red));
     if (threadIdx.x == 0) {
         int32_t F = kNoneGain, pd = -1;
@@ -1204,20 +1220,21 @@ __device__ __forceinline__ void rb_cand_row(const Level &L, int32_t v, int32_t *
 
 // One hub row of the rebalancing candidates by the whole block.
 template <bool EW, bool STRONG>
-__device__ __forceinline__ void rb_cand_block_row(const Level &L, int32_t v, int32_t *tab, long long *red, int32_t it,
+__device__ __forceinline__ void rb_cand_block_row(const Level &L, int32_t v, int32_t *tabs, long long *red, int32_t it,
                                                   int32_t nB, SmemBuckets &sb, long long &degrows) {
     const DGraph &g = L.g;
     const int32_t ps = L.part[v];
     const int32_t a = L.aidx[ps];
     const int64_t beg = ld_xadj(g.xadj, v), end = ld_xadj(g.xadj, (int64_t)v + 1);
+    int32_t *tab = tabs + (threadIdx.x >> 5) * L.k;
     for (int64_t j = beg + threadIdx.x; j < end; j += blockDim.x)
         atomicAdd(&tab[L.part[__ldg(g.adj + j)]], edge_w<EW>(g, j));
     __syncthreads();
-    const int32_t conn_s = tab[ps];
+    const int32_t conn_s = tables_sum(tabs, L.k, ps);
     unsigned long long best = 0;
     long long S = 0, cnt = 0;
     for (int p = threadIdx.x; p < L.k; p += blockDim.x) {
-        const int32_t c = tab[p];
+        const int32_t c = tables_sum(tabs, L.k, p);
         if (c > 0 && L.inB[p]) {
             if constexpr (!STRONG) {
                 const unsigned long long k2 = part_key(c, p);
@@ -1229,7 +1246,7 @@ __device__ __forceinline__ void rb_cand_block_row(const Level &L, int32_t v, int
         }
     }
     __syncthreads();
-    for (int p = threadIdx.x; p < L.k; p += blockDim.x) tab[p] = 0;
+    tables_clear(tabs, L.k);
     int32_t loss = 0;
     if constexpr (!STRONG) {
         best = block_max_u64(best, reinterpret_cast<unsigned long long *>(red));
