@@ -527,7 +527,8 @@ def run_rmat(args):
     dev = torch.device("cuda", 0)
     g = graphgen.rmat(22, seed=SEED)
     xadj, adj = torch.from_numpy(g.xadj).to(dev), torch.from_numpy(g.adjncy).to(dev)
-    with jet.Context(0, flags=jet.FLAG_TWO_HOP if args.two_hop else 0) as ctx:
+    flags = (jet.FLAG_TWO_HOP if args.two_hop else 0) | (jet.FLAG_HOSTLOOP if args.hostloop else 0)
+    with jet.Context(0, flags=flags) as ctx:
         for k in ((args.rmat_k,) if args.rmat_k else (2, 8, 64, 256)):
             ctx.partition(xadj, adj, k=k, eps=EPS, seed=SEED)                    # warm-up
             runs = [ctx.partition(xadj, adj, k=k, eps=EPS, seed=SEED, return_stats=True) for _ in range(3)]
