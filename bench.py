@@ -55,6 +55,9 @@ def parse_args(argv=None):
     p.add_argument("--no-pdl", action="store_true",
                    help="launch every refinement kernel after the previous one finishes (no programmatic "
                         "dependent launch); results are identical")
+    p.add_argument("--grid-loop", action="store_true",
+                   help="refine levels above the cluster threshold in one cooperative launch each "
+                        "(grid barriers between phases) instead of the CUDA-graph loop; results are identical")
     p.add_argument("--cluster-max-n", type=int, default=None,
                    help="largest level refined by the one-cluster loop (library default if omitted; 0 = never)")
     p.add_argument("--kernel-probe", action="store_true",
@@ -283,7 +286,8 @@ def run_ours(args):
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=device)
     copts = {} if args.cluster_max_n is None else {"cluster_max_n": args.cluster_max_n}
     pdl_off = jet.FLAG_NO_PDL if args.no_pdl else 0
-    ctx = jet.Context(local, flags=(jet.FLAG_HOSTLOOP if args.hostloop else 0) | pdl_off, **copts)
+    loop = (jet.FLAG_HOSTLOOP if args.hostloop else 0) | (jet.FLAG_GRID_LOOP if args.grid_loop else 0)
+    ctx = jet.Context(local, flags=loop | pdl_off, **copts)
     stream = torch.cuda.current_stream(device)
 
     def step():

@@ -79,6 +79,11 @@ extern "C" {
                                       refinement kernel only after the previous one has finished,
                                       instead of letting it start early and wait on the device
                                       (programmatic dependent launch) */
+#define JET_FLAG_GRID_LOOP 2048u   /* execution choice (results do not depend on it): levels above
+                                      cluster_max_n run their whole refinement loop in one
+                                      cooperative launch over the GPU (phases separated by grid
+                                      barriers, each wait bounded: JET_ETIMEOUT if one runs out)
+                                      instead of the CUDA-graph loop */
 
 /* Hyper-parameters the paper names (defaults from jet_options_default):
  *   c_fine = 0.25, c_coarse = 0.75  first-filter ratio c (Sec. 4.1.2, Eq. gainconn_filter);

@@ -22,6 +22,7 @@ FLAG_NO_LOCKS, FLAG_NO_AFTERBURN, FLAG_WEAK_AFTERBURN, FLAG_BASELINE_LP = 16, 32
 FLAG_TWO_HOP = 256
 FLAG_STRICT_GAIN = 512
 FLAG_NO_PDL = 1024
+FLAG_GRID_LOOP = 2048
 KIND_LP, KIND_RW, KIND_RS = 0, 1, 2
 NONE_GAIN = -(2 ** 31)
 

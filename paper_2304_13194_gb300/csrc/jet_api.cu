@@ -555,7 +555,9 @@ int jet_partition_batch(jet_ctx *ctx, int32_t count, jet_batch_item *items, int3
         }
         cudaStreamWaitEvent(s, start, 0);
         jet_ctx *wc = nullptr;
-        int r = jet_ctx_create(c.device, s, &c.opt, &wc);
+        jet_options wo = c.opt;
+        if (workers > 1) wo.flags &= ~JET_FLAG_GRID_LOOP;   // concurrent workers: no cooperative launches
+        int r = jet_ctx_create(c.device, s, &wo, &wc);
         if (r != JET_OK) {
             wstat[(size_t)w] = r;
             cudaStreamDestroy(s);

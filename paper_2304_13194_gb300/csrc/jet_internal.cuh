@@ -135,6 +135,10 @@ struct Ctl {
     int64_t maxw;        // max part weight of P_iter
     int64_t best_cut, best_maxw;
     int64_t L, opt, sigma;
+    // persistent level loop: grid barrier (arrivals, generation) and the
+    // flag a block sets when its bounded wait at a barrier ran out
+    uint32_t bar_count, bar_gen;
+    int32_t bar_err, pad2;
     // coarsening
     int32_t hem_stop;
     int32_t pad1;

@@ -1053,6 +1053,14 @@ int jet_partition_learned(jet_ctx *ctx, const jet_lip *h, int32_t n, const int64
     int64_t cut_learned = -1;
     cudaStream_t ws = nullptr;
     jet_ctx *wc = nullptr;
+    // Concurrent uncoarsenings never use the cooperative level loop (a
+    // cooperative launch wants the whole GPU to itself).
+    struct FlagGuard {
+        jet_options &o;
+        uint32_t saved;
+        ~FlagGuard() { o.flags = saved; }
+    } grid_flag_guard{c.opt, c.opt.flags};
+    if (learned) c.opt.flags &= ~JET_FLAG_GRID_LOOP;
     if (learned) {
         JET_CUDA_TRY(cudaStreamCreateWithFlags(&ws, cudaStreamNonBlocking));
         int rc = jet_ctx_create(c.device, ws, &c.opt, &wc);

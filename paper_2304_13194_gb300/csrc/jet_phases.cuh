@@ -42,20 +42,38 @@ struct Grid {
 
 __device__ __forceinline__ Grid launch_grid() { return Grid{(int)blockIdx.x, (int)gridDim.x}; }
 
-// The contiguous share [beg, end) of a list of `len` entries that block G.bid
-// takes (whole warps; every block gets one, so the warps of every block take
-// part in the long rows the list holds).
-struct Share {
-    int64_t beg, end;
+// The entries of a list of `len` that block G.bid takes.  On a level with
+// long rows (`spread`) the list is cut into chunks of kDealChunk entries (one
+// 32-byte sector of int32 ids) dealt round-robin over the blocks: a run of
+// long rows that one producer appended together is spread over many blocks
+// instead of landing in one block's share (contiguous shares made single
+// blocks take hundreds of long rows while the rest of the grid idled), and
+// every warp load of the list still reads whole sectors.  Otherwise each
+// block takes one contiguous share (whole warps), which keeps the neighbour
+// gathers of consecutive vertices in the block's L1.  A block walks its
+// entries blockDim at a time; all its threads make the same number of passes.
+constexpr int kDealChunk = 8;
+struct Deal {
+    int64_t len, seg;
+    int nb, bid;
+    bool spread;
+    __device__ __forceinline__ Deal(int64_t n, Grid G, bool spread_) : len(n), nb(G.nb), bid(G.bid), spread(spread_) {
+        int64_t s = (n + G.nb - 1) / G.nb;
+        seg = (s + 31) & ~int64_t(31);
+    }
+    // list index of block-local position q (increasing in q)
+    __device__ __forceinline__ int64_t at(int64_t q) const {
+        if (spread) {
+            const int64_t c = q / kDealChunk;
+            return (c * nb + bid) * kDealChunk + (q % kDealChunk);
+        }
+        return q < seg ? (int64_t)bid * seg + q : len;
+    }
+    // pass p has at least one entry for this block
+    __device__ __forceinline__ bool live(int64_t p) const { return at(p * (int64_t)blockDim.x) < len; }
+    // list index of this thread in pass p (>= len: none)
+    __device__ __forceinline__ int64_t entry(int64_t p) const { return at(p * (int64_t)blockDim.x + threadIdx.x); }
 };
-__device__ __forceinline__ Share list_share(int64_t len, Grid G) {
-    int64_t seg = (len + G.nb - 1) / G.nb;
-    seg = (seg + 31) & ~int64_t(31);
-    int64_t b = (int64_t)G.bid * seg;
-    b = b < len ? b : len;
-    int64_t e = b + seg < len ? b + seg : len;
-    return Share{b, e};
-}
 
 // A value other blocks of the same kernel changed (atomics, stores before
 // their completion ticket): a device-scope load served by L2, never by a
@@ -463,6 +481,7 @@ __device__ inline void ph_ctl_init(const Level &L, const int64_t *cut2) {
         ctl->best_bal = maxw <= ctl->L;
         ctl->it = 0; ctl->noimp = 0; ctl->weak = 0; ctl->lp_epoch = -1;
         ctl->copy_best = 0; ctl->hit_cap = 0; ctl->ticket = 0;
+        ctl->bar_count = 0; ctl->bar_gen = 0; ctl->bar_err = 0;
         ctl->kcount[0] = ctl->kcount[1] = ctl->kcount[2] = ctl->kcount[3] = 0;
         reset_counters(ctl);
         ctl->mode = choose_mode(L, maxw <= ctl->L);
@@ -665,8 +684,8 @@ template <bool EW>
 __device__ inline void ph_lp_select(const Level &L, LpExport ex, Grid G, char *arena) {
     __shared__ long long red[40];
     Ctl *ctl = L.ctl;
-    const Share sh = list_share(ctl->nW, G);
-    if (sh.beg >= sh.end) return;
+    const Deal dl(ctl->nW, G, L.nbig > 0);
+    if (!dl.live(0)) return;
     int32_t *a32 = reinterpret_cast<int32_t *>(arena);
     JET_APPENDER(xapp, a32, kListCap);
     JET_APPENDER(bigs, a32 + kListCap, kBigCap);
@@ -681,11 +700,11 @@ __device__ inline void ph_lp_select(const Level &L, LpExport ex, Grid G, char *a
     auto hub_row = [&](int32_t v) {
         lp_select_block_row<EW>(L, ex, v, a32 + kListCap + kBigCap, red, nexam, degexam, degx);
     };
-    for (int64_t i0 = sh.beg; i0 < sh.end; i0 += blockDim.x) {
-        int64_t i = i0 + threadIdx.x;
+    for (int64_t p = 0; dl.live(p); ++p) {
+        const int64_t i = dl.entry(p);
         bool inX = false, big = false;
         int32_t v = -1;
-        if (i < sh.end) {
+        if (i < dl.len) {
             v = L.listW[i];
             int64_t beg = ld_xadj(g.xadj, v), end = ld_xadj(g.xadj, (int64_t)v + 1);
             int d = (int)(end - beg);
@@ -795,8 +814,8 @@ __device__ inline void ph_afterburn(const Level &L, LpExport ex, Grid G, char *a
             L.listM[L.g.n - 1 - atomicAdd(&ctl->nMh, 1)] = v;
         }
     }
-    const Share sh = list_share(ctl->nX, G);
-    if (sh.beg >= sh.end) return;
+    const Deal dl(ctl->nX, G, L.nbig > 0);
+    if (!dl.live(0)) return;
     int32_t *a32 = reinterpret_cast<int32_t *>(arena);
     JET_APPENDER(mapp, a32, kListCap);
     JET_APPENDER(bigs, a32 + kListCap, kBigCap);
@@ -817,11 +836,11 @@ __device__ inline void ph_afterburn(const Level &L, LpExport ex, Grid G, char *a
         }
     };
     auto hub_row = [&](int32_t v) { afterburn_block_row<EW>(L, ex, v, it, red); };
-    for (int64_t i0 = sh.beg; i0 < sh.end; i0 += blockDim.x) {
-        int64_t i = i0 + threadIdx.x;
+    for (int64_t p = 0; dl.live(p); ++p) {
+        const int64_t i = dl.entry(p);
         bool inM = false, big = false;
         int32_t v = -1;
-        if (i < sh.end) {
+        if (i < dl.len) {
             v = L.listX[i];
             if (!full) {
                 inM = true;
@@ -963,12 +982,12 @@ __device__ inline void ph_apply(const Level &L, Grid G, char *arena) {
         }
     };
     auto hub_row = [&](int32_t v) { apply_block_row<EW>(L, v, it, lp, red, dc, dm); };
-    const Share sh = list_share(nM, G);
-    for (int64_t i0 = sh.beg; i0 < sh.end; i0 += blockDim.x) {
-        int64_t i = i0 + threadIdx.x;
+    const Deal dl(nM, G, L.nbig > 0);
+    for (int64_t p = 0; dl.live(p); ++p) {
+        const int64_t i = dl.entry(p);
         bool big = false;
         int32_t v = -1;
-        if (i < sh.end) {
+        if (i < dl.len) {
             v = L.listM[i];
             int32_t x = L.nxt[v];
             int32_t a = nxt_from(x), b = nxt_to(x);
@@ -1280,8 +1299,8 @@ __device__ inline void ph_rb_cand(const Level &L, Grid G, char *arena) {
     __shared__ long long red[40];
     Ctl *ctl = L.ctl;
     const int32_t nB = ctl->nB;
-    const Share sh = list_share(ctl->nW, G);
-    if (sh.beg >= sh.end) return;
+    const Deal dl(ctl->nW, G, L.nbig > 0);
+    if (!dl.live(0)) return;
     SmemBuckets sb;
     sb.init(L, reinterpret_cast<long long *>(arena));
     int32_t *a32 = reinterpret_cast<int32_t *>(arena + kSmemBuckets * 8);
@@ -1296,13 +1315,13 @@ __device__ inline void ph_rb_cand(const Level &L, Grid G, char *arena) {
     long long degrows = 0;
     auto big_row = [&](int32_t v) { rb_cand_row<EW, STRONG>(L, v, tab, it, nB, sb, degrows); };
     auto hub_row = [&](int32_t v) { rb_cand_block_row<EW, STRONG>(L, v, a32 + kBigCap, red, it, nB, sb, degrows); };
-    for (int64_t i0 = sh.beg; i0 < sh.end; i0 += blockDim.x) {
-        int64_t i = i0 + threadIdx.x;
+    for (int64_t p = 0; dl.live(p); ++p) {
+        const int64_t i = dl.entry(p);
         int32_t key = -1;
         long long wv = 0;
         bool big = false;
         int32_t v = -1;
-        if (i < sh.end) {
+        if (i < dl.len) {
             v = L.listW[i];
             int32_t ps = L.part[v];
             int32_t a = L.aidx[ps];

@@ -274,6 +274,120 @@ __global__ void __launch_bounds__(kClusterThreads, 1) k_refine_cluster(Level L) 
 }
 
 // ---------------------------------------------------------------------------
+// one cooperative launch per level: every iteration in a single grid
+// ---------------------------------------------------------------------------
+// Polls of a block waiting at a grid barrier before it gives up (with a
+// sleep of ~64 ns between polls after the first few: about a second or
+// more, orders of magnitude above the longest phase).
+constexpr long long kBarPollLimit = 1LL << 22;
+
+__device__ __forceinline__ uint32_t ld_volatile_u32(const uint32_t *p) { return *(const volatile uint32_t *)p; }
+
+// Grid barrier of the persistent loop (cooperative launch: every block is
+// resident).  A block reads the generation, fences its writes and arrives;
+// the last of the gridDim.x arrivals runs `tail` (every thread of that
+// block, with all the other blocks' writes visible), clears the count and
+// publishes the next generation; the others wait for it.  Each wait is
+// bounded: a block that runs out of polls sets ctl->bar_err and leaves, and
+// every block that passes a barrier after that sees the flag and leaves too,
+// so the launch always ends; the host then reports JET_ETIMEOUT.  Returns
+// false when the loop must stop (all threads of the block agree).
+template <class Tail>
+__device__ __forceinline__ bool grid_sync(const Level &L, Tail &&tail) {
+    __shared__ int s_last, s_ok;
+    __shared__ uint32_t s_gen;
+    Ctl *ctl = L.ctl;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const uint32_t gen = ld_volatile_u32(&ctl->bar_gen);
+        __threadfence();
+        const uint32_t a = atomicAdd(&ctl->bar_count, 1u);
+        const bool last = a == gridDim.x - 1;
+        if (last) __threadfence();
+        s_gen = gen;
+        s_last = last ? 1 : 0;
+    }
+    __syncthreads();
+    if (s_last) {
+        tail();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            atomicExch(&ctl->bar_count, 0u);
+            __threadfence();
+            atomicExch(&ctl->bar_gen, s_gen + 1u);
+        }
+    } else if (threadIdx.x == 0) {
+        long long polls = 0;
+        while (ld_volatile_u32(&ctl->bar_gen) == s_gen) {
+            if (++polls > kBarPollLimit) {
+                atomicExch(&ctl->bar_err, 1);
+                break;
+            }
+            if (polls > 16) __nanosleep(64);
+        }
+        __threadfence();
+    }
+    if (threadIdx.x == 0) s_ok = *(volatile int32_t *)&ctl->bar_err == 0;
+    __syncthreads();
+    return s_ok != 0;
+}
+
+struct NoTail {
+    __device__ __forceinline__ void operator()() const {}
+};
+
+template <bool EW, bool STRONG>
+__device__ __forceinline__ bool grid_rebalance(const Level &L, Grid G, char *arena) {
+    ph_rb_scan<STRONG>(L, G, arena);
+    if (!grid_sync(L, NoTail{})) return false;
+    ph_rb_cand<EW, STRONG>(L, G, arena);
+    if (!grid_sync(L, [&] { ph_rb_plan(L); })) return false;
+    ph_rb_tilehist(L, G, arena);
+    if (!grid_sync(L, NoTail{})) return false;
+    ph_rb_tilescan(L, G);
+    if (!grid_sync(L, NoTail{})) return false;
+    ph_rb_take<STRONG>(L, G, arena);
+    if constexpr (STRONG) {
+        if (!grid_sync(L, [&] { ph_rb_tiletaken_scan(L); })) return false;
+        ph_rb_cookie(L, G, arena);
+    }
+    return grid_sync(L, NoTail{});
+}
+
+// The whole loop of Alg. 3 on one level in one cooperative launch: the same
+// phases as the per-phase kernels, in the same order, separated by grid
+// barriers instead of kernel boundaries; the last block to reach a barrier
+// runs the serial tails (rebalancing plan, Jetrs eviction scan, controller).
+// Tiles of the rebalancing passes are one block of kRbTile threads, as in
+// the per-phase kernels.
+template <bool EW>
+__global__ void __launch_bounds__(kTB, JET_ROW_MINB) k_refine_grid(Level L) {
+    const Grid G = launch_grid();
+    char *arena = JET_ARENA;
+    const LpExport none{nullptr, nullptr, nullptr};
+    for (;;) {
+        const int32_t mode = ld_gpu(&L.ctl->mode);
+        if (mode == MODE_DONE) break;
+        ph_copy_best(L, G);   // P_best <- P_iter asked for by the previous controller
+        if (mode == MODE_LP) {
+            ph_lp_scan(L, G, arena);
+            if (!grid_sync(L, NoTail{})) return;
+            ph_lp_select<EW>(L, none, G, arena);
+            if (!grid_sync(L, NoTail{})) return;
+            ph_afterburn<EW>(L, none, G, arena);
+            if (!grid_sync(L, NoTail{})) return;
+        } else if (mode == MODE_RW) {
+            if (!grid_rebalance<EW, false>(L, G, arena)) return;
+        } else {
+            if (!grid_rebalance<EW, true>(L, G, arena)) return;
+        }
+        ph_apply<EW>(L, G, arena);
+        if (!grid_sync(L, [&] { ph_controller(L); })) return;
+    }
+    ph_copy_best(L, G);
+}
+
+// ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
 // Vertices with rows longer than kSmallDeg (only whether there are any matters).
@@ -388,8 +502,14 @@ int list_grid() { return num_sms() * 4; }
 #endif
 int scan_grid(int64_t n) { return std::min(num_sms() * JET_SCAN_BLOCKS_PER_SM, grid_for((n + 3) / 4, kTB)); }
 
-// grid of a kernel over a list of at most `items` entries (one per thread)
-int list_blocks(int64_t items) { return std::min(list_grid(), grid_for(items, kTB)); }
+// Grid of a kernel over a list of at most `items` entries: one block per
+// JET_LIST_ITEMS_PER_BLOCK entries, at most list_grid() blocks (a launch-shape
+// choice: fewer entries per block spread the long rows of small levels over
+// more warps).
+#ifndef JET_LIST_ITEMS_PER_BLOCK
+#define JET_LIST_ITEMS_PER_BLOCK 64
+#endif
+int list_blocks(int64_t items) { return std::min(list_grid(), grid_for(items, JET_LIST_ITEMS_PER_BLOCK)); }
 
 // Launch of a kernel that follows another one of the same pass: with
 // L.pdl it may be scheduled early and waits on the device (pdl_enter).
@@ -464,7 +584,7 @@ int enqueue_rb(const Level &L, cudaStream_t s, bool strong, int *nk) {
 
 // apply + commit + controller
 int enqueue_tail(const Level &L, cudaStream_t s, int *nk) {
-    int ga = std::min(list_grid(), grid_for(L.g.n, kTB));
+    int ga = list_blocks(L.g.n);
     if (L.g.ew) k_apply<true><<<ga, kTB, sm_apply(L.k), s>>>(L);
     else k_apply<false><<<ga, kTB, sm_apply(L.k), s>>>(L);
     *nk = 1;
@@ -735,6 +855,60 @@ int run_cluster_t(Ctx &c, Level L, int cs, size_t smem) {
     return JET_OK;
 }
 
+// Persistent loop: blocks of the cooperative launch (at most JET_ROW_MINB per
+// SM, as many as the device keeps resident with this arena, and no more than
+// the level's list kernels would use), cached per device and edge-weight
+// variant; 0 when the device cannot run it.
+template <bool EW>
+int grid_loop_blocks(int device, size_t smem, int64_t n, int *out) {
+    static std::mutex mu;
+    static int cache[2][256];
+    static size_t cache_smem[2][256];
+    const int e_idx = EW ? 1 : 0;
+    *out = 0;
+    if (device < 0 || device >= 256) return JET_OK;
+    int per_sm = 0;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (cache_smem[e_idx][device] < smem || cache[e_idx][device] == 0) {
+            JET_CUDA_TRY(cudaFuncSetAttribute(k_refine_grid<EW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            int nb = 0;
+            JET_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_refine_grid<EW>, kTB, smem));
+            cache[e_idx][device] = nb > 0 ? nb : -1;
+            cache_smem[e_idx][device] = smem;
+        }
+        per_sm = cache[e_idx][device];
+    }
+    if (per_sm <= 0) return JET_OK;
+    int cap = num_sms() * std::min(per_sm, JET_ROW_MINB);
+    *out = std::min(cap, list_blocks(n));
+    return JET_OK;
+}
+
+size_t grid_loop_smem(int32_t k) { return (arena_bytes(k, kTB) + 255) & ~size_t(255); }
+
+// Whole level loop in one cooperative launch; *ran = 0 when the device
+// cannot run it (the caller takes the CUDA-graph loop instead).
+template <bool EW>
+int run_grid_t(Ctx &c, Level L, int *ran) {
+    *ran = 0;
+    if (kRbTile != kTB) return JET_OK;        // tiles must be one block
+    const size_t smem = grid_loop_smem(L.k);
+    int nb = 0;
+    JET_TRY(grid_loop_blocks<EW>(c.device, smem, L.g.n, &nb));
+    if (nb <= 0) return JET_OK;
+    L.use_graph = 0;
+    void *args[] = {&L};
+    JET_CUDA_TRY(cudaLaunchCooperativeKernel((void *)k_refine_grid<EW>, dim3(nb), dim3(kTB), args, smem, c.stream));
+    *ran = 1;
+    return JET_OK;
+}
+
+int run_grid(Ctx &c, const Level &L, int *ran) {
+    if (L.g.ew) return run_grid_t<true>(c, L, ran);
+    return run_grid_t<false>(c, L, ran);
+}
+
 size_t cluster_smem(int32_t k) { return (arena_bytes(k, kClusterThreads) + 255) & ~size_t(255); }
 
 // Cluster size usable for this level (0: use the graph loop).
@@ -831,20 +1005,29 @@ int refine_level(Ctx &c, const DGraph &g, int32_t k, double eps, int32_t is_fine
     JET_TRY(enqueue_init(c, B, L_lim, opt, sigma));
     bool hostloop = (c.opt.flags & (JET_FLAG_HOSTLOOP | JET_FLAG_PROFILE)) != 0;
     int nk_branch[3] = {0, 0, 0}, nk_tail = 0;
-    int csize = 0;
+    int csize = 0, grid = 0;
     if (!hostloop) JET_TRY(pick_cluster(c, L, &csize));
     if (g.n > 0) {
-        if (hostloop) JET_TRY(run_hostloop(c, L, (c.opt.flags & JET_FLAG_PROFILE) != 0, &rep.sel_ms));
-        else if (csize > 0) JET_TRY(run_cluster(c, L, csize));
-        else JET_TRY(run_graph(c, L, nk_branch, &nk_tail));
+        if (hostloop) {
+            JET_TRY(run_hostloop(c, L, (c.opt.flags & JET_FLAG_PROFILE) != 0, &rep.sel_ms));
+        } else if (csize > 0) {
+            JET_TRY(run_cluster(c, L, csize));
+        } else {
+            if (c.opt.flags & JET_FLAG_GRID_LOOP) JET_TRY(run_grid(c, L, &grid));
+            if (!grid) JET_TRY(run_graph(c, L, nk_branch, &nk_tail));
+        }
         JET_CUDA_TRY(cudaMemcpyAsync(part_inout, L.best, (size_t)g.n * 4, cudaMemcpyDeviceToDevice, c.stream));
     }
     Ctl h;
     JET_TRY(read_ctl(c, L, h));
+    if (h.bar_err) {
+        record_error("refinement: a grid barrier wait of the persistent level loop ran out");
+        return JET_ETIMEOUT;
+    }
     int32_t iters = h.it;
     if (!hostloop && g.n > 0) {
-        if (csize > 0) {
-            c.launches += 1;  // the cluster kernel
+        if (csize > 0 || grid) {
+            c.launches += 1;  // the cluster or cooperative kernel
         } else {
             c.launches += 2;  // start kernel, final copy
             for (int kd = 0; kd < 3; ++kd) c.launches += (int64_t)h.kcount[kd] * (nk_branch[kd] + nk_tail);

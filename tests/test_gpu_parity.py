@@ -51,6 +51,14 @@ def ctx_graph():
     c.close()
 
 
+@pytest.fixture(scope="module")
+def ctx_grid():
+    """Every level on the persistent loop (one cooperative launch per level)."""
+    c = jet.Context(0, flags=jet.FLAG_GRID_LOOP, cluster_max_n=0)
+    yield c
+    c.close()
+
+
 def _np(t):
     return t.cpu().numpy()
 
@@ -364,6 +372,36 @@ def test_refine_cluster_loop_equals_graph_loop(ctx_cluster, ctx_graph, name, g, 
         assert all((ta[key] == tb[key]).all() for key in ("kind", "nx", "nm", "cut", "maxw"))
 
 
+@pytest.mark.parametrize("name,g,unit,k", [
+    ("grid3d_20_w", graphgen.grid3d(20, 20, 20, vw=(1, 4), ew=(1, 10), seed=9), False, 16),
+    ("rmat_s12", graphgen.rmat(12, seed=5), True, 64),                  # long rows: warp paths
+    ("gnp_700_dense", graphgen.gnp(700, 0.06, seed=4, ew=(1, 9)), False, 8),
+    ("rgg_30000", graphgen.rgg(30000, seed=3), True, 128),              # many tiles per block
+    ("rmat_s12_k256", graphgen.rmat(12, seed=5), True, 256),
+    ("rmat_s14_hubs", graphgen.rmat(14, seed=2), True, 32),             # rows past 1024 entries: block rows
+])
+def test_refine_grid_loop_matches_oracle(ctx_grid, name, g, unit, k):
+    """The persistent loop (grid barriers instead of kernel boundaries, the
+    serial tails in the last block to arrive) follows the oracle's whole
+    trajectory on finest and coarse settings."""
+    og = graphgen.Graph(g.n, g.xadj, g.adjncy, _vw(g, unit), None)
+    part0 = oracle.initial_partition(og, k)
+    _check_refine(ctx_grid, g, unit, k, part0, True, seed=5)
+    _check_refine(ctx_grid, g, unit, k, part0, False, seed=6)
+
+
+@pytest.mark.parametrize("name,g,unit", graphs_small()[1:4], ids=[x[0] for x in graphs_small()[1:4]])
+def test_partition_grid_loop_matches_oracle(ctx_grid, name, g, unit):
+    _check_partition(ctx_grid, g, unit, 64, seed=3)
+
+
+def test_partition_grid_loop_mesh_k64(ctx_grid):
+    """A 48^3 mesh at k = 64 on the persistent loop: Jetlp, Jetrw and Jetrs
+    iterations on every level, bit-exact with the oracle."""
+    g = graphgen.grid3d(48, 48, 48, vw=(1, 4), ew=(1, 10), seed=4)
+    _check_partition(ctx_grid, g, False, 64, seed=2)
+
+
 @pytest.mark.parametrize("blocks", [2, 4])
 def test_small_clusters_equal_graph_loop(ctx_graph, blocks):
     """cluster_blocks caps the cluster (execution choice): fewer blocks take
@@ -493,7 +531,7 @@ def test_partition_without_pdl_is_identical(ctx):
     partition with JET_FLAG_NO_PDL, on the CUDA-graph and the host loop."""
     g = graphgen.grid3d(40, 40, 40, vw=(1, 4), ew=(1, 10), seed=6)
     ref = ctx.partition(g.xadj, g.adjncy, g.vwgt, g.adjwgt, k=32, seed=2)
-    for flags in (jet.FLAG_NO_PDL, jet.FLAG_NO_PDL | jet.FLAG_HOSTLOOP, jet.FLAG_HOSTLOOP):
+    for flags in (jet.FLAG_NO_PDL, jet.FLAG_NO_PDL | jet.FLAG_HOSTLOOP, jet.FLAG_HOSTLOOP, jet.FLAG_GRID_LOOP):
         with jet.Context(0, flags=flags, cluster_max_n=0) as c:
             part, cut = c.partition(g.xadj, g.adjncy, g.vwgt, g.adjwgt, k=32, seed=2)
         assert cut == ref[1] and torch.equal(part, ref[0])
