@@ -7,8 +7,9 @@
 // neighbour, then smaller id) and mutual proposals match, round after round.
 // Contraction merges each coarse vertex's (at most two) fine rows, sorts the
 // mapped neighbour ids and sums duplicate entries: rows of <= 32 entries in
-// one warp (register bitonic network), longer rows in one block (bitonic sort
-// in shared memory, or in a global scratch segment for very long rows).
+// one thread (register bitonic network), up to 256 in one warp and longer
+// rows in one block (bitonic sorts in shared memory, or in a global scratch
+// segment for very long rows).
 #include "jet_internal.cuh"
 
 #include <algorithm>
@@ -303,24 +304,34 @@ struct HugeScratch {
     }
 };
 
+// Coarse vertex weights, and the coarse rows sorted into classes by their
+// bound (entries of the merged fine rows): <= 16 and <= 32 (one thread),
+// <= kWarpSort (one warp), longer (one block).  counts = {warp rows, block
+// rows, 16-entry thread rows, 32-entry thread rows}.
+constexpr int kWarpSort = 256;
 __global__ void k_coarse_vw(int32_t nc, const int32_t *crep, const int32_t *mate, const int32_t *vw, int32_t *vwc,
-                            int32_t *small_list, int32_t *large_list, int32_t *counts, const int64_t *boff,
-                            const int64_t *btot) {
+                            int32_t *warp_list, int32_t *large_list, int32_t *t16_list, int32_t *t32_list,
+                            int32_t *counts, const int64_t *boff, const int64_t *btot) {
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ((int64_t)nc + 31) / 32 * 32;
          c += (int64_t)gridDim.x * blockDim.x) {
         bool valid = c < nc;
-        bool small = false;
+        int64_t b = 0;
         if (valid) {
             int32_t r = crep[c];
             int32_t m = mate[r];
             vwc[c] = vw[r] + (m >= 0 ? vw[m] : 0);
-            int64_t b = (c + 1 < nc ? boff[c + 1] : *btot) - boff[c];
-            small = b <= 32;
+            b = (c + 1 < nc ? boff[c + 1] : *btot) - boff[c];
         }
-        int s1 = warp_append(&counts[0], valid && small);
-        if (valid && small) small_list[s1] = (int32_t)c;
-        int s2 = warp_append(&counts[1], valid && !small);
-        if (valid && !small) large_list[s2] = (int32_t)c;
+        const bool t16 = valid && b <= 16, t32 = valid && b > 16 && b <= 32;
+        const bool wr = valid && b > 32 && b <= kWarpSort, large = valid && b > kWarpSort;
+        int s0 = warp_append(&counts[2], t16);
+        if (t16) t16_list[s0] = (int32_t)c;
+        int s1 = warp_append(&counts[3], t32);
+        if (t32) t32_list[s1] = (int32_t)c;
+        int s2 = warp_append(&counts[0], wr);
+        if (wr) warp_list[s2] = (int32_t)c;
+        int s3 = warp_append(&counts[1], large);
+        if (large) large_list[s3] = (int32_t)c;
     }
 }
 
@@ -333,46 +344,138 @@ __device__ __forceinline__ unsigned long long row_entry(const DGraph &g, const i
     return ((unsigned long long)(uint32_t)cu << 32) | (uint32_t)cw<EW>(g, j);
 }
 
-// Rows of <= 32 entries: one warp, register bitonic sort, segmented sums.
-template <bool EW>
-__global__ void __launch_bounds__(kTB) k_contract_small(DGraph g, const int32_t *cmap, const int32_t *mate,
-                                                        const int32_t *crep, const int32_t *list, const int32_t *counts,
-                                                        const int64_t *boff, int32_t *tadj, int32_t *tw, int32_t *rowcnt) {
-    const int warps = blockDim.x >> 5;
-    const unsigned lane = lane_id();
-    const int32_t nrows = counts[0];
-    for (int64_t w = (int64_t)blockIdx.x * warps + (threadIdx.x >> 5); w < nrows; w += (int64_t)gridDim.x * warps) {
-        int32_t c = list[w];
-        int32_t r = crep[c], m = mate[r];
-        int64_t degr = ld_xadj(g.xadj, (int64_t)r + 1) - ld_xadj(g.xadj, r);
-        int64_t bound = degr + (m >= 0 ? ld_xadj(g.xadj, (int64_t)m + 1) - ld_xadj(g.xadj, m) : 0);
-        unsigned long long key = ~0ull;
-        if ((int64_t)lane < bound) key = row_entry<EW>(g, cmap, r, m, degr, lane);
+// Rows of <= N entries (N = 16 or 32): one thread each (32 rows of a warp in
+// flight together), the keys (C[u] << 32 | w) sorted by a bitonic network
+// over registers, then one pass that adds up equal coarse neighbours and
+// drops the row's own vertex.  Same output as the warp and block forms.
+// counts[slot] rows in list.
+template <bool EW, int N>
+__global__ void __launch_bounds__(kTB) k_contract_thread(DGraph g, const int32_t *cmap, const int32_t *mate,
+                                                       const int32_t *crep, const int32_t *list, const int32_t *counts,
+                                                       const int64_t *boff, int32_t *tadj, int32_t *tw, int32_t *rowcnt) {
+    const int32_t nrows = counts[N == 16 ? 2 : 3];
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nrows; w += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t c = list[w];
+        const int32_t r = crep[c], m = mate[r];
+        const int64_t r0 = ld_xadj(g.xadj, r), degr = ld_xadj(g.xadj, (int64_t)r + 1) - r0;
+        int64_t m0 = 0, degm = 0;
+        if (m >= 0) {
+            m0 = ld_xadj(g.xadj, m);
+            degm = ld_xadj(g.xadj, (int64_t)m + 1) - m0;
+        }
+        const int64_t bound = degr + degm;
+        unsigned long long key[N];
 #pragma unroll
-        for (int kk = 2; kk <= 32; kk <<= 1) {
-#pragma unroll
-            for (int j = kk >> 1; j > 0; j >>= 1) {
-                unsigned long long o = __shfl_xor_sync(0xffffffffu, key, j);
-                bool up = (lane & kk) == 0;
-                bool lower = (lane & j) == 0;
-                key = (lower == up) ? (key < o ? key : o) : (key > o ? key : o);
+        for (int t = 0; t < N; ++t) {
+            key[t] = ~0ull;
+            if (t < bound) {
+                const int64_t j = t < degr ? r0 + t : m0 + (t - degr);
+                key[t] = ((unsigned long long)(uint32_t)cmap[__ldg(g.adj + j)] << 32) | (uint32_t)cw<EW>(g, j);
             }
         }
-        uint32_t ck = (uint32_t)(key >> 32);
-        uint32_t prev = __shfl_up_sync(0xffffffffu, ck, 1);
-        bool head = key != ~0ull && (lane == 0 || prev != ck) && ck != (uint32_t)c;
+#pragma unroll
+        for (int kk = 2; kk <= N; kk <<= 1) {
+#pragma unroll
+            for (int j = kk >> 1; j > 0; j >>= 1) {
+#pragma unroll
+                for (int i = 0; i < N; ++i) {
+                    const int l = i ^ j;
+                    if (l > i) {
+                        const unsigned long long a = key[i], b = key[l];
+                        const bool swap = ((i & kk) == 0) ? (a > b) : (a < b);
+                        key[i] = swap ? b : a;
+                        key[l] = swap ? a : b;
+                    }
+                }
+            }
+        }
+        const int64_t base = boff[c];
+        int32_t cnt = 0;
+        uint32_t cur = 0xFFFFFFFFu;
         long long sum = 0;
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-            uint32_t cj = __shfl_sync(0xffffffffu, ck, j);
-            unsigned long long kj = __shfl_sync(0xffffffffu, key, j);
-            if (j >= (int)lane && cj == ck && kj != ~0ull) sum += (long long)(uint32_t)(kj & 0xFFFFFFFFull);
+        for (int t = 0; t < N; ++t) {
+            const unsigned long long kt = key[t];
+            const uint32_t ck = (uint32_t)(kt >> 32);
+            if (kt != ~0ull && ck != (uint32_t)c) {
+                if (ck != cur) {
+                    if (cur != 0xFFFFFFFFu) {
+                        tadj[base + cnt] = (int32_t)cur;
+                        tw[base + cnt] = (int32_t)sum;
+                        ++cnt;
+                    }
+                    cur = ck;
+                    sum = 0;
+                }
+                sum += (long long)(uint32_t)(kt & 0xFFFFFFFFull);
+            }
         }
-        unsigned hm = __ballot_sync(0xffffffffu, head);
-        int pos = __popc(hm & ((1u << lane) - 1u));
-        int64_t base = boff[c];
-        if (head) { tadj[base + pos] = (int32_t)ck; tw[base + pos] = (int32_t)sum; }
-        if (lane == 0) rowcnt[c] = __popc(hm);
+        if (cur != 0xFFFFFFFFu) {
+            tadj[base + cnt] = (int32_t)cur;
+            tw[base + cnt] = (int32_t)sum;
+            ++cnt;
+        }
+        rowcnt[c] = cnt;
+    }
+}
+
+// Rows of 33..kWarpSort entries: one warp each, bitonic sort over the warp's
+// shared-memory segment (pairs of a stage split over the lanes, __syncwarp
+// between stages), then heads of equal-id runs summed and written in order.
+template <bool EW>
+__global__ void __launch_bounds__(kTB) k_contract_warp(DGraph g, const int32_t *cmap, const int32_t *mate,
+                                                       const int32_t *crep, const int32_t *list, const int32_t *counts,
+                                                       const int64_t *boff, int32_t *tadj, int32_t *tw, int32_t *rowcnt) {
+    __shared__ unsigned long long sk[kTB / 32][kWarpSort];
+    const int warps = blockDim.x >> 5;
+    const unsigned lane = lane_id();
+    unsigned long long *keys = sk[threadIdx.x >> 5];
+    const int32_t nrows = counts[0];
+    for (int64_t w = (int64_t)blockIdx.x * warps + (threadIdx.x >> 5); w < nrows; w += (int64_t)gridDim.x * warps) {
+        const int32_t c = list[w];
+        const int32_t r = crep[c], m = mate[r];
+        const int64_t degr = ld_xadj(g.xadj, (int64_t)r + 1) - ld_xadj(g.xadj, r);
+        const int64_t bound = degr + (m >= 0 ? ld_xadj(g.xadj, (int64_t)m + 1) - ld_xadj(g.xadj, m) : 0);
+        const int P = (int)pow2ceil(bound);   // <= kWarpSort by the class
+        for (int i = lane; i < P; i += 32) keys[i] = i < bound ? row_entry<EW>(g, cmap, r, m, degr, i) : ~0ull;
+        __syncwarp();
+        for (int kk = 2; kk <= P; kk <<= 1) {
+            for (int j = kk >> 1; j > 0; j >>= 1) {
+                for (int i = lane; i < P; i += 32) {
+                    const int l = i ^ j;
+                    if (l > i) {
+                        const unsigned long long a = keys[i], b = keys[l];
+                        const bool up = (i & kk) == 0;
+                        if ((a > b) == up) { keys[i] = b; keys[l] = a; }
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        const int64_t base = boff[c];
+        int32_t written = 0;
+        for (int i0 = 0; i0 < bound; i0 += 32) {
+            const int i = i0 + (int)lane;
+            bool head = false;
+            uint32_t ck = 0;
+            long long sum = 0;
+            if (i < bound) {
+                ck = (uint32_t)(keys[i] >> 32);
+                head = (i == 0 || (uint32_t)(keys[i - 1] >> 32) != ck) && ck != (uint32_t)c;
+                if (head)
+                    for (int t = i; t < bound && (uint32_t)(keys[t] >> 32) == ck; ++t)
+                        sum += (long long)(uint32_t)(keys[t] & 0xFFFFFFFFull);
+            }
+            const unsigned hm = __ballot_sync(0xffffffffu, head);
+            const int pos = __popc(hm & ((1u << lane) - 1u));
+            if (head) {
+                tadj[base + written + pos] = (int32_t)ck;
+                tw[base + written + pos] = (int32_t)sum;
+            }
+            written += __popc(hm);
+        }
+        if (lane == 0) rowcnt[c] = written;
+        __syncwarp();
     }
 }
 
@@ -447,13 +550,17 @@ __global__ void k_finish_xadj(int32_t nc, const int64_t *ex, const int64_t *tot,
         xadj_c[c] = c < nc ? ex[c] : *tot;
 }
 
+// Compaction of the coarse rows: kCopyLanes lanes per row (the rows are
+// short; a warp per row left most lanes idle and serialised the rows'
+// round trips).
+constexpr int kCopyLanes = 8;
 __global__ void k_copy_rows(int32_t nc, const int64_t *boff, const int64_t *xadj_c, const int32_t *tadj, const int32_t *tw,
                             int32_t *adj_c, int32_t *ew_c) {
-    const int warps = blockDim.x >> 5;
-    const unsigned lane = lane_id();
-    for (int64_t c = (int64_t)blockIdx.x * warps + (threadIdx.x >> 5); c < nc; c += (int64_t)gridDim.x * warps) {
-        int64_t src = boff[c], dst = xadj_c[c], len = xadj_c[c + 1] - dst;
-        for (int64_t i = lane; i < len; i += 32) {
+    const int64_t groups = (int64_t)gridDim.x * blockDim.x / kCopyLanes;
+    const int gl = (int)(threadIdx.x % kCopyLanes);
+    for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kCopyLanes; c < nc; c += groups) {
+        const int64_t src = boff[c], dst = xadj_c[c], len = xadj_c[c + 1] - dst;
+        for (int64_t i = gl; i < len; i += kCopyLanes) {
             adj_c[dst + i] = tadj[src + i];
             ew_c[dst + i] = tw[src + i];
         }
@@ -506,30 +613,36 @@ static int coarsen_level(Ctx &c, const DGraph &g, uint64_t seed, int32_t level, 
     // coarse vertex weights and row classes
     DevBuf vwcb, lists, tadjb, twb, cntb, hscrb;
     JET_TRY(dev_alloc(vwcb, (size_t)std::max<int64_t>(nc, 1) * 4, s));
-    JET_TRY(dev_alloc(lists, (size_t)std::max<int64_t>(nc, 1) * 8 + 64, s));
-    int32_t *small_list = lists.as<int32_t>(), *large_list = small_list + std::max<int64_t>(nc, 1);
-    int32_t *counts = reinterpret_cast<int32_t *>(large_list + std::max<int64_t>(nc, 1));
-    JET_CUDA_TRY(cudaMemsetAsync(counts, 0, 8, s));
-    k_coarse_vw<<<grid_for(nc, kTB, 8192), kTB, 0, s>>>((int32_t)nc, crep, mate, g.vw, vwcb.as<int32_t>(), small_list,
-                                                         large_list, counts, boff, totp);
+    const int64_t ncl = std::max<int64_t>(nc, 1);
+    JET_TRY(dev_alloc(lists, (size_t)ncl * 16 + 64, s));
+    int32_t *warp_list = lists.as<int32_t>(), *large_list = warp_list + ncl;
+    int32_t *t16_list = large_list + ncl, *t32_list = t16_list + ncl;
+    int32_t *counts = t32_list + ncl;
+    JET_CUDA_TRY(cudaMemsetAsync(counts, 0, 16, s));
+    k_coarse_vw<<<grid_for(nc, kTB, 8192), kTB, 0, s>>>((int32_t)nc, crep, mate, g.vw, vwcb.as<int32_t>(), warp_list,
+                                                         large_list, t16_list, t32_list, counts, boff, totp);
     JET_TRY(dev_alloc(tadjb, (size_t)std::max<int64_t>(btotal, 1) * 4, s));
     JET_TRY(dev_alloc(twb, (size_t)std::max<int64_t>(btotal, 1) * 4, s));
     JET_TRY(dev_alloc(cntb, (size_t)std::max<int64_t>(nc, 1) * 4, s));
     JET_TRY(dev_alloc(hscrb, (size_t)std::max<int64_t>(htotal, 1) * 8, s));
     int gl = num_sms() * 8;
-    int gsmall = std::min(gl, grid_for(nc, kTB / 32));
-    int glarge = std::min(num_sms() * 4, (int)std::max<int64_t>(1, nc));
+    const int gwarp = std::min(gl, grid_for(nc, kTB / 32));
+    const int glarge = std::min(num_sms() * 4, (int)std::max<int64_t>(1, nc));
+    const int gthread = std::min(gl, grid_for(nc, kTB));
+    int32_t *tadj = tadjb.as<int32_t>(), *tw = twb.as<int32_t>(), *cnt = cntb.as<int32_t>();
+    unsigned long long *hscr = hscrb.as<unsigned long long>();
     if (g.ew) {
-        k_contract_small<true><<<gsmall, kTB, 0, s>>>(g, cmap, mate, crep, small_list, counts, boff, tadjb.as<int32_t>(), twb.as<int32_t>(), cntb.as<int32_t>());
-        c.launches += 1;
-        k_contract_large<true><<<glarge, kTB, 0, s>>>(g, cmap, mate, crep, large_list, counts, boff, hoff, hscrb.as<unsigned long long>(), tadjb.as<int32_t>(), twb.as<int32_t>(), cntb.as<int32_t>());
-        c.launches += 1;
+        k_contract_thread<true, 16><<<gthread, kTB, 0, s>>>(g, cmap, mate, crep, t16_list, counts, boff, tadj, tw, cnt);
+        k_contract_thread<true, 32><<<gthread, kTB, 0, s>>>(g, cmap, mate, crep, t32_list, counts, boff, tadj, tw, cnt);
+        k_contract_warp<true><<<gwarp, kTB, 0, s>>>(g, cmap, mate, crep, warp_list, counts, boff, tadj, tw, cnt);
+        k_contract_large<true><<<glarge, kTB, 0, s>>>(g, cmap, mate, crep, large_list, counts, boff, hoff, hscr, tadj, tw, cnt);
     } else {
-        k_contract_small<false><<<gsmall, kTB, 0, s>>>(g, cmap, mate, crep, small_list, counts, boff, tadjb.as<int32_t>(), twb.as<int32_t>(), cntb.as<int32_t>());
-        c.launches += 1;
-        k_contract_large<false><<<glarge, kTB, 0, s>>>(g, cmap, mate, crep, large_list, counts, boff, hoff, hscrb.as<unsigned long long>(), tadjb.as<int32_t>(), twb.as<int32_t>(), cntb.as<int32_t>());
-        c.launches += 1;
+        k_contract_thread<false, 16><<<gthread, kTB, 0, s>>>(g, cmap, mate, crep, t16_list, counts, boff, tadj, tw, cnt);
+        k_contract_thread<false, 32><<<gthread, kTB, 0, s>>>(g, cmap, mate, crep, t32_list, counts, boff, tadj, tw, cnt);
+        k_contract_warp<false><<<gwarp, kTB, 0, s>>>(g, cmap, mate, crep, warp_list, counts, boff, tadj, tw, cnt);
+        k_contract_large<false><<<glarge, kTB, 0, s>>>(g, cmap, mate, crep, large_list, counts, boff, hoff, hscr, tadj, tw, cnt);
     }
+    c.launches += 4;
     JET_CUDA_TRY(cudaGetLastError());
     // coarse xadj
     DevBuf xcb, exb;
@@ -545,7 +658,7 @@ static int coarsen_level(Ctx &c, const DGraph &g, uint64_t seed, int32_t level, 
     DevBuf adjcb, ewcb;
     JET_TRY(dev_alloc(adjcb, (size_t)std::max<int64_t>(nnzc, 1) * 4, s));
     JET_TRY(dev_alloc(ewcb, (size_t)std::max<int64_t>(nnzc, 1) * 4, s));
-    k_copy_rows<<<std::min(gl, grid_for(nc, kTB / 32)), kTB, 0, s>>>((int32_t)nc, boff, xcb.as<int64_t>(), tadjb.as<int32_t>(),
+    k_copy_rows<<<std::min(gl, grid_for(nc, kTB / kCopyLanes)), kTB, 0, s>>>((int32_t)nc, boff, xcb.as<int64_t>(), tadjb.as<int32_t>(),
                                                                     twb.as<int32_t>(), adjcb.as<int32_t>(), ewcb.as<int32_t>());
     JET_CUDA_TRY(cudaGetLastError());
     int32_t i = h->levels;

@@ -42,16 +42,18 @@ struct Grid {
 
 __device__ __forceinline__ Grid launch_grid() { return Grid{(int)blockIdx.x, (int)gridDim.x}; }
 
-// The entries of a list of `len` that block G.bid takes.  On a level with
-// long rows (`spread`) the list is cut into chunks of kDealChunk entries (one
-// 32-byte sector of int32 ids) dealt round-robin over the blocks: a run of
-// long rows that one producer appended together is spread over many blocks
-// instead of landing in one block's share (contiguous shares made single
-// blocks take hundreds of long rows while the rest of the grid idled), and
-// every warp load of the list still reads whole sectors.  Otherwise each
-// block takes one contiguous share (whole warps), which keeps the neighbour
-// gathers of consecutive vertices in the block's L1.  A block walks its
-// entries blockDim at a time; all its threads make the same number of passes.
+// The entries of a list of `len` that block G.bid takes.  Dealt (`spread`):
+// the list is cut into chunks of kDealChunk entries (one 32-byte sector of
+// int32 ids) dealt round-robin over the blocks, so a run of long rows that
+// one producer appended together is spread over many blocks instead of
+// landing in one block's share (contiguous shares made single blocks take
+// hundreds of long rows while the rest of the grid idled), and every warp
+// load of the list still reads whole sectors.  Otherwise each block takes
+// one contiguous share (whole warps), which keeps the neighbour gathers of
+// consecutive vertices in the block's L1: the work lists of the scans are in
+// vertex order and are dealt only on levels with long rows; X and M are in
+// append order and are always dealt.  A block walks its entries blockDim at
+// a time; all its threads make the same number of passes.
 constexpr int kDealChunk = 8;
 struct Deal {
     int64_t len, seg;
@@ -814,7 +816,7 @@ __device__ inline void ph_afterburn(const Level &L, LpExport ex, Grid G, char *a
             L.listM[L.g.n - 1 - atomicAdd(&ctl->nMh, 1)] = v;
         }
     }
-    const Deal dl(ctl->nX, G, L.nbig > 0);
+    const Deal dl(ctl->nX, G, true);
     if (!dl.live(0)) return;
     int32_t *a32 = reinterpret_cast<int32_t *>(arena);
     JET_APPENDER(mapp, a32, kListCap);
@@ -982,7 +984,7 @@ __device__ inline void ph_apply(const Level &L, Grid G, char *arena) {
         }
     };
     auto hub_row = [&](int32_t v) { apply_block_row<EW>(L, v, it, lp, red, dc, dm); };
-    const Deal dl(nM, G, L.nbig > 0);
+    const Deal dl(nM, G, true);
     for (int64_t p = 0; dl.live(p); ++p) {
         const int64_t i = dl.entry(p);
         bool big = false;
