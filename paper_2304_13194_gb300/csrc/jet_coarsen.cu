@@ -290,9 +290,10 @@ __host__ __device__ inline int64_t pow2ceil(int64_t x) {
     return p;
 }
 
-struct HugeScratch {
-    const int64_t *boff;
-    const int64_t *btot;   // unused by the functor
+// Hub rows (bound > kSortSmem) are contracted through one device-wide radix
+// sort of all their entries: HubBound gives each hub row's segment length
+// (0 for the others), HubFlag its rank among the hub rows.
+struct HubBound {
     const int32_t *crep, *mate;
     const int64_t *xadj;
     __device__ int64_t operator()(int64_t c) const {
@@ -300,8 +301,12 @@ struct HugeScratch {
         int32_t m = mate[r];
         int64_t b = xadj[r + 1] - xadj[r];
         if (m >= 0) b += xadj[(int64_t)m + 1] - xadj[m];
-        return b > kSortSmem ? pow2ceil(b) : 0;
+        return b > kSortSmem ? b : 0;
     }
+};
+struct HubFlag {
+    HubBound hb;
+    __device__ int64_t operator()(int64_t c) const { return hb(c) > 0 ? 1 : 0; }
 };
 
 // Coarse vertex weights, and the coarse rows sorted into classes by their
@@ -479,13 +484,12 @@ __global__ void __launch_bounds__(kTB) k_contract_warp(DGraph g, const int32_t *
     }
 }
 
-// Longer rows: one block per row; bitonic sort in shared memory (or in the
-// row's global scratch segment when longer than kSortSmem).
+// Rows of kWarpSort..kSortSmem entries: one block per row, bitonic sort in
+// shared memory.
 template <bool EW>
 __global__ void __launch_bounds__(kTB) k_contract_large(DGraph g, const int32_t *cmap, const int32_t *mate,
                                                         const int32_t *crep, const int32_t *list, const int32_t *counts,
-                                                        const int64_t *boff, const int64_t *hoff,
-                                                        unsigned long long *hscr, int32_t *tadj, int32_t *tw,
+                                                        const int64_t *boff, int32_t *tadj, int32_t *tw,
                                                         int32_t *rowcnt) {
     __shared__ unsigned long long sk[kSortSmem];
     __shared__ long long sh[40];
@@ -495,8 +499,9 @@ __global__ void __launch_bounds__(kTB) k_contract_large(DGraph g, const int32_t 
         int32_t r = crep[c], m = mate[r];
         int64_t degr = ld_xadj(g.xadj, (int64_t)r + 1) - ld_xadj(g.xadj, r);
         int64_t bound = degr + (m >= 0 ? ld_xadj(g.xadj, (int64_t)m + 1) - ld_xadj(g.xadj, m) : 0);
+        if (bound > kSortSmem) continue;   // hub row: the radix-sort path (uniform over the block)
         int64_t P = pow2ceil(bound);
-        unsigned long long *keys = P <= kSortSmem ? sk : hscr + hoff[c];
+        unsigned long long *keys = sk;
         for (int64_t i = threadIdx.x; i < P; i += blockDim.x)
             keys[i] = i < bound ? row_entry<EW>(g, cmap, r, m, degr, i) : ~0ull;
         __syncthreads();
@@ -550,6 +555,72 @@ __global__ void k_finish_xadj(int32_t nc, const int64_t *ex, const int64_t *tot,
         xadj_c[c] = c < nc ? ex[c] : *tot;
 }
 
+// Hub rows, step 1: every entry of hub row c becomes (rank(c) << 32 | C[u],
+// w) at its segment hoff[c] + i (one block per row).
+template <bool EW>
+__global__ void __launch_bounds__(kTB) k_hub_fill(DGraph g, const int32_t *cmap, const int32_t *mate, const int32_t *crep,
+                                                  const int32_t *list, const int32_t *counts, const int64_t *hoff,
+                                                  const int64_t *hrank, uint64_t *key, int32_t *val) {
+    const int32_t nrows = counts[1];
+    for (int64_t w = blockIdx.x; w < nrows; w += gridDim.x) {
+        const int32_t c = list[w];
+        const int32_t r = crep[c], m = mate[r];
+        const int64_t degr = ld_xadj(g.xadj, (int64_t)r + 1) - ld_xadj(g.xadj, r);
+        const int64_t bound = degr + (m >= 0 ? ld_xadj(g.xadj, (int64_t)m + 1) - ld_xadj(g.xadj, m) : 0);
+        if (bound <= kSortSmem) continue;
+        const int64_t off = hoff[c];
+        const uint64_t hi = (uint64_t)hrank[c] << 32;
+        for (int64_t i = threadIdx.x; i < bound; i += blockDim.x) {
+            const unsigned long long e = row_entry<EW>(g, cmap, r, m, degr, i);
+            key[off + i] = hi | (e >> 32);
+            val[off + i] = (int32_t)(uint32_t)(e & 0xFFFFFFFFull);
+        }
+    }
+}
+
+// Hub rows, step 2 (after the stable sort by rank, then coarse id): hub row c
+// is again the segment hoff[c] + [0, bound), now in coarse-id order; heads of
+// equal-id runs summed, own id dropped, written in order (one block per row).
+__global__ void __launch_bounds__(kTB) k_hub_reduce(DGraph g, const int32_t *mate, const int32_t *crep,
+                                                    const int32_t *list, const int32_t *counts, const int64_t *hoff,
+                                                    const uint64_t *key, const int32_t *val, const int64_t *boff,
+                                                    int32_t *tadj, int32_t *tw, int32_t *rowcnt) {
+    __shared__ long long sh[40];
+    const int32_t nrows = counts[1];
+    for (int64_t w = blockIdx.x; w < nrows; w += gridDim.x) {
+        const int32_t c = list[w];
+        const int32_t r = crep[c], m = mate[r];
+        const int64_t bound = ld_xadj(g.xadj, (int64_t)r + 1) - ld_xadj(g.xadj, r) +
+                              (m >= 0 ? ld_xadj(g.xadj, (int64_t)m + 1) - ld_xadj(g.xadj, m) : 0);
+        if (bound <= kSortSmem) continue;
+        const uint64_t *k = key + hoff[c];
+        const int32_t *v = val + hoff[c];
+        const int64_t base = boff[c];
+        long long written = 0;
+        for (int64_t i0 = 0; i0 < bound; i0 += blockDim.x) {
+            const int64_t i = i0 + threadIdx.x;
+            bool head = false;
+            uint32_t ck = 0;
+            long long sum = 0;
+            if (i < bound) {
+                ck = (uint32_t)k[i];
+                head = (i == 0 || (uint32_t)k[i - 1] != ck) && ck != (uint32_t)c;
+                if (head)
+                    for (int64_t t = i; t < bound && (uint32_t)k[t] == ck; ++t) sum += (long long)(uint32_t)v[t];
+            }
+            long long tot = 0;
+            const long long pos = block_exscan_i64(head ? 1 : 0, sh, &tot);
+            if (head) {
+                tadj[base + written + pos] = (int32_t)ck;
+                tw[base + written + pos] = (int32_t)sum;
+            }
+            written += tot;
+        }
+        if (threadIdx.x == 0) rowcnt[c] = (int32_t)written;
+        __syncthreads();
+    }
+}
+
 // Compaction of the coarse rows: kCopyLanes lanes per row (the rows are
 // short; a warp per row left most lanes idle and serialised the rows'
 // round trips).
@@ -599,19 +670,21 @@ static int coarsen_level(Ctx &c, const DGraph &g, uint64_t seed, int32_t level, 
     k_cmap<<<grid_for(n, kTB, 8192), kTB, 0, s>>>(g.n, mate, cidxb.as<int64_t>(), cmap, crep);
     c.launches += 1;
     // bounds of the coarse rows
-    DevBuf boffb, hoffb;
+    DevBuf boffb, hoffb, hrankb;
     JET_TRY(dev_alloc(boffb, (size_t)std::max<int64_t>(nc, 1) * 8, s));
     JET_TRY(dev_alloc(hoffb, (size_t)std::max<int64_t>(nc, 1) * 8, s));
-    int64_t *boff = boffb.as<int64_t>(), *hoff = hoffb.as<int64_t>();
-    c.launches += 3;
+    JET_TRY(dev_alloc(hrankb, (size_t)std::max<int64_t>(nc, 1) * 8, s));
+    int64_t *boff = boffb.as<int64_t>(), *hoff = hoffb.as<int64_t>(), *hrank = hrankb.as<int64_t>();
+    c.launches += 9;
     JET_TRY(device_exscan(RowBound{g.xadj, crep, mate}, nc, boff, totp, scan_scr.as<int64_t>(), s));
-    c.launches += 3;
-    JET_TRY(device_exscan(HugeScratch{boff, totp, crep, mate, g.xadj}, nc, hoff, totp + 1, scan_scr.as<int64_t>(), s));
-    JET_CUDA_TRY(cudaMemcpyAsync(c.pinned, totp, 16, cudaMemcpyDeviceToHost, s));
+    const HubBound hb{crep, mate, g.xadj};
+    JET_TRY(device_exscan(hb, nc, hoff, totp + 1, scan_scr.as<int64_t>(), s));
+    JET_TRY(device_exscan(HubFlag{hb}, nc, hrank, totp + 3, scan_scr.as<int64_t>(), s));
+    JET_CUDA_TRY(cudaMemcpyAsync(c.pinned, totp, 32, cudaMemcpyDeviceToHost, s));
     JET_CUDA_TRY(cudaStreamSynchronize(s));
-    int64_t btotal = c.pinned[0], htotal = c.pinned[1];
+    int64_t btotal = c.pinned[0], htotal = c.pinned[1], nhub = c.pinned[3];
     // coarse vertex weights and row classes
-    DevBuf vwcb, lists, tadjb, twb, cntb, hscrb;
+    DevBuf vwcb, lists, tadjb, twb, cntb, hsortb;
     JET_TRY(dev_alloc(vwcb, (size_t)std::max<int64_t>(nc, 1) * 4, s));
     const int64_t ncl = std::max<int64_t>(nc, 1);
     JET_TRY(dev_alloc(lists, (size_t)ncl * 16 + 64, s));
@@ -624,25 +697,38 @@ static int coarsen_level(Ctx &c, const DGraph &g, uint64_t seed, int32_t level, 
     JET_TRY(dev_alloc(tadjb, (size_t)std::max<int64_t>(btotal, 1) * 4, s));
     JET_TRY(dev_alloc(twb, (size_t)std::max<int64_t>(btotal, 1) * 4, s));
     JET_TRY(dev_alloc(cntb, (size_t)std::max<int64_t>(nc, 1) * 4, s));
-    JET_TRY(dev_alloc(hscrb, (size_t)std::max<int64_t>(htotal, 1) * 8, s));
     int gl = num_sms() * 8;
     const int gwarp = std::min(gl, grid_for(nc, kTB / 32));
     const int glarge = std::min(num_sms() * 4, (int)std::max<int64_t>(1, nc));
     const int gthread = std::min(gl, grid_for(nc, kTB));
     int32_t *tadj = tadjb.as<int32_t>(), *tw = twb.as<int32_t>(), *cnt = cntb.as<int32_t>();
-    unsigned long long *hscr = hscrb.as<unsigned long long>();
     if (g.ew) {
         k_contract_thread<true, 16><<<gthread, kTB, 0, s>>>(g, cmap, mate, crep, t16_list, counts, boff, tadj, tw, cnt);
         k_contract_thread<true, 32><<<gthread, kTB, 0, s>>>(g, cmap, mate, crep, t32_list, counts, boff, tadj, tw, cnt);
         k_contract_warp<true><<<gwarp, kTB, 0, s>>>(g, cmap, mate, crep, warp_list, counts, boff, tadj, tw, cnt);
-        k_contract_large<true><<<glarge, kTB, 0, s>>>(g, cmap, mate, crep, large_list, counts, boff, hoff, hscr, tadj, tw, cnt);
+        k_contract_large<true><<<glarge, kTB, 0, s>>>(g, cmap, mate, crep, large_list, counts, boff, tadj, tw, cnt);
     } else {
         k_contract_thread<false, 16><<<gthread, kTB, 0, s>>>(g, cmap, mate, crep, t16_list, counts, boff, tadj, tw, cnt);
         k_contract_thread<false, 32><<<gthread, kTB, 0, s>>>(g, cmap, mate, crep, t32_list, counts, boff, tadj, tw, cnt);
         k_contract_warp<false><<<gwarp, kTB, 0, s>>>(g, cmap, mate, crep, warp_list, counts, boff, tadj, tw, cnt);
-        k_contract_large<false><<<glarge, kTB, 0, s>>>(g, cmap, mate, crep, large_list, counts, boff, hoff, hscr, tadj, tw, cnt);
+        k_contract_large<false><<<glarge, kTB, 0, s>>>(g, cmap, mate, crep, large_list, counts, boff, tadj, tw, cnt);
     }
     c.launches += 4;
+    if (nhub > 0) {
+        // hub rows: all their entries in one stable radix sort by (rank, coarse id)
+        JET_TRY(dev_alloc(hsortb, sort_scratch_bytes(htotal), s));
+        SortScratch sc;
+        sort_scratch_carve(hsortb.as<char>(), htotal, sc);
+        if (g.ew) k_hub_fill<true><<<glarge, kTB, 0, s>>>(g, cmap, mate, crep, large_list, counts, hoff, hrank, sc.key[0], sc.val[0]);
+        else k_hub_fill<false><<<glarge, kTB, 0, s>>>(g, cmap, mate, crep, large_list, counts, hoff, hrank, sc.key[0], sc.val[0]);
+        c.launches += 1;
+        JET_CUDA_TRY(cudaGetLastError());
+        int which = 0;
+        JET_TRY(sort_pairs(c, sc, htotal, 32 + bits_for(nhub - 1), &which));
+        k_hub_reduce<<<glarge, kTB, 0, s>>>(g, mate, crep, large_list, counts, hoff, sc.key[which], sc.val[which], boff, tadj,
+                                            tw, cnt);
+        c.launches += 1;
+    }
     JET_CUDA_TRY(cudaGetLastError());
     // coarse xadj
     DevBuf xcb, exb;
