@@ -282,7 +282,12 @@ struct RowBound {
     }
 };
 
-constexpr int kSortSmem = 4096;   // entries sorted in shared memory by one block
+// Longest merged row sorted in shared memory by one block; longer rows go
+// through the device-wide radix sort (a launch-shape choice).
+#ifndef JET_SORT_SMEM
+#define JET_SORT_SMEM 4096
+#endif
+constexpr int kSortSmem = JET_SORT_SMEM;
 
 __host__ __device__ inline int64_t pow2ceil(int64_t x) {
     int64_t p = 1;
@@ -560,7 +565,8 @@ __global__ void k_finish_xadj(int32_t nc, const int64_t *ex, const int64_t *tot,
 template <bool EW>
 __global__ void __launch_bounds__(kTB) k_hub_fill(DGraph g, const int32_t *cmap, const int32_t *mate, const int32_t *crep,
                                                   const int32_t *list, const int32_t *counts, const int64_t *hoff,
-                                                  const int64_t *hrank, uint64_t *key, int32_t *val) {
+                                                  const int64_t *hrank, uint64_t *key, int32_t *val,
+                                                  int32_t *hub_c) {
     const int32_t nrows = counts[1];
     for (int64_t w = blockIdx.x; w < nrows; w += gridDim.x) {
         const int32_t c = list[w];
@@ -570,6 +576,7 @@ __global__ void __launch_bounds__(kTB) k_hub_fill(DGraph g, const int32_t *cmap,
         if (bound <= kSortSmem) continue;
         const int64_t off = hoff[c];
         const uint64_t hi = (uint64_t)hrank[c] << 32;
+        if (threadIdx.x == 0) hub_c[hrank[c]] = c;
         for (int64_t i = threadIdx.x; i < bound; i += blockDim.x) {
             const unsigned long long e = row_entry<EW>(g, cmap, r, m, degr, i);
             key[off + i] = hi | (e >> 32);
@@ -578,46 +585,64 @@ __global__ void __launch_bounds__(kTB) k_hub_fill(DGraph g, const int32_t *cmap,
     }
 }
 
-// Hub rows, step 2 (after the stable sort by rank, then coarse id): hub row c
-// is again the segment hoff[c] + [0, bound), now in coarse-id order; heads of
-// equal-id runs summed, own id dropped, written in order (one block per row).
-__global__ void __launch_bounds__(kTB) k_hub_reduce(DGraph g, const int32_t *mate, const int32_t *crep,
-                                                    const int32_t *list, const int32_t *counts, const int64_t *hoff,
-                                                    const uint64_t *key, const int32_t *val, const int64_t *boff,
-                                                    int32_t *tadj, int32_t *tw, int32_t *rowcnt) {
-    __shared__ long long sh[40];
+// Hub rows, step 2 (after the stable sort by rank, then coarse id): the
+// sorted entries of hub row c are the segment starting at hoff[c], in coarse
+// id order.  An entry heads its output entry when it starts a run of equal
+// (rank, coarse id) and the id is not the row's own; an exclusive scan of the
+// head flags over all hub entries places every head (hs[p] - hs[hoff[c]]),
+// so every row, however long, is spread over the whole grid.
+struct HubHead {
+    const uint64_t *key;
+    const int32_t *hub_c;
+    __device__ int64_t operator()(int64_t p) const {
+        const uint64_t kp = key[p];
+        if (p > 0 && key[p - 1] == kp) return 0;
+        return (uint32_t)kp != (uint32_t)hub_c[kp >> 32] ? 1 : 0;
+    }
+};
+
+__global__ void __launch_bounds__(kTB) k_hub_emit(int64_t htotal, const uint64_t *key, const int32_t *val,
+                                                  const int32_t *hub_c, const int64_t *hoff, const int64_t *hs,
+                                                  const int64_t *boff, int32_t *tadj, int32_t *tw) {
+    const HubHead head{key, hub_c};
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < htotal; p += (int64_t)gridDim.x * blockDim.x) {
+        if (!head(p)) continue;
+        const uint64_t kp = key[p];
+        const int32_t c = hub_c[kp >> 32];
+        long long sum = 0;
+        for (int64_t t = p; t < htotal && key[t] == kp; ++t) sum += (long long)(uint32_t)val[t];
+        const int64_t q = boff[c] + (hs[p] - hs[hoff[c]]);
+        tadj[q] = (int32_t)(uint32_t)kp;
+        tw[q] = (int32_t)sum;
+    }
+}
+
+// Hub rows, step 3: entries written per hub row (rank order; the segment of
+// rank r ends where the next one starts).
+__global__ void k_hub_rowcnt(int64_t nhub, int64_t htotal, const int32_t *hub_c, const int64_t *hoff, const int64_t *hs,
+                             const int64_t *hs_total, int32_t *rowcnt) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nhub; r += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t c = hub_c[r];
+        const int64_t beg = hoff[c];
+        const int64_t end = r + 1 < nhub ? hoff[hub_c[r + 1]] : htotal;
+        const int64_t he = end < htotal ? hs[end] : *hs_total;
+        rowcnt[c] = (int32_t)(he - hs[beg]);
+    }
+}
+
+// Long coarse rows (more than kWarpSort bound entries) are compacted by one
+// block each; k_copy_rows leaves them out.
+__global__ void __launch_bounds__(kTB) k_copy_long(const int32_t *list, const int32_t *counts, const int64_t *boff,
+                                                   const int64_t *xadj_c, const int32_t *tadj, const int32_t *tw,
+                                                   int32_t *adj_c, int32_t *ew_c) {
     const int32_t nrows = counts[1];
     for (int64_t w = blockIdx.x; w < nrows; w += gridDim.x) {
         const int32_t c = list[w];
-        const int32_t r = crep[c], m = mate[r];
-        const int64_t bound = ld_xadj(g.xadj, (int64_t)r + 1) - ld_xadj(g.xadj, r) +
-                              (m >= 0 ? ld_xadj(g.xadj, (int64_t)m + 1) - ld_xadj(g.xadj, m) : 0);
-        if (bound <= kSortSmem) continue;
-        const uint64_t *k = key + hoff[c];
-        const int32_t *v = val + hoff[c];
-        const int64_t base = boff[c];
-        long long written = 0;
-        for (int64_t i0 = 0; i0 < bound; i0 += blockDim.x) {
-            const int64_t i = i0 + threadIdx.x;
-            bool head = false;
-            uint32_t ck = 0;
-            long long sum = 0;
-            if (i < bound) {
-                ck = (uint32_t)k[i];
-                head = (i == 0 || (uint32_t)k[i - 1] != ck) && ck != (uint32_t)c;
-                if (head)
-                    for (int64_t t = i; t < bound && (uint32_t)k[t] == ck; ++t) sum += (long long)(uint32_t)v[t];
-            }
-            long long tot = 0;
-            const long long pos = block_exscan_i64(head ? 1 : 0, sh, &tot);
-            if (head) {
-                tadj[base + written + pos] = (int32_t)ck;
-                tw[base + written + pos] = (int32_t)sum;
-            }
-            written += tot;
+        const int64_t src = boff[c], dst = xadj_c[c], len = xadj_c[c + 1] - dst;
+        for (int64_t i = threadIdx.x; i < len; i += blockDim.x) {
+            adj_c[dst + i] = tadj[src + i];
+            ew_c[dst + i] = tw[src + i];
         }
-        if (threadIdx.x == 0) rowcnt[c] = (int32_t)written;
-        __syncthreads();
     }
 }
 
@@ -625,12 +650,14 @@ __global__ void __launch_bounds__(kTB) k_hub_reduce(DGraph g, const int32_t *mat
 // short; a warp per row left most lanes idle and serialised the rows'
 // round trips).
 constexpr int kCopyLanes = 8;
-__global__ void k_copy_rows(int32_t nc, const int64_t *boff, const int64_t *xadj_c, const int32_t *tadj, const int32_t *tw,
-                            int32_t *adj_c, int32_t *ew_c) {
+__global__ void k_copy_rows(int32_t nc, const int64_t *boff, const int64_t *btot, const int64_t *xadj_c,
+                            const int32_t *tadj, const int32_t *tw, int32_t *adj_c, int32_t *ew_c) {
     const int64_t groups = (int64_t)gridDim.x * blockDim.x / kCopyLanes;
     const int gl = (int)(threadIdx.x % kCopyLanes);
     for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kCopyLanes; c < nc; c += groups) {
         const int64_t src = boff[c], dst = xadj_c[c], len = xadj_c[c + 1] - dst;
+        const int64_t bound = (c + 1 < nc ? boff[c + 1] : *btot) - src;
+        if (bound > kWarpSort) continue;   // k_copy_long
         for (int64_t i = gl; i < len; i += kCopyLanes) {
             adj_c[dst + i] = tadj[src + i];
             ew_c[dst + i] = tw[src + i];
@@ -684,7 +711,7 @@ static int coarsen_level(Ctx &c, const DGraph &g, uint64_t seed, int32_t level, 
     JET_CUDA_TRY(cudaStreamSynchronize(s));
     int64_t btotal = c.pinned[0], htotal = c.pinned[1], nhub = c.pinned[3];
     // coarse vertex weights and row classes
-    DevBuf vwcb, lists, tadjb, twb, cntb, hsortb;
+    DevBuf vwcb, lists, tadjb, twb, cntb, hsortb, hubcb, hsb;
     JET_TRY(dev_alloc(vwcb, (size_t)std::max<int64_t>(nc, 1) * 4, s));
     const int64_t ncl = std::max<int64_t>(nc, 1);
     JET_TRY(dev_alloc(lists, (size_t)ncl * 16 + 64, s));
@@ -719,15 +746,21 @@ static int coarsen_level(Ctx &c, const DGraph &g, uint64_t seed, int32_t level, 
         JET_TRY(dev_alloc(hsortb, sort_scratch_bytes(htotal), s));
         SortScratch sc;
         sort_scratch_carve(hsortb.as<char>(), htotal, sc);
-        if (g.ew) k_hub_fill<true><<<glarge, kTB, 0, s>>>(g, cmap, mate, crep, large_list, counts, hoff, hrank, sc.key[0], sc.val[0]);
-        else k_hub_fill<false><<<glarge, kTB, 0, s>>>(g, cmap, mate, crep, large_list, counts, hoff, hrank, sc.key[0], sc.val[0]);
+        JET_TRY(dev_alloc(hubcb, (size_t)nhub * 4, s));
+        JET_TRY(dev_alloc(hsb, (size_t)htotal * 8 + (size_t)(scan_tiles_for(htotal) + 1) * 8 + 64, s));
+        int32_t *hub_c = hubcb.as<int32_t>();
+        int64_t *hs = hsb.as<int64_t>(), *hs_scr = hs + htotal;
+        if (g.ew) k_hub_fill<true><<<glarge, kTB, 0, s>>>(g, cmap, mate, crep, large_list, counts, hoff, hrank, sc.key[0], sc.val[0], hub_c);
+        else k_hub_fill<false><<<glarge, kTB, 0, s>>>(g, cmap, mate, crep, large_list, counts, hoff, hrank, sc.key[0], sc.val[0], hub_c);
         c.launches += 1;
         JET_CUDA_TRY(cudaGetLastError());
         int which = 0;
         JET_TRY(sort_pairs(c, sc, htotal, 32 + bits_for(nhub - 1), &which));
-        k_hub_reduce<<<glarge, kTB, 0, s>>>(g, mate, crep, large_list, counts, hoff, sc.key[which], sc.val[which], boff, tadj,
-                                            tw, cnt);
-        c.launches += 1;
+        JET_TRY(device_exscan(HubHead{sc.key[which], hub_c}, htotal, hs, totp + 4, hs_scr, s));
+        k_hub_emit<<<std::min(gl, grid_for(htotal, kTB)), kTB, 0, s>>>(htotal, sc.key[which], sc.val[which], hub_c, hoff, hs,
+                                                                      boff, tadj, tw);
+        k_hub_rowcnt<<<grid_for(nhub, kTB, 1024), kTB, 0, s>>>(nhub, htotal, hub_c, hoff, hs, totp + 4, cnt);
+        c.launches += 5;
     }
     JET_CUDA_TRY(cudaGetLastError());
     // coarse xadj
@@ -744,7 +777,10 @@ static int coarsen_level(Ctx &c, const DGraph &g, uint64_t seed, int32_t level, 
     DevBuf adjcb, ewcb;
     JET_TRY(dev_alloc(adjcb, (size_t)std::max<int64_t>(nnzc, 1) * 4, s));
     JET_TRY(dev_alloc(ewcb, (size_t)std::max<int64_t>(nnzc, 1) * 4, s));
-    k_copy_rows<<<std::min(gl, grid_for(nc, kTB / kCopyLanes)), kTB, 0, s>>>((int32_t)nc, boff, xcb.as<int64_t>(), tadjb.as<int32_t>(),
+    k_copy_long<<<glarge, kTB, 0, s>>>(large_list, counts, boff, xcb.as<int64_t>(), tadjb.as<int32_t>(), twb.as<int32_t>(),
+                                       adjcb.as<int32_t>(), ewcb.as<int32_t>());
+    c.launches += 1;
+    k_copy_rows<<<std::min(gl, grid_for(nc, kTB / kCopyLanes)), kTB, 0, s>>>((int32_t)nc, boff, totp, xcb.as<int64_t>(), tadjb.as<int32_t>(),
                                                                     twb.as<int32_t>(), adjcb.as<int32_t>(), ewcb.as<int32_t>());
     JET_CUDA_TRY(cudaGetLastError());
     int32_t i = h->levels;
