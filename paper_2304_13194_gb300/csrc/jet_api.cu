@@ -241,12 +241,26 @@ int uncoarsen(Ctx &c, const jet_hier *h, int32_t k, double eps, uint64_t seed, c
     int status = JET_OK;
     int64_t cut = 0, maxw = 0;
     int64_t edge_iters = 0, fin_edge_iters = 0;
-    cudaEvent_t lev[2] = {nullptr, nullptr};
-    cudaEventCreate(&lev[0]);
-    cudaEventCreate(&lev[1]);
+    // every level has the finest graph's total vertex weight (contraction sums them)
+    int64_t W = 0;
+    JET_TRY(total_vweight(c, level_graph(l), W));
+    // level boundaries, read once after the loop (no synchronisation per level)
+    std::vector<cudaEvent_t> lev;
+    struct EvFree {
+        std::vector<cudaEvent_t> &v;
+        ~EvFree() {
+            for (cudaEvent_t e : v)
+                if (e) cudaEventDestroy(e);
+        }
+    } lev_free{lev};
+    if (st) {
+        lev.assign((size_t)h->levels + 1, nullptr);
+        for (auto &e : lev)
+            if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); e = nullptr; }
+    }
     for (int32_t i = l; i >= 0; --i) {
         DGraph g = level_graph(i);
-        cudaEventRecord(lev[0], s);
+        if (st && lev[(size_t)i + 1]) cudaEventRecord(lev[(size_t)i + 1], s);
         if (i < l) {
             int32_t *dst = i == 0 ? part_out : other;
             JET_TRY(project(c, g.n, h->cmap[i], cur, dst));
@@ -256,7 +270,7 @@ int uncoarsen(Ctx &c, const jet_hier *h, int32_t k, double eps, uint64_t seed, c
         }
         if (i == 0) cudaEventRecord(ev.e[2], s);
         LevelReport rep;
-        int r = refine_level(c, g, k, eps, i == 0, level_seed(seed, i), cur, &cut, &maxw, &rep);
+        int r = refine_level(c, g, k, eps, i == 0, level_seed(seed, i), cur, &cut, &maxw, &rep, W);
         if (r < 0) return r;
         status = r;
         int64_t m = h->nnz[i] / 2;
@@ -270,17 +284,22 @@ int uncoarsen(Ctx &c, const jet_hier *h, int32_t k, double eps, uint64_t seed, c
             st->sel_ms[i] = rep.sel_ms;
             st->cluster_blocks[i] = rep.cluster;
             st->bytes_model += rep.bytes_model;
-            cudaEventRecord(lev[1], s);
-            cudaEventSynchronize(lev[1]);
-            float t = 0.f;
-            if (cudaEventElapsedTime(&t, lev[0], lev[1]) == cudaSuccess) st->ms_level[i] = t;
-            else cudaGetLastError();
         }
     }
+    if (st && lev[0]) cudaEventRecord(lev[0], s);
     cudaEventRecord(ev.e[3], s);
     JET_CUDA_TRY(cudaStreamSynchronize(s));
-    cudaEventDestroy(lev[0]);
-    cudaEventDestroy(lev[1]);
+    if (st) {
+        // level i ran between the events recorded at i + 1 and at i
+        for (int32_t i = l; i >= 0; --i) {
+            float t = 0.f;
+            if (lev[(size_t)i + 1] && lev[(size_t)i] &&
+                cudaEventElapsedTime(&t, lev[(size_t)i + 1], lev[(size_t)i]) == cudaSuccess)
+                st->ms_level[i] = t;
+            else
+                cudaGetLastError();
+        }
+    }
     if (cut_out) *cut_out = cut;
     if (st) {
         st->levels = h->levels;

@@ -460,8 +460,12 @@ namespace jet {
 
 // ----- functions implemented in the .cu files ------------------------------
 // jet_refine.cu
+// W_known: the graph's total vertex weight when the caller knows it (every
+// level of a hierarchy has the same), else -1 (computed on the device).
 int refine_level(Ctx &c, const DGraph &g, int32_t k, double eps, int32_t is_finest, uint64_t seed,
-                 int32_t *part_inout, int64_t *cut_out, int64_t *maxw_out, LevelReport *rep);
+                 int32_t *part_inout, int64_t *cut_out, int64_t *maxw_out, LevelReport *rep, int64_t W_known = -1);
+// Sum of the vertex weights (one device reduction and a readback).
+int total_vweight(Ctx &c, const DGraph &g, int64_t &W);
 int lp_pass(Ctx &c, const DGraph &g, int32_t k, const int32_t *part, const uint8_t *locked, double cval,
             uint32_t flags, int32_t *pd_out, int32_t *gain_out, uint8_t *inx_out, int32_t *f2_out,
             uint8_t *inm_out);

@@ -929,7 +929,7 @@ int run_cluster(Ctx &c, const Level &L, int cs) {
 }  // namespace
 
 // Weight of the whole graph (needed for the balance limit).
-static int total_vweight(Ctx &c, const DGraph &g, int64_t &W) {
+int total_vweight(Ctx &c, const DGraph &g, int64_t &W) {
     DevBuf t;
     JET_TRY(dev_alloc(t, 16, c.stream));
     JET_CUDA_TRY(cudaMemsetAsync(t.p, 0, 16, c.stream));
@@ -989,10 +989,10 @@ static void byte_model(const std::vector<TraceRec> &tr, const DGraph &g, int32_t
 }
 
 int refine_level(Ctx &c, const DGraph &g, int32_t k, double eps, int32_t is_finest, uint64_t seed,
-                 int32_t *part_inout, int64_t *cut_out, int64_t *maxw_out, LevelReport *rep_out) {
+                 int32_t *part_inout, int64_t *cut_out, int64_t *maxw_out, LevelReport *rep_out, int64_t W_known) {
     LevelReport rep;
-    int64_t W = 0;
-    JET_TRY(total_vweight(c, g, W));
+    int64_t W = W_known;
+    if (W < 0) JET_TRY(total_vweight(c, g, W));
     int64_t opt = 0;
     int64_t L_lim = balance_limit(W, k, eps, &opt);
     int64_t sigma = opt + (L_lim - opt) / 2;
