@@ -361,7 +361,7 @@ int jet_ctx_create(int device, void *cuda_stream, const jet_options *opt, jet_ct
     c->c.device = device;
     c->c.stream = static_cast<cudaStream_t>(cuda_stream);
     c->c.opt = o;
-    if (cudaMallocHost(&c->c.pinned, 4096) != cudaSuccess) {
+    if (cudaMallocHost(&c->c.pinned, kPinnedBytes) != cudaSuccess) {
         cudaGetLastError();
         delete c;
         return JET_ENOMEM;

@@ -422,12 +422,21 @@ struct LevelReport {
     int32_t cluster = 0;   // blocks of the cluster that ran the level loop (0: graph or host loop)
 };
 
+// Pinned host buffer of a context: scalar readbacks in the first 4 KB (the
+// last int64 slot holds a level's long-row count), then a control block and a
+// level's trace, read back together at the end of a level.
+constexpr size_t kPinnedScalarBytes = 4096;
+constexpr int kPinnedNbigSlot = (int)(kPinnedScalarBytes / 8) - 1;
+constexpr size_t kPinnedCtlOff = kPinnedScalarBytes;
+constexpr size_t kPinnedTraceOff = kPinnedCtlOff + ((sizeof(Ctl) + 255) & ~size_t(255));
+constexpr size_t kPinnedBytes = kPinnedTraceOff + sizeof(TraceRec) * (size_t)kTrace;
+
 struct Ctx {
     int64_t launches = 0;        // kernels launched (graph-loop iterations counted per executed kernel)
     int device = 0;
     cudaStream_t stream = nullptr;
     jet_options opt{};
-    int64_t *pinned = nullptr;   // small pinned host buffer for scalar readbacks
+    int64_t *pinned = nullptr;   // pinned host buffer (layout: kPinned* below)
     cudaMemPool_t pool = nullptr; // the context's stream-ordered pool (keeps its memory between calls)
     TraceHost last_trace;
 };

@@ -17,6 +17,7 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <cstring>
 #include <mutex>
 
 namespace jet {
@@ -427,7 +428,9 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 // Carves all per-level buffers out of two allocations.
 int allow_large_arenas(int device);
 
-int setup_level(Ctx &c, const DGraph &g, int32_t k, LevelBufs &B) {
+// With defer_nbig the long-row count is copied to the context's pinned slot
+// and not waited for: the caller synchronises and sets L.nbig.
+int setup_level(Ctx &c, const DGraph &g, int32_t k, LevelBufs &B, bool defer_nbig = false) {
     JET_TRY(allow_large_arenas(c.device));
     cudaStream_t s = c.stream;
     int64_t n = g.n;
@@ -487,6 +490,10 @@ int setup_level(Ctx &c, const DGraph &g, int32_t k, LevelBufs &B) {
         k_fill_i32<<<grid_for(n, kTB, 4096), kTB, 0, s>>>(L.prio, n, kNoneGain);
     }
     JET_CUDA_TRY(cudaGetLastError());
+    if (defer_nbig) {
+        JET_CUDA_TRY(cudaMemcpyAsync(&c.pinned[kPinnedNbigSlot], B.nbig_dev, 4, cudaMemcpyDeviceToHost, s));
+        return JET_OK;
+    }
     JET_CUDA_TRY(cudaMemcpyAsync(&B.nbig, B.nbig_dev, 4, cudaMemcpyDeviceToHost, s));
     JET_CUDA_TRY(cudaStreamSynchronize(s));
     L.nbig = B.nbig;
@@ -997,12 +1004,14 @@ int refine_level(Ctx &c, const DGraph &g, int32_t k, double eps, int32_t is_fine
     int64_t L_lim = balance_limit(W, k, eps, &opt);
     int64_t sigma = opt + (L_lim - opt) / 2;
     LevelBufs B;
-    JET_TRY(setup_level(c, g, k, B));
+    JET_TRY(setup_level(c, g, k, B, /*defer_nbig=*/true));
     c.launches += g.n > 0 ? 4 : 0;
     Level &L = B.L;
     L.part = part_inout;
     fill_level_params(c, L, is_finest, seed);
-    JET_TRY(enqueue_init(c, B, L_lim, opt, sigma));
+    JET_TRY(enqueue_init(c, B, L_lim, opt, sigma));   // synchronises the stream
+    memcpy(&B.nbig, &c.pinned[kPinnedNbigSlot], 4);
+    L.nbig = B.nbig;
     bool hostloop = (c.opt.flags & (JET_FLAG_HOSTLOOP | JET_FLAG_PROFILE)) != 0;
     int nk_branch[3] = {0, 0, 0}, nk_tail = 0;
     int csize = 0, grid = 0;
@@ -1018,8 +1027,14 @@ int refine_level(Ctx &c, const DGraph &g, int32_t k, double eps, int32_t is_fine
         }
         JET_CUDA_TRY(cudaMemcpyAsync(part_inout, L.best, (size_t)g.n * 4, cudaMemcpyDeviceToDevice, c.stream));
     }
+    // the control block and the whole trace in one round trip
+    char *pin = reinterpret_cast<char *>(c.pinned);
+    JET_CUDA_TRY(cudaMemcpyAsync(pin + kPinnedCtlOff, L.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, c.stream));
+    JET_CUDA_TRY(cudaMemcpyAsync(pin + kPinnedTraceOff, L.trace, sizeof(TraceRec) * (size_t)kTrace,
+                                 cudaMemcpyDeviceToHost, c.stream));
+    JET_CUDA_TRY(cudaStreamSynchronize(c.stream));
     Ctl h;
-    JET_TRY(read_ctl(c, L, h));
+    memcpy(&h, pin + kPinnedCtlOff, sizeof(Ctl));
     if (h.bar_err) {
         record_error("refinement: a grid barrier wait of the persistent level loop ran out");
         return JET_ETIMEOUT;
@@ -1035,13 +1050,9 @@ int refine_level(Ctx &c, const DGraph &g, int32_t k, double eps, int32_t is_fine
     }
     rep.cluster = csize;
     c.last_trace.iters = iters;
-    int32_t nrec = std::min<int32_t>(iters, kTrace);
-    c.last_trace.rec.resize((size_t)nrec);
-    if (nrec > 0) {
-        JET_CUDA_TRY(cudaMemcpyAsync(c.last_trace.rec.data(), L.trace, sizeof(TraceRec) * (size_t)nrec,
-                                     cudaMemcpyDeviceToHost, c.stream));
-        JET_CUDA_TRY(cudaStreamSynchronize(c.stream));
-    }
+    const int32_t nrec = std::min<int32_t>(iters, kTrace);
+    const TraceRec *ht = reinterpret_cast<const TraceRec *>(pin + kPinnedTraceOff);
+    c.last_trace.rec.assign(ht, ht + std::max<int32_t>(nrec, 0));
     rep.iters = iters;
     for (int kd = 0; kd < 3; ++kd) rep.kinds[kd] = h.kcount[kd];
     byte_model(c.last_trace.rec, g, k, L.abl, rep);
