@@ -338,7 +338,7 @@ int jet_coarsest_refined(jet_ctx *ctx, const jet_hier *h, int32_t k, double eps,
  * initial partition of the coarsest graph, Sec. 3) ----------------------
  *
  * A message-passing network proposes the k-way partition of the coarsest
- * graph; the plain greedy initial partition stays its fallback and its judge.
+ * graph; the plain greedy initial partition stays its fallback and the result it must beat.
  *
  * Features (JET_LIP_FEATURES float32 per vertex, each ratio one IEEE float32
  * division of float32-converted integers, the divisor taken as 1 when 0):
