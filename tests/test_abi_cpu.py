@@ -48,7 +48,7 @@ def test_library_is_sm103a_only(lib_path):
 
 
 def test_options_struct_layout_matches_header():
-    # 3 doubles, 6 int32, 1 uint32, 1 int32 -> 56 bytes
+    # 3 doubles, 6 int32, 1 uint32, 2 int32 -> 60 bytes, padded to 64
     assert ctypes.sizeof(binding.Options) == 64
     # jet_batch_item: int32, 4 pointers, int32, double, uint64, pointer, int64, int32, float
     assert ctypes.sizeof(binding._BatchItem) == 88
@@ -56,3 +56,20 @@ def test_options_struct_layout_matches_header():
     assert ctypes.sizeof(binding._TuneReport) == 16 + 4 * 64
     # jet_stats: int32 + 2*64 int64 + 3*64 int32 + 64 int64 + 2 int64 + 5 float + 2 int64
     assert ctypes.sizeof(binding._CStats) % 8 == 0
+
+
+def test_flag_values_match_header():
+    """Every JET_FLAG_* of include/jet.h has the same value in the binding."""
+    text = open(os.path.join(ROOT, "include", "jet.h")).read()
+    flags = dict(re.findall(r"#define JET_FLAG_([A-Z_]+) (\d+)u", text))
+    assert len(flags) >= 11
+    for name, value in flags.items():
+        assert getattr(binding, "FLAG_" + name) == int(value), name
+
+
+def test_status_codes_match_header():
+    """The binding's status names are the header's codes."""
+    text = open(os.path.join(ROOT, "include", "jet.h")).read()
+    codes = {name: int(v) for name, v in re.findall(r"#define (JET_(?:OK|E[A-Z]+|W[A-Z]+)) \(?(-?\d+)\)?", text)}
+    assert codes["JET_OK"] == 0 and len(codes) == 9
+    assert {v: k for k, v in codes.items()} == binding._STATUS
