@@ -611,6 +611,20 @@ def test_edge_cases(ctx):
     assert cut == ref.cut and (_np(part) == ref.part).all()
 
 
+def test_partition_star_hub_matches_oracle(ctx):
+    """One hub adjacent to 12,000 leaves that form a ring (ring edges heavier):
+    the hub row is one long row in every refinement phase, and its merged
+    coarse row (each coarse leaf twice) goes through the radix-sort path of
+    the contraction; eps = 0 as well (the tightest balance)."""
+    n = 12001
+    tri = [[0, v, 1] for v in range(1, n)]
+    tri += [[v, v % (n - 1) + 1, 2] for v in range(1, n)]
+    g = graph_from_triples(n, tri)
+    assert np.diff(g.xadj).max() == n - 1
+    _check_partition(ctx, g, False, 16, seed=4)
+    _check_partition(ctx, g, False, 8, seed=5, eps=0.0)
+
+
 def test_errors(ctx):
     g = graphgen.grid2d(6, 6)
     with pytest.raises(jet.JetError) as ei:
