@@ -37,8 +37,9 @@ UNIT = "Medges/s"
 K_PARTS, EPS, SEED = 64, 0.03, 1
 WORKLOAD = "grid3d 128x128x128 (7-point), vwgt U[1,4], adjwgt U[1,10], k=64, eps=0.03, seed=1"
 FLUSH_BYTES = 512 << 20          # written between steps (L2 is 129 MB)
-ROOFLINE_KERNEL = "Jetlp select step: k_lp_scan + k_lp_select (finest level)"
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "lp_select_grid3d_128_k64.txt")
+G3_WORKLOAD = ("rmat s22 (4,194,304 vertices, edge factor 16, a=.57 b=c=.19 d=.05, symmetrised, isolated vertices "
+               "kept), unit weights, k=64, eps=0.03, seed=1")
+PROFILES = os.path.join(ROOT, "profiles")
 
 
 def parse_args(argv=None):
@@ -48,6 +49,7 @@ def parse_args(argv=None):
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing (debug runs)")
+    p.add_argument("--no-g3", action="store_true", help="skip the R-MAT scale-22 workload (debug runs)")
     p.add_argument("--scale", type=int, default=128, help="mesh side (128 is the benchmark workload)")
     p.add_argument("--hostloop", action="store_true",
                    help="drive refinement iterations from the host (same kernels and launch configuration; "
@@ -233,12 +235,13 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic_per_launch():
-    """DRAM bytes per select launch from the committed ncu summary, if it was
-    taken on the current kernel source (else None)."""
+def ncu_traffic_per_launch(kernel, workload_tag):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary
+    profiles/<kernel>_<workload_tag>.txt, if it was taken on the current
+    kernel sources (else None)."""
     try:
         kv = {}
-        with open(PROFILE_SUMMARY) as f:
+        with open(os.path.join(PROFILES, f"{kernel}_{workload_tag}.txt")) as f:
             for line in f:
                 if ":" in line:
                     a, b = line.split(":", 1)
@@ -248,6 +251,42 @@ def ncu_traffic_per_launch():
         return int(float(kv["traffic_bytes_per_launch"]))
     except Exception:
         return None
+
+
+def kernel_table(pst, names, peak):
+    """Per refinement kernel over the whole partition, from the profiled run:
+    launches, CUDA-event ms, share of the kernel time, algorithmic bytes and
+    GB/s.  Returns (table, name of the kernel with the largest time)."""
+    tot_ms = [0.0] * len(names)
+    tot_b = [0] * len(names)
+    tot_l = [0] * len(names)
+    for lv in range(pst.levels):
+        for i in range(len(names)):
+            tot_ms[i] += pst.kern_ms[lv][i]
+            tot_b[i] += pst.kern_bytes[lv][i]
+            tot_l[i] += pst.kern_launches[lv][i]
+    all_ms = sum(tot_ms) or 1.0
+    table = {}
+    for i, name in enumerate(names):
+        if tot_l[i] == 0:
+            continue
+        gbs = tot_b[i] / (tot_ms[i] / 1e3) / 1e9 if tot_ms[i] > 0 else 0.0
+        table[name] = {"launches": tot_l[i], "ms": round(tot_ms[i], 3), "share": round(tot_ms[i] / all_ms, 4),
+                       "bytes": tot_b[i], "gbs": round(gbs, 1), "frac": round(gbs / peak, 4)}
+    top = max(table, key=lambda k: table[k]["ms"])
+    return table, top
+
+
+def roofline_of(table, top, peak, peak_kind, workload_tag):
+    t = table[top]
+    return {"bound": "hbm", "kernel": top, "achieved": t["gbs"], "peak": peak, "peak_kind": peak_kind,
+            "unit": "GB/s", "frac": t["frac"], "traffic": ncu_traffic_per_launch(top, workload_tag),
+            "bytes_per_launch": int(t["bytes"] / max(t["launches"], 1)),
+            "ms_per_launch": round(t["ms"] / max(t["launches"], 1), 5), "launches": t["launches"],
+            "time_share": t["share"],
+            "how": "algorithmic bytes of the kernel's launches (byte model of jet_stats.kern_bytes) / their "
+                   "CUDA-event time on the library stream, host-driven loop with the same kernels and launch "
+                   "configuration (JET_FLAG_PROFILE)"}
 
 
 def run_probe(args):
@@ -344,28 +383,30 @@ def run_ours(args):
     h2d = g.xadj.nbytes + g.adjncy.nbytes + g.vwgt.nbytes + g.adjwgt.nbytes
     d2h = g.n * 4
 
-    # ---- roofline of the dominant kernel: CUDA events around each select
-    # launch (profiling mode drives the same kernels from the host) ----------
+    # ---- per-kernel CUDA-event times (profiling mode drives the same kernels
+    # with the same launch configuration from the host); the roofline names
+    # the kernel with the largest share of the time ---------------------------
+    peak, peak_kind = peaks()
+    names = jet.kernel_names()
     pctx = jet.Context(local, flags=jet.FLAG_PROFILE | pdl_off)
     flush.zero_()
     _, pcut, pst = pctx.partition(xadj, adj, vw, ew, k=K_PARTS, eps=EPS, seed=SEED, return_stats=True)
     pctx.close()
-    sel_bytes, sel_ms, sel_n = pst.sel_bytes[0], pst.sel_ms[0], pst.sel_launches[0]
-    peak, peak_kind = peaks()
-    achieved = sel_bytes / (sel_ms / 1e3) / 1e9 if sel_ms > 0 else 0.0
-    traffic = ncu_traffic_per_launch()
+    table, top = kernel_table(pst, names, peak)
+    st0 = stats[-1]
+    refine_gbs = st0.bytes_model / (st0.ms_refine / 1e3) / 1e9
 
-    # ---- CPU baseline: the oracle on a bounded sample (rank 0, N = 1) ----
+    # ---- CPU baseline: the oracle over the same stages (rank 0, N = 1) ------
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        iters = 100
-        u, s, its = oracle_sample(g, iters)
-        cpu = {"value": round(u / s / 1e6, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"oracle Jet refinement of the finest level (same mesh, k=64) from the greedy initial "
-                         f"partition, {its} iterations ({s:.1f} s), single thread"}
+        cpu = oracle_partition_baseline(g, K_PARTS, SEED)
+
+    # ---- the power-law workload (R-MAT scale 22, k = 64) --------------------
+    g3 = None
+    if not args.no_g3 and ws == 1:
+        g3 = run_g3(args, jet, device, stream, flush, loop | pdl_off, copts, peak, peak_kind, names, rank == 0)
 
     if rank == 0:
-        st0 = stats[-1]
         out = {
             "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(max_step_ms, 3), "higher_is_better": True,
@@ -378,13 +419,15 @@ def run_ours(args):
                        "initpart_ms": round(st0.ms_init, 3), "finest_refine_ms": round(st0.ms_refine_finest, 3),
                        "edge_iters_per_step": st0.edge_iters, "bytes_model_per_step": st0.bytes_model,
                        "ms_level": [round(x, 3) for x in st0.ms_level],
+                       "iters_level": [a + b + c for a, b, c in zip(st0.iters_lp, st0.iters_rw, st0.iters_rs)],
                        "cluster_blocks": st0.cluster_blocks},
-            "roofline": {"bound": "hbm", "kernel": ROOFLINE_KERNEL, "achieved": round(achieved, 1),
-                         "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
-                         "frac": round(achieved / peak, 4) if peak else None,
-                         "bytes_per_launch": int(sel_bytes / max(sel_n, 1)),
-                         "ms_per_launch": round(sel_ms / max(sel_n, 1), 5), "launches": sel_n,
-                         "traffic": traffic},
+            "roofline": roofline_of(table, top, peak, peak_kind, "grid3d_128_k64"),
+            "roofline_refine": {"bound": "hbm", "achieved": round(refine_gbs, 1), "peak": peak,
+                                "peak_kind": peak_kind, "unit": "GB/s", "frac": round(refine_gbs / peak, 4),
+                                "how": "algorithmic bytes of every refinement kernel of one partition "
+                                       "(jet_stats.bytes_model) / the refinement time of the timed steps "
+                                       "(CUDA-graph loop)"},
+            "kernels": table,
             "cpu_baseline": cpu,
             "e2e": {"value": round(e2e_tot / e2e_max / 1e6, 3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
@@ -392,12 +435,92 @@ def run_ours(args):
             "clocks": clocks,
             "step_ms": [round(x, 3) for x in step_ms],
             "refine_ms_steps": [round(s.ms_refine, 3) for s in stats],
+            "g3": g3,
         }
         print(json.dumps(out), flush=True)
     ctx.close()
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def oracle_partition_baseline(g, k, seed):
+    """The oracle's whole partition of the workload (coarsening, initial
+    partition, refinement of every level: the same stages as a step), one
+    run on one host core.  value = its refinement edge passes per second."""
+    import oracle
+    t0 = time.perf_counter()
+    r = oracle.partition(g, k, EPS, seed)
+    secs = time.perf_counter() - t0
+    st = r.stats
+    return {"value": round(st["edge_iters"] / st["sec_refine"] / 1e6, 3), "unit": UNIT, "cores": 1,
+            "kind": "oracle", "partition_ms": round(1e3 * secs, 1),
+            "refine_ms": round(1e3 * st["sec_refine"], 1), "coarsen_ms": round(1e3 * st["sec_coarsen"], 1),
+            "initpart_ms": round(1e3 * st["sec_init"], 1), "cut": r.cut, "same_config": True,
+            "sample": "oracle partition of the whole workload (all stages, every level), one run, single thread"}
+
+
+def run_g3(args, jet, device, stream, flush, flags, copts, peak, peak_kind, names, with_cpu):
+    """The power-law workload: R-MAT scale 22, unit weights, k = 64.  The
+    same step, timing and flush as the mesh; its own per-kernel profile and
+    rooflines.  Heavy-edge matching stalls at the first level, so the whole
+    64M-edge graph is refined."""
+    import torch
+    import graphgen
+    g = graphgen.rmat(22, seed=SEED)
+    xadj = torch.from_numpy(g.xadj).to(device)
+    adj = torch.from_numpy(g.adjncy).to(device)
+    ctx = jet.Context(device.index, flags=flags, **copts)
+
+    def step():
+        return ctx.partition(xadj, adj, None, None, k=K_PARTS, eps=EPS, seed=SEED, return_stats=True)
+
+    for _ in range(max(args.warmup, 0)):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    stats = []
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        _, cut, st = step()
+        ev[i][1].record(stream)
+        stats.append(st)
+    torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ctx.close()
+    units = sum(s.edge_iters for s in stats)
+    refine_s = sum(s.ms_refine for s in stats) / 1e3
+    st0 = stats[-1]
+    pctx = jet.Context(device.index, flags=jet.FLAG_PROFILE | (flags & jet.FLAG_NO_PDL))
+    flush.zero_()
+    _, _, pst = pctx.partition(xadj, adj, None, None, k=K_PARTS, eps=EPS, seed=SEED, return_stats=True)
+    pctx.close()
+    table, top = kernel_table(pst, names, peak)
+    refine_gbs = st0.bytes_model / (st0.ms_refine / 1e3) / 1e9
+    cpu = None
+    if with_cpu and not args.no_cpu_baseline:
+        import oracle
+        iters = 2
+        part0 = oracle.initial_partition(g, K_PARTS)
+        t0 = time.perf_counter()
+        r = oracle.refine(g, K_PARTS, part0, eps=EPS, is_finest=True, seed=oracle.level_seed(SEED, 0),
+                          opts=oracle.Options(max_iters=iters), trace_cap=1)
+        secs = time.perf_counter() - t0
+        cpu = {"value": round(r.iters * g.m / secs / 1e6, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"oracle Jet refinement of the whole graph (the only level) from the greedy initial "
+                         f"partition, {r.iters} iterations ({secs:.1f} s), single thread"}
+    del xadj, adj
+    return {"workload": G3_WORKLOAD, "n": g.n, "m": g.m, "metric": METRIC, "unit": UNIT,
+            "value": round(units / refine_s / 1e6, 3), "ms_per_step": round(statistics.mean(step_ms), 3),
+            "refine_ms": round(st0.ms_refine, 3), "coarsen_ms": round(st0.ms_coarsen, 3),
+            "initpart_ms": round(st0.ms_init, 3), "levels": st0.levels, "cut": cut, "max_part_w": st0.max_part_w,
+            "edge_iters_per_step": st0.edge_iters, "bytes_model_per_step": st0.bytes_model,
+            "roofline": roofline_of(table, top, peak, peak_kind, "rmat22_k64"),
+            "roofline_refine": {"bound": "hbm", "achieved": round(refine_gbs, 1), "peak": peak,
+                                "peak_kind": peak_kind, "unit": "GB/s", "frac": round(refine_gbs / peak, 4)},
+            "kernels": table, "cpu_baseline": cpu}
 
 
 # Jetlp versions of the component study (Sec. 6.1.4, Table 2) as library flags

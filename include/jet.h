@@ -64,9 +64,10 @@ extern "C" {
 #define JET_FLAG_HOSTLOOP 2u       /* drive refinement iterations from the host (one launch
                                       sequence per iteration, mode read back each time)
                                       instead of the device-resident CUDA-graph loop */
-#define JET_FLAG_PROFILE 4u        /* implies JET_FLAG_HOSTLOOP; records CUDA events around every
-                                      Jetlp select launch (same kernels, same launch configuration)
-                                      and fills jet_stats.sel_ms */
+#define JET_FLAG_PROFILE 4u        /* implies JET_FLAG_HOSTLOOP; records a CUDA event before every
+                                      refinement kernel launch and after the last of each iteration
+                                      (same kernels, same launch configuration) and fills
+                                      jet_stats.kern_ms and sel_ms */
 #define JET_FLAG_NO_LOCKS 16u      /* Jetlp ablations (Sec. 6.1.4, Table 2): ignore lock bits */
 #define JET_FLAG_NO_AFTERBURN 32u  /*   M = X (skip the second filter) */
 #define JET_FLAG_WEAK_AFTERBURN 64u/*   first filter keeps only F >= 0 */
@@ -98,14 +99,34 @@ extern "C" {
  *                                   refinement loop in one thread-block-cluster launch; larger
  *                                   levels use the CUDA-graph loop; 0 = never
  *   cluster_blocks = 0              blocks (of 1024 threads) of that cluster: 0 = the largest the
- *                                   device runs (up to 16), else a power of two in [2, 16] */
+ *                                   device runs (up to 16), else a power of two in [2, 16]
+ *   barrier_polls = 0               polls a block of the persistent level loop (JET_FLAG_GRID_LOOP)
+ *                                   makes at a grid barrier before it gives up and the call returns
+ *                                   JET_ETIMEOUT; 0 = 2^22 (about a second or more, far above any
+ *                                   phase); small values make the wait run out on purpose (tests) */
 typedef struct {
     double c_fine, c_coarse, phi;
     int32_t max_no_improve, weak_limit, coarsen_target, max_levels, max_iters_per_level, hem_rounds;
     uint32_t flags;
     int32_t cluster_max_n;
     int32_t cluster_blocks;
+    int32_t barrier_polls;
 } jet_options;
+
+/* Refinement kernels (one launch each per iteration of the CUDA-graph or host
+ * loop), indices of jet_stats.kern_*; jet_kernel_name gives their names. */
+#define JET_KERNELS 16
+#define JET_K_LP_SCAN 0      /* Jetlp work list (Alg. 4: boundary, unlocked vertices) */
+#define JET_K_LP_SELECT 1    /* Jetlp P_d, F and the first filter (Alg. 4, Eq. gainconn_filter) */
+#define JET_K_AFTERBURN 2    /* Jetlp afterburner and second filter (Alg. 4, ord of Sec. 4.1.1) */
+#define JET_K_APPLY 3        /* apply the moves (Alg. 3 updatePartsAndDS) + the Alg. 3 controller */
+#define JET_K_RB_SCAN 4      /* rebalancing candidates (Alg. 5 first loop) */
+#define JET_K_RB_CAND 5      /* rebalancing destinations and losses of listed candidates */
+#define JET_K_RB_TILEHIST 6  /* rebalancing: weight of boundary-slot members per tile */
+#define JET_K_RB_TILESCAN 7  /* rebalancing: scan of the tile sums */
+#define JET_K_RB_TAKE 8      /* rebalancing: eviction in (slot, vertex id) order */
+#define JET_K_RB_COOKIE 9    /* Jetrs destinations (cookie cutter, Sec. 4.2.2) */
+#define JET_K_COUNT 10       /* kernels in use (indices below JET_KERNELS) */
 
 /* Per-call statistics (jet_partition / jet_uncoarsen).  Times are CUDA-event
  * milliseconds on the context's stream. */
@@ -127,7 +148,16 @@ typedef struct {
     float ms_level[JET_MAX_LEVELS];        /* CUDA-event time of each level's projection + refinement */
     int32_t cluster_blocks[JET_MAX_LEVELS]; /* blocks of the thread-block cluster that ran the level's
                                                loop; 0 where the CUDA-graph or host loop ran it */
+    /* per level and refinement kernel (JET_K_*): launches (0 where one cluster or cooperative launch
+     * ran the whole loop), algorithmic DRAM bytes (the byte model of bytes_model, split by kernel)
+     * and, with JET_FLAG_PROFILE, the CUDA-event time of the kernel's launches */
+    int64_t kern_launches[JET_MAX_LEVELS][JET_KERNELS];
+    int64_t kern_bytes[JET_MAX_LEVELS][JET_KERNELS];
+    float kern_ms[JET_MAX_LEVELS][JET_KERNELS];
 } jet_stats;
+
+/* Name of refinement kernel i (JET_K_*), or NULL outside [0, JET_K_COUNT). */
+const char *jet_kernel_name(int32_t i);
 
 typedef struct jet_ctx jet_ctx;
 typedef struct jet_hier jet_hier;
@@ -292,11 +322,13 @@ int jet_rebalance_pass(jet_ctx *ctx, int32_t n, const int64_t *xadj, const int32
  * until the process exits.  Larger n is rejected with JET_EINVAL (see
  * jet_last_error).  The first call on each device looks up the array's
  * device address (cudaGetSymbolAddress); make that first call before any
- * stream capture.  All calls share the one array, which keeps the previous
- * call's contents (the pass clears what must start at zero): calls that can
- * overlap on the GPU — from several contexts, streams or host threads on the
- * same device — race and must be serialised by the caller.  No cudaMalloc,
- * cudaFree or allocating library routine is called. */
+ * stream capture.  Like every call of this library it reads two counts back
+ * to the host and synchronises the context's stream before it returns.  All
+ * calls share the one array, which keeps the previous call's contents (the
+ * pass clears what must start at zero): calls that can overlap on the GPU —
+ * from several contexts, streams or host threads on the same device — race
+ * and must be serialised by the caller.  No cudaMalloc, cudaFree or
+ * allocating library routine is called (jet_alloc_count does not move). */
 #define JET_NOALLOC_MAX_N 262144
 int jet_lp_pass_noalloc(jet_ctx *ctx, int32_t n, const int64_t *xadj, const int32_t *adjncy,
                         const int32_t *vwgt, const int32_t *adjwgt, int32_t k, const int32_t *part,
@@ -438,6 +470,19 @@ typedef struct {
 int jet_partition_learned(jet_ctx *ctx, const jet_lip *m, int32_t n, const int64_t *xadj, const int32_t *adjncy,
                           const int32_t *vwgt, const int32_t *adjwgt, double eps, uint64_t seed, int32_t *part_out,
                           int64_t *cut_out, jet_stats *stats, jet_learned_info *info);
+
+/* Fault injection on the host (a diagnostic for tests; the paper has no
+ * counterpart): the nth device allocation the library attempts from now on
+ * (nth >= 1) fails without reaching CUDA, as if the device were out of
+ * memory, and the call that made it returns JET_ENOMEM after releasing what
+ * it holds; one shot, process-wide.  nth = 0 disarms it.  No GPU state is
+ * touched. */
+void jet_debug_fail_alloc(int64_t nth);
+
+/* Device allocations the library has made in this process so far (all
+ * contexts and threads; every stream-ordered scratch allocation counts one).
+ * A diagnostic: the paper has no counterpart. */
+int64_t jet_alloc_count(void);
 
 /* Human-readable name of a status code (static storage). */
 const char *jet_status_string(int status);

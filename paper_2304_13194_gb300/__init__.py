@@ -17,12 +17,12 @@ context's device (``partition_host`` takes CPU arrays).
 from __future__ import annotations
 
 from .binding import (  # noqa: F401
-    JET_MAX_K, JetError, Context, Options, Stats, load_library, status_string,
+    JET_MAX_K, JetError, Context, Options, Stats, load_library, status_string, kernel_names, JET_K_COUNT,
     FLAG_VALIDATE, FLAG_HOSTLOOP, FLAG_PROFILE, FLAG_NO_LOCKS, FLAG_NO_AFTERBURN, FLAG_WEAK_AFTERBURN, FLAG_BASELINE_LP,
     FLAG_TWO_HOP, FLAG_STRICT_GAIN, FLAG_NO_PDL, FLAG_GRID_LOOP,
     KIND_LP, KIND_RW, KIND_RS, NONE_GAIN, EXPORTED_SYMBOLS,
     LearnedPartitioner, num_lip_params, LIP_FEATURES, LIP_HIDDEN, LIP_MAX_K, LIP_MAX_N,
 )
 
-__all__ = ["Context", "Options", "Stats", "JetError", "load_library", "status_string", "JET_MAX_K",
+__all__ = ["Context", "Options", "Stats", "JetError", "load_library", "status_string", "kernel_names", "JET_MAX_K",
            "EXPORTED_SYMBOLS", "LearnedPartitioner", "num_lip_params"]

@@ -25,6 +25,8 @@ FLAG_NO_PDL = 1024
 FLAG_GRID_LOOP = 2048
 KIND_LP, KIND_RW, KIND_RS = 0, 1, 2
 NONE_GAIN = -(2 ** 31)
+JET_KERNELS = 16      # size of the per-kernel statistics rows (JET_K_* indices)
+JET_K_COUNT = 10      # refinement kernels in use
 
 EXPORTED_SYMBOLS = [
     "jet_options_default", "jet_ctx_create", "jet_ctx_destroy", "jet_coarsen", "jet_hier_destroy",
@@ -34,6 +36,7 @@ EXPORTED_SYMBOLS = [
     "jet_coarsest_refined", "jet_lip_num_params", "jet_lip_create", "jet_lip_destroy", "jet_lip_get_params",
     "jet_lip_set_params", "jet_lip_features", "jet_lip_labels", "jet_lip_forward", "jet_lip_loss_grad",
     "jet_lip_train_step", "jet_lip_decode", "jet_lip_initial_partition", "jet_partition_learned", "jet_autotune",
+    "jet_kernel_name", "jet_alloc_count", "jet_debug_fail_alloc",
 ]
 LIP_FEATURES, LIP_HIDDEN, LIP_MAX_K, LIP_MAX_N = 16, 64, 256, 1 << 20
 JET_NOALLOC_MAX_N = 262144
@@ -54,7 +57,8 @@ class Options(ctypes.Structure):
                 ("max_no_improve", ctypes.c_int32), ("weak_limit", ctypes.c_int32),
                 ("coarsen_target", ctypes.c_int32), ("max_levels", ctypes.c_int32),
                 ("max_iters_per_level", ctypes.c_int32), ("hem_rounds", ctypes.c_int32),
-                ("flags", ctypes.c_uint32), ("cluster_max_n", ctypes.c_int32), ("cluster_blocks", ctypes.c_int32)]
+                ("flags", ctypes.c_uint32), ("cluster_max_n", ctypes.c_int32), ("cluster_blocks", ctypes.c_int32),
+                ("barrier_polls", ctypes.c_int32)]
 
     @classmethod
     def default(cls, **kw) -> "Options":
@@ -80,7 +84,10 @@ class _CStats(ctypes.Structure):
                 ("bytes_model", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
                 ("sel_launches", ctypes.c_int64 * L), ("sel_bytes", ctypes.c_int64 * L),
                 ("sel_ms", ctypes.c_float * L), ("ms_level", ctypes.c_float * L),
-                ("cluster_blocks", ctypes.c_int32 * L)]
+                ("cluster_blocks", ctypes.c_int32 * L),
+                ("kern_launches", (ctypes.c_int64 * JET_KERNELS) * L),
+                ("kern_bytes", (ctypes.c_int64 * JET_KERNELS) * L),
+                ("kern_ms", (ctypes.c_float * JET_KERNELS) * L)]
 
 
 @dataclass
@@ -108,15 +115,21 @@ class Stats:
     sel_ms: list = field(default_factory=list)
     ms_level: list = field(default_factory=list)
     cluster_blocks: list = field(default_factory=list)
+    # per level, one entry per refinement kernel (JET_K_* order, kernel_names())
+    kern_launches: list = field(default_factory=list)
+    kern_bytes: list = field(default_factory=list)
+    kern_ms: list = field(default_factory=list)
 
     @classmethod
     def from_c(cls, s: _CStats) -> "Stats":
         lv = s.levels
+        rows = lambda a: [list(a[i][:JET_K_COUNT]) for i in range(lv)]   # noqa: E731
         return cls(lv, list(s.n[:lv]), list(s.m[:lv]), list(s.iters_lp[:lv]), list(s.iters_rw[:lv]),
                    list(s.iters_rs[:lv]), list(s.cut_level[:lv]), s.edge_iters, s.fin_edge_iters, s.ms_coarsen,
                    s.ms_init, s.ms_refine, s.ms_refine_finest, s.ms_total, s.cut, s.max_part_w, s.bytes_model,
                    s.kernel_launches, list(s.sel_launches[:lv]), list(s.sel_bytes[:lv]), list(s.sel_ms[:lv]),
-                   list(s.ms_level[:lv]), list(s.cluster_blocks[:lv]))
+                   list(s.ms_level[:lv]), list(s.cluster_blocks[:lv]), rows(s.kern_launches), rows(s.kern_bytes),
+                   rows(s.kern_ms))
 
 
 _lib = None
@@ -175,6 +188,9 @@ def load_library(path: str | None = None):
                                                      P(_LearnedInfo)]),
             "jet_autotune": (ctypes.c_int, [vp, i32, vp, i32, P(_TuneReport)]),
             "jet_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+            "jet_kernel_name": (ctypes.c_char_p, [i32]),
+            "jet_alloc_count": (i64, []),
+            "jet_debug_fail_alloc": (None, [i64]),
             "jet_last_error": (ctypes.c_char_p, []),
         }
         for name, (res, args) in sig.items():
@@ -183,6 +199,23 @@ def load_library(path: str | None = None):
             f.argtypes = args
         _lib = L
         return L
+
+
+def debug_fail_alloc(nth: int) -> None:
+    """Make the nth device allocation the library attempts from now on fail
+    with JET_ENOMEM (host-side injection, one shot); 0 disarms."""
+    load_library().jet_debug_fail_alloc(int(nth))
+
+
+def alloc_count() -> int:
+    """Device allocations the library has made in this process so far."""
+    return int(load_library().jet_alloc_count())
+
+
+def kernel_names() -> list[str]:
+    """Names of the refinement kernels, in the order of Stats.kern_* rows."""
+    L = load_library()
+    return [L.jet_kernel_name(i).decode() for i in range(JET_K_COUNT)]
 
 
 def status_string(status: int) -> str:

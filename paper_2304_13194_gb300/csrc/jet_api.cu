@@ -27,9 +27,21 @@ const char *last_error_text() { return g_err; }
 // use_device); null: the device's default pool.
 static thread_local cudaMemPool_t t_pool = nullptr;
 
+// Device allocations made by the library in this process (jet_alloc_count)
+// and the injected failure (jet_debug_fail_alloc): the allocation whose
+// count reaches g_fail_at fails; 0 = none armed.
+static std::atomic<int64_t> g_alloc_count{0};
+static std::atomic<int64_t> g_fail_at{0};
+
 int dev_alloc(DevBuf &b, size_t bytes, cudaStream_t s) {
     b.release();
     b.s = s;
+    const int64_t idx = g_alloc_count.fetch_add(1, std::memory_order_relaxed) + 1;
+    int64_t armed = g_fail_at.load(std::memory_order_relaxed);
+    if (armed != 0 && idx == armed && g_fail_at.compare_exchange_strong(armed, 0)) {
+        record_error("device allocation failed (injected by jet_debug_fail_alloc)");
+        return JET_ENOMEM;
+    }
     bytes = std::max<size_t>(256, (bytes + 255) & ~size_t(255));
     cudaError_t e = t_pool ? cudaMallocFromPoolAsync(&b.p, bytes, t_pool, s) : cudaMallocAsync(&b.p, bytes, s);
     if (e != cudaSuccess) {
@@ -284,6 +296,11 @@ int uncoarsen(Ctx &c, const jet_hier *h, int32_t k, double eps, uint64_t seed, c
             st->sel_ms[i] = rep.sel_ms;
             st->cluster_blocks[i] = rep.cluster;
             st->bytes_model += rep.bytes_model;
+            for (int kk = 0; kk < JET_KERNELS; ++kk) {
+                st->kern_launches[i][kk] = rep.kern_launches[kk];
+                st->kern_bytes[i][kk] = rep.kern_bytes[kk];
+                st->kern_ms[i][kk] = rep.kern_ms[kk];
+            }
         }
     }
     if (st && lev[0]) cudaEventRecord(lev[0], s);
@@ -338,6 +355,7 @@ void jet_options_default(jet_options *o) {
     o->flags = 0;
     o->cluster_max_n = 4096;
     o->cluster_blocks = 0;
+    o->barrier_polls = 0;
 }
 
 int jet_ctx_create(int device, void *cuda_stream, const jet_options *opt, jet_ctx **out) {
@@ -349,6 +367,7 @@ int jet_ctx_create(int device, void *cuda_stream, const jet_options *opt, jet_ct
     if (!(o.c_fine >= 0 && o.c_fine <= 1 && o.c_coarse >= 0 && o.c_coarse <= 1 && o.phi > 0 && o.phi <= 1) ||
         o.max_no_improve < 0 || o.weak_limit < 0 || o.coarsen_target < 0 || o.max_levels < 1 ||
         o.max_iters_per_level < 0 || o.hem_rounds < 0 || o.hem_rounds > 64 || o.cluster_max_n < 0 ||
+        o.barrier_polls < 0 ||
         !(o.cluster_blocks == 0 || o.cluster_blocks == 2 || o.cluster_blocks == 4 || o.cluster_blocks == 8 ||
           o.cluster_blocks == 16))
         return JET_EINVAL;
@@ -782,6 +801,19 @@ int jet_initial_partition(jet_ctx *ctx, int32_t n, const int64_t *xadj, const in
     DevBuf ones;
     JET_TRY(prepare_graph(c, n, xadj, adjncy, vwgt, nullptr, g, ones, true));
     return initial_partition(c, g, k, part_out);
+}
+
+int64_t jet_alloc_count(void) { return g_alloc_count.load(std::memory_order_relaxed); }
+
+void jet_debug_fail_alloc(int64_t nth) {
+    g_fail_at.store(nth > 0 ? g_alloc_count.load(std::memory_order_relaxed) + nth : 0, std::memory_order_relaxed);
+}
+
+const char *jet_kernel_name(int32_t i) {
+    static const char *const names[JET_K_COUNT] = {"k_lp_scan", "k_lp_select", "k_afterburn", "k_apply",
+                                                   "k_rb_scan", "k_rb_cand", "k_rb_tilehist", "k_rb_tilescan",
+                                                   "k_rb_take", "k_rb_cookie"};
+    return (i >= 0 && i < JET_K_COUNT) ? names[i] : nullptr;
 }
 
 const char *jet_status_string(int s) {

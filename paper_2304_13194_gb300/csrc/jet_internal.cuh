@@ -100,7 +100,10 @@ struct DGraph {
 // device control block of one refinement level (Alg. 3 state)
 // ---------------------------------------------------------------------------
 struct TraceRec {
-    int32_t kind, pad;
+    int32_t kind;
+    int32_t flags;    // bit 0: the controller ordered P_best <- P_iter (copied by the next iteration)
+    int32_t na;       // rebalancing: oversized parts (|A|) of this iteration
+    int32_t pad;
     int64_t nx, nm, cut, maxw;
     int64_t degx;     // sum of row lengths over X (Jetlp) or over the rebalancing candidates
     int64_t degm;     // sum of row lengths over M
@@ -182,6 +185,7 @@ struct Level {
     unsigned long long h_loop, h_mode;
     int32_t use_graph;
     int32_t pdl;             // launch the row and tile kernels with programmatic dependent launch
+    int64_t poll_limit;      // persistent loop: polls at a grid barrier before a block gives up
 };
 
 // ---------------------------------------------------------------------------
@@ -420,6 +424,10 @@ struct LevelReport {
     int64_t sel_launches = 0, sel_bytes = 0, bytes_model = 0;
     float sel_ms = 0.f;
     int32_t cluster = 0;   // blocks of the cluster that ran the level loop (0: graph or host loop)
+    // per refinement kernel (JET_K_*): launches, algorithmic bytes, CUDA-event ms (profiling only)
+    int64_t kern_launches[JET_KERNELS] = {};
+    int64_t kern_bytes[JET_KERNELS] = {};
+    float kern_ms[JET_KERNELS] = {};
 };
 
 // Pinned host buffer of a context: scalar readbacks in the first 4 KB (the

@@ -82,7 +82,7 @@ extern "C" int jet_lp_pass_noalloc(jet_ctx *ctx, int32_t n, const int64_t *xadj,
         return JET_EINVAL;
     }
     Ctx &c = ctx->c;
-    JET_CUDA_TRY(cudaSetDevice(c.device));
+    JET_TRY(use_device(c));
     char *scratch = nullptr;
     JET_TRY(noalloc_scratch(c.device, &scratch));
     if (n == 0) return JET_OK;

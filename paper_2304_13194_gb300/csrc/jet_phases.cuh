@@ -405,12 +405,12 @@ __device__ inline int32_t ph_controller(const Level &L) {
     // round trips overlap
     long long cut0 = 0, Llim = 0, best_cut0 = 0, best_maxw0 = 0, ncand = 0, degx = 0, nbnd = 0, nexam = 0,
               degexam = 0, dcut = 0, degm = 0;
-    int32_t it = 0, noimp0 = 0, best_bal0 = 0, kc = 0, weak = 0, hit_cap = 0, nX = 0, nM = 0;
+    int32_t it = 0, noimp0 = 0, best_bal0 = 0, kc = 0, weak = 0, hit_cap = 0, nX = 0, nM = 0, nA = 0;
     if (threadIdx.x == 0) {
         cut0 = ctl->cut; Llim = ctl->L; best_cut0 = ctl->best_cut; best_maxw0 = ctl->best_maxw;
         it = ctl->it; noimp0 = ctl->noimp; best_bal0 = ctl->best_bal; kc = ctl->kcount[kind];
         weak = ctl->weak; hit_cap = ctl->hit_cap;
-        nX = ctl->nX + ctl->nXh; nM = ctl->nM + ctl->nMh;
+        nX = ctl->nX + ctl->nXh; nM = ctl->nM + ctl->nMh; nA = ctl->nA;
         ncand = ctl->ncand; degx = ctl->degx; nbnd = ctl->nbnd; nexam = ctl->nexam; degexam = ctl->degexam;
         dcut = ld_gpu(&ctl->dcut); degm = ld_gpu(&ctl->degm);
     }
@@ -441,7 +441,7 @@ __device__ inline int32_t ph_controller(const Level &L) {
         ctl->copy_best = copy;
         if (it < kTrace && L.trace) {
             TraceRec r;
-            r.kind = kind; r.pad = 0;
+            r.kind = kind; r.flags = copy; r.na = kind == MODE_LP ? 0 : nA; r.pad = 0;
             r.nx = (kind == MODE_LP) ? (int64_t)nX : ncand;
             r.nm = nM;
             r.cut = cut; r.maxw = maxw;

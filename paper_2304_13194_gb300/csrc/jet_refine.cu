@@ -277,9 +277,10 @@ __global__ void __launch_bounds__(kClusterThreads, 1) k_refine_cluster(Level L) 
 // ---------------------------------------------------------------------------
 // one cooperative launch per level: every iteration in a single grid
 // ---------------------------------------------------------------------------
-// Polls of a block waiting at a grid barrier before it gives up (with a
-// sleep of ~64 ns between polls after the first few: about a second or
-// more, orders of magnitude above the longest phase).
+// Polls of a block waiting at a grid barrier before it gives up, unless the
+// context's options set another limit (with a sleep of ~64 ns between polls
+// after the first few: about a second or more, orders of magnitude above the
+// longest phase).
 constexpr long long kBarPollLimit = 1LL << 22;
 
 __device__ __forceinline__ uint32_t ld_volatile_u32(const uint32_t *p) { return *(const volatile uint32_t *)p; }
@@ -320,7 +321,7 @@ __device__ __forceinline__ bool grid_sync(const Level &L, Tail &&tail) {
     } else if (threadIdx.x == 0) {
         long long polls = 0;
         while (ld_volatile_u32(&ctl->bar_gen) == s_gen) {
-            if (++polls > kBarPollLimit) {
+            if (++polls > L.poll_limit) {
                 atomicExch(&ctl->bar_err, 1);
                 break;
             }
@@ -536,21 +537,66 @@ cudaError_t launch_dep(const Level &L, void (*kern)(Args...), int grid, int bloc
     return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
+// Per-kernel timing of the host-driven loop (JET_FLAG_PROFILE): a CUDA event
+// on the level's stream before every refinement kernel and one after the
+// iteration's last kernel; after the host's per-iteration synchronisation the
+// intervals are added to the kernels that ran in them.
+struct KernProf {
+    static constexpr int kMax = 16;
+    cudaEvent_t ev[kMax + 1] = {};
+    int kid[kMax] = {};
+    int cnt = 0;
+    float ms[JET_KERNELS] = {};
+    ~KernProf() {
+        for (cudaEvent_t e : ev)
+            if (e) cudaEventDestroy(e);
+    }
+    int init() {
+        for (cudaEvent_t &e : ev) JET_CUDA_TRY(cudaEventCreate(&e));
+        return JET_OK;
+    }
+    int mark(cudaStream_t s, int k) {
+        if (cnt >= kMax) return JET_EINVAL;
+        kid[cnt] = k;
+        JET_CUDA_TRY(cudaEventRecord(ev[cnt++], s));
+        return JET_OK;
+    }
+    int end(cudaStream_t s) {
+        JET_CUDA_TRY(cudaEventRecord(ev[cnt], s));
+        return JET_OK;
+    }
+    // after the stream has been synchronised
+    int collect() {
+        for (int i = 0; i < cnt; ++i) {
+            float t = 0.f;
+            JET_CUDA_TRY(cudaEventElapsedTime(&t, ev[i], ev[i + 1]));
+            ms[kid[i]] += t;
+        }
+        cnt = 0;
+        return JET_OK;
+    }
+};
+
+static inline int prof_mark(KernProf *pr, cudaStream_t s, int k) { return pr ? pr->mark(s, k) : JET_OK; }
+
 // Kernel sequences of one iteration, by kind.  Each returns, through *nk,
-// the number of kernels it enqueued.
-int enqueue_lp_select(const Level &L, cudaStream_t s, LpExport ex, int *nk) {
+// the number of kernels it enqueued; pr (host loop only) times each launch.
+int enqueue_lp_select(const Level &L, cudaStream_t s, LpExport ex, int *nk, KernProf *pr = nullptr) {
     int n = L.g.n;
     bool ew = L.g.ew != nullptr;
+    JET_TRY(prof_mark(pr, s, JET_K_LP_SCAN));
     k_lp_scan<<<scan_grid(n), kTB, sm_lp_scan(), s>>>(L);
     const size_t sm = sm_lp_select(L.k, kTB, L.nbig > 0);
+    JET_TRY(prof_mark(pr, s, JET_K_LP_SELECT));
     JET_CUDA_TRY(launch_dep(L, ew ? k_lp_select<true> : k_lp_select<false>, list_blocks(n), kTB, sm, s, L, ex));
     *nk = 2;
     JET_CUDA_TRY(cudaGetLastError());
     return JET_OK;
 }
 
-int enqueue_lp_after(const Level &L, cudaStream_t s, LpExport ex, int *nk) {
+int enqueue_lp_after(const Level &L, cudaStream_t s, LpExport ex, int *nk, KernProf *pr = nullptr) {
     int n = L.g.n;
+    JET_TRY(prof_mark(pr, s, JET_K_AFTERBURN));
     JET_CUDA_TRY(launch_dep(L, L.g.ew ? k_afterburn<true> : k_afterburn<false>, list_blocks(n), kTB, sm_afterburn(), s,
                             L, ex));
     *nk = 1;
@@ -558,26 +604,33 @@ int enqueue_lp_after(const Level &L, cudaStream_t s, LpExport ex, int *nk) {
     return JET_OK;
 }
 
-int enqueue_lp(const Level &L, cudaStream_t s, int *nk, LpExport ex = {nullptr, nullptr, nullptr}) {
+int enqueue_lp(const Level &L, cudaStream_t s, int *nk, LpExport ex = {nullptr, nullptr, nullptr},
+               KernProf *pr = nullptr) {
     int a = 0, b = 0;
-    JET_TRY(enqueue_lp_select(L, s, ex, &a));
-    JET_TRY(enqueue_lp_after(L, s, ex, &b));
+    JET_TRY(enqueue_lp_select(L, s, ex, &a, pr));
+    JET_TRY(enqueue_lp_after(L, s, ex, &b, pr));
     *nk = a + b;
     return JET_OK;
 }
 
 template <bool STRONG>
-int enqueue_rb_t(const Level &L, cudaStream_t s, int *nk) {
+int enqueue_rb_t(const Level &L, cudaStream_t s, int *nk, KernProf *pr) {
     int n = L.g.n;
     bool ew = L.g.ew != nullptr;
+    JET_TRY(prof_mark(pr, s, JET_K_RB_SCAN));
     k_rb_scan<STRONG><<<scan_grid(n), kTB, sm_rb_scan(), s>>>(L);
     const size_t sm = sm_rb_cand(L.k, kTB, L.nbig > 0);
+    JET_TRY(prof_mark(pr, s, JET_K_RB_CAND));
     JET_CUDA_TRY(launch_dep(L, ew ? k_rb_cand<true, STRONG> : k_rb_cand<false, STRONG>, list_blocks(n), kTB, sm, s, L));
+    JET_TRY(prof_mark(pr, s, JET_K_RB_TILEHIST));
     JET_CUDA_TRY(launch_dep(L, k_rb_tilehist, L.ntiles, kRbTile, sm_rb_tilehist(L.k), s, L));
+    JET_TRY(prof_mark(pr, s, JET_K_RB_TILESCAN));
     JET_CUDA_TRY(launch_dep(L, k_rb_tilescan, L.k, 1024, 0, s, L));
+    JET_TRY(prof_mark(pr, s, JET_K_RB_TAKE));
     JET_CUDA_TRY(launch_dep(L, k_rb_take<STRONG>, L.ntiles, kRbTile, sm_rb_take(L.k, kRbTile), s, L));
     *nk = 5;
     if (STRONG) {
+        JET_TRY(prof_mark(pr, s, JET_K_RB_COOKIE));
         JET_CUDA_TRY(launch_dep(L, k_rb_cookie, L.ntiles, kRbTile, sm_rb_cookie(kRbTile), s, L));
         *nk += 1;
     }
@@ -585,13 +638,14 @@ int enqueue_rb_t(const Level &L, cudaStream_t s, int *nk) {
     return JET_OK;
 }
 
-int enqueue_rb(const Level &L, cudaStream_t s, bool strong, int *nk) {
-    return strong ? enqueue_rb_t<true>(L, s, nk) : enqueue_rb_t<false>(L, s, nk);
+int enqueue_rb(const Level &L, cudaStream_t s, bool strong, int *nk, KernProf *pr = nullptr) {
+    return strong ? enqueue_rb_t<true>(L, s, nk, pr) : enqueue_rb_t<false>(L, s, nk, pr);
 }
 
 // apply + commit + controller
-int enqueue_tail(const Level &L, cudaStream_t s, int *nk) {
+int enqueue_tail(const Level &L, cudaStream_t s, int *nk, KernProf *pr = nullptr) {
     int ga = list_blocks(L.g.n);
+    JET_TRY(prof_mark(pr, s, JET_K_APPLY));
     if (L.g.ew) k_apply<true><<<ga, kTB, sm_apply(L.k), s>>>(L);
     else k_apply<false><<<ga, kTB, sm_apply(L.k), s>>>(L);
     *nk = 1;
@@ -651,48 +705,38 @@ struct EventPool {
 
 // Host-driven loop (JET_FLAG_HOSTLOOP / JET_FLAG_PROFILE): the mode is read
 // back after every iteration, as in the paper's implementation.  With
-// profiling, CUDA events bracket each Jetlp select step on the level's stream.
-int run_hostloop(Ctx &c, const Level &L, bool profile, float *sel_ms) {
-    EventPool pool;
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> marks;
+// profiling, CUDA events on the level's stream time every kernel launch;
+// kern_ms receives the sums per kernel.
+int run_hostloop(Ctx &c, const Level &L, bool profile, float *kern_ms) {
+    KernProf prof;
+    KernProf *pr = nullptr;
+    if (profile) {
+        JET_TRY(prof.init());
+        pr = &prof;
+    }
     for (;;) {
         int32_t mode = 0;
         JET_CUDA_TRY(cudaMemcpyAsync(c.pinned, &L.ctl->mode, 4, cudaMemcpyDeviceToHost, c.stream));
         JET_CUDA_TRY(cudaStreamSynchronize(c.stream));
+        if (pr) JET_TRY(pr->collect());
         memcpy(&mode, c.pinned, 4);
         if (mode == MODE_DONE) break;
         int nk = 0;
         if (mode == MODE_LP) {
             LpExport none{nullptr, nullptr, nullptr};
-            cudaEvent_t e0 = nullptr, e1 = nullptr;
-            if (profile) {
-                JET_TRY(pool.get(e0));
-                JET_TRY(pool.get(e1));
-                JET_CUDA_TRY(cudaEventRecord(e0, c.stream));
-            }
-            JET_TRY(enqueue_lp_select(L, c.stream, none, &nk));
-            c.launches += nk;
-            if (profile) {
-                JET_CUDA_TRY(cudaEventRecord(e1, c.stream));
-                marks.emplace_back(e0, e1);
-            }
-            JET_TRY(enqueue_lp_after(L, c.stream, none, &nk));
+            JET_TRY(enqueue_lp(L, c.stream, &nk, none, pr));
         } else {
-            JET_TRY(enqueue_rb(L, c.stream, mode == MODE_RS, &nk));
+            JET_TRY(enqueue_rb(L, c.stream, mode == MODE_RS, &nk, pr));
         }
         c.launches += nk;
-        JET_TRY(enqueue_tail(L, c.stream, &nk));
+        JET_TRY(enqueue_tail(L, c.stream, &nk, pr));
         c.launches += nk;
+        if (pr) JET_TRY(pr->end(c.stream));
     }
     JET_TRY(enqueue_final_copy(L, c.stream));
     c.launches += 1;
-    float tot = 0.f;
-    for (auto &m : marks) {
-        float t = 0.f;
-        JET_CUDA_TRY(cudaEventElapsedTime(&t, m.first, m.second));
-        tot += t;
-    }
-    if (sel_ms) *sel_ms = tot;
+    if (kern_ms)
+        for (int i = 0; i < JET_KERNELS; ++i) kern_ms[i] = prof.ms[i];
     return JET_OK;
 }
 
@@ -963,36 +1007,80 @@ static void fill_level_params(Ctx &c, Level &L, int32_t is_finest, uint64_t seed
     L.use_graph = 0;
     L.h_loop = L.h_mode = 0;
     L.pdl = (o.flags & JET_FLAG_NO_PDL) ? 0 : 1;
+    L.poll_limit = o.barrier_polls > 0 ? o.barrier_polls : kBarPollLimit;
 }
 
-// Algorithmic DRAM bytes of each pass, from the per-iteration trace (neighbour
-// gathers and scatters of part/prio/nxt/ext are taken as cache hits; beta =
-// bytes per CSR entry: 8 with edge weights, 4 without; "boundary" = ext > 0):
-//   Jetlp select   4 n + 4 nb + 28 w + beta deg(W) + 12 |X|
-//                  (ext of every vertex, lock stamp of the nb boundary
-//                   vertices; for the w listed ones: list write and read,
-//                   xadj pair, part, row; priority, P_d and list entry of X)
-//   afterburner    20 |X| + beta deg X + 8 |M|, plus 8 |X| to clear priorities
-//   rebalance      24 n + 16 c + 32 r + beta deg(R) (+ 16 n for Jetrs)
-//                  (part and key of every vertex, tile passes; ext, vwgt,
-//                   weighted degree or destination of the c candidates; list,
-//                   xadj pair, part, key, destination and row of the r listed)
-//   apply+commit   36 |M| + beta deg M + 16 k
-static void byte_model(const std::vector<TraceRec> &tr, const DGraph &g, int32_t k, uint32_t abl, LevelReport &rep) {
-    int64_t n = g.n, beta = g.ew ? 8 : 4;
-    bool ab = !(abl & (ABL_NO_AFTERBURN | ABL_BASELINE_LP));
+// Algorithmic DRAM bytes of each refinement kernel, from the per-iteration
+// trace: every array a kernel streams is counted once per launch over the
+// subset it touches; gathers and scatters at neighbours (part, prio, nxt,
+// mstamp, ext of u) are taken as cache hits.  beta = bytes per CSR entry (8
+// with edge weights, 4 without), n vertices, k parts, T rebalancing tiles,
+// nA oversized parts; w = rows the Jetlp select reads (unlocked boundary
+// vertices), nb = boundary vertices, c = rebalancing candidates, r = listed
+// candidates (rows read), deg(S) = total row length over S.
+//   lp_scan      4n + 4 nb + 4 w           ext of every vertex, lock stamp of the
+//                                          boundary ones, work-list writes
+//   lp_select    24 w + beta deg(W) + 12|X| list, xadj pair, part; rows; prio, nxt, X list
+//   afterburn    32|X| + beta deg(X) + 8|M|  X list, xadj pair, prio, nxt, part; rows;
+//                                          mstamp, M list (4|X| + 8|M| without afterburner)
+//   apply        36|M| + beta deg(M) + 16k  M list, nxt, vwgt, xadj pair, ext, part
+//                                          (+4|M| lock stamps and 8|X| priority resets
+//                                          after Jetlp); rows; part weights
+//   rb_scan      8n + 16c + 4r             part, bucket key; vwgt, ext, weighted degree
+//                                          and destination of candidates; work list
+//   rb_cand      28r (+4r Jetrw) + beta deg(R)  list, xadj pair, part, key (+ destination); rows
+//   rb_tilehist  4n + 4c + 4 T nA          key, vwgt of candidates, tile sums
+//   rb_tilescan  8 T nA                    tile sums read and written
+//   rb_take      4n + 4c + 4 T nA + 8|M|   key, vwgt, tile offsets; mstamp, M list
+//                (Jetrs: + 8n + 8T          evicted weight per vertex and per tile,
+//                 instead of the M list)
+//   rb_cookie    8n + 8T + 16|M|           evicted weight, tile offsets; part, nxt,
+//                                          mstamp, M list
+// plus 8n (read P_iter, write P_best) in the kernel that copies the best
+// partition, the afterburner (Jetlp) or rb_scan (rebalancing) of the
+// iteration after the controller asked for it (the copy after the level's
+// last iteration is not a refinement kernel).
+static void byte_model(const std::vector<TraceRec> &tr, const DGraph &g, int32_t k, int32_t ntiles, uint32_t abl,
+                       bool kernels, LevelReport &rep) {
+    const int64_t n = g.n, beta = g.ew ? 8 : 4, T = ntiles;
+    const bool ab = !(abl & (ABL_NO_AFTERBURN | ABL_BASELINE_LP));
+    int64_t *B = rep.kern_bytes;
+    bool copy_pending = false;   // ordered by the previous iteration's controller
     for (const TraceRec &r : tr) {
-        int64_t b = 36 * r.nm + beta * r.degm + 16 * (int64_t)k;
+        const int64_t cp = copy_pending ? 8 * n : 0;
         if (r.kind == MODE_LP) {
-            int64_t sel = 4 * n + 4 * r.nbnd + 28 * r.nexam + beta * r.degexam + 12 * r.nx;
-            rep.sel_bytes += sel;
+            const int64_t w = r.nexam, X = r.nx, M = r.nm;
+            const int64_t scan = 4 * n + 4 * r.nbnd + 4 * w;
+            const int64_t sel = 24 * w + beta * r.degexam + 12 * X;
+            B[JET_K_LP_SCAN] += scan;
+            B[JET_K_LP_SELECT] += sel;
+            B[JET_K_AFTERBURN] += cp + (ab ? 32 * X + beta * r.degx : 4 * X) + 8 * M;
+            B[JET_K_APPLY] += 40 * M + beta * r.degm + 16 * (int64_t)k + 8 * X;
+            rep.sel_bytes += scan + sel;
             rep.sel_launches += 1;
-            b += sel + (ab ? 20 * r.nx + beta * r.degx : 0) + 8 * r.nm + 8 * r.nx;
+            if (kernels)
+                for (int kk : {JET_K_LP_SCAN, JET_K_LP_SELECT, JET_K_AFTERBURN, JET_K_APPLY}) rep.kern_launches[kk] += 1;
         } else {
-            b += 24 * n + 16 * r.nx + 32 * r.nbnd + beta * r.degexam + (r.kind == MODE_RS ? 16 * n : 0);
+            const bool rs = r.kind == MODE_RS;
+            const int64_t c = r.nx, rr = r.nbnd, M = r.nm, tn = T * (int64_t)r.na;
+            B[JET_K_RB_SCAN] += cp + 8 * n + 16 * c + 4 * rr;
+            B[JET_K_RB_CAND] += (rs ? 28 : 32) * rr + beta * r.degexam;
+            B[JET_K_RB_TILEHIST] += 4 * n + 4 * c + 4 * tn;
+            B[JET_K_RB_TILESCAN] += 8 * tn;
+            B[JET_K_RB_TAKE] += 4 * n + 4 * c + 4 * tn + (rs ? 8 * n + 8 * T : 8 * M);
+            if (rs) B[JET_K_RB_COOKIE] += 8 * n + 8 * T + 16 * M;
+            B[JET_K_APPLY] += 36 * M + beta * r.degm + 16 * (int64_t)k;
+            if (kernels) {
+                for (int kk : {JET_K_RB_SCAN, JET_K_RB_CAND, JET_K_RB_TILEHIST, JET_K_RB_TILESCAN, JET_K_RB_TAKE,
+                               JET_K_APPLY})
+                    rep.kern_launches[kk] += 1;
+                if (rs) rep.kern_launches[JET_K_RB_COOKIE] += 1;
+            }
         }
-        rep.bytes_model += b;
+        copy_pending = (r.flags & 1) != 0;
     }
+    rep.bytes_model = 0;
+    for (int i = 0; i < JET_KERNELS; ++i) rep.bytes_model += B[i];
 }
 
 int refine_level(Ctx &c, const DGraph &g, int32_t k, double eps, int32_t is_finest, uint64_t seed,
@@ -1018,7 +1106,8 @@ int refine_level(Ctx &c, const DGraph &g, int32_t k, double eps, int32_t is_fine
     if (!hostloop) JET_TRY(pick_cluster(c, L, &csize));
     if (g.n > 0) {
         if (hostloop) {
-            JET_TRY(run_hostloop(c, L, (c.opt.flags & JET_FLAG_PROFILE) != 0, &rep.sel_ms));
+            JET_TRY(run_hostloop(c, L, (c.opt.flags & JET_FLAG_PROFILE) != 0, rep.kern_ms));
+            rep.sel_ms = rep.kern_ms[JET_K_LP_SCAN] + rep.kern_ms[JET_K_LP_SELECT];
         } else if (csize > 0) {
             JET_TRY(run_cluster(c, L, csize));
         } else {
@@ -1055,7 +1144,7 @@ int refine_level(Ctx &c, const DGraph &g, int32_t k, double eps, int32_t is_fine
     c.last_trace.rec.assign(ht, ht + std::max<int32_t>(nrec, 0));
     rep.iters = iters;
     for (int kd = 0; kd < 3; ++kd) rep.kinds[kd] = h.kcount[kd];
-    byte_model(c.last_trace.rec, g, k, L.abl, rep);
+    byte_model(c.last_trace.rec, g, k, L.ntiles, L.abl, csize == 0 && !grid, rep);
     if (rep_out) *rep_out = rep;
     if (cut_out) *cut_out = h.best_cut;
     if (maxw_out) *maxw_out = h.best_maxw;

@@ -3,7 +3,9 @@ library allocate device memory (a process whose memory is reserved by its own
 pool, a latency-bound loop where cudaMalloc/cudaFree would synchronise the
 device).  Its scratch is a fixed array inside the library, shared by all
 calls; this file checks, through the C ABI, that two calls in a row give
-exactly what jet_lp_pass gives, and that oversized inputs are refused.
+exactly what jet_lp_pass gives and what the oracle's Jetlp pass (Alg. 4)
+computes, that the calls make no device allocation, and that oversized
+inputs are refused.
 
 Named so that pytest collects it last."""
 import numpy as np
@@ -41,6 +43,18 @@ def _same(a, b):
         assert torch.equal(a[key], b[key]), key
 
 
+def _matches_oracle(got, g, vw, ew, k, part, locked, c):
+    og = graphgen.Graph(g.n, g.xadj, g.adjncy, vw, ew)
+    ref = oracle.jetlp(og, k, part, locked, c=c)
+    F = got["F"].cpu().numpy().astype(np.int64)
+    assert (F == np.where(ref["F"] == oracle.NONE, jet.NONE_GAIN, ref["F"])).all()
+    assert (got["Pd"].cpu().numpy() == ref["Pd"]).all()
+    inX = ref["inX"]
+    assert (got["inX"].cpu().numpy().astype(bool) == inX).all()
+    assert (got["F2"].cpu().numpy()[inX] == ref["F2"][inX]).all()
+    assert (got["inM"].cpu().numpy().astype(bool) == ref["inM"]).all()
+
+
 def test_noalloc_equals_lp_pass_on_two_calls_in_a_row(ctx):
     # call 1: weighted 3D mesh; call 2: R-MAT with rows > 16 (warp path) and
     # unit weights, a different size, so stale scratch from call 1 would show
@@ -53,7 +67,27 @@ def test_noalloc_equals_lp_pass_on_two_calls_in_a_row(ctx):
         ref = ctx.lp_pass(g.xadj, g.adjncy, vw, ew, k, part, locked, c=c)
         got = ctx.lp_pass_noalloc(g.xadj, g.adjncy, vw, ew, k, part, locked, c=c)
         _same(got, ref)
+        _matches_oracle(got, g, vw, ew, k, part, locked, c)
         assert int(got["inX"].sum()) > 0 and int(got["inM"].sum()) > 0
+
+
+def test_noalloc_makes_no_device_allocation(ctx):
+    g = graphgen.grid3d(30, 30, 20, vw=(1, 4), ew=(1, 10), seed=6)
+    part, locked = _inputs(g, 32, 7)
+    dev = torch.device("cuda", 0)
+    t = [torch.from_numpy(a).to(dev) for a in (g.xadj, g.adjncy, g.vwgt, g.adjwgt, part, locked)]
+    out = {"Pd": torch.empty(g.n, dtype=torch.int32, device=dev), "F": torch.empty(g.n, dtype=torch.int32, device=dev),
+           "inX": torch.empty(g.n, dtype=torch.uint8, device=dev), "F2": torch.empty(g.n, dtype=torch.int32, device=dev),
+           "inM": torch.empty(g.n, dtype=torch.uint8, device=dev)}
+    ctx.lp_pass_noalloc(*t[:4], 32, t[4], t[5], c=0.25, out=out)          # first call: address look-up
+    before = jet.binding.alloc_count()
+    for _ in range(2):
+        ctx.lp_pass_noalloc(*t[:4], 32, t[4], t[5], c=0.25, out=out)
+    assert jet.binding.alloc_count() == before
+    # the counter does move for the allocating entry point
+    ctx.lp_pass(*t[:4], 32, t[4], t[5], c=0.25)
+    assert jet.binding.alloc_count() > before
+    _matches_oracle(out, g, g.vwgt, g.adjwgt, 32, part, locked, 0.25)
 
 
 def test_noalloc_repeated_call_same_result(ctx):
