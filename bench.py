@@ -301,7 +301,10 @@ def run_probe(args):
     with jet.Context(0, flags=jet.FLAG_PROFILE) as ctx:
         _, cut, st = ctx.partition(*t, k=K_PARTS, eps=EPS, seed=SEED, return_stats=True)
     skip = sum(st.sel_launches[1:])
-    print(json.dumps({"probe": "lp_select", "cut": cut, "levels": st.levels, "n": st.n,
+    names = jet.kernel_names()
+    per_level = [{nm: [lv_l[i], round(lv_ms[i], 4)] for i, nm in enumerate(names) if lv_l[i]}
+                 for lv_l, lv_ms in zip(st.kern_launches, st.kern_ms)]
+    print(json.dumps({"probe": "kernels", "cut": cut, "levels": st.levels, "n": st.n, "kernels_per_level": per_level,
                       "iters": [a + b + c for a, b, c in zip(st.iters_lp, st.iters_rw, st.iters_rs)],
                       "ms_level": [round(x, 3) for x in st.ms_level], "sel_launches": st.sel_launches,
                       "sel_ms": [round(x, 4) for x in st.sel_ms], "sel_bytes": st.sel_bytes,

@@ -270,6 +270,21 @@ int uncoarsen(Ctx &c, const jet_hier *h, int32_t k, double eps, uint64_t seed, c
         for (auto &e : lev)
             if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); e = nullptr; }
     }
+    // every level is enqueued without a host wait (the host builds the next
+    // level's loop while the device refines this one); the control blocks are
+    // read after the finest level
+    struct Runs {
+        LevelRun r[JET_MAX_LEVELS];
+        int32_t lo = JET_MAX_LEVELS, hi = -1;
+        cudaStream_t s = nullptr;
+        bool done = false;
+        ~Runs() {
+            if (done || hi < lo) return;
+            cudaStreamSynchronize(s);
+            for (int32_t i = lo; i <= hi; ++i) refine_level_abandon(r[i]);
+        }
+    } runs;
+    runs.s = s;
     for (int32_t i = l; i >= 0; --i) {
         DGraph g = level_graph(i);
         if (st && lev[(size_t)i + 1]) cudaEventRecord(lev[(size_t)i + 1], s);
@@ -281,9 +296,25 @@ int uncoarsen(Ctx &c, const jet_hier *h, int32_t k, double eps, uint64_t seed, c
             cur = dst;
         }
         if (i == 0) cudaEventRecord(ev.e[2], s);
+        LevelRun &run = runs.r[i];
+        run.slot = i;
+        run.want_trace = i == 0;
+        runs.lo = std::min(runs.lo, i);
+        runs.hi = std::max(runs.hi, i);
+        JET_TRY(refine_level_enqueue(c, g, k, eps, i == 0, level_seed(seed, i), cur, W, run));
+    }
+    if (st && lev[0]) cudaEventRecord(lev[0], s);
+    cudaEventRecord(ev.e[3], s);
+    JET_CUDA_TRY(cudaStreamSynchronize(s));
+    runs.done = true;
+    int first_err = JET_OK;
+    for (int32_t i = l; i >= 0; --i) {
         LevelReport rep;
-        int r = refine_level(c, g, k, eps, i == 0, level_seed(seed, i), cur, &cut, &maxw, &rep, W);
-        if (r < 0) return r;
+        int r = refine_level_finish(c, runs.r[i], &cut, &maxw, &rep);
+        if (r < 0) {
+            if (first_err == JET_OK) first_err = r;
+            continue;
+        }
         status = r;
         int64_t m = h->nnz[i] / 2;
         edge_iters += (int64_t)rep.iters * m;
@@ -303,9 +334,7 @@ int uncoarsen(Ctx &c, const jet_hier *h, int32_t k, double eps, uint64_t seed, c
             }
         }
     }
-    if (st && lev[0]) cudaEventRecord(lev[0], s);
-    cudaEventRecord(ev.e[3], s);
-    JET_CUDA_TRY(cudaStreamSynchronize(s));
+    if (first_err != JET_OK) return first_err;
     if (st) {
         // level i ran between the events recorded at i + 1 and at i
         for (int32_t i = l; i >= 0; --i) {

@@ -141,7 +141,9 @@ struct Ctl {
     // persistent level loop: grid barrier (arrivals, generation) and the
     // flag a block sets when its bounded wait at a barrier ran out
     uint32_t bar_count, bar_gen;
-    int32_t bar_err, pad2;
+    int32_t bar_err;
+    int32_t nbig;        // vertices with rows longer than kSmallDeg (0: no per-warp tables needed)
+    int64_t kbytes[JET_KERNELS];   // algorithmic DRAM bytes per refinement kernel (byte model)
     // coarsening
     int32_t hem_stop;
     int32_t pad1;
@@ -165,7 +167,6 @@ struct Level {
     int32_t *rbloss;         // rebalancing loss export (single-pass API only; may be null)
     int32_t *listX, *listM;
     int32_t *listW;          // work list: vertices whose rows a pass must read
-    int32_t nbig;            // vertices with rows longer than kSmallDeg (0: no per-warp tables needed)
     // per-part state
     int64_t *pw;
     int32_t *aidx, *Bs;
@@ -430,13 +431,13 @@ struct LevelReport {
     float kern_ms[JET_KERNELS] = {};
 };
 
-// Pinned host buffer of a context: scalar readbacks in the first 4 KB (the
-// last int64 slot holds a level's long-row count), then a control block and a
-// level's trace, read back together at the end of a level.
+// Pinned host buffer of a context: scalar readbacks in the first 4 KB, then
+// one control block per level of an uncoarsening (copied back when the level
+// is enqueued, read after the last level), then the finest level's trace.
 constexpr size_t kPinnedScalarBytes = 4096;
-constexpr int kPinnedNbigSlot = (int)(kPinnedScalarBytes / 8) - 1;
+constexpr size_t kPinnedCtlStride = (sizeof(Ctl) + 255) & ~size_t(255);
 constexpr size_t kPinnedCtlOff = kPinnedScalarBytes;
-constexpr size_t kPinnedTraceOff = kPinnedCtlOff + ((sizeof(Ctl) + 255) & ~size_t(255));
+constexpr size_t kPinnedTraceOff = kPinnedCtlOff + kPinnedCtlStride * JET_MAX_LEVELS;
 constexpr size_t kPinnedBytes = kPinnedTraceOff + sizeof(TraceRec) * (size_t)kTrace;
 
 struct Ctx {
@@ -477,8 +478,27 @@ namespace jet {
 
 // ----- functions implemented in the .cu files ------------------------------
 // jet_refine.cu
-// W_known: the graph's total vertex weight when the caller knows it (every
-// level of a hierarchy has the same), else -1 (computed on the device).
+// One level of refinement enqueued on the context's stream without a host
+// wait (the host-driven loop excepted): its control block comes back into
+// pinned slot `slot` (and, with want_trace, its trace into the context's
+// trace area) once the stream gets there; refine_level_finish reads them
+// after the caller has synchronised the stream.
+struct LevelRun {
+    int32_t slot = 0;
+    bool want_trace = false;
+    DGraph g;
+    int32_t k = 0;
+    int32_t cluster = 0, grid = 0, hostloop = 0;
+    int nk_branch[3] = {0, 0, 0}, nk_tail = 0;
+    cudaGraphExec_t exec = nullptr;   // the level's CUDA-graph loop (destroyed by refine_level_finish)
+    LevelReport rep;                  // host-loop profile (kern_ms, sel_ms)
+};
+// W: the graph's total vertex weight (every level of a hierarchy has the same).
+int refine_level_enqueue(Ctx &c, const DGraph &g, int32_t k, double eps, int32_t is_finest, uint64_t seed,
+                         int32_t *part_inout, int64_t W, LevelRun &run);
+int refine_level_finish(Ctx &c, LevelRun &run, int64_t *cut_out, int64_t *maxw_out, LevelReport *rep);
+void refine_level_abandon(LevelRun &run);   // after an error: release what the run holds
+// Enqueue + synchronise + finish.  W_known: -1 = computed on the device.
 int refine_level(Ctx &c, const DGraph &g, int32_t k, double eps, int32_t is_finest, uint64_t seed,
                  int32_t *part_inout, int64_t *cut_out, int64_t *maxw_out, LevelReport *rep, int64_t W_known = -1);
 // Sum of the vertex weights (one device reduction and a readback).

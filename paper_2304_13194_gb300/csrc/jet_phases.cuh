@@ -378,6 +378,65 @@ __device__ __forceinline__ void reset_counters(Ctl *ctl) {
     ctl->nbnd = ctl->nexam = ctl->degexam = 0;
 }
 
+// Algorithmic DRAM bytes of one iteration's refinement kernels, from the
+// counters the iteration gathered: every array a kernel streams is counted
+// once per launch over the subset it touches; gathers and scatters at
+// neighbours (part, prio, nxt, mstamp, ext of u) are taken as cache hits.
+// beta = bytes per CSR entry (8 with edge weights, 4 without), n vertices,
+// k parts, T rebalancing tiles, nA oversized parts; w = rows the Jetlp select
+// reads (unlocked boundary vertices), nb = boundary vertices, c =
+// rebalancing candidates, r = listed candidates (rows read), deg(S) = total
+// row length over S.
+//   lp_scan      4n + 4 nb + 4 w           ext of every vertex, lock stamp of the
+//                                          boundary ones, work-list writes
+//   lp_select    24 w + beta deg(W) + 12|X| list, xadj pair, part; rows; prio, nxt, X list
+//   afterburn    32|X| + beta deg(X) + 8|M|  X list, xadj pair, prio, nxt, part; rows;
+//                                          mstamp, M list (4|X| + 8|M| without afterburner)
+//   apply        36|M| + beta deg(M) + 16k  M list, nxt, vwgt, xadj pair, ext, part
+//                                          (+4|M| lock stamps and 8|X| priority resets
+//                                          after Jetlp); rows; part weights
+//   rb_scan      8n + 16c + 4r             part, bucket key; vwgt, ext, weighted degree
+//                                          and destination of candidates; work list
+//   rb_cand      28r (+4r Jetrw) + beta deg(R)  list, xadj pair, part, key (+ destination); rows
+//   rb_tilehist  4n + 4c + 4 T nA          key, vwgt of candidates, tile sums
+//   rb_tilescan  8 T nA                    tile sums read and written
+//   rb_take      4n + 4c + 4 T nA + 8|M|   key, vwgt, tile offsets; mstamp, M list
+//                (Jetrs: + 8n + 8T          evicted weight per vertex and per tile,
+//                 instead of the M list)
+//   rb_cookie    8n + 8T + 16|M|           evicted weight, tile offsets; part, nxt,
+//                                          mstamp, M list
+// plus 8n (read P_iter, write P_best) in the kernel that copied the best
+// partition during this iteration (the afterburner for Jetlp, rb_scan for
+// rebalancing) when the previous controller asked for it; the copy after
+// the level's last iteration is not a refinement kernel.
+struct IterCounts {
+    int64_t nx, nm, degx, degm, nbnd, nexam, degexam, ncand, na;
+    bool copied;
+};
+__device__ __forceinline__ void iter_bytes(const Level &L, int32_t kind, const IterCounts &q, int64_t *b /* [JET_K_COUNT] */) {
+    const int64_t n = L.g.n, beta = L.g.ew ? 8 : 4, T = L.ntiles, k = L.k;
+    const int64_t cp = q.copied ? 8 * n : 0;
+    for (int i = 0; i < JET_K_COUNT; ++i) b[i] = 0;
+    if (kind == MODE_LP) {
+        const bool ab = !(L.abl & (ABL_NO_AFTERBURN | ABL_BASELINE_LP));
+        const int64_t w = q.nexam, X = q.nx, M = q.nm;
+        b[JET_K_LP_SCAN] = 4 * n + 4 * q.nbnd + 4 * w;
+        b[JET_K_LP_SELECT] = 24 * w + beta * q.degexam + 12 * X;
+        b[JET_K_AFTERBURN] = cp + (ab ? 32 * X + beta * q.degx : 4 * X) + 8 * M;
+        b[JET_K_APPLY] = 40 * M + beta * q.degm + 16 * k + 8 * X;
+    } else {
+        const bool rs = kind == MODE_RS;
+        const int64_t c = q.ncand, r = q.nbnd, M = q.nm, tn = T * q.na;
+        b[JET_K_RB_SCAN] = cp + 8 * n + 16 * c + 4 * r;
+        b[JET_K_RB_CAND] = (rs ? 28 : 32) * r + beta * q.degexam;
+        b[JET_K_RB_TILEHIST] = 4 * n + 4 * c + 4 * tn;
+        b[JET_K_RB_TILESCAN] = 8 * tn;
+        b[JET_K_RB_TAKE] = 4 * n + 4 * c + 4 * tn + (rs ? 8 * n + 8 * T : 8 * M);
+        if (rs) b[JET_K_RB_COOKIE] = 8 * n + 8 * T + 16 * M;
+        b[JET_K_APPLY] = 36 * M + beta * q.degm + 16 * k;
+    }
+}
+
 // End of an iteration (Alg. 3 after updatePartsAndDS), one block, after every
 // block of the apply phase: exact cut, max part weight, P_best / counters,
 // trace record, next mode, rebalancing classes for the next iteration.
@@ -405,14 +464,17 @@ __device__ inline int32_t ph_controller(const Level &L) {
     // round trips overlap
     long long cut0 = 0, Llim = 0, best_cut0 = 0, best_maxw0 = 0, ncand = 0, degx = 0, nbnd = 0, nexam = 0,
               degexam = 0, dcut = 0, degm = 0;
-    int32_t it = 0, noimp0 = 0, best_bal0 = 0, kc = 0, weak = 0, hit_cap = 0, nX = 0, nM = 0, nA = 0;
+    int32_t it = 0, noimp0 = 0, best_bal0 = 0, kc = 0, weak = 0, hit_cap = 0, nX = 0, nM = 0, nA = 0, copied = 0;
+    int64_t kb0[JET_K_COUNT];
     if (threadIdx.x == 0) {
         cut0 = ctl->cut; Llim = ctl->L; best_cut0 = ctl->best_cut; best_maxw0 = ctl->best_maxw;
         it = ctl->it; noimp0 = ctl->noimp; best_bal0 = ctl->best_bal; kc = ctl->kcount[kind];
         weak = ctl->weak; hit_cap = ctl->hit_cap;
-        nX = ctl->nX + ctl->nXh; nM = ctl->nM + ctl->nMh; nA = ctl->nA;
+        nX = ctl->nX + ctl->nXh; nM = ctl->nM + ctl->nMh; nA = ctl->nA; copied = ctl->copy_best;
         ncand = ctl->ncand; degx = ctl->degx; nbnd = ctl->nbnd; nexam = ctl->nexam; degexam = ctl->degexam;
         dcut = ld_gpu(&ctl->dcut); degm = ld_gpu(&ctl->degm);
+#pragma unroll
+        for (int i = 0; i < JET_K_COUNT; ++i) kb0[i] = ctl->kbytes[i];
     }
     long long maxw = block_max_pw(L.pw, L.k, sh, spw);
     if (threadIdx.x == 0) {
@@ -448,6 +510,14 @@ __device__ inline int32_t ph_controller(const Level &L) {
             r.degx = degx; r.degm = degm;
             r.nbnd = nbnd; r.nexam = nexam; r.degexam = degexam;
             L.trace[it] = r;
+        }
+        {
+            const IterCounts q{kind == MODE_LP ? (int64_t)nX : 0, nM, degx, degm, nbnd, nexam, degexam, ncand,
+                               kind == MODE_LP ? 0 : nA, copied != 0};
+            int64_t kb[JET_K_COUNT];
+            iter_bytes(L, kind, q, kb);
+#pragma unroll
+            for (int i = 0; i < JET_K_COUNT; ++i) ctl->kbytes[i] = kb0[i] + kb[i];
         }
         if (kind == MODE_LP) ctl->lp_epoch = it;
         ctl->kcount[kind] = kc + 1;
@@ -485,6 +555,7 @@ __device__ inline void ph_ctl_init(const Level &L, const int64_t *cut2) {
         ctl->copy_best = 0; ctl->hit_cap = 0; ctl->ticket = 0;
         ctl->bar_count = 0; ctl->bar_gen = 0; ctl->bar_err = 0;
         ctl->kcount[0] = ctl->kcount[1] = ctl->kcount[2] = ctl->kcount[3] = 0;
+        for (int i = 0; i < JET_KERNELS; ++i) ctl->kbytes[i] = 0;
         reset_counters(ctl);
         ctl->mode = choose_mode(L, maxw <= ctl->L);
     }
@@ -686,13 +757,14 @@ template <bool EW>
 __device__ inline void ph_lp_select(const Level &L, LpExport ex, Grid G, char *arena) {
     __shared__ long long red[40];
     Ctl *ctl = L.ctl;
-    const Deal dl(ctl->nW, G, L.nbig > 0);
+    const int32_t nbig = ctl->nbig;
+    const Deal dl(ctl->nW, G, nbig > 0);
     if (!dl.live(0)) return;
     int32_t *a32 = reinterpret_cast<int32_t *>(arena);
     JET_APPENDER(xapp, a32, kListCap);
     JET_APPENDER(bigs, a32 + kListCap, kBigCap);
     int32_t *tab = a32 + kListCap + kBigCap + (threadIdx.x >> 5) * L.k;
-    if (L.nbig > 0) {
+    if (nbig > 0) {
         for (int i = threadIdx.x; i < (int)(blockDim.x >> 5) * L.k; i += blockDim.x) a32[kListCap + kBigCap + i] = 0;
         __syncthreads();
     }
@@ -1301,14 +1373,15 @@ __device__ inline void ph_rb_cand(const Level &L, Grid G, char *arena) {
     __shared__ long long red[40];
     Ctl *ctl = L.ctl;
     const int32_t nB = ctl->nB;
-    const Deal dl(ctl->nW, G, L.nbig > 0);
+    const int32_t nbig = ctl->nbig;
+    const Deal dl(ctl->nW, G, nbig > 0);
     if (!dl.live(0)) return;
     SmemBuckets sb;
     sb.init(L, reinterpret_cast<long long *>(arena));
     int32_t *a32 = reinterpret_cast<int32_t *>(arena + kSmemBuckets * 8);
     JET_APPENDER(bigs, a32, kBigCap);
     int32_t *tab = a32 + kBigCap + (threadIdx.x >> 5) * L.k;
-    if (L.nbig > 0) {
+    if (nbig > 0) {
         for (int i = threadIdx.x; i < (int)(blockDim.x >> 5) * L.k; i += blockDim.x) a32[kBigCap + i] = 0;
         __syncthreads();
     }

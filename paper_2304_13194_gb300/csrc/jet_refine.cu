@@ -141,7 +141,18 @@ __device__ __forceinline__ void pdl_enter() {
     asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
-__global__ void __launch_bounds__(1024) k_ctl_init(Level L, const int64_t *cut2) { ph_ctl_init(L, cut2); }
+// Level start: the host-known limits into the control block, then its state
+// from the initial cut and part weights.
+__global__ void __launch_bounds__(1024) k_ctl_init(Level L, const int64_t *cut2, int64_t Llim, int64_t opt,
+                                                   int64_t sigma) {
+    if (threadIdx.x == 0) {
+        L.ctl->L = Llim;
+        L.ctl->opt = opt;
+        L.ctl->sigma = sigma;
+    }
+    __syncthreads();
+    ph_ctl_init(L, cut2);
+}
 
 // Sets the CUDA-graph conditionals for the first iteration.
 __global__ void k_graph_start(Level L) {
@@ -392,7 +403,8 @@ __global__ void __launch_bounds__(kTB, JET_ROW_MINB) k_refine_grid(Level L) {
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
-// Vertices with rows longer than kSmallDeg (only whether there are any matters).
+// Vertices with rows longer than kSmallDeg (only whether there are any
+// matters), counted into the level's control block.
 __global__ void k_count_big(DGraph g, int32_t *count) {
     int32_t v = blockIdx.x * blockDim.x + threadIdx.x;
     bool big = v < g.n && ld_xadj(g.xadj, (int64_t)v + 1) - ld_xadj(g.xadj, v) > kSmallDeg;
@@ -419,9 +431,7 @@ namespace {
 struct LevelBufs {
     DevBuf vert, part_, misc;
     Level L{};
-    int32_t nbig = 0;
     int64_t *cut2 = nullptr;
-    int32_t *nbig_dev = nullptr;
 };
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -429,9 +439,9 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 // Carves all per-level buffers out of two allocations.
 int allow_large_arenas(int device);
 
-// With defer_nbig the long-row count is copied to the context's pinned slot
-// and not waited for: the caller synchronises and sets L.nbig.
-int setup_level(Ctx &c, const DGraph &g, int32_t k, LevelBufs &B, bool defer_nbig = false) {
+// Buffers and start state of one level, enqueued on the context's stream (no
+// host wait): the control block gets the level's long-row count.
+int setup_level(Ctx &c, const DGraph &g, int32_t k, LevelBufs &B) {
     JET_TRY(allow_large_arenas(c.device));
     cudaStream_t s = c.stream;
     int64_t n = g.n;
@@ -458,7 +468,7 @@ int setup_level(Ctx &c, const DGraph &g, int32_t k, LevelBufs &B, bool defer_nbi
                     align256(kk) /*inB*/ + align256((kk + 1) * 8) /*capC*/ + align256(kk * 8) /*excess*/ +
                     align256(kk * kSlots * 8) /*bucketw*/ + align256(kk * 4) /*sstar*/ + align256(kk * 8) /*need*/ +
                     align256((size_t)ntiles * kk * 4) /*tilehist*/ + align256((size_t)ntiles * 8) /*tiletaken*/ +
-                    align256(sizeof(TraceRec) * kTrace) + align256(16) /*cut2*/ + align256(16) /*nbig*/;
+                    align256(sizeof(TraceRec) * kTrace) + align256(16) /*cut2*/;
     JET_TRY(dev_alloc(B.misc, mbytes, s));
     char *q = B.misc.as<char>();
     auto take = [&](size_t bytes) { char *r = q; q += align256(bytes); return r; };
@@ -476,28 +486,19 @@ int setup_level(Ctx &c, const DGraph &g, int32_t k, LevelBufs &B, bool defer_nbi
     L.tiletaken = reinterpret_cast<int64_t *>(take((size_t)ntiles * 8));
     L.trace = reinterpret_cast<TraceRec *>(take(sizeof(TraceRec) * kTrace));
     B.cut2 = reinterpret_cast<int64_t *>(take(16));
-    B.nbig_dev = reinterpret_cast<int32_t *>(take(16));
     L.ntiles = ntiles;
     L.g = g;
     L.k = k;
     JET_CUDA_TRY(cudaMemsetAsync(L.ctl, 0, sizeof(Ctl), s));
     JET_CUDA_TRY(cudaMemsetAsync(L.pw, 0, kk * 8, s));
     JET_CUDA_TRY(cudaMemsetAsync(B.cut2, 0, 16, s));
-    JET_CUDA_TRY(cudaMemsetAsync(B.nbig_dev, 0, 16, s));
     if (n > 0) {
-        k_count_big<<<grid_for(n, kTB), kTB, 0, s>>>(g, B.nbig_dev);
+        k_count_big<<<grid_for(n, kTB), kTB, 0, s>>>(g, &L.ctl->nbig);
         k_fill_i32<<<grid_for(n, kTB, 4096), kTB, 0, s>>>(L.lstamp, n, -2);
         k_fill_i32<<<grid_for(n, kTB, 4096), kTB, 0, s>>>(L.mstamp, n, -2);
         k_fill_i32<<<grid_for(n, kTB, 4096), kTB, 0, s>>>(L.prio, n, kNoneGain);
     }
     JET_CUDA_TRY(cudaGetLastError());
-    if (defer_nbig) {
-        JET_CUDA_TRY(cudaMemcpyAsync(&c.pinned[kPinnedNbigSlot], B.nbig_dev, 4, cudaMemcpyDeviceToHost, s));
-        return JET_OK;
-    }
-    JET_CUDA_TRY(cudaMemcpyAsync(&B.nbig, B.nbig_dev, 4, cudaMemcpyDeviceToHost, s));
-    JET_CUDA_TRY(cudaStreamSynchronize(s));
-    L.nbig = B.nbig;
     return JET_OK;
 }
 
@@ -586,7 +587,7 @@ int enqueue_lp_select(const Level &L, cudaStream_t s, LpExport ex, int *nk, Kern
     bool ew = L.g.ew != nullptr;
     JET_TRY(prof_mark(pr, s, JET_K_LP_SCAN));
     k_lp_scan<<<scan_grid(n), kTB, sm_lp_scan(), s>>>(L);
-    const size_t sm = sm_lp_select(L.k, kTB, L.nbig > 0);
+    const size_t sm = sm_lp_select(L.k, kTB, true);
     JET_TRY(prof_mark(pr, s, JET_K_LP_SELECT));
     JET_CUDA_TRY(launch_dep(L, ew ? k_lp_select<true> : k_lp_select<false>, list_blocks(n), kTB, sm, s, L, ex));
     *nk = 2;
@@ -619,7 +620,7 @@ int enqueue_rb_t(const Level &L, cudaStream_t s, int *nk, KernProf *pr) {
     bool ew = L.g.ew != nullptr;
     JET_TRY(prof_mark(pr, s, JET_K_RB_SCAN));
     k_rb_scan<STRONG><<<scan_grid(n), kTB, sm_rb_scan(), s>>>(L);
-    const size_t sm = sm_rb_cand(L.k, kTB, L.nbig > 0);
+    const size_t sm = sm_rb_cand(L.k, kTB, true);
     JET_TRY(prof_mark(pr, s, JET_K_RB_CAND));
     JET_CUDA_TRY(launch_dep(L, ew ? k_rb_cand<true, STRONG> : k_rb_cand<false, STRONG>, list_blocks(n), kTB, sm, s, L));
     JET_TRY(prof_mark(pr, s, JET_K_RB_TILEHIST));
@@ -660,27 +661,21 @@ int enqueue_final_copy(const Level &L, cudaStream_t s) {
     return JET_OK;
 }
 
-// Level start: part weights, cut, control block, P_best = P_0.
+// Level start: part weights, cut, control block, P_best = P_0 (no host wait).
 int enqueue_init(Ctx &c, LevelBufs &B, int64_t L_lim, int64_t opt, int64_t sigma) {
     cudaStream_t s = c.stream;
     Level &L = B.L;
     int64_t n = L.g.n;
-    // host-known constants go straight into the control block
-    int64_t consts[3] = {L_lim, opt, sigma};
-    static_assert(offsetof(Ctl, opt) == offsetof(Ctl, L) + 8 && offsetof(Ctl, sigma) == offsetof(Ctl, L) + 16, "layout");
-    JET_CUDA_TRY(cudaMemcpyAsync(&L.ctl->L, consts, sizeof(consts), cudaMemcpyHostToDevice, s));
     if (n > 0) {
         int gcut = std::min(list_grid(), grid_for(n, kTB));
         if (L.g.ew) k_cut_pw<true><<<gcut, kTB, sm_cut_pw(L.k), s>>>(L.g, L.k, L.part, L.pw, B.cut2, L.ext, L.wdeg);
         else k_cut_pw<false><<<gcut, kTB, sm_cut_pw(L.k), s>>>(L.g, L.k, L.part, L.pw, B.cut2, L.ext, L.wdeg);
         c.launches += 1;
     }
-    k_ctl_init<<<1, 1024, 0, s>>>(L, B.cut2);
+    k_ctl_init<<<1, 1024, 0, s>>>(L, B.cut2, L_lim, opt, sigma);
     c.launches += 1;
     if (n > 0) JET_CUDA_TRY(cudaMemcpyAsync(L.best, L.part, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
     JET_CUDA_TRY(cudaGetLastError());
-    // the consts memcpy source lives on this stack frame: make it complete
-    JET_CUDA_TRY(cudaStreamSynchronize(s));
     return JET_OK;
 }
 
@@ -743,10 +738,14 @@ int run_hostloop(Ctx &c, const Level &L, bool profile, float *kern_ms) {
 // Device-resident loop: graph = start kernel -> WHILE(h_loop) { SWITCH(h_mode)
 // {Jetlp | Jetrw | Jetrs} -> apply + commit + controller } -> final best copy.
 // nk_branch[3] / *nk_tail receive the kernel counts of the captured pieces.
-int run_graph(Ctx &c, Level L, int *nk_branch, int *nk_tail) {
+// The graph is launched on the context's stream and not waited for; *exec_out
+// receives the executable graph, which the caller destroys once the stream
+// has passed it.
+int run_graph(Ctx &c, Level L, int *nk_branch, int *nk_tail, cudaGraphExec_t *exec_out) {
     cudaStream_t s = c.stream;
     cudaGraph_t g = nullptr;
     cudaGraphExec_t ge = nullptr;
+    *exec_out = nullptr;
     int rc = JET_OK;
     cudaStream_t cap = nullptr;
     auto fail = [&](cudaError_t e, const char *what) {
@@ -815,9 +814,13 @@ int run_graph(Ctx &c, Level L, int *nk_branch, int *nk_tail) {
         if (e != cudaSuccess) { fail(e, "end capture tail"); break; }
         if ((e = cudaGraphInstantiate(&ge, g, 0)) != cudaSuccess) { fail(e, "cudaGraphInstantiate"); break; }
         if ((e = cudaGraphLaunch(ge, s)) != cudaSuccess) { fail(e, "cudaGraphLaunch"); break; }
-        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) { fail(e, "sync graph"); break; }
     } while (0);
-    if (ge) cudaGraphExecDestroy(ge);
+    if (rc == JET_OK) {
+        *exec_out = ge;
+    } else if (ge) {
+        cudaStreamSynchronize(s);
+        cudaGraphExecDestroy(ge);
+    }
     if (g) cudaGraphDestroy(g);
     if (cap) cudaStreamDestroy(cap);
     return rc;
@@ -1010,147 +1013,126 @@ static void fill_level_params(Ctx &c, Level &L, int32_t is_finest, uint64_t seed
     L.poll_limit = o.barrier_polls > 0 ? o.barrier_polls : kBarPollLimit;
 }
 
-// Algorithmic DRAM bytes of each refinement kernel, from the per-iteration
-// trace: every array a kernel streams is counted once per launch over the
-// subset it touches; gathers and scatters at neighbours (part, prio, nxt,
-// mstamp, ext of u) are taken as cache hits.  beta = bytes per CSR entry (8
-// with edge weights, 4 without), n vertices, k parts, T rebalancing tiles,
-// nA oversized parts; w = rows the Jetlp select reads (unlocked boundary
-// vertices), nb = boundary vertices, c = rebalancing candidates, r = listed
-// candidates (rows read), deg(S) = total row length over S.
-//   lp_scan      4n + 4 nb + 4 w           ext of every vertex, lock stamp of the
-//                                          boundary ones, work-list writes
-//   lp_select    24 w + beta deg(W) + 12|X| list, xadj pair, part; rows; prio, nxt, X list
-//   afterburn    32|X| + beta deg(X) + 8|M|  X list, xadj pair, prio, nxt, part; rows;
-//                                          mstamp, M list (4|X| + 8|M| without afterburner)
-//   apply        36|M| + beta deg(M) + 16k  M list, nxt, vwgt, xadj pair, ext, part
-//                                          (+4|M| lock stamps and 8|X| priority resets
-//                                          after Jetlp); rows; part weights
-//   rb_scan      8n + 16c + 4r             part, bucket key; vwgt, ext, weighted degree
-//                                          and destination of candidates; work list
-//   rb_cand      28r (+4r Jetrw) + beta deg(R)  list, xadj pair, part, key (+ destination); rows
-//   rb_tilehist  4n + 4c + 4 T nA          key, vwgt of candidates, tile sums
-//   rb_tilescan  8 T nA                    tile sums read and written
-//   rb_take      4n + 4c + 4 T nA + 8|M|   key, vwgt, tile offsets; mstamp, M list
-//                (Jetrs: + 8n + 8T          evicted weight per vertex and per tile,
-//                 instead of the M list)
-//   rb_cookie    8n + 8T + 16|M|           evicted weight, tile offsets; part, nxt,
-//                                          mstamp, M list
-// plus 8n (read P_iter, write P_best) in the kernel that copies the best
-// partition, the afterburner (Jetlp) or rb_scan (rebalancing) of the
-// iteration after the controller asked for it (the copy after the level's
-// last iteration is not a refinement kernel).
-static void byte_model(const std::vector<TraceRec> &tr, const DGraph &g, int32_t k, int32_t ntiles, uint32_t abl,
-                       bool kernels, LevelReport &rep) {
-    const int64_t n = g.n, beta = g.ew ? 8 : 4, T = ntiles;
-    const bool ab = !(abl & (ABL_NO_AFTERBURN | ABL_BASELINE_LP));
-    int64_t *B = rep.kern_bytes;
-    bool copy_pending = false;   // ordered by the previous iteration's controller
-    for (const TraceRec &r : tr) {
-        const int64_t cp = copy_pending ? 8 * n : 0;
-        if (r.kind == MODE_LP) {
-            const int64_t w = r.nexam, X = r.nx, M = r.nm;
-            const int64_t scan = 4 * n + 4 * r.nbnd + 4 * w;
-            const int64_t sel = 24 * w + beta * r.degexam + 12 * X;
-            B[JET_K_LP_SCAN] += scan;
-            B[JET_K_LP_SELECT] += sel;
-            B[JET_K_AFTERBURN] += cp + (ab ? 32 * X + beta * r.degx : 4 * X) + 8 * M;
-            B[JET_K_APPLY] += 40 * M + beta * r.degm + 16 * (int64_t)k + 8 * X;
-            rep.sel_bytes += scan + sel;
-            rep.sel_launches += 1;
-            if (kernels)
-                for (int kk : {JET_K_LP_SCAN, JET_K_LP_SELECT, JET_K_AFTERBURN, JET_K_APPLY}) rep.kern_launches[kk] += 1;
-        } else {
-            const bool rs = r.kind == MODE_RS;
-            const int64_t c = r.nx, rr = r.nbnd, M = r.nm, tn = T * (int64_t)r.na;
-            B[JET_K_RB_SCAN] += cp + 8 * n + 16 * c + 4 * rr;
-            B[JET_K_RB_CAND] += (rs ? 28 : 32) * rr + beta * r.degexam;
-            B[JET_K_RB_TILEHIST] += 4 * n + 4 * c + 4 * tn;
-            B[JET_K_RB_TILESCAN] += 8 * tn;
-            B[JET_K_RB_TAKE] += 4 * n + 4 * c + 4 * tn + (rs ? 8 * n + 8 * T : 8 * M);
-            if (rs) B[JET_K_RB_COOKIE] += 8 * n + 8 * T + 16 * M;
-            B[JET_K_APPLY] += 36 * M + beta * r.degm + 16 * (int64_t)k;
-            if (kernels) {
-                for (int kk : {JET_K_RB_SCAN, JET_K_RB_CAND, JET_K_RB_TILEHIST, JET_K_RB_TILESCAN, JET_K_RB_TAKE,
-                               JET_K_APPLY})
-                    rep.kern_launches[kk] += 1;
-                if (rs) rep.kern_launches[JET_K_RB_COOKIE] += 1;
-            }
-        }
-        copy_pending = (r.flags & 1) != 0;
-    }
-    rep.bytes_model = 0;
-    for (int i = 0; i < JET_KERNELS; ++i) rep.bytes_model += B[i];
-}
-
-int refine_level(Ctx &c, const DGraph &g, int32_t k, double eps, int32_t is_finest, uint64_t seed,
-                 int32_t *part_inout, int64_t *cut_out, int64_t *maxw_out, LevelReport *rep_out, int64_t W_known) {
-    LevelReport rep;
-    int64_t W = W_known;
-    if (W < 0) JET_TRY(total_vweight(c, g, W));
+int refine_level_enqueue(Ctx &c, const DGraph &g, int32_t k, double eps, int32_t is_finest, uint64_t seed,
+                         int32_t *part_inout, int64_t W, LevelRun &run) {
+    run.g = g;
+    run.k = k;
+    if (run.slot < 0 || run.slot >= JET_MAX_LEVELS) return JET_EINVAL;
     int64_t opt = 0;
     int64_t L_lim = balance_limit(W, k, eps, &opt);
     int64_t sigma = opt + (L_lim - opt) / 2;
     LevelBufs B;
-    JET_TRY(setup_level(c, g, k, B, /*defer_nbig=*/true));
+    JET_TRY(setup_level(c, g, k, B));
     c.launches += g.n > 0 ? 4 : 0;
     Level &L = B.L;
     L.part = part_inout;
     fill_level_params(c, L, is_finest, seed);
-    JET_TRY(enqueue_init(c, B, L_lim, opt, sigma));   // synchronises the stream
-    memcpy(&B.nbig, &c.pinned[kPinnedNbigSlot], 4);
-    L.nbig = B.nbig;
-    bool hostloop = (c.opt.flags & (JET_FLAG_HOSTLOOP | JET_FLAG_PROFILE)) != 0;
-    int nk_branch[3] = {0, 0, 0}, nk_tail = 0;
-    int csize = 0, grid = 0;
-    if (!hostloop) JET_TRY(pick_cluster(c, L, &csize));
+    JET_TRY(enqueue_init(c, B, L_lim, opt, sigma));
+    run.hostloop = (c.opt.flags & (JET_FLAG_HOSTLOOP | JET_FLAG_PROFILE)) != 0;
+    if (!run.hostloop) JET_TRY(pick_cluster(c, L, &run.cluster));
     if (g.n > 0) {
-        if (hostloop) {
-            JET_TRY(run_hostloop(c, L, (c.opt.flags & JET_FLAG_PROFILE) != 0, rep.kern_ms));
-            rep.sel_ms = rep.kern_ms[JET_K_LP_SCAN] + rep.kern_ms[JET_K_LP_SELECT];
-        } else if (csize > 0) {
-            JET_TRY(run_cluster(c, L, csize));
+        if (run.hostloop) {
+            JET_TRY(run_hostloop(c, L, (c.opt.flags & JET_FLAG_PROFILE) != 0, run.rep.kern_ms));
+            run.rep.sel_ms = run.rep.kern_ms[JET_K_LP_SCAN] + run.rep.kern_ms[JET_K_LP_SELECT];
+        } else if (run.cluster > 0) {
+            JET_TRY(run_cluster(c, L, run.cluster));
         } else {
-            if (c.opt.flags & JET_FLAG_GRID_LOOP) JET_TRY(run_grid(c, L, &grid));
-            if (!grid) JET_TRY(run_graph(c, L, nk_branch, &nk_tail));
+            if (c.opt.flags & JET_FLAG_GRID_LOOP) JET_TRY(run_grid(c, L, &run.grid));
+            if (!run.grid) JET_TRY(run_graph(c, L, run.nk_branch, &run.nk_tail, &run.exec));
         }
         JET_CUDA_TRY(cudaMemcpyAsync(part_inout, L.best, (size_t)g.n * 4, cudaMemcpyDeviceToDevice, c.stream));
     }
-    // the control block and the whole trace in one round trip
+    // the control block (and the trace) come back when the stream gets here;
+    // the level's buffers are released in stream order after these copies
     char *pin = reinterpret_cast<char *>(c.pinned);
-    JET_CUDA_TRY(cudaMemcpyAsync(pin + kPinnedCtlOff, L.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, c.stream));
-    JET_CUDA_TRY(cudaMemcpyAsync(pin + kPinnedTraceOff, L.trace, sizeof(TraceRec) * (size_t)kTrace,
+    JET_CUDA_TRY(cudaMemcpyAsync(pin + kPinnedCtlOff + kPinnedCtlStride * (size_t)run.slot, L.ctl, sizeof(Ctl),
                                  cudaMemcpyDeviceToHost, c.stream));
-    JET_CUDA_TRY(cudaStreamSynchronize(c.stream));
+    if (run.want_trace)
+        JET_CUDA_TRY(cudaMemcpyAsync(pin + kPinnedTraceOff, L.trace, sizeof(TraceRec) * (size_t)kTrace,
+                                     cudaMemcpyDeviceToHost, c.stream));
+    return JET_OK;
+}
+
+void refine_level_abandon(LevelRun &run) {
+    if (run.exec) {
+        cudaGraphExecDestroy(run.exec);   // an executable graph still in flight is released on completion
+        run.exec = nullptr;
+    }
+}
+
+int refine_level_finish(Ctx &c, LevelRun &run, int64_t *cut_out, int64_t *maxw_out, LevelReport *rep_out) {
+    refine_level_abandon(run);
+    const char *pin = reinterpret_cast<const char *>(c.pinned);
     Ctl h;
-    memcpy(&h, pin + kPinnedCtlOff, sizeof(Ctl));
+    memcpy(&h, pin + kPinnedCtlOff + kPinnedCtlStride * (size_t)run.slot, sizeof(Ctl));
     if (h.bar_err) {
         record_error("refinement: a grid barrier wait of the persistent level loop ran out");
         return JET_ETIMEOUT;
     }
-    int32_t iters = h.it;
-    if (!hostloop && g.n > 0) {
-        if (csize > 0 || grid) {
+    LevelReport rep = run.rep;
+    const int32_t iters = h.it;
+    const bool kernels = run.cluster == 0 && !run.grid;
+    if (!run.hostloop && run.g.n > 0) {
+        if (!kernels) {
             c.launches += 1;  // the cluster or cooperative kernel
         } else {
             c.launches += 2;  // start kernel, final copy
-            for (int kd = 0; kd < 3; ++kd) c.launches += (int64_t)h.kcount[kd] * (nk_branch[kd] + nk_tail);
+            for (int kd = 0; kd < 3; ++kd) c.launches += (int64_t)h.kcount[kd] * (run.nk_branch[kd] + run.nk_tail);
         }
     }
-    rep.cluster = csize;
-    c.last_trace.iters = iters;
-    const int32_t nrec = std::min<int32_t>(iters, kTrace);
-    const TraceRec *ht = reinterpret_cast<const TraceRec *>(pin + kPinnedTraceOff);
-    c.last_trace.rec.assign(ht, ht + std::max<int32_t>(nrec, 0));
+    rep.cluster = run.cluster;
     rep.iters = iters;
     for (int kd = 0; kd < 3; ++kd) rep.kinds[kd] = h.kcount[kd];
-    byte_model(c.last_trace.rec, g, k, L.ntiles, L.abl, csize == 0 && !grid, rep);
+    // launches per refinement kernel (one per iteration of its kind) and the
+    // byte model the controllers accumulated
+    if (kernels && run.g.n > 0) {
+        const int32_t lp = h.kcount[MODE_LP], rw = h.kcount[MODE_RW], rs = h.kcount[MODE_RS];
+        for (int kk : {JET_K_LP_SCAN, JET_K_LP_SELECT, JET_K_AFTERBURN}) rep.kern_launches[kk] = lp;
+        for (int kk : {JET_K_RB_SCAN, JET_K_RB_CAND, JET_K_RB_TILEHIST, JET_K_RB_TILESCAN, JET_K_RB_TAKE})
+            rep.kern_launches[kk] = rw + rs;
+        rep.kern_launches[JET_K_RB_COOKIE] = rs;
+        rep.kern_launches[JET_K_APPLY] = lp + rw + rs;
+    }
+    rep.bytes_model = 0;
+    for (int i = 0; i < JET_K_COUNT; ++i) {
+        rep.kern_bytes[i] = h.kbytes[i];
+        rep.bytes_model += h.kbytes[i];
+    }
+    rep.sel_bytes = h.kbytes[JET_K_LP_SCAN] + h.kbytes[JET_K_LP_SELECT];
+    rep.sel_launches = h.kcount[MODE_LP];
+    if (run.want_trace) {
+        c.last_trace.iters = iters;
+        const int32_t nrec = std::min<int32_t>(iters, kTrace);
+        const TraceRec *ht = reinterpret_cast<const TraceRec *>(pin + kPinnedTraceOff);
+        c.last_trace.rec.assign(ht, ht + std::max<int32_t>(nrec, 0));
+    }
     if (rep_out) *rep_out = rep;
     if (cut_out) *cut_out = h.best_cut;
     if (maxw_out) *maxw_out = h.best_maxw;
     if (!h.best_bal) return JET_WUNBALANCED;
     if (h.hit_cap) return JET_WITERLIMIT;
     return JET_OK;
+}
+
+int refine_level(Ctx &c, const DGraph &g, int32_t k, double eps, int32_t is_finest, uint64_t seed,
+                 int32_t *part_inout, int64_t *cut_out, int64_t *maxw_out, LevelReport *rep_out, int64_t W_known) {
+    int64_t W = W_known;
+    if (W < 0) JET_TRY(total_vweight(c, g, W));
+    LevelRun run;
+    run.slot = 0;
+    run.want_trace = true;
+    int r = refine_level_enqueue(c, g, k, eps, is_finest, seed, part_inout, W, run);
+    if (r < 0) {
+        refine_level_abandon(run);
+        return r;
+    }
+    cudaError_t e = cudaStreamSynchronize(c.stream);
+    if (e != cudaSuccess) {
+        record_cuda_error(e, "refine: synchronise", __FILE__, __LINE__);
+        refine_level_abandon(run);
+        return JET_ECUDA;
+    }
+    return refine_level_finish(c, run, cut_out, maxw_out, rep_out);
 }
 
 // ---- single passes --------------------------------------------------------
@@ -1323,8 +1305,7 @@ int lp_pass_in_scratch(Ctx &c, const DGraph &g, int32_t k, const int32_t *part, 
     L.listW = take32();
     L.ctl = reinterpret_cast<Ctl *>(p);
     p += align256c(sizeof(Ctl));
-    int32_t *nbig_dev = reinterpret_cast<int32_t *>(p);
-    p += 256;
+    p += 256;   // spare
     L.pw = reinterpret_cast<int64_t *>(p);
     p += align256c((size_t)JET_MAX_K * 8);
     int64_t *cut2 = reinterpret_cast<int64_t *>(p);
@@ -1333,7 +1314,6 @@ int lp_pass_in_scratch(Ctx &c, const DGraph &g, int32_t k, const int32_t *part, 
     L.abl = flags & ABL_ALL;
     // the array keeps the previous call's contents: clear what must start at zero
     JET_CUDA_TRY(cudaMemsetAsync(L.ctl, 0, sizeof(Ctl), s));
-    JET_CUDA_TRY(cudaMemsetAsync(nbig_dev, 0, 16, s));
     JET_CUDA_TRY(cudaMemsetAsync(L.pw, 0, (size_t)k * 8, s));
     JET_CUDA_TRY(cudaMemsetAsync(cut2, 0, 16, s));
     {
@@ -1341,15 +1321,12 @@ int lp_pass_in_scratch(Ctx &c, const DGraph &g, int32_t k, const int32_t *part, 
         if (g.ew) k_cut_pw<true><<<gcut, kTB, sm_cut_pw(k), s>>>(g, k, L.part, L.pw, cut2, L.ext, nullptr);
         else k_cut_pw<false><<<gcut, kTB, sm_cut_pw(k), s>>>(g, k, L.part, L.pw, cut2, L.ext, nullptr);
     }
-    k_count_big<<<grid_for(g.n, kTB), kTB, 0, s>>>(g, nbig_dev);
+    k_count_big<<<grid_for(g.n, kTB), kTB, 0, s>>>(g, &L.ctl->nbig);
     k_fill_i32<<<grid_for(g.n, kTB, 4096), kTB, 0, s>>>(L.mstamp, g.n, -2);
     k_fill_i32<<<grid_for(g.n, kTB, 4096), kTB, 0, s>>>(L.prio, g.n, kNoneGain);
     k_locks_from_mask<<<grid_for(g.n, kTB, 4096), kTB, 0, s>>>(locked, L.lstamp, g.n);
     k_set_epoch<<<1, 1, 0, s>>>(L.ctl, 0, MODE_LP);
     JET_CUDA_TRY(cudaGetLastError());
-    JET_CUDA_TRY(cudaMemcpyAsync(c.pinned, nbig_dev, 4, cudaMemcpyDeviceToHost, s));
-    JET_CUDA_TRY(cudaStreamSynchronize(s));
-    L.nbig = (int32_t)(c.pinned[0] & 0xFFFFFFFF);
     LpExport ex{pd_out ? pd_out : tmp_pd, gain_out ? gain_out : tmp_gain, f2_out};
     if (f2_out) JET_CUDA_TRY(cudaMemsetAsync(f2_out, 0, nn * 4, s));
     JET_CUDA_TRY(cudaMemcpyAsync(ex.pd, part, nn * 4, cudaMemcpyDeviceToDevice, s));
