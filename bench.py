@@ -66,7 +66,7 @@ def parse_args(argv=None):
                    help="run one profiled partition and report per-level select launches (profiler target)")
     p.add_argument("--rmat-k", type=int, default=None, help="with --sweep rmat: only this k")
     p.add_argument("--two-hop", action="store_true", help="with --sweep rmat: coarsen with two-hop matches")
-    p.add_argument("--sweep", choices=["lp_versions", "batched", "rmat"], default=None,
+    p.add_argument("--sweep", choices=["lp_versions", "batched", "rmat", "shapes"], default=None,
                    help="the Jetlp versions of the paper's component study and the phi trade-off, on the "
                         "mesh, power-law and large-grid workloads (one JSON line per run and a summary)")
     return p.parse_args(argv)
@@ -635,13 +635,13 @@ def run_batched(args):
         torch.cuda.synchronize()
         t_b = time.perf_counter() - t0
         same = all(o[1] == c for o, c in zip(out, seq))
-        print(json.dumps({"sweep": "batched", "mode": "autotuned", "cluster_max_n": rep["cluster_max_n"],
-                          "cluster_blocks": rep["cluster_blocks"],
-                          "workers": rep["workers"], "tune_seconds": round(t_tune, 3), "graphs": len(items),
+        chosen = {k: v for k, v in rep.items() if k not in ("candidates", "parts")}
+        print(json.dumps({"sweep": "batched", "mode": "autotuned", "chosen": chosen,
+                          "tune_seconds": round(t_tune, 3), "graphs": len(items),
                           "seconds": round(t_b, 4), "speedup_vs_sequential": round(t_seq / t_b, 3),
                           "cuts_equal_to_sequential": same,
-                          "candidates": [[c["cluster_blocks"], c["cluster_max_n"], c["workers"], round(c["ms"], 2)]
-                                         for c in rep["candidates"]]}), flush=True)
+                          "candidates": [[c["stage"], c["value"], round(c["ms"], 2)] for c in rep["candidates"]]}),
+              flush=True)
     return 0
 
 
@@ -678,10 +678,54 @@ def run_rmat(args):
     return 0
 
 
+SHAPE_CANDIDATES = [("list_blocks_per_sm", (2, 8)), ("apply_blocks_per_sm", (1, 2)),
+                    ("list_items_per_block", (32, 128, 256)), ("scan_blocks_per_sm", (4, 16)),
+                    ("hub_degree", (256, 4096))]
+
+
+def run_shapes(args):
+    """Launch shapes of the refinement kernels, one option at a time from the
+    defaults, on the mesh and the power-law workloads: median refinement ms
+    of three partitions after one warm-up (CUDA-graph loop), cut checked
+    against the default's (execution choices never change results)."""
+    import torch
+    import graphgen
+    import paper_2304_13194_gb300 as jet
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    for gname, g in (("grid3d_128_w", workload_graph(128)), ("rmat22", graphgen.rmat(22, seed=SEED))):
+        t = [torch.from_numpy(a).to(dev) if a is not None else None for a in (g.xadj, g.adjncy, g.vwgt, g.adjwgt)]
+        if gname == "rmat22":
+            t[2] = t[3] = None
+        runs = [("default", None, 0)] + [(opt, opt, v) for opt, vals in SHAPE_CANDIDATES for v in vals]
+        ref_cut = None
+        for label, opt, val in runs:
+            kw = {opt: val} if opt else {}
+            with jet.Context(0, **kw) as ctx:
+                ctx.partition(*t, k=K_PARTS, eps=EPS, seed=SEED)
+                res = []
+                for _ in range(3):
+                    flush.zero_()
+                    res.append(ctx.partition(*t, k=K_PARTS, eps=EPS, seed=SEED, return_stats=True))
+            cut = res[0][1]
+            if ref_cut is None:
+                ref_cut = cut
+            ms = sorted(r[2].ms_refine for r in res)[1]
+            tot = sorted(r[2].ms_total for r in res)[1]
+            print(json.dumps({"sweep": "shapes", "graph": gname, "option": label, "value": val,
+                              "refine_ms": round(ms, 3), "total_ms": round(tot, 3), "cut": cut,
+                              "cut_equal": cut == ref_cut}), flush=True)
+        del t
+    return 0
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.sweep == "batched":
         return run_batched(args)
+    if args.sweep == "shapes":
+        return run_shapes(args)
     if args.sweep == "rmat":
         return run_rmat(args)
     if args.impl == "reference":

@@ -103,7 +103,16 @@ extern "C" {
  *   barrier_polls = 0               polls a block of the persistent level loop (JET_FLAG_GRID_LOOP)
  *                                   makes at a grid barrier before it gives up and the call returns
  *                                   JET_ETIMEOUT; 0 = 2^22 (about a second or more, far above any
- *                                   phase); small values make the wait run out on purpose (tests) */
+ *                                   phase); small values make the wait run out on purpose (tests)
+ *   launch shapes of the refinement kernels (0 = the default in brackets; jet_autotune picks them):
+ *   list_blocks_per_sm [4]          most blocks per SM of the list kernels (select, afterburner,
+ *                                   rebalancing rows)
+ *   list_items_per_block [64]       list entries per block below that cap
+ *   apply_blocks_per_sm [list]      most blocks per SM of the apply kernel
+ *   scan_blocks_per_sm [8]          most blocks per SM of the two scan kernels
+ *   hub_degree [1024]               rows longer than this are taken by a whole block (shorter
+ *                                   rows above 16 entries by one warp, up to 16 by one thread);
+ *                                   0 or at least 32 */
 typedef struct {
     double c_fine, c_coarse, phi;
     int32_t max_no_improve, weak_limit, coarsen_target, max_levels, max_iters_per_level, hem_rounds;
@@ -111,6 +120,7 @@ typedef struct {
     int32_t cluster_max_n;
     int32_t cluster_blocks;
     int32_t barrier_polls;
+    int32_t list_blocks_per_sm, list_items_per_block, apply_blocks_per_sm, scan_blocks_per_sm, hub_degree;
 } jet_options;
 
 /* Refinement kernels (one launch each per iteration of the CUDA-graph or host
@@ -260,22 +270,37 @@ int jet_partition_batch(jet_ctx *ctx, int32_t count, jet_batch_item *items, int3
 /* Autotuner of the execution choices (no counterpart in the paper; results
  * are bit-identical under every choice).  Times `items` (a batch, or one
  * graph with count = 1) with jet_partition_batch under each candidate, one
- * choice at a time, each stage keeping the best of the earlier ones:
- * cluster_blocks in {16, 8, 4, 2} (at cluster_max_n 4096), then
- * cluster_max_n in {0, 1024, 2048, 4096, 8192, 16384} (the largest level that
- * runs its whole refinement loop in one thread-block-cluster launch), then,
- * for count > 1, workers in {1, 2, 4, 8, 16} — taking the median of `reps`
- * timed runs (reps <= 0: 3) after one untimed run, and writes the fastest
- * cluster_blocks and cluster_max_n into the context's options.  The items' outputs
- * hold the last run's results.  report (may be NULL) lists every candidate. */
-#define JET_TUNE_MAX_CAND 16
+ * choice (stage) at a time, each stage keeping the best of the earlier ones:
+ *   JET_TUNE_CLUSTER_BLOCKS  cluster_blocks in {16, 8, 4, 2} (at cluster_max_n 4096)
+ *   JET_TUNE_CLUSTER_MAX_N   cluster_max_n in {0, 1024, 2048, 4096, 8192, 16384} (the largest
+ *                            level that runs its whole refinement loop in one cluster launch)
+ *   JET_TUNE_WORKERS         workers in {1, 2, 4, 8, 16} (count > 1 only)
+ *   JET_TUNE_LIST_BLOCKS     list_blocks_per_sm in {2, 4, 8}
+ *   JET_TUNE_APPLY_BLOCKS    apply_blocks_per_sm in {1, 2, 4}
+ *   JET_TUNE_LIST_ITEMS      list_items_per_block in {32, 64, 128}
+ *   JET_TUNE_SCAN_BLOCKS     scan_blocks_per_sm in {4, 8, 16}
+ *   JET_TUNE_HUB_DEGREE      hub_degree in {256, 1024, 4096} (the degree threshold of the
+ *                            block-per-row schedule)
+ * — taking the median of `reps` timed runs (reps <= 0: 3) after one untimed
+ * run, and writes every chosen option into the context's options.  The
+ * items' outputs hold the last run's results.  report (may be NULL) lists
+ * every candidate. */
+#define JET_TUNE_MAX_CAND 48
+#define JET_TUNE_CLUSTER_BLOCKS 0
+#define JET_TUNE_CLUSTER_MAX_N 1
+#define JET_TUNE_WORKERS 2
+#define JET_TUNE_LIST_BLOCKS 3
+#define JET_TUNE_APPLY_BLOCKS 4
+#define JET_TUNE_LIST_ITEMS 5
+#define JET_TUNE_SCAN_BLOCKS 6
+#define JET_TUNE_HUB_DEGREE 7
 typedef struct {
-    int32_t cluster_max_n;                  /* chosen (now in the context's options) */
-    int32_t cluster_blocks;                 /* chosen (now in the context's options) */
-    int32_t workers;                        /* chosen worker count for jet_partition_batch */
+    /* chosen values (all but workers are now in the context's options) */
+    int32_t cluster_max_n, cluster_blocks, workers;
+    int32_t list_blocks_per_sm, apply_blocks_per_sm, list_items_per_block, scan_blocks_per_sm, hub_degree;
     int32_t ncand;                          /* candidates timed */
-    int32_t cand_cluster_max_n[JET_TUNE_MAX_CAND], cand_cluster_blocks[JET_TUNE_MAX_CAND],
-        cand_workers[JET_TUNE_MAX_CAND];
+    int32_t cand_stage[JET_TUNE_MAX_CAND];  /* JET_TUNE_* of the stage */
+    int32_t cand_value[JET_TUNE_MAX_CAND];  /* the value timed */
     float cand_ms[JET_TUNE_MAX_CAND];       /* median host wall time of the whole batch */
 } jet_tune_report;
 int jet_autotune(jet_ctx *ctx, int32_t count, jet_batch_item *items, int32_t reps, jet_tune_report *report);

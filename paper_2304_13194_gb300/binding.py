@@ -58,7 +58,9 @@ class Options(ctypes.Structure):
                 ("coarsen_target", ctypes.c_int32), ("max_levels", ctypes.c_int32),
                 ("max_iters_per_level", ctypes.c_int32), ("hem_rounds", ctypes.c_int32),
                 ("flags", ctypes.c_uint32), ("cluster_max_n", ctypes.c_int32), ("cluster_blocks", ctypes.c_int32),
-                ("barrier_polls", ctypes.c_int32)]
+                ("barrier_polls", ctypes.c_int32), ("list_blocks_per_sm", ctypes.c_int32),
+                ("list_items_per_block", ctypes.c_int32), ("apply_blocks_per_sm", ctypes.c_int32),
+                ("scan_blocks_per_sm", ctypes.c_int32), ("hub_degree", ctypes.c_int32)]
 
     @classmethod
     def default(cls, **kw) -> "Options":
@@ -256,12 +258,18 @@ class _BatchItem(ctypes.Structure):
                 ("status", ctypes.c_int32), ("ms", ctypes.c_float)]
 
 
+TUNE_MAX_CAND = 48
+TUNE_STAGES = ["cluster_blocks", "cluster_max_n", "workers", "list_blocks_per_sm", "apply_blocks_per_sm",
+               "list_items_per_block", "scan_blocks_per_sm", "hub_degree"]   # JET_TUNE_* order
+
+
 class _TuneReport(ctypes.Structure):
     """jet_tune_report."""
-    _fields_ = [("cluster_max_n", ctypes.c_int32), ("cluster_blocks", ctypes.c_int32), ("workers", ctypes.c_int32),
-                ("ncand", ctypes.c_int32), ("cand_cluster_max_n", ctypes.c_int32 * 16),
-                ("cand_cluster_blocks", ctypes.c_int32 * 16), ("cand_workers", ctypes.c_int32 * 16),
-                ("cand_ms", ctypes.c_float * 16)]
+    _fields_ = [(f, ctypes.c_int32) for f in ("cluster_max_n", "cluster_blocks", "workers", "list_blocks_per_sm",
+                                             "apply_blocks_per_sm", "list_items_per_block", "scan_blocks_per_sm",
+                                             "hub_degree", "ncand")] + \
+               [("cand_stage", ctypes.c_int32 * TUNE_MAX_CAND), ("cand_value", ctypes.c_int32 * TUNE_MAX_CAND),
+                ("cand_ms", ctypes.c_float * TUNE_MAX_CAND)]
 
 
 class _LearnedInfo(ctypes.Structure):
@@ -543,13 +551,13 @@ class Context:
             it.part_out = _ptr(part)
         rep = _TuneReport()
         _check(load_library().jet_autotune(self._h, len(graphs), items, int(reps), ctypes.byref(rep)), "jet_autotune")
-        self.options.cluster_max_n = rep.cluster_max_n
-        self.options.cluster_blocks = rep.cluster_blocks
+        chosen = {f: getattr(rep, f) for f in TUNE_STAGES}
+        for f, v in chosen.items():
+            if f != "workers":
+                setattr(self.options, f, v)
         m = rep.ncand
-        return dict(cluster_max_n=rep.cluster_max_n, cluster_blocks=rep.cluster_blocks, workers=rep.workers,
-                    candidates=[dict(cluster_max_n=rep.cand_cluster_max_n[i],
-                                     cluster_blocks=rep.cand_cluster_blocks[i], workers=rep.cand_workers[i],
-                                     ms=rep.cand_ms[i]) for i in range(m)],
+        return dict(chosen, candidates=[dict(stage=TUNE_STAGES[rep.cand_stage[i]], value=rep.cand_value[i],
+                                             ms=rep.cand_ms[i]) for i in range(m)],
                     parts=[(keep[i][4], items[i].cut) for i in range(len(graphs))])
 
     def partition_host(self, xadj, adjncy, vwgt=None, adjwgt=None, k=2, eps=0.03, seed=1, part_out=None,

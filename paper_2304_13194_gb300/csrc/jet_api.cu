@@ -83,7 +83,7 @@ static uint64_t host_splitmix64(uint64_t x) {
 }
 
 // Seed of Jetrw's random destination on level i of the hierarchy.
-static uint64_t level_seed(uint64_t seed, int32_t level) {
+uint64_t level_seed(uint64_t seed, int32_t level) {
     return host_splitmix64(seed ^ (0xA0761D6478BD642FULL * (uint64_t)(level + 1)));
 }
 
@@ -224,11 +224,12 @@ struct EventTimer {
 };
 
 int uncoarsen(Ctx &c, const jet_hier *h, int32_t k, double eps, uint64_t seed, const int32_t *init_coarsest,
-              int32_t *part_out, int64_t *cut_out, jet_stats *st) {
+              int32_t *part_out, int64_t *cut_out, jet_stats *st, int32_t top, bool top_refined) {
     cudaStream_t s = c.stream;
-    int32_t l = h->levels - 1;
+    int32_t l = top >= 0 ? top : h->levels - 1;
+    if (l >= h->levels || (top >= 0 && !init_coarsest)) return JET_EINVAL;
     int32_t nmax = 1;
-    for (int32_t i = 1; i < h->levels; ++i) nmax = std::max(nmax, h->n[i]);
+    for (int32_t i = 1; i <= l; ++i) nmax = std::max(nmax, h->n[i]);
     DevBuf pa, pb;
     if (l > 0) {
         JET_TRY(dev_alloc(pa, (size_t)nmax * 4, s));
@@ -296,6 +297,7 @@ int uncoarsen(Ctx &c, const jet_hier *h, int32_t k, double eps, uint64_t seed, c
             cur = dst;
         }
         if (i == 0) cudaEventRecord(ev.e[2], s);
+        if (i == l && top_refined) continue;   // the given partition is already refined there
         LevelRun &run = runs.r[i];
         run.slot = i;
         run.want_trace = i == 0;
@@ -309,6 +311,7 @@ int uncoarsen(Ctx &c, const jet_hier *h, int32_t k, double eps, uint64_t seed, c
     runs.done = true;
     int first_err = JET_OK;
     for (int32_t i = l; i >= 0; --i) {
+        if (i == l && top_refined) continue;
         LevelReport rep;
         int r = refine_level_finish(c, runs.r[i], &cut, &maxw, &rep);
         if (r < 0) {
@@ -385,6 +388,8 @@ void jet_options_default(jet_options *o) {
     o->cluster_max_n = 4096;
     o->cluster_blocks = 0;
     o->barrier_polls = 0;
+    o->list_blocks_per_sm = o->list_items_per_block = o->apply_blocks_per_sm = o->scan_blocks_per_sm = 0;
+    o->hub_degree = 0;
 }
 
 int jet_ctx_create(int device, void *cuda_stream, const jet_options *opt, jet_ctx **out) {
@@ -396,7 +401,9 @@ int jet_ctx_create(int device, void *cuda_stream, const jet_options *opt, jet_ct
     if (!(o.c_fine >= 0 && o.c_fine <= 1 && o.c_coarse >= 0 && o.c_coarse <= 1 && o.phi > 0 && o.phi <= 1) ||
         o.max_no_improve < 0 || o.weak_limit < 0 || o.coarsen_target < 0 || o.max_levels < 1 ||
         o.max_iters_per_level < 0 || o.hem_rounds < 0 || o.hem_rounds > 64 || o.cluster_max_n < 0 ||
-        o.barrier_polls < 0 ||
+        o.barrier_polls < 0 || o.list_blocks_per_sm < 0 || o.list_blocks_per_sm > 64 || o.list_items_per_block < 0 ||
+        o.apply_blocks_per_sm < 0 || o.apply_blocks_per_sm > 64 || o.scan_blocks_per_sm < 0 ||
+        o.scan_blocks_per_sm > 64 || (o.hub_degree != 0 && o.hub_degree < 32) ||
         !(o.cluster_blocks == 0 || o.cluster_blocks == 2 || o.cluster_blocks == 4 || o.cluster_blocks == 8 ||
           o.cluster_blocks == 16))
         return JET_EINVAL;
@@ -594,6 +601,15 @@ int jet_partition(jet_ctx *ctx, int32_t n, const int64_t *xadj, const int32_t *a
     return r;
 }
 
+// Batched form.  Three stages, each bit-identical to jet_partition per item:
+//  1. the workers (host threads, each with its own context, stream and pool)
+//     coarsen every graph and compute the greedy start of its coarsest level;
+//  2. the small levels of all graphs — each graph's chain of levels of at
+//     most cluster_max_n vertices, coarsest first — are refined in one
+//     persistent cluster launch that takes graphs from a work queue
+//     (refine_small_chains);
+//  3. the workers refine every graph's larger levels (projection + the
+//     CUDA-graph loop per level).
 int jet_partition_batch(jet_ctx *ctx, int32_t count, jet_batch_item *items, int32_t workers) {
     if (!ctx || count < 0 || (count > 0 && !items)) return JET_EINVAL;
     if (count == 0) return JET_OK;
@@ -601,61 +617,159 @@ int jet_partition_batch(jet_ctx *ctx, int32_t count, jet_batch_item *items, int3
     JET_TRY(use_device(c));
     if (workers <= 0) workers = 8;
     workers = std::min(workers, count);
+    for (int32_t i = 0; i < count; ++i)
+        if (bad_k_eps(items[i].k, items[i].eps) || items[i].n < 0 || (items[i].n > 0 && !items[i].part_out))
+            return JET_EINVAL;
     // the workers' streams start after the work already on the caller's stream
     cudaEvent_t start = nullptr;
     JET_CUDA_TRY(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
-    cudaError_t e = cudaEventRecord(start, c.stream);
-    if (e != cudaSuccess) {
-        cudaEventDestroy(start);
-        record_cuda_error(e, "cudaEventRecord", __FILE__, __LINE__);
-        return JET_ECUDA;
-    }
-    std::atomic<int32_t> next{0};
-    std::vector<int> wstat((size_t)workers, JET_OK);
-    auto worker = [&](int w) {
-        cudaSetDevice(c.device);
+    struct EventFree {
+        cudaEvent_t e;
+        ~EventFree() { cudaEventDestroy(e); }
+    } start_free{start};
+    JET_CUDA_TRY(cudaEventRecord(start, c.stream));
+    struct Worker {
         cudaStream_t s = nullptr;
-        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
-            cudaGetLastError();
-            wstat[(size_t)w] = JET_ECUDA;
-            return;
-        }
-        cudaStreamWaitEvent(s, start, 0);
         jet_ctx *wc = nullptr;
-        jet_options wo = c.opt;
-        if (workers > 1) wo.flags &= ~JET_FLAG_GRID_LOOP;   // concurrent workers: no cooperative launches
-        int r = jet_ctx_create(c.device, s, &wo, &wc);
-        if (r != JET_OK) {
-            wstat[(size_t)w] = r;
-            cudaStreamDestroy(s);
+        ~Worker() {
+            if (wc) jet_ctx_destroy(wc);
+            if (s) cudaStreamDestroy(s);
+        }
+    };
+    std::vector<Worker> wk((size_t)workers);
+    jet_options wo = c.opt;
+    if (workers > 1) wo.flags &= ~JET_FLAG_GRID_LOOP;   // concurrent workers: no cooperative launches
+    for (auto &w : wk) {
+        JET_CUDA_TRY(cudaStreamCreateWithFlags(&w.s, cudaStreamNonBlocking));
+        JET_CUDA_TRY(cudaStreamWaitEvent(w.s, start, 0));
+        JET_TRY(jet_ctx_create(c.device, w.s, &wo, &w.wc));
+    }
+    JET_TRY(use_device(c));
+    struct Item {
+        jet_hier *h = nullptr;
+        DevBuf init;                 // greedy start of the coarsest level (worker's pool)
+        int64_t W = 0;
+        int32_t bottom = -1;         // finest level of the small chain (-1: none)
+        int32_t chain = -1;
+        bool done = false;
+        double ms = 0;
+        ~Item() {
+            if (h) jet_hier_destroy(h);
+        }
+    };
+    std::vector<Item> st((size_t)count);
+    std::vector<int> wstat((size_t)workers, JET_OK);
+    // runs fn(worker context, item) over all items on the workers
+    auto run_workers = [&](auto &&fn) {
+        std::atomic<int32_t> next{0};
+        auto body = [&](int w) {
+            jet_ctx *wc = wk[(size_t)w].wc;
+            for (;;) {
+                int32_t i = next.fetch_add(1);
+                if (i >= count) break;
+                if (st[(size_t)i].done) continue;
+                auto t0 = std::chrono::steady_clock::now();
+                fn(wc, i);
+                st[(size_t)i].ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+            }
+            if (cudaStreamSynchronize(wk[(size_t)w].s) != cudaSuccess) {
+                cudaGetLastError();
+                wstat[(size_t)w] = JET_ECUDA;
+            }
+        };
+        std::vector<std::thread> pool;
+        int started = 0;
+        try {
+            pool.reserve((size_t)workers);
+            for (int w = 0; w < workers; ++w) {
+                pool.emplace_back(body, w);
+                ++started;
+            }
+        } catch (...) {   // no exception crosses the C ABI: the workers that started take every item
+            if (started == 0) body(0);   // none did: the calling thread takes the whole batch
+        }
+        for (auto &t : pool) t.join();
+    };
+    const int32_t thr = c.opt.cluster_max_n;
+    // stage 1: coarsening and the greedy start of the coarsest level
+    run_workers([&](jet_ctx *wc, int32_t i) {
+        jet_batch_item &it = items[i];
+        Item &s1 = st[(size_t)i];
+        it.cut = 0;
+        it.status = JET_OK;
+        if (it.n == 0) {
+            s1.done = true;
             return;
         }
-        for (;;) {
-            int32_t i = next.fetch_add(1);
-            if (i >= count) break;
-            jet_batch_item &it = items[i];
-            auto t0 = std::chrono::steady_clock::now();
-            it.cut = 0;
-            it.status = jet_partition(wc, it.n, it.xadj, it.adjncy, it.vwgt, it.adjwgt, it.k, it.eps, it.seed,
-                                      it.part_out, &it.cut, nullptr);
-            it.ms = std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        int r = jet_coarsen(wc, it.n, it.xadj, it.adjncy, it.vwgt, it.adjwgt, it.k, it.seed, &s1.h);
+        if (r < 0) { it.status = r; s1.done = true; return; }
+        Ctx &w = wc->c;
+        const jet_hier *h = s1.h;
+        const int32_t l = h->levels - 1;
+        DGraph gl;
+        gl.n = h->n[l]; gl.nnz = h->nnz[l]; gl.xadj = h->xadj[l]; gl.adj = h->adj[l]; gl.vw = h->vw[l]; gl.ew = h->ew[l];
+        r = use_device(w);
+        if (r >= 0) r = dev_alloc(s1.init, (size_t)std::max<int32_t>(gl.n, 1) * 4, w.stream);
+        if (r >= 0) r = initial_partition(w, gl, it.k, s1.init.as<int32_t>());
+        if (r >= 0) r = total_vweight(w, gl, s1.W);
+        if (r < 0) { it.status = r; s1.done = true; return; }
+        if (thr > 0 && h->n[l] <= thr) {
+            int32_t b = l;
+            while (b > 0 && h->n[b - 1] <= thr) --b;
+            s1.bottom = b;
         }
-        jet_ctx_destroy(wc);
-        cudaStreamDestroy(s);
-    };
-    std::vector<std::thread> pool;
-    int started = 0;
-    try {
-        pool.reserve((size_t)workers);
-        for (int w = 0; w < workers; ++w) {
-            pool.emplace_back(worker, w);
-            ++started;
+    });
+    for (int w = 0; w < workers; ++w)
+        if (wstat[(size_t)w] != JET_OK) return wstat[(size_t)w];
+    // stage 2: every graph's small levels in one persistent launch
+    std::vector<SmallChain> chains;
+    std::vector<DevBuf> chain_out;
+    for (int32_t i = 0; i < count; ++i) {
+        Item &s1 = st[(size_t)i];
+        if (s1.done || s1.bottom < 0) continue;
+        const jet_batch_item &it = items[i];
+        SmallChain ch;
+        ch.h = s1.h;
+        ch.top = s1.h->levels - 1;
+        ch.bottom = s1.bottom;
+        ch.k = it.k;
+        ch.eps = it.eps;
+        ch.seed = it.seed;
+        ch.W = s1.W;
+        ch.init = s1.init.as<int32_t>();
+        if (s1.bottom == 0) {
+            ch.out = it.part_out;
+        } else {
+            chain_out.emplace_back();
+            JET_TRY(dev_alloc(chain_out.back(), (size_t)s1.h->n[s1.bottom] * 4, c.stream));
+            ch.out = chain_out.back().as<int32_t>();
         }
-    } catch (...) {   // no exception crosses the C ABI: the workers that started take every item
-        if (started == 0) worker(0);   // none did: the calling thread takes the whole batch
+        s1.chain = (int32_t)chains.size();
+        chains.push_back(ch);
     }
-    for (auto &t : pool) t.join();
-    cudaEventDestroy(start);
+    int ran = 0;
+    JET_TRY(refine_small_chains(c, chains.data(), (int32_t)chains.size(), c.opt.cluster_blocks, &ran));
+    // stage 3: the larger levels
+    run_workers([&](jet_ctx *wc, int32_t i) {
+        jet_batch_item &it = items[i];
+        Item &s1 = st[(size_t)i];
+        const SmallChain *ch = (ran && s1.chain >= 0) ? &chains[(size_t)s1.chain] : nullptr;
+        int r;
+        if (ch && ch->bottom == 0) {
+            it.cut = ch->cut;
+            r = ch->status;
+        } else if (ch) {
+            r = use_device(wc->c);
+            if (r >= 0) r = uncoarsen(wc->c, s1.h, it.k, it.eps, it.seed, ch->out, it.part_out, &it.cut, nullptr,
+                                      ch->bottom, true);
+        } else {
+            r = use_device(wc->c);
+            if (r >= 0) r = uncoarsen(wc->c, s1.h, it.k, it.eps, it.seed, s1.init.as<int32_t>(), it.part_out, &it.cut,
+                                      nullptr);
+        }
+        it.status = r;
+    });
+    for (int32_t i = 0; i < count; ++i) items[i].ms = (float)st[(size_t)i].ms;
     for (int w = 0; w < workers; ++w)
         if (wstat[(size_t)w] != JET_OK) return wstat[(size_t)w];
     for (int32_t i = 0; i < count; ++i)
@@ -687,7 +801,7 @@ int jet_autotune(jet_ctx *ctx, int32_t count, jet_batch_item *items, int32_t rep
     int32_t workers = count > 1 ? 8 : 1;
     // One stage: each value of one choice (*target) timed with the others
     // fixed; the fastest stays.
-    auto stage = [&](const int32_t *vals, int nv, int32_t *target) -> int {
+    auto stage = [&](int32_t id, const int32_t *vals, int nv, int32_t *target) -> int {
         int32_t best_v = *target;
         float best = 0.f;
         for (int i = 0; i < nv; ++i) {
@@ -695,9 +809,8 @@ int jet_autotune(jet_ctx *ctx, int32_t count, jet_batch_item *items, int32_t rep
             float ms = 0.f;
             JET_TRY(time_batch(workers, &ms));
             if (rep.ncand < JET_TUNE_MAX_CAND) {
-                rep.cand_cluster_max_n[rep.ncand] = c.opt.cluster_max_n;
-                rep.cand_cluster_blocks[rep.ncand] = c.opt.cluster_blocks;
-                rep.cand_workers[rep.ncand] = workers;
+                rep.cand_stage[rep.ncand] = id;
+                rep.cand_value[rep.ncand] = vals[i];
                 rep.cand_ms[rep.ncand] = ms;
                 rep.ncand += 1;
             }
@@ -709,18 +822,39 @@ int jet_autotune(jet_ctx *ctx, int32_t count, jet_batch_item *items, int32_t rep
     static const int32_t blocks[] = {16, 8, 4, 2};
     static const int32_t thresholds[] = {0, 1024, 2048, 4096, 8192, 16384};
     static const int32_t wcands[] = {1, 2, 4, 8, 16};
+    static const int32_t list_bpsm[] = {2, 4, 8};
+    static const int32_t apply_bpsm[] = {1, 2, 4};
+    static const int32_t items_pb[] = {32, 64, 128};
+    static const int32_t scan_bpsm[] = {4, 8, 16};
+    static const int32_t hubs[] = {256, 1024, 4096};
     const jet_options saved = c.opt;
-    c.opt.cluster_max_n = 4096;
-    int st = stage(blocks, 4, &c.opt.cluster_blocks);
-    if (st >= 0) st = stage(thresholds, 6, &c.opt.cluster_max_n);
-    if (st >= 0 && count > 1) st = stage(wcands, 5, &workers);
+    jet_options &o = c.opt;
+    o.cluster_max_n = 4096;
+    o.list_blocks_per_sm = 4;
+    o.apply_blocks_per_sm = 4;
+    o.list_items_per_block = 64;
+    o.scan_blocks_per_sm = 8;
+    o.hub_degree = 1024;
+    int st = stage(JET_TUNE_CLUSTER_BLOCKS, blocks, 4, &o.cluster_blocks);
+    if (st >= 0) st = stage(JET_TUNE_CLUSTER_MAX_N, thresholds, 6, &o.cluster_max_n);
+    if (st >= 0 && count > 1) st = stage(JET_TUNE_WORKERS, wcands, 5, &workers);
+    if (st >= 0) st = stage(JET_TUNE_LIST_BLOCKS, list_bpsm, 3, &o.list_blocks_per_sm);
+    if (st >= 0) st = stage(JET_TUNE_APPLY_BLOCKS, apply_bpsm, 3, &o.apply_blocks_per_sm);
+    if (st >= 0) st = stage(JET_TUNE_LIST_ITEMS, items_pb, 3, &o.list_items_per_block);
+    if (st >= 0) st = stage(JET_TUNE_SCAN_BLOCKS, scan_bpsm, 3, &o.scan_blocks_per_sm);
+    if (st >= 0) st = stage(JET_TUNE_HUB_DEGREE, hubs, 3, &o.hub_degree);
     if (st < 0) {
         c.opt = saved;
         return st;
     }
-    rep.cluster_max_n = c.opt.cluster_max_n;
-    rep.cluster_blocks = c.opt.cluster_blocks;
+    rep.cluster_max_n = o.cluster_max_n;
+    rep.cluster_blocks = o.cluster_blocks;
     rep.workers = workers;
+    rep.list_blocks_per_sm = o.list_blocks_per_sm;
+    rep.apply_blocks_per_sm = o.apply_blocks_per_sm;
+    rep.list_items_per_block = o.list_items_per_block;
+    rep.scan_blocks_per_sm = o.scan_blocks_per_sm;
+    rep.hub_degree = o.hub_degree;
     if (report) *report = rep;
     return JET_OK;
 }
@@ -804,7 +938,8 @@ int jet_hem(jet_ctx *ctx, int32_t n, const int64_t *xadj, const int32_t *adjncy,
     DGraph g;
     DevBuf ones;
     JET_TRY(prepare_graph(c, n, xadj, adjncy, nullptr, adjwgt, g, ones, true));
-    return hem(c, g, seed, level, rounds, mate_out);
+    JET_TRY(hem(c, g, seed, level, rounds, mate_out));
+    return sync_stream(c);
 }
 
 int jet_two_hop(jet_ctx *ctx, int32_t n, const int64_t *xadj, const int32_t *adjncy, int32_t *mate_inout,

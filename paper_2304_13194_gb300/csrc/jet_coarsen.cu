@@ -245,8 +245,7 @@ int hem(Ctx &c, const DGraph &g, uint64_t seed, int32_t level, int32_t rounds, i
         c.launches += 1;
     }
     JET_CUDA_TRY(cudaGetLastError());
-    JET_CUDA_TRY(cudaStreamSynchronize(s));
-    return JET_OK;
+    return JET_OK;   // mate is final once the stream passes here (the scratch is freed in stream order)
 }
 
 // ---------------------------------------------------------------------------
@@ -797,8 +796,7 @@ static int coarsen_level(Ctx &c, const DGraph &g, uint64_t seed, int32_t level, 
     h->bufs.push_back(std::move(adjcb));
     h->bufs.push_back(std::move(vwcb));
     h->bufs.push_back(std::move(ewcb));
-    JET_CUDA_TRY(cudaStreamSynchronize(s));
-    return JET_OK;
+    return JET_OK;   // the next level's work follows in stream order
 }
 
 __global__ void k_ones(int32_t *p, int64_t n) {

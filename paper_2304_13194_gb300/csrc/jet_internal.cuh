@@ -187,6 +187,12 @@ struct Level {
     int32_t use_graph;
     int32_t pdl;             // launch the row and tile kernels with programmatic dependent launch
     int64_t poll_limit;      // persistent loop: polls at a grid barrier before a block gives up
+    int32_t hub_deg;         // rows longer than this are taken by a whole block in the row phases
+    // launch shapes (host side; execution choices, results do not depend on them)
+    int32_t list_cap;        // most blocks of a list kernel (select, afterburner, rebalancing rows)
+    int32_t apply_cap;       // most blocks of the apply kernel
+    int32_t scan_cap;        // most blocks of a scan kernel
+    int32_t items_per_block; // list entries per block below those caps
 };
 
 // ---------------------------------------------------------------------------
@@ -498,6 +504,27 @@ int refine_level_enqueue(Ctx &c, const DGraph &g, int32_t k, double eps, int32_t
                          int32_t *part_inout, int64_t W, LevelRun &run);
 int refine_level_finish(Ctx &c, LevelRun &run, int64_t *cut_out, int64_t *maxw_out, LevelReport *rep);
 void refine_level_abandon(LevelRun &run);   // after an error: release what the run holds
+// The batched form's small levels: one graph's chain of levels of at most
+// cluster_max_n vertices, refined with those of the other chains in one
+// persistent cluster launch (refine_small_chains).
+struct SmallChain {
+    const jet_hier *h = nullptr;
+    int32_t top = 0, bottom = 0;     // the coarsest level and the finest small level (top >= bottom)
+    int32_t k = 2;
+    double eps = 0.03;
+    uint64_t seed = 1;               // the partition's seed (level seeds derive from it)
+    int64_t W = 0;                   // total vertex weight
+    const int32_t *init = nullptr;   // device: start partition of level `top`
+    int32_t *out = nullptr;          // device: receives the refined partition of level `bottom`
+    int64_t cut = 0, maxw = 0;       // out: of level `bottom`
+    int32_t status = JET_OK;         // out: of level `bottom`
+};
+// cluster_blocks: blocks of each cluster (0 = 4).  On success every chain's
+// `out` holds its result; JET_ECUDA with *ran = 0 when the device cannot
+// co-schedule one cluster (the caller refines the levels one by one).
+int refine_small_chains(Ctx &c, SmallChain *chains, int32_t nchains, int32_t cluster_blocks, int *ran);
+uint64_t level_seed(uint64_t seed, int32_t level);   // Jetrw seed of hierarchy level `level`
+
 // Enqueue + synchronise + finish.  W_known: -1 = computed on the device.
 int refine_level(Ctx &c, const DGraph &g, int32_t k, double eps, int32_t is_finest, uint64_t seed,
                  int32_t *part_inout, int64_t *cut_out, int64_t *maxw_out, LevelReport *rep, int64_t W_known = -1);
@@ -565,8 +592,11 @@ int check_part(Ctx &c, int32_t n, const int32_t *part, int32_t k);   // JET_EINV
 int prepare_graph(Ctx &c, int32_t n, const int64_t *xadj, const int32_t *adjncy, const int32_t *vwgt,
                   const int32_t *adjwgt, DGraph &g, DevBuf &ones, bool need_vw);
 // Alg. 1 after coarsening; init_coarsest (device, n of the coarsest level)
-// replaces the greedy initial partition when not null.
+// replaces the greedy initial partition when not null.  With top >= 0 the
+// uncoarsening starts at level `top` from init_coarsest (n[top] entries):
+// refined there too unless top_refined, then projected and refined on
+// every finer level.
 int uncoarsen(Ctx &c, const jet_hier *h, int32_t k, double eps, uint64_t seed, const int32_t *init_coarsest,
-              int32_t *part_out, int64_t *cut_out, jet_stats *st);
+              int32_t *part_out, int64_t *cut_out, jet_stats *st, int32_t top = -1, bool top_refined = false);
 
 }  // namespace jet

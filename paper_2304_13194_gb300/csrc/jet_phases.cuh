@@ -198,13 +198,14 @@ struct Appender {
     }
     // Long rows staged for the block: when another round could overflow the
     // buffer (or with force), the block's warps take the staged rows in turn
-    // (`row(v)`, all 32 lanes), except rows longer than kHugeDeg, which are
+    // (`row(v)`, all 32 lanes), except rows longer than `hub`, which are
     // set aside (up to kHugeCap of them; more stay with the warps) and then
     // taken by the whole block one after another (`block_row(v)`, every
     // thread): a hub row no longer serialises one warp for the whole pass.
     // All threads call it.
     template <class Row, class BlockRow>
-    __device__ __forceinline__ void drain(bool force, const int64_t *xadj, Row &&row, BlockRow &&block_row) {
+    __device__ __forceinline__ void drain(bool force, const int64_t *xadj, Row &&row, BlockRow &&block_row,
+                                          int64_t hub = kHugeDeg) {
         __shared__ int32_t huge[kHugeCap];
         __shared__ int nhuge;
         __syncthreads();
@@ -216,7 +217,7 @@ struct Appender {
             for (int s = threadIdx.x >> 5; s < c; s += warps) {
                 const int32_t v = buf[s];
                 int defer = 0;
-                if (lane_id() == 0 && ld_xadj(xadj, (int64_t)v + 1) - ld_xadj(xadj, v) > kHugeDeg) {
+                if (lane_id() == 0 && ld_xadj(xadj, (int64_t)v + 1) - ld_xadj(xadj, v) > hub) {
                     const int slot = atomicAdd(&nhuge, 1);
                     if (slot < kHugeCap) {
                         huge[slot] = v;
@@ -829,10 +830,10 @@ __device__ inline void ph_lp_select(const Level &L, LpExport ex, Grid G, char *a
         xapp.add(inX, v);
         bigs.add(big, v);
         xapp.flush(&ctl->nX, L.listX, false);
-        bigs.drain(false, g.xadj, big_row, hub_row);
+        bigs.drain(false, g.xadj, big_row, hub_row, L.hub_deg);
     }
     xapp.flush(&ctl->nX, L.listX, true);
-    bigs.drain(true, g.xadj, big_row, hub_row);
+    bigs.drain(true, g.xadj, big_row, hub_row, L.hub_deg);
     flush_counter(&ctl->nexam, nexam, red);
     flush_counter(&ctl->degexam, degexam, red);
     flush_counter(&ctl->degx, degx, red);
@@ -952,10 +953,10 @@ __device__ inline void ph_afterburn(const Level &L, LpExport ex, Grid G, char *a
         mapp.add(inM, v);
         bigs.add(big, v);
         mapp.flush(&ctl->nM, L.listM, false);
-        bigs.drain(false, L.g.xadj, big_row, hub_row);
+        bigs.drain(false, L.g.xadj, big_row, hub_row, L.hub_deg);
     }
     mapp.flush(&ctl->nM, L.listM, true);
-    bigs.drain(true, L.g.xadj, big_row, hub_row);
+    bigs.drain(true, L.g.xadj, big_row, hub_row, L.hub_deg);
 }
 
 // ---------------------------------------------------------------------------
@@ -1093,9 +1094,9 @@ __device__ inline void ph_apply(const Level &L, Grid G, char *arena) {
             }
         }
         bigs.add(big, v);
-        bigs.drain(false, L.g.xadj, big_row, hub_row);
+        bigs.drain(false, L.g.xadj, big_row, hub_row, L.hub_deg);
     }
-    bigs.drain(true, L.g.xadj, big_row, hub_row);
+    bigs.drain(true, L.g.xadj, big_row, hub_row, L.hub_deg);
     // hub rows of M, one block each, dealt round-robin over the blocks
     for (int32_t h = G.bid; h < nMh; h += G.nb) {
         const int32_t v = L.listM[L.g.n - 1 - h];
@@ -1461,9 +1462,9 @@ __device__ inline void ph_rb_cand(const Level &L, Grid G, char *arena) {
         }
         sb.add(L, key, wv);
         bigs.add(big, v);
-        bigs.drain(false, g.xadj, big_row, hub_row);
+        bigs.drain(false, g.xadj, big_row, hub_row, L.hub_deg);
     }
-    bigs.drain(true, g.xadj, big_row, hub_row);
+    bigs.drain(true, g.xadj, big_row, hub_row, L.hub_deg);
     sb.flush(L);
     flush_counter(&ctl->degexam, degrows, red);
 }

@@ -32,12 +32,13 @@ extern __shared__ __align__(16) unsigned char jet_arena[];
 // ---------------------------------------------------------------------------
 // Short rows (up to 2 kSmallDeg entries) one thread each; longer rows staged
 // for the block's warps, hub rows (over kHugeDeg) for the whole block.
+// (A phase over the blocks of a Grid: one kernel launch, or one cluster.)
 template <bool EW>
-__global__ void __launch_bounds__(kTB) k_cut_pw(DGraph g, int32_t k, const int32_t *__restrict__ part,
-                                                 int64_t *__restrict__ pw, int64_t *__restrict__ cut2,
-                                                 int32_t *__restrict__ ext, int32_t *__restrict__ wdeg) {
-    long long *shpw = reinterpret_cast<long long *>(jet_arena);
-    int32_t *stage = reinterpret_cast<int32_t *>(jet_arena + align16((size_t)k * 8));
+__device__ inline void ph_cut_pw(const DGraph &g, int32_t k, const int32_t *__restrict__ part,
+                                 int64_t *__restrict__ pw, int64_t *__restrict__ cut2, int32_t *__restrict__ ext,
+                                 int32_t *__restrict__ wdeg, Grid G, char *arena) {
+    long long *shpw = reinterpret_cast<long long *>(arena);
+    int32_t *stage = reinterpret_cast<int32_t *>(arena + align16((size_t)k * 8));
     __shared__ long long red[40];
     for (int i = threadIdx.x; i < k; i += blockDim.x) shpw[i] = 0;
     JET_APPENDER(bigs, stage, kBigCap);
@@ -84,7 +85,7 @@ __global__ void __launch_bounds__(kTB) k_cut_pw(DGraph g, int32_t k, const int32
             if (wdeg) wdeg[v] = (int32_t)wd;
         }
     };
-    for (int64_t v0 = (int64_t)blockIdx.x * blockDim.x; v0 < g.n; v0 += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t v0 = (int64_t)G.bid * blockDim.x; v0 < g.n; v0 += (int64_t)G.nb * blockDim.x) {
         const int64_t v = v0 + threadIdx.x;
         bool big = false;
         if (v < g.n) {
@@ -116,6 +117,14 @@ __global__ void __launch_bounds__(kTB) k_cut_pw(DGraph g, int32_t k, const int32
     __syncthreads();
     for (int i = threadIdx.x; i < k; i += blockDim.x)
         if (shpw[i]) atomic_add_i64(&pw[i], shpw[i]);
+    __syncthreads();
+}
+
+template <bool EW>
+__global__ void __launch_bounds__(kTB) k_cut_pw(DGraph g, int32_t k, const int32_t *__restrict__ part,
+                                                 int64_t *__restrict__ pw, int64_t *__restrict__ cut2,
+                                                 int32_t *__restrict__ ext, int32_t *__restrict__ wdeg) {
+    ph_cut_pw<EW>(g, k, part, pw, cut2, ext, wdeg, launch_grid(), reinterpret_cast<char *>(jet_arena));
 }
 
 // dynamic shared memory of k_cut_pw
@@ -254,12 +263,10 @@ __device__ __forceinline__ void cluster_rebalance(const Level &L, Grid G, char *
 // The whole loop of Alg. 3 on one level.  The blocks of the cluster take the
 // phases in lockstep (cluster barrier between phases; block 0 runs the
 // tails); the loop ends when the controller chooses DONE, which the stop
-// rule or the iteration cap guarantees.
+// rule or the iteration cap guarantees.  Every block reads the same mode
+// after the same barrier, so all of them meet every barrier.
 template <bool EW>
-__global__ void __launch_bounds__(kClusterThreads, 1) k_refine_cluster(Level L) {
-    cg::cluster_group cl = cg::this_cluster();
-    const Grid G{(int)cl.block_rank(), (int)cl.num_blocks()};
-    char *arena = JET_ARENA;
+__device__ inline void cluster_level_loop(const Level &L, Grid G, char *arena, cg::cluster_group &cl) {
     const LpExport none{nullptr, nullptr, nullptr};
     for (;;) {
         const int32_t mode = L.ctl->mode;
@@ -283,6 +290,13 @@ __global__ void __launch_bounds__(kClusterThreads, 1) k_refine_cluster(Level L) 
         cl.sync();
     }
     ph_copy_best(L, G);
+}
+
+template <bool EW>
+__global__ void __launch_bounds__(kClusterThreads, 1) k_refine_cluster(Level L) {
+    cg::cluster_group cl = cg::this_cluster();
+    const Grid G{(int)cl.block_rank(), (int)cl.num_blocks()};
+    cluster_level_loop<EW>(L, G, JET_ARENA, cl);
 }
 
 // ---------------------------------------------------------------------------
@@ -401,6 +415,141 @@ __global__ void __launch_bounds__(kTB, JET_ROW_MINB) k_refine_grid(Level L) {
 }
 
 // ---------------------------------------------------------------------------
+// batched form: the small levels of many graphs in one persistent launch
+// ---------------------------------------------------------------------------
+// A job is one graph's chain of small levels, coarsest first (the levels of
+// at most cluster_max_n vertices form the coarse end of its hierarchy).  The
+// clusters of one launch take jobs from a counter; a cluster runs the whole
+// chain of its job: per level the projection of the coarser level's
+// partition, the level's start state (the work of setup_level and
+// enqueue_init, as cluster phases), the whole Alg. 3 loop, and the P_best
+// copy; then it takes the next job.  Every decision is the one the
+// per-level launches take, so results are bit-identical.
+struct BatchLevel {
+    DGraph g;
+    const int32_t *cmap;     // this level -> the next coarser one (unused on the job's coarsest level)
+    uint64_t seed;           // Jetrw seed of the level
+    int32_t cq16;            // first-filter ratio c of the level (c_fine on level 0)
+    int32_t pad;
+};
+struct BatchStat {           // the control block's outcome of one level
+    int64_t best_cut, best_maxw;
+    int64_t kbytes[JET_K_COUNT];
+    int32_t it, best_bal, hit_cap, pad;
+    int32_t kcount[4];
+};
+struct BatchJob {
+    Level L;                 // buffers sized for the chain's largest level; the level fields are set per level
+    const BatchLevel *lv;    // [nlv], coarsest first
+    BatchStat *stat;         // [nlv]
+    const int32_t *init;     // start partition of the coarsest level
+    int32_t *part[2];        // level partitions, alternating (level i in part[i & 1])
+    int32_t *out;            // receives the finest level's partition (may be null)
+    int64_t *cut2;           // scratch: twice the start cut of a level
+    int64_t Llim, opt, sigma;
+    int32_t nlv, pad;
+};
+
+// Start of one level inside a job (all blocks of the cluster): projection,
+// per-vertex start values, cut / part weights / ext / weighted degree, the
+// long-row count, then the control block (block 0) and P_best = P_0.
+__device__ inline void batch_level_start(const BatchJob &job, const Level &L, int32_t i, Grid G, char *arena,
+                                         cg::cluster_group &cl) {
+    const int64_t n = L.g.n;
+    const int64_t t0 = (int64_t)G.bid * blockDim.x + threadIdx.x, stride = (int64_t)G.nb * blockDim.x;
+    int32_t *cur = L.part;
+    if (i == 0) {
+        for (int64_t v = t0; v < n; v += stride) cur[v] = job.init[v];
+    } else {
+        const int32_t *prev = job.part[(i - 1) & 1];
+        const int32_t *cmap = job.lv[i].cmap;
+        for (int64_t v = t0; v < n; v += stride) cur[v] = prev[cmap[v]];
+    }
+    for (int64_t v = t0; v < n; v += stride) {
+        L.lstamp[v] = -2;
+        L.mstamp[v] = -2;
+        L.prio[v] = kNoneGain;
+    }
+    if (G.bid == 0) {
+        int64_t *w = reinterpret_cast<int64_t *>(L.ctl);
+        for (int q = threadIdx.x; q < (int)(sizeof(Ctl) / 8); q += blockDim.x) w[q] = 0;
+        for (int p = threadIdx.x; p < L.k; p += blockDim.x) L.pw[p] = 0;
+        if (threadIdx.x == 0) job.cut2[0] = 0;
+    }
+    cl.sync();
+    for (int64_t v0 = (int64_t)G.bid * blockDim.x; v0 < n; v0 += stride) {
+        const int64_t v = v0 + threadIdx.x;
+        const bool big = v < n && ld_xadj(L.g.xadj, v + 1) - ld_xadj(L.g.xadj, v) > kSmallDeg;
+        const unsigned m = __ballot_sync(0xffffffffu, big);
+        if (lane_id() == 0 && m) atomicAdd(&L.ctl->nbig, __popc(m));
+    }
+    if (L.g.ew) ph_cut_pw<true>(L.g, L.k, cur, L.pw, job.cut2, L.ext, L.wdeg, G, arena);
+    else ph_cut_pw<false>(L.g, L.k, cur, L.pw, job.cut2, L.ext, L.wdeg, G, arena);
+    cl.sync();
+    if (G.bid == 0) {
+        if (threadIdx.x == 0) {
+            L.ctl->L = job.Llim;
+            L.ctl->opt = job.opt;
+            L.ctl->sigma = job.sigma;
+        }
+        __syncthreads();
+        ph_ctl_init(L, job.cut2);
+    }
+    for (int64_t v = t0; v < n; v += stride) L.best[v] = cur[v];
+    cl.sync();
+}
+
+__global__ void __launch_bounds__(kClusterThreads, 1) k_refine_batch(const BatchJob *jobs, int32_t njobs,
+                                                                     int32_t *queue) {
+    cg::cluster_group cl = cg::this_cluster();
+    const Grid G{(int)cl.block_rank(), (int)cl.num_blocks()};
+    char *arena = JET_ARENA;
+    __shared__ int s_job;
+    __shared__ Level L;   // the level's parameters, in shared memory rather than on each thread's stack
+    for (;;) {
+        if (G.bid == 0 && threadIdx.x == 0) s_job = atomicAdd(queue, 1);
+        cl.sync();
+        const int j = *cl.map_shared_rank(&s_job, 0);
+        cl.sync();   // every block has read the job before block 0 takes the next
+        if (j >= njobs) break;
+        const BatchJob &job = jobs[j];
+        for (int32_t i = 0; i < job.nlv; ++i) {
+            if (threadIdx.x == 0) {
+                const BatchLevel &bl = job.lv[i];
+                L = job.L;
+                L.g = bl.g;
+                L.seed = bl.seed;
+                L.cq16 = bl.cq16;
+                L.ntiles = (int32_t)(((int64_t)bl.g.n + kClusterThreads - 1) / kClusterThreads);
+                if (L.ntiles < 1) L.ntiles = 1;
+                L.part = job.part[i & 1];
+            }
+            __syncthreads();
+            batch_level_start(job, L, i, G, arena, cl);
+            if (L.g.ew) cluster_level_loop<true>(L, G, arena, cl);
+            else cluster_level_loop<false>(L, G, arena, cl);
+            cl.sync();
+            // P_best is the level's result
+            const int64_t n = L.g.n, t0 = (int64_t)G.bid * blockDim.x + threadIdx.x, stride = (int64_t)G.nb * blockDim.x;
+            int32_t *dst = (i + 1 == job.nlv && job.out) ? job.out : L.part;
+            for (int64_t v = t0; v < n; v += stride) dst[v] = L.best[v];
+            if (G.bid == 0 && threadIdx.x == 0) {
+                const Ctl *c = L.ctl;
+                BatchStat &st = job.stat[i];
+                st.best_cut = c->best_cut;
+                st.best_maxw = c->best_maxw;
+                for (int q = 0; q < JET_K_COUNT; ++q) st.kbytes[q] = c->kbytes[q];
+                st.it = c->it;
+                st.best_bal = c->best_bal;
+                st.hit_cap = c->hit_cap;
+                for (int q = 0; q < 4; ++q) st.kcount[q] = c->kcount[q];
+            }
+            cl.sync();
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
 // Vertices with rows longer than kSmallDeg (only whether there are any
@@ -439,21 +588,26 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 // Carves all per-level buffers out of two allocations.
 int allow_large_arenas(int device);
 
-// Buffers and start state of one level, enqueued on the context's stream (no
-// host wait): the control block gets the level's long-row count.
-int setup_level(Ctx &c, const DGraph &g, int32_t k, LevelBufs &B) {
-    JET_TRY(allow_large_arenas(c.device));
-    cudaStream_t s = c.stream;
-    int64_t n = g.n;
-    size_t nn = (size_t)std::max<int64_t>(n, 1);
-    int32_t ntiles = (int32_t)std::max<int64_t>((n + kRbTile - 1) / kRbTile, 1);
-    // per-vertex int32 arrays: best, nxt, prio, mstamp, lstamp, key, listX, listM, ext, wdeg, listW
-    const int nv32 = 11;
-    size_t vbytes = nv32 * align256(nn * 4) + align256(nn * 8) /* etaken */;
-    JET_TRY(dev_alloc(B.vert, vbytes, s));
-    char *p = B.vert.as<char>();
+// Per-level buffers: 11 int32 arrays per vertex (best, nxt, prio, mstamp,
+// lstamp, key, listX, listM, ext, wdeg, listW), then the control block,
+// per-part state, rebalancing tiles, the trace (optional) and the cut
+// accumulator, in two allocations.
+void level_bytes(int64_t nmax, int32_t k, bool with_trace, size_t *vbytes, size_t *mbytes) {
+    const size_t nn = (size_t)std::max<int64_t>(nmax, 1), kk = (size_t)k;
+    const size_t ntiles = (size_t)std::max<int64_t>((nmax + kRbTile - 1) / kRbTile, 1);
+    *vbytes = 11 * align256(nn * 4) + align256(nn * 8) /* etaken */;
+    *mbytes = align256(sizeof(Ctl)) + align256(kk * 8) /*pw*/ + align256(kk * 4) /*aidx*/ + align256(kk * 4) /*Bs*/ +
+              align256(kk) /*inB*/ + align256((kk + 1) * 8) /*capC*/ + align256(kk * 8) /*excess*/ +
+              align256(kk * kSlots * 8) /*bucketw*/ + align256(kk * 4) /*sstar*/ + align256(kk * 8) /*need*/ +
+              align256(ntiles * kk * 4) /*tilehist*/ + align256(ntiles * 8) /*tiletaken*/ +
+              (with_trace ? align256(sizeof(TraceRec) * kTrace) : 0) + align256(16) /*cut2*/;
+}
+
+void carve_level(Level &L, char *vert, char *misc, int64_t nmax, int32_t k, bool with_trace, int64_t **cut2) {
+    const size_t nn = (size_t)std::max<int64_t>(nmax, 1), kk = (size_t)k;
+    const int32_t ntiles = (int32_t)std::max<int64_t>((nmax + kRbTile - 1) / kRbTile, 1);
+    char *p = vert;
     auto take32 = [&](void) { int32_t *r = reinterpret_cast<int32_t *>(p); p += align256(nn * 4); return r; };
-    Level &L = B.L;
     L.best = take32(); L.nxt = take32(); L.prio = take32(); L.mstamp = take32(); L.lstamp = take32();
     L.key = take32(); L.listX = take32(); L.listM = take32();
     L.ext = take32();
@@ -461,16 +615,7 @@ int setup_level(Ctx &c, const DGraph &g, int32_t k, LevelBufs &B) {
     L.listW = take32();
     L.rbloss = nullptr;
     L.etaken = reinterpret_cast<int64_t *>(p);
-    p += align256(nn * 8);
-    // per-part and control
-    size_t kk = (size_t)k;
-    size_t mbytes = align256(sizeof(Ctl)) + align256(kk * 8) /*pw*/ + align256(kk * 4) /*aidx*/ + align256(kk * 4) /*Bs*/ +
-                    align256(kk) /*inB*/ + align256((kk + 1) * 8) /*capC*/ + align256(kk * 8) /*excess*/ +
-                    align256(kk * kSlots * 8) /*bucketw*/ + align256(kk * 4) /*sstar*/ + align256(kk * 8) /*need*/ +
-                    align256((size_t)ntiles * kk * 4) /*tilehist*/ + align256((size_t)ntiles * 8) /*tiletaken*/ +
-                    align256(sizeof(TraceRec) * kTrace) + align256(16) /*cut2*/;
-    JET_TRY(dev_alloc(B.misc, mbytes, s));
-    char *q = B.misc.as<char>();
+    char *q = misc;
     auto take = [&](size_t bytes) { char *r = q; q += align256(bytes); return r; };
     L.ctl = reinterpret_cast<Ctl *>(take(sizeof(Ctl)));
     L.pw = reinterpret_cast<int64_t *>(take(kk * 8));
@@ -484,13 +629,27 @@ int setup_level(Ctx &c, const DGraph &g, int32_t k, LevelBufs &B) {
     L.need = reinterpret_cast<int64_t *>(take(kk * 8));
     L.tilehist = reinterpret_cast<int32_t *>(take((size_t)ntiles * kk * 4));
     L.tiletaken = reinterpret_cast<int64_t *>(take((size_t)ntiles * 8));
-    L.trace = reinterpret_cast<TraceRec *>(take(sizeof(TraceRec) * kTrace));
-    B.cut2 = reinterpret_cast<int64_t *>(take(16));
+    L.trace = with_trace ? reinterpret_cast<TraceRec *>(take(sizeof(TraceRec) * kTrace)) : nullptr;
+    *cut2 = reinterpret_cast<int64_t *>(take(16));
     L.ntiles = ntiles;
-    L.g = g;
     L.k = k;
+}
+
+// Buffers and start state of one level, enqueued on the context's stream (no
+// host wait): the control block gets the level's long-row count.
+int setup_level(Ctx &c, const DGraph &g, int32_t k, LevelBufs &B) {
+    JET_TRY(allow_large_arenas(c.device));
+    cudaStream_t s = c.stream;
+    int64_t n = g.n;
+    size_t vbytes = 0, mbytes = 0;
+    level_bytes(n, k, true, &vbytes, &mbytes);
+    JET_TRY(dev_alloc(B.vert, vbytes, s));
+    JET_TRY(dev_alloc(B.misc, mbytes, s));
+    Level &L = B.L;
+    carve_level(L, B.vert.as<char>(), B.misc.as<char>(), n, k, true, &B.cut2);
+    L.g = g;
     JET_CUDA_TRY(cudaMemsetAsync(L.ctl, 0, sizeof(Ctl), s));
-    JET_CUDA_TRY(cudaMemsetAsync(L.pw, 0, kk * 8, s));
+    JET_CUDA_TRY(cudaMemsetAsync(L.pw, 0, (size_t)k * 8, s));
     JET_CUDA_TRY(cudaMemsetAsync(B.cut2, 0, 16, s));
     if (n > 0) {
         k_count_big<<<grid_for(n, kTB), kTB, 0, s>>>(g, &L.ctl->nbig);
@@ -504,21 +663,17 @@ int setup_level(Ctx &c, const DGraph &g, int32_t k, LevelBufs &B) {
 
 int list_grid() { return num_sms() * 4; }
 
-// Blocks per SM of the two scan kernels (grid-stride over vertices in
-// groups of four), a launch-shape choice.
-#ifndef JET_SCAN_BLOCKS_PER_SM
-#define JET_SCAN_BLOCKS_PER_SM 8
-#endif
-int scan_grid(int64_t n) { return std::min(num_sms() * JET_SCAN_BLOCKS_PER_SM, grid_for((n + 3) / 4, kTB)); }
-
-// Grid of a kernel over a list of at most `items` entries: one block per
-// JET_LIST_ITEMS_PER_BLOCK entries, at most list_grid() blocks (a launch-shape
-// choice: fewer entries per block spread the long rows of small levels over
-// more warps).
-#ifndef JET_LIST_ITEMS_PER_BLOCK
-#define JET_LIST_ITEMS_PER_BLOCK 64
-#endif
-int list_blocks(int64_t items) { return std::min(list_grid(), grid_for(items, JET_LIST_ITEMS_PER_BLOCK)); }
+// Launch shapes of the refinement kernels (execution choices: results do not
+// depend on them), from the context's options:
+//   scan kernels   grid-stride over vertices in groups of four, at most
+//                  scan_cap blocks (scan_blocks_per_sm per SM, default 8);
+//   list kernels   one block per items_per_block list entries (default 64),
+//                  at most list_cap blocks (list_blocks_per_sm, default 4);
+//   apply          the same, at most apply_cap blocks (apply_blocks_per_sm,
+//                  default: the list kernels' value).
+int scan_grid(const Level &L, int64_t n) { return std::min(L.scan_cap, grid_for((n + 3) / 4, kTB)); }
+int list_blocks(const Level &L, int64_t items) { return std::min(L.list_cap, grid_for(items, L.items_per_block)); }
+int apply_blocks(const Level &L, int64_t items) { return std::min(L.apply_cap, grid_for(items, L.items_per_block)); }
 
 // Launch of a kernel that follows another one of the same pass: with
 // L.pdl it may be scheduled early and waits on the device (pdl_enter).
@@ -586,10 +741,10 @@ int enqueue_lp_select(const Level &L, cudaStream_t s, LpExport ex, int *nk, Kern
     int n = L.g.n;
     bool ew = L.g.ew != nullptr;
     JET_TRY(prof_mark(pr, s, JET_K_LP_SCAN));
-    k_lp_scan<<<scan_grid(n), kTB, sm_lp_scan(), s>>>(L);
+    k_lp_scan<<<scan_grid(L, n), kTB, sm_lp_scan(), s>>>(L);
     const size_t sm = sm_lp_select(L.k, kTB, true);
     JET_TRY(prof_mark(pr, s, JET_K_LP_SELECT));
-    JET_CUDA_TRY(launch_dep(L, ew ? k_lp_select<true> : k_lp_select<false>, list_blocks(n), kTB, sm, s, L, ex));
+    JET_CUDA_TRY(launch_dep(L, ew ? k_lp_select<true> : k_lp_select<false>, list_blocks(L, n), kTB, sm, s, L, ex));
     *nk = 2;
     JET_CUDA_TRY(cudaGetLastError());
     return JET_OK;
@@ -598,7 +753,7 @@ int enqueue_lp_select(const Level &L, cudaStream_t s, LpExport ex, int *nk, Kern
 int enqueue_lp_after(const Level &L, cudaStream_t s, LpExport ex, int *nk, KernProf *pr = nullptr) {
     int n = L.g.n;
     JET_TRY(prof_mark(pr, s, JET_K_AFTERBURN));
-    JET_CUDA_TRY(launch_dep(L, L.g.ew ? k_afterburn<true> : k_afterburn<false>, list_blocks(n), kTB, sm_afterburn(), s,
+    JET_CUDA_TRY(launch_dep(L, L.g.ew ? k_afterburn<true> : k_afterburn<false>, list_blocks(L, n), kTB, sm_afterburn(), s,
                             L, ex));
     *nk = 1;
     JET_CUDA_TRY(cudaGetLastError());
@@ -619,10 +774,10 @@ int enqueue_rb_t(const Level &L, cudaStream_t s, int *nk, KernProf *pr) {
     int n = L.g.n;
     bool ew = L.g.ew != nullptr;
     JET_TRY(prof_mark(pr, s, JET_K_RB_SCAN));
-    k_rb_scan<STRONG><<<scan_grid(n), kTB, sm_rb_scan(), s>>>(L);
+    k_rb_scan<STRONG><<<scan_grid(L, n), kTB, sm_rb_scan(), s>>>(L);
     const size_t sm = sm_rb_cand(L.k, kTB, true);
     JET_TRY(prof_mark(pr, s, JET_K_RB_CAND));
-    JET_CUDA_TRY(launch_dep(L, ew ? k_rb_cand<true, STRONG> : k_rb_cand<false, STRONG>, list_blocks(n), kTB, sm, s, L));
+    JET_CUDA_TRY(launch_dep(L, ew ? k_rb_cand<true, STRONG> : k_rb_cand<false, STRONG>, list_blocks(L, n), kTB, sm, s, L));
     JET_TRY(prof_mark(pr, s, JET_K_RB_TILEHIST));
     JET_CUDA_TRY(launch_dep(L, k_rb_tilehist, L.ntiles, kRbTile, sm_rb_tilehist(L.k), s, L));
     JET_TRY(prof_mark(pr, s, JET_K_RB_TILESCAN));
@@ -645,7 +800,7 @@ int enqueue_rb(const Level &L, cudaStream_t s, bool strong, int *nk, KernProf *p
 
 // apply + commit + controller
 int enqueue_tail(const Level &L, cudaStream_t s, int *nk, KernProf *pr = nullptr) {
-    int ga = list_blocks(L.g.n);
+    int ga = apply_blocks(L, L.g.n);
     JET_TRY(prof_mark(pr, s, JET_K_APPLY));
     if (L.g.ew) k_apply<true><<<ga, kTB, sm_apply(L.k), s>>>(L);
     else k_apply<false><<<ga, kTB, sm_apply(L.k), s>>>(L);
@@ -935,7 +1090,7 @@ int grid_loop_blocks(int device, size_t smem, int64_t n, int *out) {
     }
     if (per_sm <= 0) return JET_OK;
     int cap = num_sms() * std::min(per_sm, JET_ROW_MINB);
-    *out = std::min(cap, list_blocks(n));
+    *out = std::min(cap, grid_for(n, 64));
     return JET_OK;
 }
 
@@ -1010,6 +1165,12 @@ static void fill_level_params(Ctx &c, Level &L, int32_t is_finest, uint64_t seed
     L.use_graph = 0;
     L.h_loop = L.h_mode = 0;
     L.pdl = (o.flags & JET_FLAG_NO_PDL) ? 0 : 1;
+    const int sms = num_sms();
+    L.hub_deg = o.hub_degree > 0 ? o.hub_degree : kHugeDeg;
+    L.list_cap = sms * (o.list_blocks_per_sm > 0 ? o.list_blocks_per_sm : 4);
+    L.apply_cap = o.apply_blocks_per_sm > 0 ? sms * o.apply_blocks_per_sm : L.list_cap;
+    L.scan_cap = sms * (o.scan_blocks_per_sm > 0 ? o.scan_blocks_per_sm : 8);
+    L.items_per_block = o.list_items_per_block > 0 ? o.list_items_per_block : 64;
     L.poll_limit = o.barrier_polls > 0 ? o.barrier_polls : kBarPollLimit;
 }
 
@@ -1133,6 +1294,133 @@ int refine_level(Ctx &c, const DGraph &g, int32_t k, double eps, int32_t is_fine
         return JET_ECUDA;
     }
     return refine_level_finish(c, run, cut_out, maxw_out, rep_out);
+}
+
+// ---- batched form: small levels of many graphs ----------------------------
+
+int refine_small_chains(Ctx &c, SmallChain *chains, int32_t nchains, int32_t cluster_blocks, int *ran) {
+    *ran = 0;
+    if (nchains <= 0) {
+        *ran = 1;
+        return JET_OK;
+    }
+    cudaStream_t s = c.stream;
+    JET_TRY(allow_large_arenas(c.device));
+    int32_t kmax = 1;
+    int64_t nlv_total = 0;
+    size_t total = 0;
+    std::vector<size_t> off((size_t)nchains);
+    for (int32_t j = 0; j < nchains; ++j) {
+        const SmallChain &ch = chains[j];
+        int64_t nmax = 1;
+        for (int32_t lv = ch.bottom; lv <= ch.top; ++lv) nmax = std::max<int64_t>(nmax, ch.h->n[lv]);
+        size_t vb = 0, mb = 0;
+        level_bytes(nmax, ch.k, false, &vb, &mb);
+        off[(size_t)j] = total;
+        total += align256(vb) + align256(mb) + 2 * align256((size_t)nmax * 4);
+        nlv_total += ch.top - ch.bottom + 1;
+        kmax = std::max(kmax, ch.k);
+    }
+    const size_t jobs_off = total;
+    const size_t lv_off = jobs_off + align256(sizeof(BatchJob) * (size_t)nchains);
+    const size_t st_off = lv_off + align256(sizeof(BatchLevel) * (size_t)nlv_total);
+    const size_t q_off = st_off + align256(sizeof(BatchStat) * (size_t)nlv_total);
+    DevBuf buf;
+    JET_TRY(dev_alloc(buf, q_off + 256, s));
+    char *base = buf.as<char>();
+    BatchJob *d_jobs = reinterpret_cast<BatchJob *>(base + jobs_off);
+    BatchLevel *d_lv = reinterpret_cast<BatchLevel *>(base + lv_off);
+    BatchStat *d_st = reinterpret_cast<BatchStat *>(base + st_off);
+    int32_t *d_queue = reinterpret_cast<int32_t *>(base + q_off);
+    std::vector<BatchJob> jobs((size_t)nchains);
+    std::vector<BatchLevel> lvs((size_t)nlv_total);
+    int64_t li = 0;
+    for (int32_t j = 0; j < nchains; ++j) {
+        const SmallChain &ch = chains[j];
+        int64_t nmax = 1;
+        for (int32_t lv = ch.bottom; lv <= ch.top; ++lv) nmax = std::max<int64_t>(nmax, ch.h->n[lv]);
+        size_t vb = 0, mb = 0;
+        level_bytes(nmax, ch.k, false, &vb, &mb);
+        char *p = base + off[(size_t)j];
+        BatchJob &jb = jobs[(size_t)j];
+        memset(&jb, 0, sizeof(jb));
+        Level &L = jb.L;
+        carve_level(L, p, p + align256(vb), nmax, ch.k, false, &jb.cut2);
+        fill_level_params(c, L, 0, 0);   // per-level fields (c, seed, graph) are set in the kernel
+        jb.part[0] = reinterpret_cast<int32_t *>(p + align256(vb) + align256(mb));
+        jb.part[1] = jb.part[0] + align256((size_t)nmax * 4) / 4;
+        jb.init = ch.init;
+        jb.out = ch.out;
+        jb.lv = d_lv + li;
+        jb.stat = d_st + li;
+        jb.nlv = ch.top - ch.bottom + 1;
+        jb.Llim = balance_limit(ch.W, ch.k, ch.eps, &jb.opt);
+        jb.sigma = jb.opt + (jb.Llim - jb.opt) / 2;
+        for (int32_t lv = ch.top; lv >= ch.bottom; --lv, ++li) {
+            BatchLevel &bl = lvs[(size_t)li];
+            memset(&bl, 0, sizeof(bl));
+            bl.g.n = ch.h->n[lv]; bl.g.nnz = ch.h->nnz[lv]; bl.g.xadj = ch.h->xadj[lv]; bl.g.adj = ch.h->adj[lv];
+            bl.g.vw = ch.h->vw[lv]; bl.g.ew = ch.h->ew[lv];
+            bl.cmap = ch.h->cmap[lv];
+            bl.seed = level_seed(ch.seed, lv);
+            bl.cq16 = (int32_t)llround((lv == 0 ? c.opt.c_fine : c.opt.c_coarse) * 65536.0);
+        }
+    }
+    // launch shape: clusters of cluster_blocks blocks, as many as are co-resident
+    const size_t smem = cluster_smem(kmax);
+    JET_CUDA_TRY(cudaFuncSetAttribute(k_refine_batch, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    JET_CUDA_TRY(cudaFuncSetAttribute(k_refine_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int cs = cluster_blocks > 0 ? cluster_blocks : 4;
+    int nclusters = 0;
+    for (; cs >= 2; cs /= 2) {
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3(cs);
+        cfg.blockDim = dim3(kClusterThreads);
+        cfg.dynamicSmemBytes = smem;
+        cudaLaunchAttribute at{};
+        at.id = cudaLaunchAttributeClusterDimension;
+        at.val.clusterDim.x = cs;
+        at.val.clusterDim.y = 1;
+        at.val.clusterDim.z = 1;
+        cfg.attrs = &at;
+        cfg.numAttrs = 1;
+        cudaError_t e = cudaOccupancyMaxActiveClusters(&nclusters, k_refine_batch, &cfg);
+        if (e != cudaSuccess) { cudaGetLastError(); nclusters = 0; }
+        if (nclusters >= 1) break;
+    }
+    if (nclusters < 1) return JET_OK;   // *ran = 0: the caller takes the levels one by one
+    nclusters = std::min(nclusters, nchains);
+    JET_CUDA_TRY(cudaMemcpyAsync(d_jobs, jobs.data(), sizeof(BatchJob) * (size_t)nchains, cudaMemcpyHostToDevice, s));
+    JET_CUDA_TRY(cudaMemcpyAsync(d_lv, lvs.data(), sizeof(BatchLevel) * (size_t)nlv_total, cudaMemcpyHostToDevice, s));
+    JET_CUDA_TRY(cudaMemsetAsync(d_queue, 0, 4, s));
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)(nclusters * cs));
+    cfg.blockDim = dim3(kClusterThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at{};
+    at.id = cudaLaunchAttributeClusterDimension;
+    at.val.clusterDim.x = cs;
+    at.val.clusterDim.y = 1;
+    at.val.clusterDim.z = 1;
+    cfg.attrs = &at;
+    cfg.numAttrs = 1;
+    JET_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_refine_batch, (const BatchJob *)d_jobs, nchains, d_queue));
+    c.launches += 1;
+    std::vector<BatchStat> st((size_t)nlv_total);
+    JET_CUDA_TRY(cudaMemcpyAsync(st.data(), d_st, sizeof(BatchStat) * (size_t)nlv_total, cudaMemcpyDeviceToHost, s));
+    JET_CUDA_TRY(cudaStreamSynchronize(s));   // also keeps the host arrays of the copies alive until done
+    li = 0;
+    for (int32_t j = 0; j < nchains; ++j) {
+        SmallChain &ch = chains[j];
+        li += ch.top - ch.bottom + 1;
+        const BatchStat &b = st[(size_t)li - 1];   // the chain's finest level
+        ch.cut = b.best_cut;
+        ch.maxw = b.best_maxw;
+        ch.status = !b.best_bal ? JET_WUNBALANCED : (b.hit_cap ? JET_WITERLIMIT : JET_OK);
+    }
+    *ran = 1;
+    return JET_OK;
 }
 
 // ---- single passes --------------------------------------------------------

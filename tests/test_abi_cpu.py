@@ -47,15 +47,38 @@ def test_library_is_sm103a_only(lib_path):
     assert os.path.getsize(lib_path) > 0
 
 
-def test_options_struct_layout_matches_header():
-    # 3 doubles, 6 int32, 1 uint32, 2 int32 -> 60 bytes, padded to 64
-    assert ctypes.sizeof(binding.Options) == 64
-    # jet_batch_item: int32, 4 pointers, int32, double, uint64, pointer, int64, int32, float
-    assert ctypes.sizeof(binding._BatchItem) == 88
-    assert ctypes.sizeof(binding._LearnedInfo) == 48
-    assert ctypes.sizeof(binding._TuneReport) == 16 + 4 * 64
-    # jet_stats: int32 + 2*64 int64 + 3*64 int32 + 64 int64 + 2 int64 + 5 float + 2 int64
-    assert ctypes.sizeof(binding._CStats) % 8 == 0
+def _c_layout(exprs):
+    """sizeof / offsetof values of the header's structs, from gcc."""
+    import subprocess
+    import tempfile
+    src = "#include <stddef.h>\n#include <stdio.h>\n#include \"jet.h\"\nint main(void){\n"
+    for e in exprs:
+        src += f'printf("%zu\\n", (size_t)({e}));\n'
+    src += "return 0;}\n"
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "layout.c")
+        exe = os.path.join(d, "layout")
+        with open(c, "w") as f:
+            f.write(src)
+        subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), c, "-o", exe])
+        out = subprocess.check_output([exe]).decode().split()
+    return [int(x) for x in out]
+
+
+def test_struct_layouts_match_header():
+    """Every struct the binding passes across the ABI has the size and field
+    offsets the C compiler gives the header's declaration."""
+    cases = [("jet_options", binding.Options), ("jet_stats", binding._CStats), ("jet_batch_item", binding._BatchItem),
+             ("jet_learned_info", binding._LearnedInfo), ("jet_tune_report", binding._TuneReport)]
+    exprs = []
+    for cname, py in cases:
+        exprs.append(f"sizeof({cname})")
+        exprs += [f"offsetof({cname}, {f[0]})" for f in py._fields_]
+    vals = iter(_c_layout(exprs))
+    for cname, py in cases:
+        assert next(vals) == ctypes.sizeof(py), cname
+        for f in py._fields_:
+            assert next(vals) == getattr(py, f[0]).offset, (cname, f[0])
 
 
 def test_flag_values_match_header():

@@ -512,6 +512,37 @@ def test_partition_batch_matches_oracle(ctx):
         assert status == ref.status and cut == ref.cut and (_np(part) == ref.part).all()
 
 
+def _batch_graphs():
+    """Uneven sizes and kinds: small RGGs (every level within the cluster
+    threshold), weighted meshes, a weighted R-MAT graph, larger RGGs."""
+    rng = np.random.default_rng(11)
+    gs = [graphgen.rgg(int(n), seed=i + 20) for i, n in enumerate(rng.integers(300, 4000, 14))]
+    gs += [graphgen.grid3d(12, 10, 9, vw=(1, 4), ew=(1, 10), seed=3), graphgen.grid2d(70, 50, ew=(1, 5), seed=2),
+           graphgen.rmat(11, seed=8, vw=(1, 3), ew=(1, 5)), graphgen.rgg(20000, seed=5), graphgen.rgg(45000, seed=6)]
+    ks = [int(x) for x in rng.choice([2, 4, 8, 16, 32, 64, 128], len(gs))]
+    return gs, ks
+
+
+@pytest.mark.parametrize("opts", [{}, {"cluster_blocks": 2}, {"cluster_blocks": 8}, {"cluster_max_n": 0},
+                                  {"cluster_max_n": 64}, {"cluster_max_n": 1 << 20}],
+                         ids=["default", "clusters2", "clusters8", "no_small_levels", "threshold64", "all_small"])
+def test_partition_batch_small_levels_in_one_launch(opts):
+    """The batched form refines every graph's levels up to cluster_max_n in
+    one persistent cluster launch over a queue of graphs (the rest level by
+    level); each graph bit-exact with the oracle, under every threshold and
+    cluster size."""
+    gs, ks = _batch_graphs()
+    items = [dict(xadj=g.xadj, adjncy=g.adjncy, vwgt=g.vwgt if i >= 14 else None,
+                  adjwgt=g.adjwgt if i >= 14 else None, k=k, eps=0.03, seed=i + 3) for i, (g, k) in enumerate(zip(gs, ks))]
+    with jet.Context(0, **opts) as c:
+        out = c.partition_batch(items, workers=3)
+    for i, ((part, cut, status, ms), g, k, it) in enumerate(zip(out, gs, ks, items)):
+        og = graphgen.Graph(g.n, g.xadj, g.adjncy, it["vwgt"], it["adjwgt"])
+        ref = oracle.partition(og, k, 0.03, it["seed"])
+        assert status == ref.status and cut == ref.cut, i
+        assert (_np(part) == ref.part).all(), i
+
+
 @pytest.mark.parametrize("g,k", [(graphgen.grid3d(24, 24, 24, vw=(1, 4), ew=(1, 10), seed=9), 64),
                                  (graphgen.rmat(12, seed=5), 16)], ids=["grid24w_k64", "rmat12_k16"])
 def test_coarsest_refined_matches_oracle(ctx, g, k):
@@ -552,12 +583,13 @@ def test_autotune_picks_fastest_and_keeps_results():
     c = jet.Context(0)
     rep = c.autotune(items, reps=1)
     cands = rep["candidates"]
-    assert len(cands) == 4 + 6 + 5
-    assert rep["cluster_blocks"] == min(cands[:4], key=lambda x: x["ms"])["cluster_blocks"]
-    assert rep["cluster_max_n"] == min(cands[4:10], key=lambda x: x["ms"])["cluster_max_n"]
-    assert rep["workers"] == min(cands[10:], key=lambda x: x["ms"])["workers"]
-    assert all(x["cluster_blocks"] == rep["cluster_blocks"] for x in cands[4:])
-    assert c.options.cluster_max_n == rep["cluster_max_n"] and c.options.cluster_blocks == rep["cluster_blocks"]
+    sizes = {"cluster_blocks": 4, "cluster_max_n": 6, "workers": 5, "list_blocks_per_sm": 3, "apply_blocks_per_sm": 3,
+             "list_items_per_block": 3, "scan_blocks_per_sm": 3, "hub_degree": 3}
+    assert [x["stage"] for x in cands] == [st for st, m in sizes.items() for _ in range(m)]
+    for st in sizes:
+        assert rep[st] == min((x for x in cands if x["stage"] == st), key=lambda x: x["ms"])["value"], st
+        if st != "workers":
+            assert getattr(c.options, st) == rep[st], st
     for (part, cut), g, k, it in zip(rep["parts"], gs, ks, items):
         ref = oracle.partition(g, k, 0.03, it["seed"])
         assert cut == ref.cut and (_np(part) == ref.part).all()
