@@ -64,6 +64,8 @@ def parse_args(argv=None):
                    help="largest level refined by the one-cluster loop (library default if omitted; 0 = never)")
     p.add_argument("--kernel-probe", action="store_true",
                    help="run one profiled partition and report per-level select launches (profiler target)")
+    p.add_argument("--probe-graph", choices=["mesh", "rmat22"], default="mesh",
+                   help="with --kernel-probe: the mesh workload (--scale) or R-MAT scale 22")
     p.add_argument("--rmat-k", type=int, default=None, help="with --sweep rmat: only this k")
     p.add_argument("--two-hop", action="store_true", help="with --sweep rmat: coarsen with two-hop matches")
     p.add_argument("--sweep", choices=["lp_versions", "batched", "rmat", "shapes"], default=None,
@@ -290,14 +292,20 @@ def roofline_of(table, top, peak, peak_kind, workload_tag):
 
 
 def run_probe(args):
-    """One partition of the workload with the select kernels bracketed by
-    CUDA events; prints how many select launches precede the finest level."""
+    """One profiled partition (CUDA events around every refinement kernel) of
+    the mesh workload, or of R-MAT scale 22 with --probe-graph rmat22; prints
+    per-level kernel times (a target for profiler launch lists)."""
     import torch
     import paper_2304_13194_gb300 as jet
     torch.cuda.set_device(0)
-    g = workload_graph(args.scale)
     dev = torch.device("cuda", 0)
-    t = [torch.from_numpy(a).to(dev) for a in (g.xadj, g.adjncy, g.vwgt, g.adjwgt)]
+    if args.probe_graph == "rmat22":
+        import graphgen
+        g = graphgen.rmat(22, seed=SEED)
+        t = [torch.from_numpy(g.xadj).to(dev), torch.from_numpy(g.adjncy).to(dev), None, None]
+    else:
+        g = workload_graph(args.scale)
+        t = [torch.from_numpy(a).to(dev) for a in (g.xadj, g.adjncy, g.vwgt, g.adjwgt)]
     with jet.Context(0, flags=jet.FLAG_PROFILE) as ctx:
         _, cut, st = ctx.partition(*t, k=K_PARTS, eps=EPS, seed=SEED, return_stats=True)
     skip = sum(st.sel_launches[1:])

@@ -721,12 +721,27 @@ __device__ __forceinline__ void lp_select_row(const Level &L, LpExport ex, int32
     int32_t conn_s = tab[ps];
     __syncwarp();
     unsigned long long best = 0;
-    for (int64_t j = beg + lane; j < end; j += 32) {
-        int32_t p = L.part[__ldg(g.adj + j)];
-        int32_t c = atomicExch(&tab[p], 0);
-        if (c > 0 && p != ps) {
-            unsigned long long key = part_key(c, p);
-            best = key > best ? key : best;
+    if (end - beg > L.k) {
+        // a row longer than the table: read (and clear) the k entries instead
+        // of gathering the row's parts a second time
+        for (int p = lane; p < L.k; p += 32) {
+            const int32_t c = tab[p];
+            if (c != 0) {
+                tab[p] = 0;
+                if (p != ps) {
+                    const unsigned long long key = part_key(c, p);
+                    best = key > best ? key : best;
+                }
+            }
+        }
+    } else {
+        for (int64_t j = beg + lane; j < end; j += 32) {
+            int32_t p = L.part[__ldg(g.adj + j)];
+            int32_t c = atomicExch(&tab[p], 0);
+            if (c > 0 && p != ps) {
+                unsigned long long key = part_key(c, p);
+                best = key > best ? key : best;
+            }
         }
     }
     __syncwarp();
@@ -1277,16 +1292,30 @@ __device__ __forceinline__ void rb_cand_row(const Level &L, int32_t v, int32_t *
     unsigned long long best = 0;
     long long S = 0;
     int32_t cnt = 0;
-    for (int64_t j = beg + lane; j < end; j += 32) {
-        int32_t p = L.part[__ldg(g.adj + j)];
-        int32_t c = atomicExch(&tab[p], 0);
-        if (c > 0 && L.inB[p]) {
+    auto take = [&](int32_t c, int32_t p) {   // part p met once with connectivity c > 0
+        if (L.inB[p]) {
             if constexpr (!STRONG) {
                 unsigned long long k2 = part_key(c, p);
                 best = k2 > best ? k2 : best;
             } else {
                 S += c; cnt += 1;
             }
+        }
+    };
+    if (end - beg > L.k) {
+        // a row longer than the table: read (and clear) the k entries instead
+        for (int p = lane; p < L.k; p += 32) {
+            const int32_t c = tab[p];
+            if (c != 0) {
+                tab[p] = 0;
+                take(c, p);
+            }
+        }
+    } else {
+        for (int64_t j = beg + lane; j < end; j += 32) {
+            int32_t p = L.part[__ldg(g.adj + j)];
+            int32_t c = atomicExch(&tab[p], 0);
+            if (c > 0) take(c, p);
         }
     }
     __syncwarp();
