@@ -86,6 +86,32 @@ __global__ void __launch_bounds__(kTB) k_hem_propose_small(DGraph g, const int32
     prop[v] = bu;
 }
 
+// The heaviest unmatched neighbour over the entries first, first + step, ...
+// < end of a row, four at a time (ids, then their mates, in flight
+// together); folds into (bu, bw, bh).
+template <bool EW>
+__device__ __forceinline__ void hem_row(const DGraph &g, const int32_t *mate, uint64_t seed, uint64_t salt, int64_t first,
+                                        int64_t end, int64_t step, int32_t &bu, int32_t &bw, uint64_t &bh) {
+    constexpr int U = 4;
+    for (int64_t j0 = first; j0 < end; j0 += U * step) {
+        int32_t u[U], m[U];
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+            const int64_t j = j0 + q * step;
+            u[q] = j < end ? __ldg(g.adj + j) : -1;
+        }
+#pragma unroll
+        for (int q = 0; q < U; ++q) m[q] = u[q] >= 0 ? mate[u[q]] : 0;
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+            if (u[q] < 0 || m[q] >= 0) continue;
+            const int32_t ww = cw<EW>(g, j0 + q * step);
+            const uint64_t h = hem_hash(seed, salt, u[q]);
+            if (hem_better(ww, h, u[q], bw, bh, bu)) { bu = u[q]; bw = ww; bh = h; }
+        }
+    }
+}
+
 template <bool EW>
 __global__ void __launch_bounds__(kTB) k_hem_propose_big(DGraph g, const int32_t *bigv, int32_t nbig, const int32_t *mate,
                                                          int32_t *prop, uint64_t seed, uint64_t salt, int r, HemCtl *hc) {
@@ -98,13 +124,7 @@ __global__ void __launch_bounds__(kTB) k_hem_propose_big(DGraph g, const int32_t
         uint64_t bh = 0;
         if (mate[v] < 0) {
             int64_t beg = ld_xadj(g.xadj, v), end = ld_xadj(g.xadj, (int64_t)v + 1);
-            for (int64_t j = beg + lane; j < end; j += 32) {
-                int32_t u = __ldg(g.adj + j);
-                if (mate[u] >= 0) continue;
-                int32_t ww = cw<EW>(g, j);
-                uint64_t h = hem_hash(seed, salt, u);
-                if (hem_better(ww, h, u, bw, bh, bu)) { bu = u; bw = ww; bh = h; }
-            }
+            hem_row<EW>(g, mate, seed, salt, beg + lane, end, 32, bu, bw, bh);
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -132,13 +152,7 @@ __global__ void __launch_bounds__(kTB) k_hem_propose_huge(DGraph g, const int32_
         uint64_t bh = 0;
         if (mate[v] < 0) {
             const int64_t beg = ld_xadj(g.xadj, v), end = ld_xadj(g.xadj, (int64_t)v + 1);
-            for (int64_t j = beg + threadIdx.x; j < end; j += blockDim.x) {
-                const int32_t u = __ldg(g.adj + j);
-                if (mate[u] >= 0) continue;
-                const int32_t ww = cw<EW>(g, j);
-                const uint64_t h = hem_hash(seed, salt, u);
-                if (hem_better(ww, h, u, bw, bh, bu)) { bu = u; bw = ww; bh = h; }
-            }
+            hem_row<EW>(g, mate, seed, salt, beg + threadIdx.x, end, blockDim.x, bu, bw, bh);
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {

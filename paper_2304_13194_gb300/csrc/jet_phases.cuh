@@ -658,6 +658,33 @@ __device__ __forceinline__ void tables_clear(int32_t *tabs, int32_t k) {
     for (int i = threadIdx.x; i < n; i += blockDim.x) tabs[i] = 0;
 }
 
+// Long rows are walked kRowBatch entries per thread at a time: the entries'
+// neighbour ids (and weights) are loaded together, then the neighbours'
+// fields, then they are used, so a thread keeps kRowBatch dependent gather
+// chains in flight instead of one (a hub row of 160k entries otherwise takes
+// a block as long as a whole pass).
+constexpr int kRowBatch = 4;
+
+// conn(v, .) of the entries first, first + step, ... < end added into tab.
+template <bool EW>
+__device__ __forceinline__ void row_to_table(const Level &L, int64_t first, int64_t end, int64_t step, int32_t *tab) {
+    const DGraph &g = L.g;
+    for (int64_t j0 = first; j0 < end; j0 += kRowBatch * step) {
+        int32_t u[kRowBatch], w[kRowBatch], p[kRowBatch];
+#pragma unroll
+        for (int q = 0; q < kRowBatch; ++q) {
+            const int64_t j = j0 + q * step;
+            u[q] = j < end ? __ldg(g.adj + j) : -1;
+            w[q] = j < end ? edge_w<EW>(g, j) : 0;
+        }
+#pragma unroll
+        for (int q = 0; q < kRowBatch; ++q) p[q] = u[q] >= 0 ? L.part[u[q]] : -1;
+#pragma unroll
+        for (int q = 0; q < kRowBatch; ++q)
+            if (p[q] >= 0) atomicAdd(&tab[p[q]], w[q]);
+    }
+}
+
 // One hub row of step 1 (longer than kHugeDeg) by the whole block: each warp
 // adds its share of conn(v, .) into its own k-entry table (tabs, zero
 // between rows), the parts then sum the warps' entries; the same result as
@@ -669,8 +696,7 @@ __device__ __forceinline__ void lp_select_block_row(const Level &L, LpExport ex,
     const int32_t ps = L.part[v];
     const int64_t beg = ld_xadj(g.xadj, v), end = ld_xadj(g.xadj, (int64_t)v + 1);
     int32_t *tab = tabs + (threadIdx.x >> 5) * L.k;
-    for (int64_t j = beg + threadIdx.x; j < end; j += blockDim.x)
-        atomicAdd(&tab[L.part[__ldg(g.adj + j)]], edge_w<EW>(g, j));
+    row_to_table<EW>(L, beg + threadIdx.x, end, blockDim.x, tab);
     __syncthreads();
     const int32_t conn_s = tables_sum(tabs, L.k, ps);
     unsigned long long best = 0;
@@ -716,7 +742,7 @@ __device__ __forceinline__ void lp_select_row(const Level &L, LpExport ex, int32
     int32_t F = kNoneGain, pd = -1;
     bool inX = false;
     int64_t beg = ld_xadj(g.xadj, v), end = ld_xadj(g.xadj, (int64_t)v + 1);
-    for (int64_t j = beg + lane; j < end; j += 32) atomicAdd(&tab[L.part[__ldg(g.adj + j)]], edge_w<EW>(g, j));
+    row_to_table<EW>(L, beg + lane, end, 32, tab);
     __syncwarp();
     int32_t conn_s = tab[ps];
     __syncwarp();
@@ -857,17 +883,34 @@ __device__ inline void ph_lp_select(const Level &L, LpExport ex, Grid G, char *a
 // Step 2: afterburner (Alg. 4 second loop, ord of Sec. 4.1.1) and the second
 // filter M = {v in X : F2 >= 0}.  A neighbour u counts in its destination
 // part when it precedes v in ord (higher F, ties to the lower id).
+// F2 share of the entries first, first + step, ... < end of v's row (batched
+// as row_to_table): a neighbour counts at its destination when it precedes
+// v in ord; its move is loaded only for the neighbours that take it.
 template <bool EW>
-__device__ __forceinline__ int32_t afterburn_term(const Level &L, int32_t v, int32_t Fv, int32_t pd, int32_t ps,
-                                                  int64_t j) {
-    int32_t u = __ldg(L.g.adj + j);
-    // long rows (one warp each) are bandwidth-bound: the move is loaded only
-    // for the neighbours that take it
-    int32_t pu = L.part[u];
-    const int32_t fu = L.prio[u];
-    if (fu > Fv || (fu == Fv && u < v)) pu = nxt_to(L.nxt[u]);
-    int32_t w = edge_w<EW>(L.g, j);
-    return pu == pd ? w : (pu == ps ? -w : 0);
+__device__ __forceinline__ long long afterburn_row(const Level &L, int32_t v, int32_t Fv, int32_t pd, int32_t ps,
+                                                   int64_t first, int64_t end, int64_t step) {
+    const DGraph &g = L.g;
+    long long f2 = 0;
+    for (int64_t j0 = first; j0 < end; j0 += kRowBatch * step) {
+        int32_t u[kRowBatch], w[kRowBatch], pu[kRowBatch], fu[kRowBatch];
+#pragma unroll
+        for (int q = 0; q < kRowBatch; ++q) {
+            const int64_t j = j0 + q * step;
+            u[q] = j < end ? __ldg(g.adj + j) : -1;
+            w[q] = j < end ? edge_w<EW>(g, j) : 0;
+        }
+#pragma unroll
+        for (int q = 0; q < kRowBatch; ++q) {
+            pu[q] = u[q] >= 0 ? L.part[u[q]] : -1;
+            fu[q] = u[q] >= 0 ? L.prio[u[q]] : kNoneGain;
+        }
+#pragma unroll
+        for (int q = 0; q < kRowBatch; ++q)
+            if (u[q] >= 0 && (fu[q] > Fv || (fu[q] == Fv && u[q] < v))) pu[q] = nxt_to(L.nxt[u[q]]);
+#pragma unroll
+        for (int q = 0; q < kRowBatch; ++q) f2 += pu[q] == pd ? w[q] : (pu[q] == ps ? -w[q] : 0);
+    }
+    return f2;
 }
 
 // One hub row of step 2 by the whole block.
@@ -875,8 +918,7 @@ template <bool EW>
 __device__ __forceinline__ void afterburn_block_row(const Level &L, LpExport ex, int32_t v, int32_t it, long long *red) {
     const int32_t Fv = L.prio[v], pd = nxt_to(L.nxt[v]), ps = L.part[v];
     const int64_t beg = ld_xadj(L.g.xadj, v), end = ld_xadj(L.g.xadj, (int64_t)v + 1);
-    long long f2 = 0;
-    for (int64_t j = beg + threadIdx.x; j < end; j += blockDim.x) f2 += afterburn_term<EW>(L, v, Fv, pd, ps, j);
+    long long f2 = afterburn_row<EW>(L, v, Fv, pd, ps, beg + threadIdx.x, end, blockDim.x);
     f2 = block_sum_i64(f2, red);
     if (threadIdx.x == 0) {
         if (ex.f2) ex.f2[v] = (int32_t)f2;
@@ -914,8 +956,7 @@ __device__ inline void ph_afterburn(const Level &L, LpExport ex, Grid G, char *a
     auto big_row = [&](int32_t v) {
         int32_t Fv = L.prio[v], pd = nxt_to(L.nxt[v]), ps = L.part[v];
         int64_t beg = ld_xadj(L.g.xadj, v), end = ld_xadj(L.g.xadj, (int64_t)v + 1);
-        int32_t f2 = 0;
-        for (int64_t j = beg + lane; j < end; j += 32) f2 += afterburn_term<EW>(L, v, Fv, pd, ps, j);
+        int32_t f2 = (int32_t)afterburn_row<EW>(L, v, Fv, pd, ps, beg + lane, end, 32);
         f2 = warp_sum_i32(f2);
         if (lane == 0) {
             if (ex.f2) ex.f2[v] = f2;
@@ -1012,6 +1053,44 @@ __device__ __forceinline__ int64_t apply_edge(const Level &L, int32_t v, int32_t
     return (int64_t)w * diff;
 }
 
+// apply_edge over the entries first, first + step, ... < end of the row of
+// v (moving a -> b), batched as row_to_table: the stamps of a batch are
+// loaded together, then the move or the part of each neighbour, whichever
+// it needs.  c: cut change, ne: neighbours in other parts after the move.
+template <bool EW>
+__device__ __forceinline__ void apply_row(const Level &L, int32_t v, int32_t a, int32_t b, int32_t it, int64_t first,
+                                          int64_t end, int64_t step, long long &c, long long &ne) {
+    const DGraph &g = L.g;
+    for (int64_t j0 = first; j0 < end; j0 += kRowBatch * step) {
+        int32_t u[kRowBatch], w[kRowBatch], x[kRowBatch];
+        bool mu[kRowBatch];
+#pragma unroll
+        for (int q = 0; q < kRowBatch; ++q) {
+            const int64_t j = j0 + q * step;
+            u[q] = j < end ? __ldg(g.adj + j) : -1;
+            w[q] = j < end ? edge_w<EW>(g, j) : 0;
+        }
+#pragma unroll
+        for (int q = 0; q < kRowBatch; ++q) mu[q] = u[q] >= 0 && L.mstamp[u[q]] == it;
+#pragma unroll
+        for (int q = 0; q < kRowBatch; ++q) x[q] = u[q] < 0 ? 0 : (mu[q] ? L.nxt[u[q]] : L.part[u[q]]);
+#pragma unroll
+        for (int q = 0; q < kRowBatch; ++q) {
+            if (u[q] < 0) continue;
+            const int32_t pu = mu[q] ? nxt_from(x[q]) : x[q];
+            const int32_t pn = mu[q] ? nxt_to(x[q]) : x[q];
+            const int32_t diff = (int)(pn != b) - (int)(pu != a);
+            ne += pn != b;
+            if (!mu[q]) {
+                if (diff) atomicAdd(&L.ext[u[q]], diff);
+                c += (long long)w[q] * diff;
+            } else if (u[q] > v) {
+                c += (long long)w[q] * diff;   // an edge whose ends both move counts at the smaller id
+            }
+        }
+    }
+}
+
 // One hub row of the apply phase by the whole block.
 template <bool EW>
 __device__ __forceinline__ void apply_block_row(const Level &L, int32_t v, int32_t it, bool lp, long long *red,
@@ -1020,11 +1099,7 @@ __device__ __forceinline__ void apply_block_row(const Level &L, int32_t v, int32
     const int32_t a = nxt_from(x), b = nxt_to(x);
     const int64_t beg = ld_xadj(L.g.xadj, v), end = ld_xadj(L.g.xadj, (int64_t)v + 1);
     long long c = 0, ne = 0;
-    for (int64_t j = beg + threadIdx.x; j < end; j += blockDim.x) {
-        int32_t o;
-        c += apply_edge<EW, false>(L, v, a, b, it, __ldg(L.g.adj + j), edge_w<EW>(L.g, j), &o);
-        ne += o;
-    }
+    apply_row<EW>(L, v, a, b, it, beg + threadIdx.x, end, blockDim.x, c, ne);
     c = block_sum_i64(c, red);
     ne = block_sum_i64(ne, red);
     if (threadIdx.x == 0) {
@@ -1054,19 +1129,14 @@ __device__ inline void ph_apply(const Level &L, Grid G, char *arena) {
         int32_t x = L.nxt[v];
         int32_t a = nxt_from(x), b = nxt_to(x);
         int64_t beg = ld_xadj(L.g.xadj, v), end = ld_xadj(L.g.xadj, (int64_t)v + 1);
-        long long c = 0;
-        int32_t ne = 0;
-        for (int64_t j = beg + lane; j < end; j += 32) {
-            int32_t o;
-            c += apply_edge<EW, false>(L, v, a, b, it, __ldg(L.g.adj + j), edge_w<EW>(L.g, j), &o);
-            ne += o;
-        }
+        long long c = 0, ne = 0;
+        apply_row<EW>(L, v, a, b, it, beg + lane, end, 32, c, ne);
         c = warp_sum_i64(c);
-        ne = warp_sum_i32(ne);
+        ne = warp_sum_i64(ne);
         if (lane == 0) {
             dc += c;
             dm += end - beg;
-            L.ext[v] = ne;
+            L.ext[v] = (int32_t)ne;
             L.part[v] = b;
             if (lp) L.lstamp[v] = it;
         }
@@ -1285,7 +1355,7 @@ __device__ __forceinline__ void rb_cand_row(const Level &L, int32_t v, int32_t *
     int32_t ps = L.part[v];
     int32_t a = L.aidx[ps];
     int64_t beg = ld_xadj(g.xadj, v), end = ld_xadj(g.xadj, (int64_t)v + 1);
-    for (int64_t j = beg + lane; j < end; j += 32) atomicAdd(&tab[L.part[__ldg(g.adj + j)]], edge_w<EW>(g, j));
+    row_to_table<EW>(L, beg + lane, end, 32, tab);
     __syncwarp();
     int32_t conn_s = tab[ps];
     __syncwarp();
@@ -1350,8 +1420,7 @@ __device__ __forceinline__ void rb_cand_block_row(const Level &L, int32_t v, int
     const int32_t a = L.aidx[ps];
     const int64_t beg = ld_xadj(g.xadj, v), end = ld_xadj(g.xadj, (int64_t)v + 1);
     int32_t *tab = tabs + (threadIdx.x >> 5) * L.k;
-    for (int64_t j = beg + threadIdx.x; j < end; j += blockDim.x)
-        atomicAdd(&tab[L.part[__ldg(g.adj + j)]], edge_w<EW>(g, j));
+    row_to_table<EW>(L, beg + threadIdx.x, end, blockDim.x, tab);
     __syncthreads();
     const int32_t conn_s = tables_sum(tabs, L.k, ps);
     unsigned long long best = 0;

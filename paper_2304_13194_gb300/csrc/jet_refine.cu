@@ -44,18 +44,34 @@ __device__ inline void ph_cut_pw(const DGraph &g, int32_t k, const int32_t *__re
     JET_APPENDER(bigs, stage, kBigCap);
     long long c = 0;
     const unsigned lane = lane_id();
-    // one row's cut share, ext and weighted degree; `part_v` is v's part
+    // one row's cut share, ext and weighted degree over the entries first,
+    // first + step, ... (four entries per thread at a time: their ids, then
+    // their parts, in flight together)
+    auto row_share = [&](int64_t first, int64_t e, int64_t step, int32_t p, long long &cv, long long &nx,
+                         long long &wd) {
+        constexpr int U = 4;
+        for (int64_t j0 = first; j0 < e; j0 += U * step) {
+            int32_t u[U], w[U];
+#pragma unroll
+            for (int q = 0; q < U; ++q) {
+                const int64_t j = j0 + q * step;
+                u[q] = j < e ? g.adj[j] : -1;
+                w[q] = j < e ? edge_w<EW>(g, j) : 0;
+            }
+#pragma unroll
+            for (int q = 0; q < U; ++q) {
+                const bool other = u[q] >= 0 && part[u[q]] != p;
+                cv += other ? w[q] : 0;
+                nx += other ? 1 : 0;
+                wd += w[q];
+            }
+        }
+    };
     auto warp_row = [&](int32_t v) {
         const int32_t p = part[v];
         const int64_t b = ld_xadj(g.xadj, v), e = ld_xadj(g.xadj, (int64_t)v + 1);
         long long cv = 0, nx = 0, wd = 0;
-        for (int64_t j = b + lane; j < e; j += 32) {
-            const int32_t w = edge_w<EW>(g, j);
-            const bool other = part[g.adj[j]] != p;
-            cv += other ? w : 0;
-            nx += other ? 1 : 0;
-            wd += w;
-        }
+        row_share(b + lane, e, 32, p, cv, nx, wd);
         cv = warp_sum_i64(cv);
         nx = warp_sum_i64(nx);
         wd = warp_sum_i64(wd);
@@ -69,13 +85,7 @@ __device__ inline void ph_cut_pw(const DGraph &g, int32_t k, const int32_t *__re
         const int32_t p = part[v];
         const int64_t b = ld_xadj(g.xadj, v), e = ld_xadj(g.xadj, (int64_t)v + 1);
         long long cv = 0, nx = 0, wd = 0;
-        for (int64_t j = b + threadIdx.x; j < e; j += blockDim.x) {
-            const int32_t w = edge_w<EW>(g, j);
-            const bool other = part[g.adj[j]] != p;
-            cv += other ? w : 0;
-            nx += other ? 1 : 0;
-            wd += w;
-        }
+        row_share(b + threadIdx.x, e, blockDim.x, p, cv, nx, wd);
         cv = block_sum_i64(cv, red);
         nx = block_sum_i64(nx, red);
         wd = block_sum_i64(wd, red);
@@ -839,19 +849,6 @@ int read_ctl(Ctx &c, const Level &L, Ctl &h) {
     JET_CUDA_TRY(cudaStreamSynchronize(c.stream));
     return JET_OK;
 }
-
-struct EventPool {
-    std::vector<cudaEvent_t> ev;
-    ~EventPool() {
-        for (cudaEvent_t e : ev) cudaEventDestroy(e);
-    }
-    int get(cudaEvent_t &e) {
-        cudaError_t r = cudaEventCreate(&e);
-        if (r != cudaSuccess) { record_cuda_error(r, "cudaEventCreate", __FILE__, __LINE__); return JET_ECUDA; }
-        ev.push_back(e);
-        return JET_OK;
-    }
-};
 
 // Host-driven loop (JET_FLAG_HOSTLOOP / JET_FLAG_PROFILE): the mode is read
 // back after every iteration, as in the paper's implementation.  With
