@@ -87,12 +87,11 @@ __global__ void __launch_bounds__(kTB) k_hem_propose_small(DGraph g, const int32
 }
 
 // The heaviest unmatched neighbour over the entries first, first + step, ...
-// < end of a row, four at a time (ids, then their mates, in flight
-// together); folds into (bu, bw, bh).
-template <bool EW>
+// < end of a row, U at a time (ids, then their mates, in flight together);
+// folds into (bu, bw, bh).
+template <bool EW, int U = 4>
 __device__ __forceinline__ void hem_row(const DGraph &g, const int32_t *mate, uint64_t seed, uint64_t salt, int64_t first,
                                         int64_t end, int64_t step, int32_t &bu, int32_t &bw, uint64_t &bh) {
-    constexpr int U = 4;
     for (int64_t j0 = first; j0 < end; j0 += U * step) {
         int32_t u[U], m[U];
 #pragma unroll
@@ -152,7 +151,7 @@ __global__ void __launch_bounds__(kTB) k_hem_propose_huge(DGraph g, const int32_
         uint64_t bh = 0;
         if (mate[v] < 0) {
             const int64_t beg = ld_xadj(g.xadj, v), end = ld_xadj(g.xadj, (int64_t)v + 1);
-            hem_row<EW>(g, mate, seed, salt, beg + threadIdx.x, end, blockDim.x, bu, bw, bh);
+            hem_row<EW, 8>(g, mate, seed, salt, beg + threadIdx.x, end, blockDim.x, bu, bw, bh);
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {

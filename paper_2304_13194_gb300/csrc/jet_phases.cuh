@@ -663,24 +663,25 @@ __device__ __forceinline__ void tables_clear(int32_t *tabs, int32_t k) {
 // fields, then they are used, so a thread keeps kRowBatch dependent gather
 // chains in flight instead of one (a hub row of 160k entries otherwise takes
 // a block as long as a whole pass).
-constexpr int kRowBatch = 4;
+constexpr int kRowBatch = 4;    // warp rows (17 to hub_degree entries)
+constexpr int kHubBatch = 8;    // hub rows (one block each)
 
 // conn(v, .) of the entries first, first + step, ... < end added into tab.
-template <bool EW>
+template <bool EW, int U = kRowBatch>
 __device__ __forceinline__ void row_to_table(const Level &L, int64_t first, int64_t end, int64_t step, int32_t *tab) {
     const DGraph &g = L.g;
-    for (int64_t j0 = first; j0 < end; j0 += kRowBatch * step) {
-        int32_t u[kRowBatch], w[kRowBatch], p[kRowBatch];
+    for (int64_t j0 = first; j0 < end; j0 += U * step) {
+        int32_t u[U], w[U], p[U];
 #pragma unroll
-        for (int q = 0; q < kRowBatch; ++q) {
+        for (int q = 0; q < U; ++q) {
             const int64_t j = j0 + q * step;
             u[q] = j < end ? __ldg(g.adj + j) : -1;
             w[q] = j < end ? edge_w<EW>(g, j) : 0;
         }
 #pragma unroll
-        for (int q = 0; q < kRowBatch; ++q) p[q] = u[q] >= 0 ? L.part[u[q]] : -1;
+        for (int q = 0; q < U; ++q) p[q] = u[q] >= 0 ? L.part[u[q]] : -1;
 #pragma unroll
-        for (int q = 0; q < kRowBatch; ++q)
+        for (int q = 0; q < U; ++q)
             if (p[q] >= 0) atomicAdd(&tab[p[q]], w[q]);
     }
 }
@@ -696,7 +697,7 @@ __device__ __forceinline__ void lp_select_block_row(const Level &L, LpExport ex,
     const int32_t ps = L.part[v];
     const int64_t beg = ld_xadj(g.xadj, v), end = ld_xadj(g.xadj, (int64_t)v + 1);
     int32_t *tab = tabs + (threadIdx.x >> 5) * L.k;
-    row_to_table<EW>(L, beg + threadIdx.x, end, blockDim.x, tab);
+    row_to_table<EW, kHubBatch>(L, beg + threadIdx.x, end, blockDim.x, tab);
     __syncthreads();
     const int32_t conn_s = tables_sum(tabs, L.k, ps);
     unsigned long long best = 0;
@@ -886,29 +887,29 @@ __device__ inline void ph_lp_select(const Level &L, LpExport ex, Grid G, char *a
 // F2 share of the entries first, first + step, ... < end of v's row (batched
 // as row_to_table): a neighbour counts at its destination when it precedes
 // v in ord; its move is loaded only for the neighbours that take it.
-template <bool EW>
+template <bool EW, int U = kRowBatch>
 __device__ __forceinline__ long long afterburn_row(const Level &L, int32_t v, int32_t Fv, int32_t pd, int32_t ps,
                                                    int64_t first, int64_t end, int64_t step) {
     const DGraph &g = L.g;
     long long f2 = 0;
-    for (int64_t j0 = first; j0 < end; j0 += kRowBatch * step) {
-        int32_t u[kRowBatch], w[kRowBatch], pu[kRowBatch], fu[kRowBatch];
+    for (int64_t j0 = first; j0 < end; j0 += U * step) {
+        int32_t u[U], w[U], pu[U], fu[U];
 #pragma unroll
-        for (int q = 0; q < kRowBatch; ++q) {
+        for (int q = 0; q < U; ++q) {
             const int64_t j = j0 + q * step;
             u[q] = j < end ? __ldg(g.adj + j) : -1;
             w[q] = j < end ? edge_w<EW>(g, j) : 0;
         }
 #pragma unroll
-        for (int q = 0; q < kRowBatch; ++q) {
+        for (int q = 0; q < U; ++q) {
             pu[q] = u[q] >= 0 ? L.part[u[q]] : -1;
             fu[q] = u[q] >= 0 ? L.prio[u[q]] : kNoneGain;
         }
 #pragma unroll
-        for (int q = 0; q < kRowBatch; ++q)
+        for (int q = 0; q < U; ++q)
             if (u[q] >= 0 && (fu[q] > Fv || (fu[q] == Fv && u[q] < v))) pu[q] = nxt_to(L.nxt[u[q]]);
 #pragma unroll
-        for (int q = 0; q < kRowBatch; ++q) f2 += pu[q] == pd ? w[q] : (pu[q] == ps ? -w[q] : 0);
+        for (int q = 0; q < U; ++q) f2 += pu[q] == pd ? w[q] : (pu[q] == ps ? -w[q] : 0);
     }
     return f2;
 }
@@ -918,7 +919,7 @@ template <bool EW>
 __device__ __forceinline__ void afterburn_block_row(const Level &L, LpExport ex, int32_t v, int32_t it, long long *red) {
     const int32_t Fv = L.prio[v], pd = nxt_to(L.nxt[v]), ps = L.part[v];
     const int64_t beg = ld_xadj(L.g.xadj, v), end = ld_xadj(L.g.xadj, (int64_t)v + 1);
-    long long f2 = afterburn_row<EW>(L, v, Fv, pd, ps, beg + threadIdx.x, end, blockDim.x);
+    long long f2 = afterburn_row<EW, kHubBatch>(L, v, Fv, pd, ps, beg + threadIdx.x, end, blockDim.x);
     f2 = block_sum_i64(f2, red);
     if (threadIdx.x == 0) {
         if (ex.f2) ex.f2[v] = (int32_t)f2;
@@ -1057,25 +1058,25 @@ __device__ __forceinline__ int64_t apply_edge(const Level &L, int32_t v, int32_t
 // v (moving a -> b), batched as row_to_table: the stamps of a batch are
 // loaded together, then the move or the part of each neighbour, whichever
 // it needs.  c: cut change, ne: neighbours in other parts after the move.
-template <bool EW>
+template <bool EW, int U = kRowBatch>
 __device__ __forceinline__ void apply_row(const Level &L, int32_t v, int32_t a, int32_t b, int32_t it, int64_t first,
                                           int64_t end, int64_t step, long long &c, long long &ne) {
     const DGraph &g = L.g;
-    for (int64_t j0 = first; j0 < end; j0 += kRowBatch * step) {
-        int32_t u[kRowBatch], w[kRowBatch], x[kRowBatch];
-        bool mu[kRowBatch];
+    for (int64_t j0 = first; j0 < end; j0 += U * step) {
+        int32_t u[U], w[U], x[U];
+        bool mu[U];
 #pragma unroll
-        for (int q = 0; q < kRowBatch; ++q) {
+        for (int q = 0; q < U; ++q) {
             const int64_t j = j0 + q * step;
             u[q] = j < end ? __ldg(g.adj + j) : -1;
             w[q] = j < end ? edge_w<EW>(g, j) : 0;
         }
 #pragma unroll
-        for (int q = 0; q < kRowBatch; ++q) mu[q] = u[q] >= 0 && L.mstamp[u[q]] == it;
+        for (int q = 0; q < U; ++q) mu[q] = u[q] >= 0 && L.mstamp[u[q]] == it;
 #pragma unroll
-        for (int q = 0; q < kRowBatch; ++q) x[q] = u[q] < 0 ? 0 : (mu[q] ? L.nxt[u[q]] : L.part[u[q]]);
+        for (int q = 0; q < U; ++q) x[q] = u[q] < 0 ? 0 : (mu[q] ? L.nxt[u[q]] : L.part[u[q]]);
 #pragma unroll
-        for (int q = 0; q < kRowBatch; ++q) {
+        for (int q = 0; q < U; ++q) {
             if (u[q] < 0) continue;
             const int32_t pu = mu[q] ? nxt_from(x[q]) : x[q];
             const int32_t pn = mu[q] ? nxt_to(x[q]) : x[q];
@@ -1099,7 +1100,7 @@ __device__ __forceinline__ void apply_block_row(const Level &L, int32_t v, int32
     const int32_t a = nxt_from(x), b = nxt_to(x);
     const int64_t beg = ld_xadj(L.g.xadj, v), end = ld_xadj(L.g.xadj, (int64_t)v + 1);
     long long c = 0, ne = 0;
-    apply_row<EW>(L, v, a, b, it, beg + threadIdx.x, end, blockDim.x, c, ne);
+    apply_row<EW, kHubBatch>(L, v, a, b, it, beg + threadIdx.x, end, blockDim.x, c, ne);
     c = block_sum_i64(c, red);
     ne = block_sum_i64(ne, red);
     if (threadIdx.x == 0) {
@@ -1420,7 +1421,7 @@ __device__ __forceinline__ void rb_cand_block_row(const Level &L, int32_t v, int
     const int32_t a = L.aidx[ps];
     const int64_t beg = ld_xadj(g.xadj, v), end = ld_xadj(g.xadj, (int64_t)v + 1);
     int32_t *tab = tabs + (threadIdx.x >> 5) * L.k;
-    row_to_table<EW>(L, beg + threadIdx.x, end, blockDim.x, tab);
+    row_to_table<EW, kHubBatch>(L, beg + threadIdx.x, end, blockDim.x, tab);
     __syncthreads();
     const int32_t conn_s = tables_sum(tabs, L.k, ps);
     unsigned long long best = 0;
