@@ -192,6 +192,7 @@ struct Level {
     int32_t list_cap;        // most blocks of a list kernel (select, afterburner, rebalancing rows)
     int32_t apply_cap;       // most blocks of the apply kernel
     int32_t scan_cap;        // most blocks of a scan kernel
+    int32_t rb_scan_cap;     // the same for the rebalancing scan, at most one wave of resident blocks
     int32_t items_per_block; // list entries per block below those caps
 };
 

@@ -314,7 +314,8 @@ __device__ inline long long block_max_pw(const int64_t *pw, int32_t k, long long
 // B = {p : w_p <= sigma} listed in ascending id, excess of each A part, the
 // capacity prefix of B (Jetrs) and zeroed slot buckets.  Any block size;
 // spw holds the part weights (block_max_pw).
-__device__ inline void compute_classes(const Level &L, long long *sh, const long long *spw) {
+__device__ inline void compute_classes(const Level &L, long long *sh, const long long *spw, long long Llim,
+                                       long long sigma) {
     Ctl *ctl = L.ctl;
     long long ca = 0, cb = 0, cc = 0;
     for (int p0 = 0; p0 < L.k; p0 += blockDim.x) {
@@ -323,18 +324,18 @@ __device__ inline void compute_classes(const Level &L, long long *sh, const long
         long long w = 0;
         if (p < L.k) {
             w = spw[p];
-            inA = w > ctl->L;
-            inB = w <= ctl->sigma;
+            inA = w > Llim;
+            inB = w <= sigma;
         }
         long long tA = 0, tB = 0, tC = 0;
         long long ia = ca + block_exscan_i64(inA ? 1 : 0, sh, &tA);
         long long ib = cb + block_exscan_i64(inB ? 1 : 0, sh, &tB);
-        long long cap = inB ? (ctl->sigma - w) : 0;
+        long long cap = inB ? (sigma - w) : 0;
         long long ic = cc + block_exscan_i64(cap, sh, &tC);
         if (p < L.k) {
             L.aidx[p] = inA ? (int32_t)ia : -1;
             L.inB[p] = inB ? 1 : 0;
-            if (inA) L.excess[ia] = w - ctl->L;
+            if (inA) L.excess[ia] = w - Llim;
             if (inB) { L.Bs[ib] = p; L.capC[ib] = ic; }
         }
         ca += tA; cb += tB; cc += tC;
@@ -448,8 +449,29 @@ __device__ inline int32_t ph_controller(const Level &L) {
     __shared__ long long sh[40];
     __shared__ long long spw[JET_MAX_K];
     __shared__ int32_t next_mode;
+    __shared__ long long s_lim[2];
     Ctl *ctl = L.ctl;
-    int32_t kind = ctl->mode;
+    // thread 0 gathers: values of earlier kernels (plain loads) and of this
+    // one (ld_gpu), issued together with the mode and before the part-weight
+    // reduction so that the round trips overlap
+    long long cut0 = 0, Llim = 0, sigma = 0, best_cut0 = 0, best_maxw0 = 0, ncand = 0, degx = 0, nbnd = 0, nexam = 0,
+              degexam = 0, dcut = 0, degm = 0;
+    int32_t it = 0, noimp0 = 0, best_bal0 = 0, kc = 0, weak = 0, hit_cap = 0, nX = 0, nM = 0, nA = 0, copied = 0;
+    int64_t kb0[JET_K_COUNT];
+    int32_t kc4[4] = {0, 0, 0, 0};
+    const int32_t kind = ctl->mode;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) kc4[i] = ctl->kcount[i];
+        cut0 = ctl->cut; Llim = ctl->L; sigma = ctl->sigma; best_cut0 = ctl->best_cut; best_maxw0 = ctl->best_maxw;
+        it = ctl->it; noimp0 = ctl->noimp; best_bal0 = ctl->best_bal;
+        weak = ctl->weak; hit_cap = ctl->hit_cap;
+        nX = ctl->nX + ctl->nXh; nM = ctl->nM + ctl->nMh; nA = ctl->nA; copied = ctl->copy_best;
+        ncand = ctl->ncand; degx = ctl->degx; nbnd = ctl->nbnd; nexam = ctl->nexam; degexam = ctl->degexam;
+        dcut = ld_gpu(&ctl->dcut); degm = ld_gpu(&ctl->degm);
+#pragma unroll
+        for (int i = 0; i < JET_K_COUNT; ++i) kb0[i] = ctl->kbytes[i];
+    }
     if (kind == MODE_DONE) {
         if (threadIdx.x == 0) {
             ctl->copy_best = 0;
@@ -460,23 +482,7 @@ __device__ inline int32_t ph_controller(const Level &L) {
         }
         return MODE_DONE;
     }
-    // thread 0 gathers: values of earlier kernels (plain loads) and of this
-    // one (ld_gpu), issued before the part-weight reduction so that the two
-    // round trips overlap
-    long long cut0 = 0, Llim = 0, best_cut0 = 0, best_maxw0 = 0, ncand = 0, degx = 0, nbnd = 0, nexam = 0,
-              degexam = 0, dcut = 0, degm = 0;
-    int32_t it = 0, noimp0 = 0, best_bal0 = 0, kc = 0, weak = 0, hit_cap = 0, nX = 0, nM = 0, nA = 0, copied = 0;
-    int64_t kb0[JET_K_COUNT];
-    if (threadIdx.x == 0) {
-        cut0 = ctl->cut; Llim = ctl->L; best_cut0 = ctl->best_cut; best_maxw0 = ctl->best_maxw;
-        it = ctl->it; noimp0 = ctl->noimp; best_bal0 = ctl->best_bal; kc = ctl->kcount[kind];
-        weak = ctl->weak; hit_cap = ctl->hit_cap;
-        nX = ctl->nX + ctl->nXh; nM = ctl->nM + ctl->nMh; nA = ctl->nA; copied = ctl->copy_best;
-        ncand = ctl->ncand; degx = ctl->degx; nbnd = ctl->nbnd; nexam = ctl->nexam; degexam = ctl->degexam;
-        dcut = ld_gpu(&ctl->dcut); degm = ld_gpu(&ctl->degm);
-#pragma unroll
-        for (int i = 0; i < JET_K_COUNT; ++i) kb0[i] = ctl->kbytes[i];
-    }
+    if (threadIdx.x == 0) kc = kind == 0 ? kc4[0] : kind == 1 ? kc4[1] : kind == 2 ? kc4[2] : kc4[3];
     long long maxw = block_max_pw(L.pw, L.k, sh, spw);
     if (threadIdx.x == 0) {
         // decide
@@ -528,6 +534,8 @@ __device__ inline int32_t ph_controller(const Level &L) {
         reset_counters(ctl);
         ctl->mode = m;
         next_mode = m;
+        s_lim[0] = Llim;
+        s_lim[1] = sigma;
         if (L.use_graph) {
             cudaGraphSetConditional((cudaGraphConditionalHandle)L.h_mode, (unsigned)m);
             cudaGraphSetConditional((cudaGraphConditionalHandle)L.h_loop, m == MODE_DONE ? 0u : 1u);
@@ -535,7 +543,7 @@ __device__ inline int32_t ph_controller(const Level &L) {
     }
     __syncthreads();
     int32_t m = next_mode;
-    if (m == MODE_RW || m == MODE_RS) compute_classes(L, sh, spw);
+    if (m == MODE_RW || m == MODE_RS) compute_classes(L, sh, spw, s_lim[0], s_lim[1]);
     return m;
 }
 
@@ -561,13 +569,12 @@ __device__ inline void ph_ctl_init(const Level &L, const int64_t *cut2) {
         ctl->mode = choose_mode(L, maxw <= ctl->L);
     }
     __syncthreads();
-    if (ctl->mode == MODE_RW || ctl->mode == MODE_RS) compute_classes(L, sh, spw);
+    if (ctl->mode == MODE_RW || ctl->mode == MODE_RS) compute_classes(L, sh, spw, ctl->L, ctl->sigma);
 }
 
 // P_best <- P_iter when the controller asked for it (first phase of the next
 // iteration, and once after the level's loop).
-__device__ inline void ph_copy_best(const Level &L, Grid G) {
-    if (!L.ctl->copy_best) return;
+__device__ inline void copy_best_rows(const Level &L, Grid G) {
     const int64_t stride = (int64_t)G.nb * blockDim.x;
     if (((reinterpret_cast<uintptr_t>(L.part) | reinterpret_cast<uintptr_t>(L.best)) & 15) != 0) {
         for (int64_t i = (int64_t)G.bid * blockDim.x + threadIdx.x; i < L.g.n; i += stride) L.best[i] = L.part[i];
@@ -582,6 +589,9 @@ __device__ inline void ph_copy_best(const Level &L, Grid G) {
         L.best[i] = L.part[i];
     }
 }
+__device__ inline void ph_copy_best(const Level &L, Grid G) {
+    if (L.ctl->copy_best) copy_best_rows(L, G);
+}
 
 // ---------------------------------------------------------------------------
 // Jetlp (Alg. 4)
@@ -594,9 +604,9 @@ __device__ inline void ph_copy_best(const Level &L, Grid G) {
 __device__ inline void ph_lp_scan(const Level &L, Grid G, char *arena) {
     disarm_loop(L, G);
     __shared__ long long red[40];
-    JET_APPENDER(wapp, reinterpret_cast<int32_t *>(arena), kScanCap);
     Ctl *ctl = L.ctl;
-    const int32_t epoch = ctl->lp_epoch;
+    const int32_t epoch = ctl->lp_epoch;   // loaded before the appender's barrier
+    JET_APPENDER(wapp, reinterpret_cast<int32_t *>(arena), kScanCap);
     const bool use_locks = !ablate_locks(L.abl);
     const int64_t n = L.g.n, nq = (n + 3) / 4;
     const bool vec = (reinterpret_cast<uintptr_t>(L.ext) & 15) == 0;
@@ -934,10 +944,9 @@ template <bool EW>
 __device__ inline void ph_afterburn(const Level &L, LpExport ex, Grid G, char *arena) {
     __shared__ long long red[40];
     Ctl *ctl = L.ctl;
-    const int32_t it = ctl->it;
+    const int32_t it = ctl->it, nX = ctl->nX, nXh = ctl->nXh;   // one round trip
     const bool full_ab = !(L.abl & (ABL_NO_AFTERBURN | ABL_BASELINE_LP));
     // hub rows of X, one block each, dealt round-robin over the blocks
-    const int32_t nXh = ctl->nXh;
     for (int32_t h = G.bid; h < nXh; h += G.nb) {
         const int32_t v = L.listX[L.g.n - 1 - h];
         if (full_ab) {
@@ -947,7 +956,7 @@ __device__ inline void ph_afterburn(const Level &L, LpExport ex, Grid G, char *a
             L.listM[L.g.n - 1 - atomicAdd(&ctl->nMh, 1)] = v;
         }
     }
-    const Deal dl(ctl->nX, G, true);
+    const Deal dl(nX, G, true);
     if (!dl.live(0)) return;
     int32_t *a32 = reinterpret_cast<int32_t *>(arena);
     JET_APPENDER(mapp, a32, kListCap);
@@ -1024,40 +1033,12 @@ __device__ inline void ph_afterburn(const Level &L, LpExport ex, Grid G, char *a
 // old part read from nxt, never from part[] (which the commit overwrites);
 // for an edge with both ends moving the smaller id accounts for the cut.
 // ---------------------------------------------------------------------------
-// FLAT (short rows, one thread each, latency-bound): stamp, packed move and
-// part loaded together, one round trip; otherwise (long rows, bandwidth-bound)
-// the move or the part is loaded after the stamp, whichever is needed.
-template <bool EW, bool FLAT>
-__device__ __forceinline__ int64_t apply_edge(const Level &L, int32_t v, int32_t a, int32_t b, int32_t it, int32_t u,
-                                              int32_t w, int32_t *other) {
-    const bool mu = L.mstamp[u] == it;
-    int32_t pu, pn;
-    if constexpr (FLAT) {
-        const int32_t x = L.nxt[u];
-        const int32_t p = L.part[u];
-        pu = mu ? nxt_from(x) : p;
-        pn = mu ? nxt_to(x) : p;
-    } else if (mu) {
-        const int32_t x = L.nxt[u];
-        pu = nxt_from(x);
-        pn = nxt_to(x);
-    } else {
-        pu = pn = L.part[u];
-    }
-    *other = pn != b;
-    int32_t diff = (int)(pn != b) - (int)(pu != a);
-    if (!mu) {
-        if (diff) atomicAdd(&L.ext[u], diff);
-    } else if (u < v) {
-        return 0;
-    }
-    return (int64_t)w * diff;
-}
-
-// apply_edge over the entries first, first + step, ... < end of the row of
-// v (moving a -> b), batched as row_to_table: the stamps of a batch are
-// loaded together, then the move or the part of each neighbour, whichever
-// it needs.  c: cut change, ne: neighbours in other parts after the move.
+// Effect of v's move a -> b over the entries first, first + step, ... < end
+// of its row, batched as row_to_table: the stamps of a batch are loaded
+// together, then the move or the part of each neighbour, whichever it needs.
+// A neighbour that stays gets its ext[] updated; c receives the cut change
+// (an edge whose ends both move counts once, at the smaller id), ne the
+// neighbours in other parts after the move.
 template <bool EW, int U = kRowBatch>
 __device__ __forceinline__ void apply_row(const Level &L, int32_t v, int32_t a, int32_t b, int32_t it, int64_t first,
                                           int64_t end, int64_t step, long long &c, long long &ne) {
@@ -1092,6 +1073,49 @@ __device__ __forceinline__ void apply_row(const Level &L, int32_t v, int32_t a, 
     }
 }
 
+// The same over a short row (at most kSmallDeg entries, one thread), in
+// batches of U neighbours whose stamps, packed moves and parts are loaded
+// together before any of them is updated: a batch costs one round trip,
+// where an update of ext[] between two neighbours would hold the next
+// neighbour's loads behind it.
+template <bool EW, int U = kSmallDeg / 2>
+__device__ __forceinline__ void apply_short_row(const Level &L, int32_t v, int32_t a, int32_t b, int32_t it,
+                                                int64_t beg, int d, long long &c, long long &ne) {
+    const DGraph &g = L.g;
+#pragma unroll
+    for (int t0 = 0; t0 < kSmallDeg; t0 += U) {
+        if (t0 >= d) break;
+        int32_t u[U], w[U], ms[U], x[U], p[U];
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+            const int t = t0 + q;
+            u[q] = t < d ? __ldg(g.adj + beg + t) : -1;
+            w[q] = t < d ? edge_w<EW>(g, beg + t) : 0;
+        }
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+            ms[q] = u[q] >= 0 ? L.mstamp[u[q]] : 0;
+            x[q] = u[q] >= 0 ? L.nxt[u[q]] : 0;
+            p[q] = u[q] >= 0 ? L.part[u[q]] : 0;
+        }
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+            if (u[q] < 0) continue;
+            const bool mu = ms[q] == it;
+            const int32_t pu = mu ? nxt_from(x[q]) : p[q];
+            const int32_t pn = mu ? nxt_to(x[q]) : p[q];
+            const int32_t diff = (int)(pn != b) - (int)(pu != a);
+            ne += pn != b;
+            if (!mu) {
+                if (diff) atomicAdd(&L.ext[u[q]], diff);
+                c += (long long)w[q] * diff;
+            } else if (u[q] > v) {
+                c += (long long)w[q] * diff;   // an edge whose ends both move counts at the smaller id
+            }
+        }
+    }
+}
+
 // One hub row of the apply phase by the whole block.
 template <bool EW>
 __device__ __forceinline__ void apply_block_row(const Level &L, int32_t v, int32_t it, bool lp, long long *red,
@@ -1116,9 +1140,8 @@ template <bool EW>
 __device__ inline void ph_apply(const Level &L, Grid G, char *arena) {
     __shared__ long long red[40];
     Ctl *ctl = L.ctl;
-    const int32_t kind = ctl->mode;
+    const int32_t kind = ctl->mode, nM = ctl->nM, nX = ctl->nX, it = ctl->it, nMh = ctl->nMh, nXh = ctl->nXh;
     if (kind == MODE_DONE) return;
-    const int32_t nM = ctl->nM, nX = ctl->nX, it = ctl->it, nMh = ctl->nMh, nXh = ctl->nXh;
     const bool lp = kind == MODE_LP;
     long long *shpw = reinterpret_cast<long long *>(arena);
     int32_t *stage = reinterpret_cast<int32_t *>(arena + align16((size_t)L.k * 8));
@@ -1160,20 +1183,10 @@ __device__ inline void ph_apply(const Level &L, Grid G, char *arena) {
             if (d > kSmallDeg) {
                 big = true;
             } else {
-                // short row: preloaded so that its gathers are in flight together
-                int32_t uu[kSmallDeg];
-#pragma unroll
-                for (int t = 0; t < kSmallDeg; ++t) uu[t] = t < d ? __ldg(L.g.adj + beg + t) : -1;
-                int32_t ne = 0;
-#pragma unroll
-                for (int t = 0; t < kSmallDeg; ++t) {
-                    if (t < d) {
-                        int32_t o;
-                        dc += apply_edge<EW, true>(L, v, a, b, it, uu[t], edge_w<EW>(L.g, beg + t), &o);
-                        ne += o;
-                    }
-                }
-                L.ext[v] = ne;
+                long long c = 0, ne = 0;
+                apply_short_row<EW>(L, v, a, b, it, beg, d, c, ne);
+                dc += c;
+                L.ext[v] = (int32_t)ne;
                 L.part[v] = b;
                 if (lp) L.lstamp[v] = it;
                 dm += d;
@@ -1274,13 +1287,12 @@ template <bool STRONG>
 __device__ inline void ph_rb_scan(const Level &L, Grid G, char *arena) {
     disarm_loop(L, G);
     __shared__ long long red[40];
+    Ctl *ctl = L.ctl;
+    const int32_t it = ctl->it, nB = ctl->nB;   // loaded before the barriers of the set-up below
+    const int64_t opt = ctl->opt;
     SmemBuckets sb;
     sb.init(L, reinterpret_cast<long long *>(arena));
     JET_APPENDER(wapp, reinterpret_cast<int32_t *>(arena + kSmemBuckets * 8), kScanCap);
-    Ctl *ctl = L.ctl;
-    const int32_t it = ctl->it;
-    const int32_t nB = ctl->nB;
-    const int64_t opt = ctl->opt;
     const int64_t n = L.g.n, nq = (n + 3) / 4;
     const bool vec = (reinterpret_cast<uintptr_t>(L.part) & 15) == 0;
     long long ncand = 0, nlist = 0;
@@ -1472,8 +1484,7 @@ template <bool EW, bool STRONG>
 __device__ inline void ph_rb_cand(const Level &L, Grid G, char *arena) {
     __shared__ long long red[40];
     Ctl *ctl = L.ctl;
-    const int32_t nB = ctl->nB;
-    const int32_t nbig = ctl->nbig;
+    const int32_t nB = ctl->nB, nbig = ctl->nbig, it = ctl->it;   // one round trip
     const Deal dl(ctl->nW, G, nbig > 0);
     if (!dl.live(0)) return;
     SmemBuckets sb;
@@ -1485,7 +1496,6 @@ __device__ inline void ph_rb_cand(const Level &L, Grid G, char *arena) {
         for (int i = threadIdx.x; i < (int)(blockDim.x >> 5) * L.k; i += blockDim.x) a32[kBigCap + i] = 0;
         __syncthreads();
     }
-    const int32_t it = ctl->it;
     const DGraph g = L.g;
     long long degrows = 0;
     auto big_row = [&](int32_t v) { rb_cand_row<EW, STRONG>(L, v, tab, it, nB, sb, degrows); };
@@ -1627,15 +1637,13 @@ __device__ inline void ph_rb_tilehist(const Level &L, Grid G, char *arena) {
     int32_t *h = reinterpret_cast<int32_t *>(arena);
     const int32_t nA = L.ctl->nA;
     for (int64_t t = G.bid; t < L.ntiles; t += G.nb) {
+        const int64_t v = t * blockDim.x + threadIdx.x;
+        const int32_t kv = v < L.g.n ? L.key[v] : -1;   // in flight with nA and the clearing below
         for (int i = threadIdx.x; i < nA; i += blockDim.x) h[i] = 0;
         __syncthreads();
-        int64_t v = t * blockDim.x + threadIdx.x;
-        if (v < L.g.n) {
-            int32_t kv = L.key[v];
-            if (kv >= 0) {
-                int32_t a = kv / kSlots, s = kv - a * kSlots;
-                if (s == L.sstar[a]) atomicAdd(&h[a], L.g.vw[v]);
-            }
+        if (kv >= 0) {
+            int32_t a = kv / kSlots, s = kv - a * kSlots;
+            if (s == L.sstar[a]) atomicAdd(&h[a], L.g.vw[v]);
         }
         __syncthreads();
         for (int i = threadIdx.x; i < nA; i += blockDim.x) L.tilehist[t * nA + i] = h[i];

@@ -198,8 +198,11 @@ __global__ void __launch_bounds__(kTB, JET_ROW_MINB) k_lp_select(Level L, LpExpo
 template <bool EW>
 __global__ void __launch_bounds__(kTB, JET_ROW_MINB) k_afterburn(Level L, LpExport ex) {
     pdl_enter();
-    ph_copy_best(L, launch_grid());
+    // the P_best copy only reads part, which this phase leaves alone: its
+    // flag is loaded with the phase's first loads, the copy runs last
+    const int32_t copy = L.ctl->copy_best;
     ph_afterburn<EW>(L, ex, launch_grid(), JET_ARENA);
+    if (copy) copy_best_rows(L, launch_grid());
 }
 // apply + commit; the last block runs the controller
 template <bool EW>
@@ -213,8 +216,9 @@ __global__ void __launch_bounds__(kTB, JET_ROW_MINB) k_apply(Level L) {
 template <bool STRONG>
 __global__ void __launch_bounds__(kTB) k_rb_scan(Level L) {
     pdl_enter();
-    ph_copy_best(L, launch_grid());
+    const int32_t copy = L.ctl->copy_best;   // as in k_afterburn
     ph_rb_scan<STRONG>(L, launch_grid(), JET_ARENA);
+    if (copy) copy_best_rows(L, launch_grid());
 }
 template <bool EW, bool STRONG>
 __global__ void __launch_bounds__(kTB, JET_ROW_MINB) k_rb_cand(Level L) {
@@ -784,7 +788,7 @@ int enqueue_rb_t(const Level &L, cudaStream_t s, int *nk, KernProf *pr) {
     int n = L.g.n;
     bool ew = L.g.ew != nullptr;
     JET_TRY(prof_mark(pr, s, JET_K_RB_SCAN));
-    k_rb_scan<STRONG><<<scan_grid(L, n), kTB, sm_rb_scan(), s>>>(L);
+    k_rb_scan<STRONG><<<std::min(L.rb_scan_cap, scan_grid(L, n)), kTB, sm_rb_scan(), s>>>(L);
     const size_t sm = sm_rb_cand(L.k, kTB, true);
     JET_TRY(prof_mark(pr, s, JET_K_RB_CAND));
     JET_CUDA_TRY(launch_dep(L, ew ? k_rb_cand<true, STRONG> : k_rb_cand<false, STRONG>, list_blocks(L, n), kTB, sm, s, L));
@@ -812,8 +816,7 @@ int enqueue_rb(const Level &L, cudaStream_t s, bool strong, int *nk, KernProf *p
 int enqueue_tail(const Level &L, cudaStream_t s, int *nk, KernProf *pr = nullptr) {
     int ga = apply_blocks(L, L.g.n);
     JET_TRY(prof_mark(pr, s, JET_K_APPLY));
-    if (L.g.ew) k_apply<true><<<ga, kTB, sm_apply(L.k), s>>>(L);
-    else k_apply<false><<<ga, kTB, sm_apply(L.k), s>>>(L);
+    JET_CUDA_TRY(launch_dep(L, L.g.ew ? k_apply<true> : k_apply<false>, ga, kTB, sm_apply(L.k), s, L));
     *nk = 1;
     JET_CUDA_TRY(cudaGetLastError());
     return JET_OK;
@@ -888,7 +891,10 @@ int run_hostloop(Ctx &c, const Level &L, bool profile, float *kern_ms) {
 }
 
 // Device-resident loop: graph = start kernel -> WHILE(h_loop) { SWITCH(h_mode)
-// {Jetlp | Jetrw | Jetrs} -> apply + commit + controller } -> final best copy.
+// {Jetlp | Jetrw | Jetrs, each followed by apply + commit + controller} } ->
+// final best copy.  The apply kernel sits inside every branch so that it
+// follows the branch's last kernel by programmatic dependent launch instead
+// of waiting for the conditional node to complete.
 // nk_branch[3] / *nk_tail receive the kernel counts of the captured pieces.
 // The graph is launched on the context's stream and not waited for; *exec_out
 // receives the executable graph, which the caller destroys once the stream
@@ -952,18 +958,13 @@ int run_graph(Ctx &c, Level L, int *nk_branch, int *nk_tail, cudaGraphExec_t *ex
             cudaGraph_t bg = sp.conditional.phGraph_out[b];
             if ((e = cudaStreamBeginCaptureToGraph(cap, bg, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed)) != cudaSuccess) { fail(e, "capture branch"); ok = false; break; }
             int r = b == 0 ? enqueue_lp(L, cap, &nk_branch[0]) : enqueue_rb(L, cap, b == 2, &nk_branch[b]);
+            if (r == JET_OK) r = enqueue_tail(L, cap, nk_tail);
             cudaGraph_t outg = nullptr;
             e = cudaStreamEndCapture(cap, &outg);
             if (r != JET_OK) { rc = r; ok = false; break; }
             if (e != cudaSuccess) { fail(e, "end capture branch"); ok = false; break; }
         }
         if (!ok) break;
-        if ((e = cudaStreamBeginCaptureToGraph(cap, body, &snode, nullptr, 1, cudaStreamCaptureModeRelaxed)) != cudaSuccess) { fail(e, "capture tail"); break; }
-        int r = enqueue_tail(L, cap, nk_tail);
-        cudaGraph_t outg = nullptr;
-        e = cudaStreamEndCapture(cap, &outg);
-        if (r != JET_OK) { rc = r; break; }
-        if (e != cudaSuccess) { fail(e, "end capture tail"); break; }
         if ((e = cudaGraphInstantiate(&ge, g, 0)) != cudaSuccess) { fail(e, "cudaGraphInstantiate"); break; }
         if ((e = cudaGraphLaunch(ge, s)) != cudaSuccess) { fail(e, "cudaGraphLaunch"); break; }
     } while (0);
@@ -1150,6 +1151,26 @@ int total_vweight(Ctx &c, const DGraph &g, int64_t &W) {
     return JET_OK;
 }
 
+// Blocks of the rebalancing scan resident on one SM (per device, once).
+static int rb_scan_resident() {
+    static std::mutex mu;
+    static int cached[256];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 256) return 1;
+    std::lock_guard<std::mutex> lock(mu);
+    if (cached[dev] == 0) {
+        int a = 0, b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_rb_scan<false>, kTB, sm_rb_scan()) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_rb_scan<true>, kTB, sm_rb_scan()) != cudaSuccess) {
+            cudaGetLastError();
+            return 4;
+        }
+        cached[dev] = std::max(1, std::min(a, b));
+    }
+    return cached[dev];
+}
+
 static void fill_level_params(Ctx &c, Level &L, int32_t is_finest, uint64_t seed) {
     const jet_options &o = c.opt;
     L.cq16 = (int32_t)llround((is_finest ? o.c_fine : o.c_coarse) * 65536.0);
@@ -1167,6 +1188,9 @@ static void fill_level_params(Ctx &c, Level &L, int32_t is_finest, uint64_t seed
     L.list_cap = sms * (o.list_blocks_per_sm > 0 ? o.list_blocks_per_sm : 4);
     L.apply_cap = o.apply_blocks_per_sm > 0 ? sms * o.apply_blocks_per_sm : L.list_cap;
     L.scan_cap = sms * (o.scan_blocks_per_sm > 0 ? o.scan_blocks_per_sm : 8);
+    // the rebalancing scan holds more registers than the other scans: a
+    // second wave of its blocks would start only as the first one leaves
+    L.rb_scan_cap = std::min(L.scan_cap, sms * rb_scan_resident());
     L.items_per_block = o.list_items_per_block > 0 ? o.list_items_per_block : 64;
     L.poll_limit = o.barrier_polls > 0 ? o.barrier_polls : kBarPollLimit;
 }
@@ -1500,7 +1524,7 @@ __global__ void __launch_bounds__(1024) k_rb_pass_init(Level L, const int64_t *c
         reset_counters(ctl);
     }
     block_max_pw(L.pw, L.k, sh, spw);   // part weights into shared memory
-    compute_classes(L, sh, spw);
+    compute_classes(L, sh, spw, ctl->L, ctl->sigma);
 }
 
 __global__ void k_clear_keys(Level L) {
