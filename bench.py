@@ -66,6 +66,9 @@ def parse_args(argv=None):
                    help="run one profiled partition and report per-level select launches (profiler target)")
     p.add_argument("--probe-graph", choices=["mesh", "rmat22"], default="mesh",
                    help="with --kernel-probe: the mesh workload (--scale) or R-MAT scale 22")
+    p.add_argument("--max-levels", type=int, default=None,
+                   help="with --kernel-probe: at most this many levels (1 = refine the input graph only, so "
+                        "that its first refinement kernels come after a few dozen launches: a profiler target)")
     p.add_argument("--rmat-k", type=int, default=None, help="with --sweep rmat: only this k")
     p.add_argument("--two-hop", action="store_true", help="with --sweep rmat: coarsen with two-hop matches")
     p.add_argument("--sweep", choices=["lp_versions", "batched", "rmat", "shapes"], default=None,
@@ -306,7 +309,8 @@ def run_probe(args):
     else:
         g = workload_graph(args.scale)
         t = [torch.from_numpy(a).to(dev) for a in (g.xadj, g.adjncy, g.vwgt, g.adjwgt)]
-    with jet.Context(0, flags=jet.FLAG_PROFILE) as ctx:
+    copts = {} if args.max_levels is None else {"max_levels": args.max_levels}
+    with jet.Context(0, flags=jet.FLAG_PROFILE, **copts) as ctx:
         _, cut, st = ctx.partition(*t, k=K_PARTS, eps=EPS, seed=SEED, return_stats=True)
     skip = sum(st.sel_launches[1:])
     names = jet.kernel_names()

@@ -742,8 +742,8 @@ __device__ __forceinline__ void lp_select_block_row(const Level &L, LpExport ex,
 }
 
 // One long row of step 1, by a whole warp: conn(v, .) in the warp's dense
-// table, which is all-zero between rows (the read pass takes every touched
-// entry with atomicExch(.., 0), which also meets each distinct part once).
+// table, which is all-zero between rows (the read pass clears every entry it
+// finds set, and meets each distinct part once).
 template <bool EW>
 __device__ __forceinline__ void lp_select_row(const Level &L, LpExport ex, int32_t v, int32_t *tab, long long &nexam,
                                               long long &degexam, long long &degx) {
@@ -758,25 +758,14 @@ __device__ __forceinline__ void lp_select_row(const Level &L, LpExport ex, int32
     int32_t conn_s = tab[ps];
     __syncwarp();
     unsigned long long best = 0;
-    if (end - beg > L.k) {
-        // a row longer than the table: read (and clear) the k entries instead
-        // of gathering the row's parts a second time
-        for (int p = lane; p < L.k; p += 32) {
-            const int32_t c = tab[p];
-            if (c != 0) {
-                tab[p] = 0;
-                if (p != ps) {
-                    const unsigned long long key = part_key(c, p);
-                    best = key > best ? key : best;
-                }
-            }
-        }
-    } else {
-        for (int64_t j = beg + lane; j < end; j += 32) {
-            int32_t p = L.part[__ldg(g.adj + j)];
-            int32_t c = atomicExch(&tab[p], 0);
-            if (c > 0 && p != ps) {
-                unsigned long long key = part_key(c, p);
+    // read (and clear) the k entries of the table: at most k / 32 shared
+    // loads a lane, cheaper than gathering the row's parts a second time
+    for (int p = lane; p < L.k; p += 32) {
+        const int32_t c = tab[p];
+        if (c != 0) {
+            tab[p] = 0;
+            if (p != ps) {
+                const unsigned long long key = part_key(c, p);
                 best = key > best ? key : best;
             }
         }
@@ -1385,20 +1374,12 @@ __device__ __forceinline__ void rb_cand_row(const Level &L, int32_t v, int32_t *
             }
         }
     };
-    if (end - beg > L.k) {
-        // a row longer than the table: read (and clear) the k entries instead
-        for (int p = lane; p < L.k; p += 32) {
-            const int32_t c = tab[p];
-            if (c != 0) {
-                tab[p] = 0;
-                take(c, p);
-            }
-        }
-    } else {
-        for (int64_t j = beg + lane; j < end; j += 32) {
-            int32_t p = L.part[__ldg(g.adj + j)];
-            int32_t c = atomicExch(&tab[p], 0);
-            if (c > 0) take(c, p);
+    // read (and clear) the k entries of the table, as in lp_select_row
+    for (int p = lane; p < L.k; p += 32) {
+        const int32_t c = tab[p];
+        if (c != 0) {
+            tab[p] = 0;
+            take(c, p);
         }
     }
     __syncwarp();
