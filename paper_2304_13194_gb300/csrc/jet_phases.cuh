@@ -105,6 +105,19 @@ __device__ __forceinline__ int32_t edge_w(const DGraph &g, int64_t j) {
     else return 1;
 }
 
+// An entry of a long row (read once per pass, coalesced over the lanes):
+// kept out of L1 so that the neighbours' fields gathered next stay there.
+__device__ __forceinline__ int32_t ld_stream(const int32_t *p) {
+    int32_t v;
+    asm("ld.global.nc.L1::no_allocate.b32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+template <bool EW>
+__device__ __forceinline__ int32_t edge_w_stream(const DGraph &g, int64_t j) {
+    if constexpr (EW) return ld_stream(g.ew + j);
+    else return 1;
+}
+
 __device__ __forceinline__ bool ablate_locks(uint32_t abl) { return (abl & (ABL_NO_LOCKS | ABL_BASELINE_LP)) != 0; }
 
 // First filter, Eq. gainconn_filter: -F < floor(c * conn(v,P_s)) or F >= 0
@@ -685,8 +698,8 @@ __device__ __forceinline__ void row_to_table(const Level &L, int64_t first, int6
 #pragma unroll
         for (int q = 0; q < U; ++q) {
             const int64_t j = j0 + q * step;
-            u[q] = j < end ? __ldg(g.adj + j) : -1;
-            w[q] = j < end ? edge_w<EW>(g, j) : 0;
+            u[q] = j < end ? ld_stream(g.adj + j) : -1;
+            w[q] = j < end ? edge_w_stream<EW>(g, j) : 0;
         }
 #pragma unroll
         for (int q = 0; q < U; ++q) p[q] = u[q] >= 0 ? L.part[u[q]] : -1;
@@ -896,8 +909,8 @@ __device__ __forceinline__ long long afterburn_row(const Level &L, int32_t v, in
 #pragma unroll
         for (int q = 0; q < U; ++q) {
             const int64_t j = j0 + q * step;
-            u[q] = j < end ? __ldg(g.adj + j) : -1;
-            w[q] = j < end ? edge_w<EW>(g, j) : 0;
+            u[q] = j < end ? ld_stream(g.adj + j) : -1;
+            w[q] = j < end ? edge_w_stream<EW>(g, j) : 0;
         }
 #pragma unroll
         for (int q = 0; q < U; ++q) {
@@ -1038,8 +1051,8 @@ __device__ __forceinline__ void apply_row(const Level &L, int32_t v, int32_t a, 
 #pragma unroll
         for (int q = 0; q < U; ++q) {
             const int64_t j = j0 + q * step;
-            u[q] = j < end ? __ldg(g.adj + j) : -1;
-            w[q] = j < end ? edge_w<EW>(g, j) : 0;
+            u[q] = j < end ? ld_stream(g.adj + j) : -1;
+            w[q] = j < end ? edge_w_stream<EW>(g, j) : 0;
         }
 #pragma unroll
         for (int q = 0; q < U; ++q) mu[q] = u[q] >= 0 && L.mstamp[u[q]] == it;
