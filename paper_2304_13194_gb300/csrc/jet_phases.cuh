@@ -155,22 +155,25 @@ __device__ __forceinline__ void disarm_loop(const Level &L, Grid G) {
 }
 
 // In a kernel launch: true in the last block to finish (all blocks call it
-// once, after their part of the phase).  Every thread fences its writes
-// before the block takes its ticket, so the last block sees all of them.
+// once, after their part of the phase).  The block's threads meet at a
+// barrier, then one thread fences (which orders every write the barrier
+// made it wait for) and takes the block's ticket, so the last block sees
+// the writes of all blocks; the tails read them with device-scope loads.
 // No block waits for another.
 __device__ __forceinline__ bool last_block(Ctl *ctl) {
     __shared__ int s_last;
-    __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
-        int t = atomicAdd(&ctl->ticket, 1);
+        __threadfence();
+        const int t = atomicAdd(&ctl->ticket, 1);
         s_last = t == (int)gridDim.x - 1;
-        if (s_last) ctl->ticket = 0;   // for the next kernel that counts
+        if (s_last) {
+            __threadfence();
+            ctl->ticket = 0;   // for the next kernel that counts
+        }
     }
     __syncthreads();
-    bool last = s_last != 0;
-    if (last) __threadfence();
-    return last;
+    return s_last != 0;
 }
 
 // Block-aggregated append into a global list: members are staged in shared
@@ -550,7 +553,10 @@ __device__ inline int32_t ph_controller(const Level &L) {
         s_lim[0] = Llim;
         s_lim[1] = sigma;
         if (L.use_graph) {
-            cudaGraphSetConditional((cudaGraphConditionalHandle)L.h_mode, (unsigned)m);
+            // the switch value persists over the loop's iterations: set it
+            // when the mode changes; the loop flag every time (the next
+            // iteration's first kernel clears it)
+            if (m != kind) cudaGraphSetConditional((cudaGraphConditionalHandle)L.h_mode, (unsigned)m);
             cudaGraphSetConditional((cudaGraphConditionalHandle)L.h_loop, m == MODE_DONE ? 0u : 1u);
         }
     }
