@@ -9,13 +9,21 @@
 // vertices here):
 //  1. components by union-find, the larger root always hooked under the
 //     smaller, so every tree ends at its component's lowest id whatever the
-//     order of the hooks; then double-buffered pointer jumping (a fixed
-//     number of rounds, each reading one array and writing the other) gives
-//     every vertex its root exactly — path compression done in place would
-//     let a late halving store overwrite a finished root with an ancestor;
+//     order of the hooks.  The hooks are sampled first (each vertex's first
+//     two row entries), the root that most of an evenly spaced sample of
+//     vertices reaches is taken as the large component's, and then only the
+//     rows of vertices outside it are hooked in full (every edge with an
+//     end outside that component is met from that end; an edge between two
+//     vertices inside it joins nothing new).  Double-buffered pointer
+//     jumping (a fixed number of rounds, each reading one array and writing
+//     the other) then gives every vertex its root exactly — path
+//     compression done in place would let a late halving store overwrite a
+//     finished root with an ancestor;
 //  2. breadth-first levels from all those roots at once, one frontier per
 //     level (each kernel launch takes one level and exits at once when the
-//     frontier is empty, so the host enqueues levels in batches);
+//     frontier is empty, so the host enqueues levels in batches); frontier
+//     rows in degree classes as in the refinement passes (one thread, one
+//     warp, one block per row);
 //  3. a stable LSD radix sort of the vertices (in id order) by the key
 //     (root, distance): the id order inside a key is kept;
 //  4. an exclusive scan of the weights in that order, then P.
@@ -36,7 +44,7 @@ struct IpCtl {
     int32_t level;       // level the next k_bfs_level launch expands
     int32_t ticket;      // blocks of the current launch that finished
     int32_t error;       // a union-find loop hit kFindCap
-    int32_t pad;
+    int32_t major;       // root reached by most of the sampled vertices after the sampled hooks
     int64_t total;       // scan total (W)
 };
 
@@ -73,19 +81,61 @@ __device__ __forceinline__ void uf_hook_edge(int32_t *parent, int32_t u, int32_t
     }
 }
 
-// One warp per vertex v hooks the edges {u, v} with u < v; rows longer than
-// kHugeDeg are set aside (up to kHugeCap per block) and taken by the whole
-// block at the end.
-__global__ void __launch_bounds__(kTB) k_uf_hook(DGraph g, int32_t *parent, IpCtl *ctl) {
+// Sampled hooks: every vertex hooks the edges of its first kSampleHooks row
+// entries.
+constexpr int kSampleHooks = 2;
+__global__ void k_uf_hook_sample(DGraph g, int32_t *parent, IpCtl *ctl) {
+    int32_t err = 0;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < g.n; v += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t beg = ld_xadj(g.xadj, v), end = ld_xadj(g.xadj, v + 1);
+        for (int64_t j = beg; j < end && j < beg + kSampleHooks; ++j) {
+            const int32_t u = __ldg(g.adj + j);
+            if (u != v) uf_hook_edge(parent, u, (int32_t)v, &err);
+        }
+    }
+    if (err) ctl->error = 1;
+}
+
+// The root most of kMajorSample evenly spaced vertices reach (ties: the
+// smaller root); one block of kMajorSample threads.  Only a work saving: a
+// poor pick costs hooks, not correctness.
+constexpr int kMajorSample = 256;
+__global__ void __launch_bounds__(kMajorSample) k_uf_major(int32_t n, int32_t *parent, IpCtl *ctl) {
+    __shared__ int32_t r[kMajorSample];
+    __shared__ unsigned long long best;
+    int32_t err = 0;
+    const int32_t v = (int32_t)(((int64_t)threadIdx.x * n) / kMajorSample);
+    r[threadIdx.x] = uf_find(parent, v, &err);
+    if (threadIdx.x == 0) best = 0;
+    __syncthreads();
+    int32_t cnt = 0;
+    for (int i = 0; i < kMajorSample; ++i) cnt += r[i] == r[threadIdx.x];
+    // larger count first, then the smaller root
+    atomicMax(&best, ((unsigned long long)cnt << 32) | (unsigned long long)(uint32_t)(INT32_MAX - r[threadIdx.x]));
+    __syncthreads();
+    if (threadIdx.x == 0) ctl->major = INT32_MAX - (int32_t)(uint32_t)(best & 0xffffffffull);
+    if (err) ctl->error = 1;
+}
+
+// One warp per vertex v outside the major component hooks every edge of its
+// row; rows longer than kHugeDeg are set aside (up to kHugeCap per block)
+// and taken by the whole block at the end.
+__global__ void __launch_bounds__(kTB) k_uf_hook_rest(DGraph g, int32_t *parent, IpCtl *ctl) {
     __shared__ int32_t huge[kHugeCap];
     __shared__ int nhuge;
     if (threadIdx.x == 0) nhuge = 0;
     __syncthreads();
+    const int32_t major = ctl->major;
     const int warps = blockDim.x >> 5;
     const unsigned lane = lane_id();
     int32_t err = 0;
     for (int64_t v = (int64_t)blockIdx.x * warps + (threadIdx.x >> 5); v < g.n; v += (int64_t)gridDim.x * warps) {
-        int64_t beg = ld_xadj(g.xadj, v), end = ld_xadj(g.xadj, v + 1);
+        const int64_t beg = ld_xadj(g.xadj, v), end = ld_xadj(g.xadj, v + 1);
+        if (end == beg) continue;
+        int32_t rv = 0;
+        if (lane == 0) rv = uf_find(parent, (int32_t)v, &err);
+        rv = __shfl_sync(0xffffffffu, rv, 0);
+        if (rv == major) continue;
         if (end - beg > kHugeDeg) {
             int slot = 0;
             if (lane == 0) slot = atomicAdd(&nhuge, 1);
@@ -96,8 +146,8 @@ __global__ void __launch_bounds__(kTB) k_uf_hook(DGraph g, int32_t *parent, IpCt
             }
         }
         for (int64_t j = beg + lane; j < end; j += 32) {
-            int32_t u = __ldg(g.adj + j);
-            if (u < v) uf_hook_edge(parent, u, (int32_t)v, &err);
+            const int32_t u = __ldg(g.adj + j);
+            if (u != v) uf_hook_edge(parent, u, (int32_t)v, &err);
         }
     }
     __syncthreads();
@@ -106,8 +156,8 @@ __global__ void __launch_bounds__(kTB) k_uf_hook(DGraph g, int32_t *parent, IpCt
         const int32_t v = huge[s];
         const int64_t beg = ld_xadj(g.xadj, v), end = ld_xadj(g.xadj, (int64_t)v + 1);
         for (int64_t j = beg + threadIdx.x; j < end; j += blockDim.x) {
-            int32_t u = __ldg(g.adj + j);
-            if (u < v) uf_hook_edge(parent, u, v, &err);
+            const int32_t u = __ldg(g.adj + j);
+            if (u != v) uf_hook_edge(parent, u, v, &err);
         }
     }
     if (err) ctl->error = 1;
@@ -134,9 +184,21 @@ __global__ void k_uf_finish(int32_t n, const int32_t *root, int32_t *dist, int32
     }
 }
 
-// One breadth-first level: the frontier of level l (parity l & 1), one warp
-// per vertex; a neighbour is claimed for level l + 1 by a CAS on its
-// distance.  The last block to finish closes the level.
+// Claims neighbour u for level l + 1 (a CAS on its distance) and appends the
+// claimed ones to `out` (whole warp; u < 0: nothing).
+__device__ __forceinline__ void bfs_claim_warp(int32_t *dist, int32_t u, int32_t l, int32_t *out, int32_t *out_size) {
+    const bool claim = u >= 0 && dist[u] == kInf && atomicCAS(&dist[u], kInf, l + 1) == kInf;
+    const int slot = warp_append(out_size, claim);
+    if (claim) out[slot] = u;
+}
+
+// One breadth-first level: the frontier of level l (parity l & 1).  Rows of
+// at most kSmallDeg entries are taken one thread each (the row's ids, then
+// their distances, in flight together; the claims of a warp appended with
+// one atomic), longer rows are staged for the block's warps, rows longer
+// than kHugeDeg for the whole block at the end.  A neighbour is claimed for
+// level l + 1 by a CAS on its distance, so the distances are exact whatever
+// the order.  The last block to finish closes the level.
 __global__ void __launch_bounds__(kTB) k_bfs_level(DGraph g, int32_t *dist, int32_t *front0, int32_t *front1,
                                                    IpCtl *ctl) {
     const int32_t l = ctl->level;
@@ -148,37 +210,72 @@ __global__ void __launch_bounds__(kTB) k_bfs_level(DGraph g, int32_t *dist, int3
     const int warps = blockDim.x >> 5;
     const unsigned lane = lane_id();
     __shared__ int32_t huge[kHugeCap];
-    __shared__ int nhuge;
+    __shared__ int32_t stage[kTB];
+    __shared__ int nhuge, nstage;
     if (threadIdx.x == 0) nhuge = 0;
-    __syncthreads();
-    for (int64_t w0 = (int64_t)blockIdx.x * warps; w0 < cur; w0 += (int64_t)gridDim.x * warps) {
-        int64_t w = w0 + (threadIdx.x >> 5);
-        int64_t beg = 0, end = 0;
+    for (int64_t w0 = (int64_t)blockIdx.x * blockDim.x; w0 < cur; w0 += (int64_t)gridDim.x * blockDim.x) {
+        __syncthreads();
+        if (threadIdx.x == 0) nstage = 0;
+        __syncthreads();
+        const int64_t w = w0 + threadIdx.x;
         int32_t v = -1;
+        int64_t beg = 0, end = 0;
         if (w < cur) {
             v = in[w];
             beg = ld_xadj(g.xadj, v);
             end = ld_xadj(g.xadj, (int64_t)v + 1);
         }
-        if (end - beg > kHugeDeg) {              // hub row: the whole block, below
-            int slot = 0;
-            if (lane == 0) slot = atomicAdd(&nhuge, 1);
-            slot = __shfl_sync(0xffffffffu, slot, 0);
-            if (slot < kHugeCap) {
-                if (lane == 0) huge[slot] = v;
-                end = beg;
+        const int64_t d = end - beg;
+        if (d > kSmallDeg) {
+            bool staged = false;
+            if (d > kHugeDeg) {
+                const int slot = atomicAdd(&nhuge, 1);
+                if (slot < kHugeCap) {
+                    huge[slot] = v;
+                    staged = true;
+                }
             }
+            if (!staged) stage[atomicAdd(&nstage, 1)] = v;
         }
-        for (int64_t j0 = beg; j0 < end; j0 += 32) {   // whole warp: same row
-            int64_t j = j0 + lane;
-            bool claim = false;
-            int32_t u = -1;
-            if (j < end) {
-                u = __ldg(g.adj + j);
-                claim = dist[u] == kInf && atomicCAS(&dist[u], kInf, l + 1) == kInf;
+        // short rows, one thread each
+        const int ds = d <= kSmallDeg ? (int)d : 0;
+        int32_t u[kSmallDeg];
+#pragma unroll
+        for (int t = 0; t < kSmallDeg; ++t) u[t] = t < ds ? __ldg(g.adj + beg + t) : -1;
+        uint32_t cand = 0;
+#pragma unroll
+        for (int t = 0; t < kSmallDeg; ++t)
+            if (u[t] >= 0 && dist[u[t]] == kInf) cand |= 1u << t;
+        uint32_t won = 0;
+#pragma unroll
+        for (int t = 0; t < kSmallDeg; ++t)
+            if ((cand >> t) & 1u) won |= (uint32_t)(atomicCAS(&dist[u[t]], kInf, l + 1) == kInf) << t;
+        // the warp's claims: one reservation for all of them
+        const int nw = __popc(won);
+        int incl = nw;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int x = __shfl_up_sync(0xffffffffu, incl, o);
+            if ((int)lane >= o) incl += x;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        int base = 0;
+        if (total > 0 && lane == 31) base = atomicAdd(out_size, total);
+        base = __shfl_sync(0xffffffffu, base, 31);
+        int at = base + incl - nw;
+#pragma unroll
+        for (int t = 0; t < kSmallDeg; ++t)
+            if ((won >> t) & 1u) out[at++] = u[t];
+        __syncthreads();
+        // staged rows, one warp each
+        const int ns = nstage;
+        for (int q = threadIdx.x >> 5; q < ns; q += warps) {
+            const int32_t sv = stage[q];
+            const int64_t sb = ld_xadj(g.xadj, sv), se = ld_xadj(g.xadj, (int64_t)sv + 1);
+            for (int64_t j0 = sb; j0 < se; j0 += 32) {   // whole warp: same row
+                const int64_t j = j0 + lane;
+                bfs_claim_warp(dist, j < se ? __ldg(g.adj + j) : -1, l, out, out_size);
             }
-            int slot = warp_append(out_size, claim);
-            if (claim) out[slot] = u;
         }
     }
     __syncthreads();
@@ -187,15 +284,8 @@ __global__ void __launch_bounds__(kTB) k_bfs_level(DGraph g, int32_t *dist, int3
         const int32_t v = huge[s];
         const int64_t beg = ld_xadj(g.xadj, v), end = ld_xadj(g.xadj, (int64_t)v + 1);
         for (int64_t j0 = beg + (int64_t)(threadIdx.x >> 5) * 32; j0 < end; j0 += blockDim.x) {
-            int64_t j = j0 + lane;
-            bool claim = false;
-            int32_t u = -1;
-            if (j < end) {
-                u = __ldg(g.adj + j);
-                claim = dist[u] == kInf && atomicCAS(&dist[u], kInf, l + 1) == kInf;
-            }
-            int slot = warp_append(out_size, claim);
-            if (claim) out[slot] = u;
+            const int64_t j = j0 + lane;
+            bfs_claim_warp(dist, j < end ? __ldg(g.adj + j) : -1, l, out, out_size);
         }
     }
     __shared__ int s_last;
@@ -277,7 +367,9 @@ int initial_partition(Ctx &c, const DGraph &g, int32_t k, int32_t *part, GreedyO
 
     // 1. components
     k_uf_init<<<gv, kTB, 0, s>>>((int32_t)n, parent);
-    k_uf_hook<<<gw, kTB, 0, s>>>(g, parent, ctl);
+    k_uf_hook_sample<<<gv, kTB, 0, s>>>(g, parent, ctl);
+    k_uf_major<<<1, kMajorSample, 0, s>>>((int32_t)n, parent, ctl);
+    k_uf_hook_rest<<<gw, kTB, 0, s>>>(g, parent, ctl);
     int32_t *ra = parent, *rb = rootb;
     const int rounds = bits_for(n);
     for (int r = 0; r < rounds; ++r) {
@@ -286,7 +378,7 @@ int initial_partition(Ctx &c, const DGraph &g, int32_t k, int32_t *part, GreedyO
     }
     const int32_t *root = ra;
     k_uf_finish<<<gv, kTB, 0, s>>>((int32_t)n, root, dist, front0, ctl);
-    c.launches += 3 + rounds;
+    c.launches += 5 + rounds;
     JET_CUDA_TRY(cudaGetLastError());
 
     // 2. breadth-first levels, kBfsBatch launches between checks
