@@ -21,9 +21,7 @@
 //     finished root with an ancestor;
 //  2. breadth-first levels from all those roots at once, one frontier per
 //     level (each kernel launch takes one level and exits at once when the
-//     frontier is empty, so the host enqueues levels in batches); frontier
-//     rows in degree classes as in the refinement passes (one thread, one
-//     warp, one block per row);
+//     frontier is empty, so the host enqueues levels in batches);
 //  3. a stable LSD radix sort of the vertices (in id order) by the key
 //     (root, distance): the id order inside a key is kept;
 //  4. an exclusive scan of the weights in that order, then P.
@@ -184,21 +182,9 @@ __global__ void k_uf_finish(int32_t n, const int32_t *root, int32_t *dist, int32
     }
 }
 
-// Claims neighbour u for level l + 1 (a CAS on its distance) and appends the
-// claimed ones to `out` (whole warp; u < 0: nothing).
-__device__ __forceinline__ void bfs_claim_warp(int32_t *dist, int32_t u, int32_t l, int32_t *out, int32_t *out_size) {
-    const bool claim = u >= 0 && dist[u] == kInf && atomicCAS(&dist[u], kInf, l + 1) == kInf;
-    const int slot = warp_append(out_size, claim);
-    if (claim) out[slot] = u;
-}
-
-// One breadth-first level: the frontier of level l (parity l & 1).  Rows of
-// at most kSmallDeg entries are taken one thread each (the row's ids, then
-// their distances, in flight together; the claims of a warp appended with
-// one atomic), longer rows are staged for the block's warps, rows longer
-// than kHugeDeg for the whole block at the end.  A neighbour is claimed for
-// level l + 1 by a CAS on its distance, so the distances are exact whatever
-// the order.  The last block to finish closes the level.
+// One breadth-first level: the frontier of level l (parity l & 1), one warp
+// per vertex; a neighbour is claimed for level l + 1 by a CAS on its
+// distance.  The last block to finish closes the level.
 __global__ void __launch_bounds__(kTB) k_bfs_level(DGraph g, int32_t *dist, int32_t *front0, int32_t *front1,
                                                    IpCtl *ctl) {
     const int32_t l = ctl->level;
@@ -210,72 +196,37 @@ __global__ void __launch_bounds__(kTB) k_bfs_level(DGraph g, int32_t *dist, int3
     const int warps = blockDim.x >> 5;
     const unsigned lane = lane_id();
     __shared__ int32_t huge[kHugeCap];
-    __shared__ int32_t stage[kTB];
-    __shared__ int nhuge, nstage;
+    __shared__ int nhuge;
     if (threadIdx.x == 0) nhuge = 0;
-    for (int64_t w0 = (int64_t)blockIdx.x * blockDim.x; w0 < cur; w0 += (int64_t)gridDim.x * blockDim.x) {
-        __syncthreads();
-        if (threadIdx.x == 0) nstage = 0;
-        __syncthreads();
-        const int64_t w = w0 + threadIdx.x;
-        int32_t v = -1;
+    __syncthreads();
+    for (int64_t w0 = (int64_t)blockIdx.x * warps; w0 < cur; w0 += (int64_t)gridDim.x * warps) {
+        int64_t w = w0 + (threadIdx.x >> 5);
         int64_t beg = 0, end = 0;
+        int32_t v = -1;
         if (w < cur) {
             v = in[w];
             beg = ld_xadj(g.xadj, v);
             end = ld_xadj(g.xadj, (int64_t)v + 1);
         }
-        const int64_t d = end - beg;
-        if (d > kSmallDeg) {
-            bool staged = false;
-            if (d > kHugeDeg) {
-                const int slot = atomicAdd(&nhuge, 1);
-                if (slot < kHugeCap) {
-                    huge[slot] = v;
-                    staged = true;
-                }
+        if (end - beg > kHugeDeg) {              // hub row: the whole block, below
+            int slot = 0;
+            if (lane == 0) slot = atomicAdd(&nhuge, 1);
+            slot = __shfl_sync(0xffffffffu, slot, 0);
+            if (slot < kHugeCap) {
+                if (lane == 0) huge[slot] = v;
+                end = beg;
             }
-            if (!staged) stage[atomicAdd(&nstage, 1)] = v;
         }
-        // short rows, one thread each
-        const int ds = d <= kSmallDeg ? (int)d : 0;
-        int32_t u[kSmallDeg];
-#pragma unroll
-        for (int t = 0; t < kSmallDeg; ++t) u[t] = t < ds ? __ldg(g.adj + beg + t) : -1;
-        uint32_t cand = 0;
-#pragma unroll
-        for (int t = 0; t < kSmallDeg; ++t)
-            if (u[t] >= 0 && dist[u[t]] == kInf) cand |= 1u << t;
-        uint32_t won = 0;
-#pragma unroll
-        for (int t = 0; t < kSmallDeg; ++t)
-            if ((cand >> t) & 1u) won |= (uint32_t)(atomicCAS(&dist[u[t]], kInf, l + 1) == kInf) << t;
-        // the warp's claims: one reservation for all of them
-        const int nw = __popc(won);
-        int incl = nw;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int x = __shfl_up_sync(0xffffffffu, incl, o);
-            if ((int)lane >= o) incl += x;
-        }
-        const int total = __shfl_sync(0xffffffffu, incl, 31);
-        int base = 0;
-        if (total > 0 && lane == 31) base = atomicAdd(out_size, total);
-        base = __shfl_sync(0xffffffffu, base, 31);
-        int at = base + incl - nw;
-#pragma unroll
-        for (int t = 0; t < kSmallDeg; ++t)
-            if ((won >> t) & 1u) out[at++] = u[t];
-        __syncthreads();
-        // staged rows, one warp each
-        const int ns = nstage;
-        for (int q = threadIdx.x >> 5; q < ns; q += warps) {
-            const int32_t sv = stage[q];
-            const int64_t sb = ld_xadj(g.xadj, sv), se = ld_xadj(g.xadj, (int64_t)sv + 1);
-            for (int64_t j0 = sb; j0 < se; j0 += 32) {   // whole warp: same row
-                const int64_t j = j0 + lane;
-                bfs_claim_warp(dist, j < se ? __ldg(g.adj + j) : -1, l, out, out_size);
+        for (int64_t j0 = beg; j0 < end; j0 += 32) {   // whole warp: same row
+            int64_t j = j0 + lane;
+            bool claim = false;
+            int32_t u = -1;
+            if (j < end) {
+                u = __ldg(g.adj + j);
+                claim = dist[u] == kInf && atomicCAS(&dist[u], kInf, l + 1) == kInf;
             }
+            int slot = warp_append(out_size, claim);
+            if (claim) out[slot] = u;
         }
     }
     __syncthreads();
@@ -284,8 +235,15 @@ __global__ void __launch_bounds__(kTB) k_bfs_level(DGraph g, int32_t *dist, int3
         const int32_t v = huge[s];
         const int64_t beg = ld_xadj(g.xadj, v), end = ld_xadj(g.xadj, (int64_t)v + 1);
         for (int64_t j0 = beg + (int64_t)(threadIdx.x >> 5) * 32; j0 < end; j0 += blockDim.x) {
-            const int64_t j = j0 + lane;
-            bfs_claim_warp(dist, j < end ? __ldg(g.adj + j) : -1, l, out, out_size);
+            int64_t j = j0 + lane;
+            bool claim = false;
+            int32_t u = -1;
+            if (j < end) {
+                u = __ldg(g.adj + j);
+                claim = dist[u] == kInf && atomicCAS(&dist[u], kInf, l + 1) == kInf;
+            }
+            int slot = warp_append(out_size, claim);
+            if (claim) out[slot] = u;
         }
     }
     __shared__ int s_last;
