@@ -21,7 +21,9 @@
 //     finished root with an ancestor;
 //  2. breadth-first levels from all those roots at once, one frontier per
 //     level (each kernel launch takes one level and exits at once when the
-//     frontier is empty, so the host enqueues levels in batches);
+//     frontier is empty, so the host enqueues levels in batches); a level
+//     whose frontier carries many row entries is taken bottom-up (the
+//     vertices not reached yet look for a parent), the others top-down;
 //  3. a stable LSD radix sort of the vertices (in id order) by the key
 //     (root, distance): the id order inside a key is kept;
 //  4. an exclusive scan of the weights in that order, then P.
@@ -44,6 +46,8 @@ struct IpCtl {
     int32_t error;       // a union-find loop hit kFindCap
     int32_t major;       // root reached by most of the sampled vertices after the sampled hooks
     int64_t total;       // scan total (W)
+    int64_t mf[2];       // row entries of the frontier, by level parity
+    int64_t mv;          // row entries of the vertices reached so far
 };
 
 // Root of x with path halving.  parent[] only ever decreases (parent[x] <= x),
@@ -168,23 +172,56 @@ __global__ void k_uf_jump(int32_t n, const int32_t *in, int32_t *out) {
         out[v] = in[in[v]];
 }
 
-// Distance 0 at the roots, which form the first frontier.
-__global__ void k_uf_finish(int32_t n, const int32_t *root, int32_t *dist, int32_t *front0, IpCtl *ctl) {
+// Distance 0 at the roots, which form the first frontier (and their row
+// entries the first frontier's).
+__global__ void __launch_bounds__(kTB) k_uf_finish(DGraph g, const int32_t *root, int32_t *dist, int32_t *front0,
+                                                   IpCtl *ctl) {
+    __shared__ long long red[40];
+    const int32_t n = g.n;
+    long long mf = 0;
     for (int64_t v0 = (int64_t)blockIdx.x * blockDim.x; v0 < n; v0 += (int64_t)gridDim.x * blockDim.x) {
         int64_t v = v0 + threadIdx.x;
         bool is_root = false;
         if (v < n) {
             is_root = root[v] == v;
             dist[v] = is_root ? 0 : kInf;
+            if (is_root) mf += ld_xadj(g.xadj, v + 1) - ld_xadj(g.xadj, v);
         }
         int slot = warp_append(&ctl->size[0], is_root);
         if (is_root) front0[slot] = (int32_t)v;
     }
+    mf = block_sum_i64(mf, red);
+    if (threadIdx.x == 0 && mf) {
+        atomic_add_i64(&ctl->mf[0], mf);
+        atomic_add_i64(&ctl->mv, mf);
+    }
 }
 
-// One breadth-first level: the frontier of level l (parity l & 1), one warp
-// per vertex; a neighbour is claimed for level l + 1 by a CAS on its
-// distance.  The last block to finish closes the level.
+// Bottom-up steps (Beamer's direction switch) are taken while the
+// frontier's row entries exceed 1/kBottomUpAlpha of those of the vertices
+// not reached yet.  4 rather than Beamer's 14: on a mesh the vertices not
+// reached yet mostly have no parent in the frontier and would read their
+// whole rows, so only a frontier whose rows rival theirs switches.
+constexpr int64_t kBottomUpAlpha = 4;
+
+// Whether the warp's row chunk holds a vertex of level l (whole warp).
+__device__ __forceinline__ bool bfs_parent_in_chunk(const DGraph &g, const int32_t *dist, int64_t j, int64_t end,
+                                                    int32_t l) {
+    const int32_t w = j < end ? __ldg(g.adj + j) : -1;
+    return __any_sync(0xffffffffu, w >= 0 && dist[w] == l);
+}
+
+// One breadth-first level l -> l + 1 (frontier of parity l & 1).  Distances
+// are exact whichever way a level is taken:
+//  * top-down: one warp per frontier vertex; a neighbour is claimed for
+//    level l + 1 by a CAS on its distance;
+//  * bottom-up: every vertex not reached yet looks for a neighbour at level
+//    l (rows of up to 32 entries one thread each, 8 entries in flight,
+//    longer rows one warp each, rows longer than kHugeDeg the whole block;
+//    each stops at the first one found) and writes its own distance.
+// The new frontier is appended either way; the row entries of its vertices
+// are counted for the next level's choice.  The last block to finish closes
+// the level.
 __global__ void __launch_bounds__(kTB) k_bfs_level(DGraph g, int32_t *dist, int32_t *front0, int32_t *front1,
                                                    IpCtl *ctl) {
     const int32_t l = ctl->level;
@@ -193,59 +230,142 @@ __global__ void __launch_bounds__(kTB) k_bfs_level(DGraph g, int32_t *dist, int3
     const int32_t *in = (l & 1) ? front1 : front0;
     int32_t *out = (l & 1) ? front0 : front1;
     int32_t *out_size = &ctl->size[(l + 1) & 1];
+    const bool bottom_up = ctl->mf[l & 1] * kBottomUpAlpha > g.nnz - ctl->mv;
     const int warps = blockDim.x >> 5;
     const unsigned lane = lane_id();
     __shared__ int32_t huge[kHugeCap];
     __shared__ int nhuge;
+    __shared__ long long red[40];
+    long long mf_next = 0;
     if (threadIdx.x == 0) nhuge = 0;
     __syncthreads();
-    for (int64_t w0 = (int64_t)blockIdx.x * warps; w0 < cur; w0 += (int64_t)gridDim.x * warps) {
-        int64_t w = w0 + (threadIdx.x >> 5);
-        int64_t beg = 0, end = 0;
-        int32_t v = -1;
-        if (w < cur) {
-            v = in[w];
-            beg = ld_xadj(g.xadj, v);
-            end = ld_xadj(g.xadj, (int64_t)v + 1);
-        }
-        if (end - beg > kHugeDeg) {              // hub row: the whole block, below
-            int slot = 0;
-            if (lane == 0) slot = atomicAdd(&nhuge, 1);
-            slot = __shfl_sync(0xffffffffu, slot, 0);
-            if (slot < kHugeCap) {
-                if (lane == 0) huge[slot] = v;
-                end = beg;
+    if (!bottom_up) {
+        for (int64_t w0 = (int64_t)blockIdx.x * warps; w0 < cur; w0 += (int64_t)gridDim.x * warps) {
+            int64_t w = w0 + (threadIdx.x >> 5);
+            int64_t beg = 0, end = 0;
+            int32_t v = -1;
+            if (w < cur) {
+                v = in[w];
+                beg = ld_xadj(g.xadj, v);
+                end = ld_xadj(g.xadj, (int64_t)v + 1);
+            }
+            if (end - beg > kHugeDeg) {              // hub row: the whole block, below
+                int slot = 0;
+                if (lane == 0) slot = atomicAdd(&nhuge, 1);
+                slot = __shfl_sync(0xffffffffu, slot, 0);
+                if (slot < kHugeCap) {
+                    if (lane == 0) huge[slot] = v;
+                    end = beg;
+                }
+            }
+            for (int64_t j0 = beg; j0 < end; j0 += 32) {   // whole warp: same row
+                int64_t j = j0 + lane;
+                bool claim = false;
+                int32_t u = -1;
+                if (j < end) {
+                    u = __ldg(g.adj + j);
+                    claim = dist[u] == kInf && atomicCAS(&dist[u], kInf, l + 1) == kInf;
+                }
+                int slot = warp_append(out_size, claim);
+                if (claim) {
+                    out[slot] = u;
+                    mf_next += ld_xadj(g.xadj, (int64_t)u + 1) - ld_xadj(g.xadj, u);
+                }
             }
         }
-        for (int64_t j0 = beg; j0 < end; j0 += 32) {   // whole warp: same row
-            int64_t j = j0 + lane;
-            bool claim = false;
-            int32_t u = -1;
-            if (j < end) {
-                u = __ldg(g.adj + j);
-                claim = dist[u] == kInf && atomicCAS(&dist[u], kInf, l + 1) == kInf;
+        __syncthreads();
+        const int nh = nhuge < kHugeCap ? nhuge : kHugeCap;
+        for (int s = 0; s < nh; ++s) {
+            const int32_t v = huge[s];
+            const int64_t beg = ld_xadj(g.xadj, v), end = ld_xadj(g.xadj, (int64_t)v + 1);
+            for (int64_t j0 = beg + (int64_t)(threadIdx.x >> 5) * 32; j0 < end; j0 += blockDim.x) {
+                int64_t j = j0 + lane;
+                bool claim = false;
+                int32_t u = -1;
+                if (j < end) {
+                    u = __ldg(g.adj + j);
+                    claim = dist[u] == kInf && atomicCAS(&dist[u], kInf, l + 1) == kInf;
+                }
+                int slot = warp_append(out_size, claim);
+                if (claim) {
+                    out[slot] = u;
+                    mf_next += ld_xadj(g.xadj, (int64_t)u + 1) - ld_xadj(g.xadj, u);
+                }
             }
-            int slot = warp_append(out_size, claim);
-            if (claim) out[slot] = u;
+        }
+    } else {
+        __shared__ int32_t stage[kTB];
+        __shared__ int nstage;
+        for (int64_t v0 = (int64_t)blockIdx.x * blockDim.x; v0 < g.n; v0 += (int64_t)gridDim.x * blockDim.x) {
+            if (threadIdx.x == 0) nstage = 0;
+            __syncthreads();
+            const int64_t v = v0 + threadIdx.x;
+            bool found = false;
+            int64_t beg = 0, end = 0;
+            if (v < g.n && dist[v] == kInf) {
+                beg = ld_xadj(g.xadj, v);
+                end = ld_xadj(g.xadj, v + 1);
+                if (end - beg > 32) {
+                    bool staged = false;
+                    if (end - beg > kHugeDeg) {
+                        const int slot = atomicAdd(&nhuge, 1);
+                        if (slot < kHugeCap) {
+                            huge[slot] = (int32_t)v;
+                            staged = true;
+                        }
+                    }
+                    if (!staged) stage[atomicAdd(&nstage, 1)] = (int32_t)v;
+                } else {
+                    for (int64_t j0 = beg; j0 < end && !found; j0 += 8) {
+                        int32_t w[8];
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) w[q] = j0 + q < end ? __ldg(g.adj + j0 + q) : -1;
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) found |= w[q] >= 0 && dist[w[q]] == l;
+                    }
+                    if (found) {
+                        dist[v] = l + 1;
+                        mf_next += end - beg;
+                    }
+                }
+            }
+            const int slot = warp_append(out_size, found);
+            if (found) out[slot] = (int32_t)v;
+            __syncthreads();
+            const int ns = nstage;
+            for (int q = threadIdx.x >> 5; q < ns; q += warps) {   // staged rows, one warp each
+                const int32_t sv = stage[q];
+                const int64_t sb = ld_xadj(g.xadj, sv), se = ld_xadj(g.xadj, (int64_t)sv + 1);
+                bool hit = false;
+                for (int64_t j0 = sb; j0 < se && !hit; j0 += 32) hit = bfs_parent_in_chunk(g, dist, j0 + lane, se, l);
+                if (hit && lane == 0) {
+                    dist[sv] = l + 1;
+                    out[atomicAdd(out_size, 1)] = sv;
+                    mf_next += se - sb;
+                }
+            }
+            __syncthreads();
+        }
+        const int nh = nhuge < kHugeCap ? nhuge : kHugeCap;
+        for (int s = 0; s < nh; ++s) {           // hub rows, the whole block
+            const int32_t hv = huge[s];
+            const int64_t hb = ld_xadj(g.xadj, hv), he = ld_xadj(g.xadj, (int64_t)hv + 1);
+            bool hit = false;
+            for (int64_t j0 = hb; j0 < he; j0 += blockDim.x) {
+                const int64_t j = j0 + threadIdx.x;
+                const int32_t w = j < he ? __ldg(g.adj + j) : -1;
+                hit = __syncthreads_or(w >= 0 && dist[w] == l);
+                if (hit) break;
+            }
+            if (hit && threadIdx.x == 0) {
+                dist[hv] = l + 1;
+                out[atomicAdd(out_size, 1)] = hv;
+                mf_next += he - hb;
+            }
         }
     }
-    __syncthreads();
-    const int nh = nhuge < kHugeCap ? nhuge : kHugeCap;
-    for (int s = 0; s < nh; ++s) {
-        const int32_t v = huge[s];
-        const int64_t beg = ld_xadj(g.xadj, v), end = ld_xadj(g.xadj, (int64_t)v + 1);
-        for (int64_t j0 = beg + (int64_t)(threadIdx.x >> 5) * 32; j0 < end; j0 += blockDim.x) {
-            int64_t j = j0 + lane;
-            bool claim = false;
-            int32_t u = -1;
-            if (j < end) {
-                u = __ldg(g.adj + j);
-                claim = dist[u] == kInf && atomicCAS(&dist[u], kInf, l + 1) == kInf;
-            }
-            int slot = warp_append(out_size, claim);
-            if (claim) out[slot] = u;
-        }
-    }
+    mf_next = block_sum_i64(mf_next, red);
+    if (threadIdx.x == 0 && mf_next) atomic_add_i64(&ctl->mf[(l + 1) & 1], mf_next);
     __shared__ int s_last;
     __threadfence();
     __syncthreads();
@@ -253,8 +373,11 @@ __global__ void __launch_bounds__(kTB) k_bfs_level(DGraph g, int32_t *dist, int3
         int t = atomicAdd(&ctl->ticket, 1);
         s_last = t == (int)gridDim.x - 1;
         if (s_last) {
+            __threadfence();
             ctl->ticket = 0;
             ctl->size[l & 1] = 0;
+            ctl->mv += __ldcg(reinterpret_cast<const long long *>(&ctl->mf[(l + 1) & 1]));   // from L2: other blocks added it
+            ctl->mf[l & 1] = 0;
             ctl->level = l + 1;
         }
     }
@@ -335,7 +458,7 @@ int initial_partition(Ctx &c, const DGraph &g, int32_t k, int32_t *part, GreedyO
         std::swap(ra, rb);
     }
     const int32_t *root = ra;
-    k_uf_finish<<<gv, kTB, 0, s>>>((int32_t)n, root, dist, front0, ctl);
+    k_uf_finish<<<gv, kTB, 0, s>>>(g, root, dist, front0, ctl);
     c.launches += 5 + rounds;
     JET_CUDA_TRY(cudaGetLastError());
 
