@@ -64,6 +64,7 @@ __device__ __forceinline__ bool hem_skip(const HemCtl *hc, int r) {
 template <bool EW>
 __global__ void __launch_bounds__(kTB) k_hem_propose_small(DGraph g, const int32_t *mate, int32_t *prop, uint64_t seed,
                                                            uint64_t salt, int r, HemCtl *hc) {
+    pdl_enter();
     if (hem_skip(hc, r)) {
         if (blockIdx.x == 0 && threadIdx.x == 0) hc->stop = 1;
         return;
@@ -114,6 +115,7 @@ __device__ __forceinline__ void hem_row(const DGraph &g, const int32_t *mate, ui
 template <bool EW>
 __global__ void __launch_bounds__(kTB) k_hem_propose_big(DGraph g, const int32_t *bigv, int32_t nbig, const int32_t *mate,
                                                          int32_t *prop, uint64_t seed, uint64_t salt, int r, HemCtl *hc) {
+    pdl_enter();
     if (hem_skip(hc, r)) return;
     const int warps = blockDim.x >> 5;
     const unsigned lane = lane_id();
@@ -141,6 +143,7 @@ template <bool EW>
 __global__ void __launch_bounds__(kTB) k_hem_propose_huge(DGraph g, const int32_t *hugev, int32_t nhuge,
                                                           const int32_t *mate, int32_t *prop, uint64_t seed,
                                                           uint64_t salt, int r, HemCtl *hc) {
+    pdl_enter();
     if (hem_skip(hc, r)) return;
     __shared__ int32_t su[32], sw[32];
     __shared__ uint64_t shh[32];
@@ -175,6 +178,7 @@ __global__ void __launch_bounds__(kTB) k_hem_propose_huge(DGraph g, const int32_
 // before any mate changes matter, since proposals only name unmatched ones).
 __global__ void __launch_bounds__(kTB) k_hem_match(int32_t n, int32_t *mate, const int32_t *prop, int r, HemCtl *hc) {
     __shared__ long long red[40];
+    pdl_enter();
     if (hc->stop) return;
     long long c = 0;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
@@ -237,24 +241,30 @@ int hem(Ctx &c, const DGraph &g, uint64_t seed, int32_t level, int32_t rounds, i
     c.launches += 1;
     rounds = std::min(rounds, 64);
     int gl = num_sms() * 8;
+    // the rounds follow one another by programmatic launch (each kernel waits
+    // for the previous one on the device before it reads anything)
+    const bool pdl = !(c.opt.flags & JET_FLAG_NO_PDL);
+    int32_t *prop = pbuf.as<int32_t>();
+    const int32_t *bigv = bigbuf.as<int32_t>();
     for (int r = 0; r < rounds; ++r) {
         uint64_t salt = 0xD1B54A32D192ED03ULL * (uint64_t)(64 * (int64_t)level + r + 1);
-        if (g.ew) k_hem_propose_small<true><<<grid_for(g.n, kTB), kTB, 0, s>>>(g, mate, pbuf.as<int32_t>(), seed, salt, r, hc);
-        else k_hem_propose_small<false><<<grid_for(g.n, kTB), kTB, 0, s>>>(g, mate, pbuf.as<int32_t>(), seed, salt, r, hc);
+        const int gs = grid_for(g.n, kTB);
+        if (g.ew) JET_CUDA_TRY(launch_pdl(k_hem_propose_small<true>, gs, kTB, 0, s, pdl, g, (const int32_t *)mate, prop, seed, salt, r, hc));
+        else JET_CUDA_TRY(launch_pdl(k_hem_propose_small<false>, gs, kTB, 0, s, pdl, g, (const int32_t *)mate, prop, seed, salt, r, hc));
         c.launches += 1;
         if (nbig > 0) {
             int gb = std::min(gl, grid_for(nbig, kTB / 32));
-            if (g.ew) k_hem_propose_big<true><<<gb, kTB, 0, s>>>(g, bigbuf.as<int32_t>(), nbig, mate, pbuf.as<int32_t>(), seed, salt, r, hc);
-            else k_hem_propose_big<false><<<gb, kTB, 0, s>>>(g, bigbuf.as<int32_t>(), nbig, mate, pbuf.as<int32_t>(), seed, salt, r, hc);
+            if (g.ew) JET_CUDA_TRY(launch_pdl(k_hem_propose_big<true>, gb, kTB, 0, s, pdl, g, bigv, nbig, (const int32_t *)mate, prop, seed, salt, r, hc));
+            else JET_CUDA_TRY(launch_pdl(k_hem_propose_big<false>, gb, kTB, 0, s, pdl, g, bigv, nbig, (const int32_t *)mate, prop, seed, salt, r, hc));
             c.launches += 1;
         }
         if (nhuge > 0) {
             int gh = std::min(gl, nhuge);
-            if (g.ew) k_hem_propose_huge<true><<<gh, kTB, 0, s>>>(g, hugev, nhuge, mate, pbuf.as<int32_t>(), seed, salt, r, hc);
-            else k_hem_propose_huge<false><<<gh, kTB, 0, s>>>(g, hugev, nhuge, mate, pbuf.as<int32_t>(), seed, salt, r, hc);
+            if (g.ew) JET_CUDA_TRY(launch_pdl(k_hem_propose_huge<true>, gh, kTB, 0, s, pdl, g, (const int32_t *)hugev, nhuge, (const int32_t *)mate, prop, seed, salt, r, hc));
+            else JET_CUDA_TRY(launch_pdl(k_hem_propose_huge<false>, gh, kTB, 0, s, pdl, g, (const int32_t *)hugev, nhuge, (const int32_t *)mate, prop, seed, salt, r, hc));
             c.launches += 1;
         }
-        k_hem_match<<<std::min(gl, grid_for(g.n, kTB)), kTB, 0, s>>>(g.n, mate, pbuf.as<int32_t>(), r, hc);
+        JET_CUDA_TRY(launch_pdl(k_hem_match, std::min(gl, grid_for(g.n, kTB)), kTB, 0, s, pdl, g.n, mate, (const int32_t *)prop, r, hc));
         c.launches += 1;
     }
     JET_CUDA_TRY(cudaGetLastError());

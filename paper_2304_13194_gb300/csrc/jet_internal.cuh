@@ -235,6 +235,33 @@ __device__ __forceinline__ int warp_sum_i32(int v) {
     return v;
 }
 
+// Programmatic dependent launch: a kernel lets the next one in the stream be
+// scheduled as soon as all its own blocks have started, and waits for the
+// previous kernel to complete (memory visible) before it touches any data.
+// Both are no-ops for a kernel launched without the attribute.
+__device__ __forceinline__ void pdl_enter() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+// A launch that, with pdl, may be scheduled before the previous kernel in
+// the stream completes; the kernel must begin with pdl_enter().
+template <class... KArgs, class... Args>
+cudaError_t launch_pdl(void (*kern)(KArgs...), int grid, int block, size_t smem, cudaStream_t s, bool pdl,
+                       Args... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at{};
+    at.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at.val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = &at;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 // Append from any subset of a warp's lanes: one atomic per warp; returns the
 // slot for the calling lane.  All lanes of the warp must call it (pred may be
 // false).

@@ -151,15 +151,6 @@ size_t sm_cut_pw(int32_t k) { return align16((size_t)k * 8) + (size_t)kBigCap * 
 #define JET_ROW_MINB 4
 #endif
 
-// Programmatic dependent launch: a kernel lets the next one in the stream be
-// scheduled as soon as all its own blocks have started, and waits for the
-// previous kernel to complete (memory visible) before it touches any data.
-// Both are no-ops for a kernel launched without the attribute.
-__device__ __forceinline__ void pdl_enter() {
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-}
-
 // Level start: the host-known limits into the control block, then its state
 // from the initial cut and part weights.
 __global__ void __launch_bounds__(1024) k_ctl_init(Level L, const int64_t *cut2, int64_t Llim, int64_t opt,
@@ -694,17 +685,7 @@ int apply_blocks(const Level &L, int64_t items) { return std::min(L.apply_cap, g
 template <class... Args>
 cudaError_t launch_dep(const Level &L, void (*kern)(Args...), int grid, int block, size_t smem, cudaStream_t s,
                        Args... args) {
-    cudaLaunchConfig_t cfg{};
-    cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(block);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cudaLaunchAttribute at{};
-    at.id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at.val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = &at;
-    cfg.numAttrs = L.pdl ? 1 : 0;
-    return cudaLaunchKernelEx(&cfg, kern, args...);
+    return launch_pdl(kern, grid, block, smem, s, L.pdl != 0, args...);
 }
 
 // Per-kernel timing of the host-driven loop (JET_FLAG_PROFILE): a CUDA event
