@@ -26,6 +26,7 @@ __device__ __forceinline__ int32_t cw(const DGraph &g, int64_t j) {
 // Phase 2 of device_exscan: exclusive scan of the tile sums (one block).
 __global__ void __launch_bounds__(1024) k_scan_sums(int64_t *tile_sums, int64_t ntiles, int64_t *total_dev) {
     __shared__ long long sh[40];
+    pdl_enter();
     long long carry = 0;
     for (int64_t t0 = 0; t0 < ntiles; t0 += blockDim.x) {
         int64_t t = t0 + threadIdx.x;
@@ -284,6 +285,7 @@ struct RepFlag {
 };
 
 __global__ void k_cmap(int32_t n, const int32_t *mate, const int64_t *cidx, int32_t *cmap, int32_t *crep) {
+    pdl_enter();
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
         int32_t m = mate[v];
         int64_t r = (m >= 0 && m < v) ? m : v;
@@ -344,6 +346,7 @@ constexpr int kWarpSort = 256;
 __global__ void k_coarse_vw(int32_t nc, const int32_t *crep, const int32_t *mate, const int32_t *vw, int32_t *vwc,
                             int32_t *warp_list, int32_t *large_list, int32_t *t16_list, int32_t *t32_list,
                             int32_t *counts, const int64_t *boff, const int64_t *btot) {
+    pdl_enter();
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ((int64_t)nc + 31) / 32 * 32;
          c += (int64_t)gridDim.x * blockDim.x) {
         bool valid = c < nc;
@@ -385,6 +388,7 @@ template <bool EW, int N>
 __global__ void __launch_bounds__(kTB) k_contract_thread(DGraph g, const int32_t *cmap, const int32_t *mate,
                                                        const int32_t *crep, const int32_t *list, const int32_t *counts,
                                                        const int64_t *boff, int32_t *tadj, int32_t *tw, int32_t *rowcnt) {
+    pdl_enter();
     const int32_t nrows = counts[N == 16 ? 2 : 3];
     for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nrows; w += (int64_t)gridDim.x * blockDim.x) {
         const int32_t c = list[w];
@@ -459,6 +463,7 @@ __global__ void __launch_bounds__(kTB) k_contract_warp(DGraph g, const int32_t *
                                                        const int32_t *crep, const int32_t *list, const int32_t *counts,
                                                        const int64_t *boff, int32_t *tadj, int32_t *tw, int32_t *rowcnt) {
     __shared__ unsigned long long sk[kTB / 32][kWarpSort];
+    pdl_enter();
     const int warps = blockDim.x >> 5;
     const unsigned lane = lane_id();
     unsigned long long *keys = sk[threadIdx.x >> 5];
@@ -519,6 +524,7 @@ __global__ void __launch_bounds__(kTB) k_contract_large(DGraph g, const int32_t 
                                                         const int64_t *boff, int32_t *tadj, int32_t *tw,
                                                         int32_t *rowcnt) {
     __shared__ unsigned long long sk[kSortSmem];
+    pdl_enter();
     __shared__ long long sh[40];
     const int32_t nrows = counts[1];
     for (int64_t w = blockIdx.x; w < nrows; w += gridDim.x) {
@@ -578,6 +584,7 @@ struct CountVal {
 };
 
 __global__ void k_finish_xadj(int32_t nc, const int64_t *ex, const int64_t *tot, int64_t *xadj_c) {
+    pdl_enter();
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c <= nc; c += (int64_t)gridDim.x * blockDim.x)
         xadj_c[c] = c < nc ? ex[c] : *tot;
 }
@@ -657,6 +664,7 @@ __global__ void k_hub_rowcnt(int64_t nhub, int64_t htotal, const int32_t *hub_c,
 __global__ void __launch_bounds__(kTB) k_copy_long(const int32_t *list, const int32_t *counts, const int64_t *boff,
                                                    const int64_t *xadj_c, const int32_t *tadj, const int32_t *tw,
                                                    int32_t *adj_c, int32_t *ew_c) {
+    pdl_enter();
     const int32_t nrows = counts[1];
     for (int64_t w = blockIdx.x; w < nrows; w += gridDim.x) {
         const int32_t c = list[w];
@@ -674,6 +682,7 @@ __global__ void __launch_bounds__(kTB) k_copy_long(const int32_t *list, const in
 constexpr int kCopyLanes = 8;
 __global__ void k_copy_rows(int32_t nc, const int64_t *boff, const int64_t *btot, const int64_t *xadj_c,
                             const int32_t *tadj, const int32_t *tw, int32_t *adj_c, int32_t *ew_c) {
+    pdl_enter();
     const int64_t groups = (int64_t)gridDim.x * blockDim.x / kCopyLanes;
     const int gl = (int)(threadIdx.x % kCopyLanes);
     for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kCopyLanes; c < nc; c += groups) {
@@ -716,7 +725,8 @@ static int coarsen_level(Ctx &c, const DGraph &g, uint64_t seed, int32_t level, 
     JET_TRY(dev_alloc(cmapb, (size_t)n * 4, s));
     JET_TRY(dev_alloc(crepb, (size_t)std::max<int64_t>(nc, 1) * 4, s));
     int32_t *cmap = cmapb.as<int32_t>(), *crep = crepb.as<int32_t>();
-    k_cmap<<<grid_for(n, kTB, 8192), kTB, 0, s>>>(g.n, mate, cidxb.as<int64_t>(), cmap, crep);
+    JET_CUDA_TRY(launch_pdl(k_cmap, grid_for(n, kTB, 8192), kTB, 0, s, true, g.n, (const int32_t *)mate,
+                            (const int64_t *)cidxb.as<int64_t>(), cmap, crep));
     c.launches += 1;
     // bounds of the coarse rows
     DevBuf boffb, hoffb, hrankb;
@@ -741,8 +751,9 @@ static int coarsen_level(Ctx &c, const DGraph &g, uint64_t seed, int32_t level, 
     int32_t *t16_list = large_list + ncl, *t32_list = t16_list + ncl;
     int32_t *counts = t32_list + ncl;
     JET_CUDA_TRY(cudaMemsetAsync(counts, 0, 16, s));
-    k_coarse_vw<<<grid_for(nc, kTB, 8192), kTB, 0, s>>>((int32_t)nc, crep, mate, g.vw, vwcb.as<int32_t>(), warp_list,
-                                                         large_list, t16_list, t32_list, counts, boff, totp);
+    JET_CUDA_TRY(launch_pdl(k_coarse_vw, grid_for(nc, kTB, 8192), kTB, 0, s, true, (int32_t)nc, (const int32_t *)crep,
+                            (const int32_t *)mate, g.vw, vwcb.as<int32_t>(), warp_list, large_list, t16_list, t32_list,
+                            counts, (const int64_t *)boff, (const int64_t *)totp));
     JET_TRY(dev_alloc(tadjb, (size_t)std::max<int64_t>(btotal, 1) * 4, s));
     JET_TRY(dev_alloc(twb, (size_t)std::max<int64_t>(btotal, 1) * 4, s));
     JET_TRY(dev_alloc(cntb, (size_t)std::max<int64_t>(nc, 1) * 4, s));
@@ -751,16 +762,20 @@ static int coarsen_level(Ctx &c, const DGraph &g, uint64_t seed, int32_t level, 
     const int glarge = std::min(num_sms() * 4, (int)std::max<int64_t>(1, nc));
     const int gthread = std::min(gl, grid_for(nc, kTB));
     int32_t *tadj = tadjb.as<int32_t>(), *tw = twb.as<int32_t>(), *cnt = cntb.as<int32_t>();
-    if (g.ew) {
-        k_contract_thread<true, 16><<<gthread, kTB, 0, s>>>(g, cmap, mate, crep, t16_list, counts, boff, tadj, tw, cnt);
-        k_contract_thread<true, 32><<<gthread, kTB, 0, s>>>(g, cmap, mate, crep, t32_list, counts, boff, tadj, tw, cnt);
-        k_contract_warp<true><<<gwarp, kTB, 0, s>>>(g, cmap, mate, crep, warp_list, counts, boff, tadj, tw, cnt);
-        k_contract_large<true><<<glarge, kTB, 0, s>>>(g, cmap, mate, crep, large_list, counts, boff, tadj, tw, cnt);
-    } else {
-        k_contract_thread<false, 16><<<gthread, kTB, 0, s>>>(g, cmap, mate, crep, t16_list, counts, boff, tadj, tw, cnt);
-        k_contract_thread<false, 32><<<gthread, kTB, 0, s>>>(g, cmap, mate, crep, t32_list, counts, boff, tadj, tw, cnt);
-        k_contract_warp<false><<<gwarp, kTB, 0, s>>>(g, cmap, mate, crep, warp_list, counts, boff, tadj, tw, cnt);
-        k_contract_large<false><<<glarge, kTB, 0, s>>>(g, cmap, mate, crep, large_list, counts, boff, tadj, tw, cnt);
+    {
+        const int32_t *cm = cmap, *mt = mate, *cr = crep, *cts = counts;
+        const int64_t *bo = boff;
+        if (g.ew) {
+            JET_CUDA_TRY(launch_pdl(k_contract_thread<true, 16>, gthread, kTB, 0, s, true, g, cm, mt, cr, (const int32_t *)t16_list, cts, bo, tadj, tw, cnt));
+            JET_CUDA_TRY(launch_pdl(k_contract_thread<true, 32>, gthread, kTB, 0, s, true, g, cm, mt, cr, (const int32_t *)t32_list, cts, bo, tadj, tw, cnt));
+            JET_CUDA_TRY(launch_pdl(k_contract_warp<true>, gwarp, kTB, 0, s, true, g, cm, mt, cr, (const int32_t *)warp_list, cts, bo, tadj, tw, cnt));
+            JET_CUDA_TRY(launch_pdl(k_contract_large<true>, glarge, kTB, 0, s, true, g, cm, mt, cr, (const int32_t *)large_list, cts, bo, tadj, tw, cnt));
+        } else {
+            JET_CUDA_TRY(launch_pdl(k_contract_thread<false, 16>, gthread, kTB, 0, s, true, g, cm, mt, cr, (const int32_t *)t16_list, cts, bo, tadj, tw, cnt));
+            JET_CUDA_TRY(launch_pdl(k_contract_thread<false, 32>, gthread, kTB, 0, s, true, g, cm, mt, cr, (const int32_t *)t32_list, cts, bo, tadj, tw, cnt));
+            JET_CUDA_TRY(launch_pdl(k_contract_warp<false>, gwarp, kTB, 0, s, true, g, cm, mt, cr, (const int32_t *)warp_list, cts, bo, tadj, tw, cnt));
+            JET_CUDA_TRY(launch_pdl(k_contract_large<false>, glarge, kTB, 0, s, true, g, cm, mt, cr, (const int32_t *)large_list, cts, bo, tadj, tw, cnt));
+        }
     }
     c.launches += 4;
     if (nhub > 0) {
@@ -791,7 +806,8 @@ static int coarsen_level(Ctx &c, const DGraph &g, uint64_t seed, int32_t level, 
     JET_TRY(dev_alloc(exb, (size_t)std::max<int64_t>(nc, 1) * 8, s));
     c.launches += 3;
     JET_TRY(device_exscan(CountVal{cntb.as<int32_t>()}, nc, exb.as<int64_t>(), totp + 2, scan_scr.as<int64_t>(), s));
-    k_finish_xadj<<<grid_for(nc + 1, kTB, 8192), kTB, 0, s>>>((int32_t)nc, exb.as<int64_t>(), totp + 2, xcb.as<int64_t>());
+    JET_CUDA_TRY(launch_pdl(k_finish_xadj, grid_for(nc + 1, kTB, 8192), kTB, 0, s, true, (int32_t)nc,
+                            (const int64_t *)exb.as<int64_t>(), (const int64_t *)(totp + 2), xcb.as<int64_t>()));
     c.launches += 1;
     JET_CUDA_TRY(cudaMemcpyAsync(c.pinned, totp + 2, 8, cudaMemcpyDeviceToHost, s));
     JET_CUDA_TRY(cudaStreamSynchronize(s));
@@ -799,11 +815,14 @@ static int coarsen_level(Ctx &c, const DGraph &g, uint64_t seed, int32_t level, 
     DevBuf adjcb, ewcb;
     JET_TRY(dev_alloc(adjcb, (size_t)std::max<int64_t>(nnzc, 1) * 4, s));
     JET_TRY(dev_alloc(ewcb, (size_t)std::max<int64_t>(nnzc, 1) * 4, s));
-    k_copy_long<<<glarge, kTB, 0, s>>>(large_list, counts, boff, xcb.as<int64_t>(), tadjb.as<int32_t>(), twb.as<int32_t>(),
-                                       adjcb.as<int32_t>(), ewcb.as<int32_t>());
+    JET_CUDA_TRY(launch_pdl(k_copy_long, glarge, kTB, 0, s, true, (const int32_t *)large_list, (const int32_t *)counts,
+                            (const int64_t *)boff, (const int64_t *)xcb.as<int64_t>(), (const int32_t *)tadjb.as<int32_t>(),
+                            (const int32_t *)twb.as<int32_t>(), adjcb.as<int32_t>(), ewcb.as<int32_t>()));
     c.launches += 1;
-    k_copy_rows<<<std::min(gl, grid_for(nc, kTB / kCopyLanes)), kTB, 0, s>>>((int32_t)nc, boff, totp, xcb.as<int64_t>(), tadjb.as<int32_t>(),
-                                                                    twb.as<int32_t>(), adjcb.as<int32_t>(), ewcb.as<int32_t>());
+    JET_CUDA_TRY(launch_pdl(k_copy_rows, std::min(gl, grid_for(nc, kTB / kCopyLanes)), kTB, 0, s, true, (int32_t)nc,
+                            (const int64_t *)boff, (const int64_t *)totp, (const int64_t *)xcb.as<int64_t>(),
+                            (const int32_t *)tadjb.as<int32_t>(), (const int32_t *)twb.as<int32_t>(), adjcb.as<int32_t>(),
+                            ewcb.as<int32_t>()));
     JET_CUDA_TRY(cudaGetLastError());
     int32_t i = h->levels;
     h->cmap[i - 1] = cmap;

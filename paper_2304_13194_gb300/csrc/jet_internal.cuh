@@ -399,6 +399,7 @@ constexpr int kScanTile = kTB * kScanItems;
 template <class F>
 __global__ void __launch_bounds__(kTB) k_scan_tiles(F f, int64_t n, int64_t *tile_sums) {
     __shared__ long long sh[40];
+    pdl_enter();
     int64_t base = (int64_t)blockIdx.x * kScanTile;
     long long s = 0;
 #pragma unroll
@@ -413,6 +414,7 @@ __global__ void __launch_bounds__(kTB) k_scan_tiles(F f, int64_t n, int64_t *til
 template <class F>
 __global__ void __launch_bounds__(kTB) k_scan_apply(F f, int64_t n, const int64_t *tile_off, int64_t *out) {
     __shared__ long long sh[40];
+    pdl_enter();
     int64_t base = (int64_t)blockIdx.x * kScanTile;
     long long vals[kScanItems];
     long long s = 0;
@@ -438,10 +440,10 @@ template <class F>
 int device_exscan(F f, int64_t n, int64_t *out, int64_t *total_dev, int64_t *tile_scratch, cudaStream_t s) {
     int64_t nt = scan_tiles_for(n);
     if (nt < 1) nt = 1;
-    k_scan_tiles<F><<<(unsigned)nt, kTB, 0, s>>>(f, n, tile_scratch);
-    k_scan_sums<<<1, 1024, 0, s>>>(tile_scratch, nt, total_dev);
-    k_scan_apply<F><<<(unsigned)nt, kTB, 0, s>>>(f, n, tile_scratch, out);
-    JET_CUDA_TRY(cudaGetLastError());
+    // the three kernels (and the next one) follow by programmatic launch
+    JET_CUDA_TRY(launch_pdl(k_scan_tiles<F>, (int)nt, kTB, 0, s, true, f, n, tile_scratch));
+    JET_CUDA_TRY(launch_pdl(k_scan_sums, 1, 1024, 0, s, true, tile_scratch, nt, total_dev));
+    JET_CUDA_TRY(launch_pdl(k_scan_apply<F>, (int)nt, kTB, 0, s, true, f, n, (const int64_t *)tile_scratch, out));
     return JET_OK;
 }
 
