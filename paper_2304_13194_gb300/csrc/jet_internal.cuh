@@ -184,6 +184,7 @@ struct Level {
     Ctl *ctl;
     // CUDA-graph loop control (0 when driven from the host)
     unsigned long long h_loop, h_mode;
+    unsigned long long h_next;   // switch of the next iteration (the loop body holds two iterations)
     int32_t use_graph;
     int32_t pdl;             // launch the row and tile kernels with programmatic dependent launch
     int64_t poll_limit;      // persistent loop: polls at a grid barrier before a block gives up

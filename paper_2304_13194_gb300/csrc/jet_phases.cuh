@@ -493,7 +493,7 @@ __device__ inline int32_t ph_controller(const Level &L) {
             ctl->copy_best = 0;
             if (L.use_graph) {
                 cudaGraphSetConditional((cudaGraphConditionalHandle)L.h_loop, 0u);
-                cudaGraphSetConditional((cudaGraphConditionalHandle)L.h_mode, (unsigned)MODE_DONE);
+                cudaGraphSetConditional((cudaGraphConditionalHandle)L.h_next, (unsigned)MODE_DONE);
             }
         }
         return MODE_DONE;
@@ -553,10 +553,9 @@ __device__ inline int32_t ph_controller(const Level &L) {
         s_lim[0] = Llim;
         s_lim[1] = sigma;
         if (L.use_graph) {
-            // the switch value persists over the loop's iterations: set it
-            // when the mode changes; the loop flag every time (the next
-            // iteration's first kernel clears it)
-            if (m != kind) cudaGraphSetConditional((cudaGraphConditionalHandle)L.h_mode, (unsigned)m);
+            // the next iteration's switch (DONE: no branch) and the loop flag
+            // (the next iteration's first kernel clears it)
+            cudaGraphSetConditional((cudaGraphConditionalHandle)L.h_next, (unsigned)m);
             cudaGraphSetConditional((cudaGraphConditionalHandle)L.h_loop, m == MODE_DONE ? 0u : 1u);
         }
     }

@@ -871,11 +871,15 @@ int run_hostloop(Ctx &c, const Level &L, bool profile, float *kern_ms) {
     return JET_OK;
 }
 
-// Device-resident loop: graph = start kernel -> WHILE(h_loop) { SWITCH(h_mode)
-// {Jetlp | Jetrw | Jetrs, each followed by apply + commit + controller} } ->
-// final best copy.  The apply kernel sits inside every branch so that it
-// follows the branch's last kernel by programmatic dependent launch instead
-// of waiting for the conditional node to complete.
+// Device-resident loop: graph = start kernel -> WHILE(h_loop) { SWITCH(hA)
+// {...} -> SWITCH(hB) {...} } -> final best copy, each SWITCH holding one
+// iteration {Jetlp | Jetrw | Jetrs, each followed by apply + commit +
+// controller}.  Two iterations per loop body: the step from one SWITCH to
+// the next costs less than a restart of the loop body.  The controller of
+// an iteration sets the other SWITCH's value (DONE: no branch runs) and the
+// loop flag.  The apply kernel sits inside every branch so that it follows
+// the branch's last kernel by programmatic dependent launch instead of
+// waiting for the conditional node to complete.
 // nk_branch[3] / *nk_tail receive the kernel counts of the captured pieces.
 // The graph is launched on the context's stream and not waited for; *exec_out
 // receives the executable graph, which the caller destroys once the stream
@@ -895,10 +899,11 @@ int run_graph(Ctx &c, Level L, int *nk_branch, int *nk_tail, cudaGraphExec_t *ex
         cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
         if (e != cudaSuccess) { fail(e, "cudaStreamCreate"); break; }
         if ((e = cudaGraphCreate(&g, 0)) != cudaSuccess) { fail(e, "cudaGraphCreate"); break; }
-        cudaGraphConditionalHandle h_loop, h_mode;
+        cudaGraphConditionalHandle h_loop, h_a, h_b;
         if ((e = cudaGraphConditionalHandleCreate(&h_loop, g, 1, cudaGraphCondAssignDefault)) != cudaSuccess) { fail(e, "handle loop"); break; }
-        if ((e = cudaGraphConditionalHandleCreate(&h_mode, g, 0, cudaGraphCondAssignDefault)) != cudaSuccess) { fail(e, "handle mode"); break; }
-        L.h_loop = h_loop; L.h_mode = h_mode; L.use_graph = 1;
+        if ((e = cudaGraphConditionalHandleCreate(&h_a, g, 0, cudaGraphCondAssignDefault)) != cudaSuccess) { fail(e, "handle mode"); break; }
+        if ((e = cudaGraphConditionalHandleCreate(&h_b, g, 0, cudaGraphCondAssignDefault)) != cudaSuccess) { fail(e, "handle mode"); break; }
+        L.h_loop = h_loop; L.h_mode = h_a; L.h_next = h_b; L.use_graph = 1;
         // start kernel
         cudaGraphNode_t start;
         {
@@ -927,23 +932,32 @@ int run_graph(Ctx &c, Level L, int *nk_branch, int *nk_tail, cudaGraphExec_t *ex
             if ((e = cudaGraphAddKernelNode(&fin, g, &wnode, 1, &kp)) != cudaSuccess) { fail(e, "final copy node"); break; }
         }
         cudaGraph_t body = wp.conditional.phGraph_out[0];
-        cudaGraphNodeParams sp{};
-        sp.type = cudaGraphNodeTypeConditional;
-        sp.conditional.handle = h_mode;
-        sp.conditional.type = cudaGraphCondTypeSwitch;
-        sp.conditional.size = 3;
-        cudaGraphNode_t snode;
-        if ((e = cudaGraphAddNode(&snode, body, nullptr, nullptr, 0, &sp)) != cudaSuccess) { fail(e, "switch node"); break; }
         bool ok = true;
-        for (int b = 0; b < 3 && ok; ++b) {
-            cudaGraph_t bg = sp.conditional.phGraph_out[b];
-            if ((e = cudaStreamBeginCaptureToGraph(cap, bg, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed)) != cudaSuccess) { fail(e, "capture branch"); ok = false; break; }
-            int r = b == 0 ? enqueue_lp(L, cap, &nk_branch[0]) : enqueue_rb(L, cap, b == 2, &nk_branch[b]);
-            if (r == JET_OK) r = enqueue_tail(L, cap, nk_tail);
-            cudaGraph_t outg = nullptr;
-            e = cudaStreamEndCapture(cap, &outg);
-            if (r != JET_OK) { rc = r; ok = false; break; }
-            if (e != cudaSuccess) { fail(e, "end capture branch"); ok = false; break; }
+        cudaGraphNode_t prev{};
+        for (int u = 0; u < 2 && ok; ++u) {
+            // iteration u of the body: its switch reads hA (u = 0) or hB, its
+            // controller sets the other one
+            Level Lu = L;
+            Lu.h_mode = u == 0 ? h_a : h_b;
+            Lu.h_next = u == 0 ? h_b : h_a;
+            cudaGraphNodeParams sp{};
+            sp.type = cudaGraphNodeTypeConditional;
+            sp.conditional.handle = u == 0 ? h_a : h_b;
+            sp.conditional.type = cudaGraphCondTypeSwitch;
+            sp.conditional.size = 3;
+            cudaGraphNode_t snode;
+            if ((e = cudaGraphAddNode(&snode, body, u ? &prev : nullptr, nullptr, u ? 1 : 0, &sp)) != cudaSuccess) { fail(e, "switch node"); ok = false; break; }
+            prev = snode;
+            for (int b = 0; b < 3 && ok; ++b) {
+                cudaGraph_t bg = sp.conditional.phGraph_out[b];
+                if ((e = cudaStreamBeginCaptureToGraph(cap, bg, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed)) != cudaSuccess) { fail(e, "capture branch"); ok = false; break; }
+                int r = b == 0 ? enqueue_lp(Lu, cap, &nk_branch[0]) : enqueue_rb(Lu, cap, b == 2, &nk_branch[b]);
+                if (r == JET_OK) r = enqueue_tail(Lu, cap, nk_tail);
+                cudaGraph_t outg = nullptr;
+                e = cudaStreamEndCapture(cap, &outg);
+                if (r != JET_OK) { rc = r; ok = false; break; }
+                if (e != cudaSuccess) { fail(e, "end capture branch"); ok = false; break; }
+            }
         }
         if (!ok) break;
         if ((e = cudaGraphInstantiate(&ge, g, 0)) != cudaSuccess) { fail(e, "cudaGraphInstantiate"); break; }
@@ -1162,7 +1176,7 @@ static void fill_level_params(Ctx &c, Level &L, int32_t is_finest, uint64_t seed
     L.abl = o.flags & ABL_ALL;
     L.seed = seed;
     L.use_graph = 0;
-    L.h_loop = L.h_mode = 0;
+    L.h_loop = L.h_mode = L.h_next = 0;
     L.pdl = (o.flags & JET_FLAG_NO_PDL) ? 0 : 1;
     const int sms = num_sms();
     L.hub_deg = o.hub_degree > 0 ? o.hub_degree : kHugeDeg;
