@@ -4,9 +4,10 @@
 // The passes themselves are device functions in jet_phases.cuh.  They run in
 // one of two ways:
 //  * large levels: one kernel per phase, and the whole level loop is a CUDA
-//    graph with a WHILE node around a SWITCH over {Jetlp, Jetrw, Jetrs}; a
-//    one-block controller kernel sets the conditionals, so no host round trip
-//    happens per iteration (the paper blames that round trip for its weaker
+//    graph with a WHILE node around SWITCH nodes over {Jetlp, Jetrw, Jetrs}
+//    (two iterations per loop body); the controller, in the last block of
+//    the apply kernel, sets the conditionals, so no host round trip happens
+//    per iteration (the paper blames that round trip for its weaker
 //    coarse-level speedup, Sec. 6.2);
 //  * small levels: one thread block cluster (up to 16 SMs) runs every
 //    iteration of the level in a single launch, the phases separated by the
@@ -174,9 +175,9 @@ __global__ void k_graph_start(Level L) {
 }
 
 __global__ void __launch_bounds__(kTB) k_copy_best(Level L) { ph_copy_best(L, launch_grid()); }
-// Jetlp: work list, select; P_best copy + afterburner (the copy only reads
-// part, which the afterburner does not change, and stays out of the select
-// step)
+// Jetlp: work list, select, afterburner (+ the P_best copy at its end: the
+// copy only reads part, which the afterburner does not change, and stays
+// out of the select step)
 __global__ void __launch_bounds__(kTB) k_lp_scan(Level L) {
     pdl_enter();
     ph_lp_scan(L, launch_grid(), JET_ARENA);
@@ -202,8 +203,8 @@ __global__ void __launch_bounds__(kTB, JET_ROW_MINB) k_apply(Level L) {
     ph_apply<EW>(L, launch_grid(), JET_ARENA);
     if (last_block(L.ctl)) ph_controller(L);
 }
-// rebalancing: P_best copy + candidates, rows (+ plan), tile sums, tile scan,
-// take (+ Jetrs eviction scan), cookie cutter
+// rebalancing: candidates (+ the P_best copy at the end), rows (+ plan), tile
+// sums, tile scan, take (+ Jetrs eviction scan), cookie cutter
 template <bool STRONG>
 __global__ void __launch_bounds__(kTB) k_rb_scan(Level L) {
     pdl_enter();
