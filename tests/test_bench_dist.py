@@ -52,3 +52,18 @@ def test_aggregate_single_process():
     sys.path.insert(0, ROOT)
     import bench
     assert bench.aggregate(10, 2.0, [3.0], None) == (10.0, 2.0, [3.0])
+
+
+def test_reference_arm_line_on_a_small_mesh():
+    """The reference arm (the oracle, whole partitions per step) prints one
+    JSON line with the contract's keys, on a small mesh, on the CPU."""
+    import json
+    import subprocess
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "2",
+                        "--warmup", "1", "--scale", "12"], capture_output=True, text=True, timeout=300, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads([l for l in r.stdout.splitlines() if l.startswith("{")][-1])
+    assert line["impl"] == "reference" and line["steps"] == 2 and line["warmup"] == 1
+    assert line["value"] > 0 and line["higher_is_better"] is True and line["config"]["same_config"] is True
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
+    assert line["e2e"]["value"] == line["value"] and line["e2e"]["h2d_bytes_per_step"] == 0
