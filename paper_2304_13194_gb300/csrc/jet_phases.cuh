@@ -763,8 +763,8 @@ __device__ __forceinline__ void lp_select_block_row(const Level &L, LpExport ex,
 // table, which is all-zero between rows (the read pass clears every entry it
 // finds set, and meets each distinct part once).
 template <bool EW>
-__device__ __forceinline__ void lp_select_row(const Level &L, LpExport ex, int32_t v, int32_t *tab, long long &nexam,
-                                              long long &degexam, long long &degx) {
+__device__ __forceinline__ void lp_select_row(const Level &L, LpExport ex, int32_t v, int32_t *tab, Appender &xapp,
+                                              long long &nexam, long long &degexam, long long &degx) {
     const DGraph &g = L.g;
     const unsigned lane = lane_id();
     int32_t ps = L.part[v];
@@ -801,11 +801,11 @@ __device__ __forceinline__ void lp_select_row(const Level &L, LpExport ex, int32
         if (inX) {
             L.prio[v] = F;
             L.nxt[v] = nxt_pack(ps, pd);
-            L.listX[atomicAdd(&L.ctl->nX, 1)] = v;
             degx += end - beg;
         }
         if (ex.pd) { ex.pd[v] = pd >= 0 ? pd : ps; ex.gain[v] = F; }
     }
+    xapp.add(lane == 0 && inX, v);   // the block's X staging: no global atomic per row
 }
 
 // Step 1 (Alg. 4 first loop, Eq. for P_d, Eq. gainconn_filter) over the work
@@ -830,7 +830,7 @@ __device__ inline void ph_lp_select(const Level &L, LpExport ex, Grid G, char *a
     }
     const DGraph g = L.g;
     long long nexam = 0, degexam = 0, degx = 0;
-    auto big_row = [&](int32_t v) { lp_select_row<EW>(L, ex, v, tab, nexam, degexam, degx); };
+    auto big_row = [&](int32_t v) { lp_select_row<EW>(L, ex, v, tab, xapp, nexam, degexam, degx); };
     auto hub_row = [&](int32_t v) {
         lp_select_block_row<EW>(L, ex, v, a32 + kListCap + kBigCap, red, nexam, degexam, degx);
     };
@@ -888,11 +888,14 @@ __device__ inline void ph_lp_select(const Level &L, LpExport ex, Grid G, char *a
         }
         xapp.add(inX, v);
         bigs.add(big, v);
-        xapp.flush(&ctl->nX, L.listX, false);
+        // room for this pass's adds and a whole drain of warp rows (each of
+        // which may add its vertex)
+        xapp.flush(&ctl->nX, L.listX, false, 1 + kBigCap / (int)blockDim.x);
         bigs.drain(false, g.xadj, big_row, hub_row, L.hub_deg);
     }
     xapp.flush(&ctl->nX, L.listX, true);
     bigs.drain(true, g.xadj, big_row, hub_row, L.hub_deg);
+    xapp.flush(&ctl->nX, L.listX, true);
     flush_counter(&ctl->nexam, nexam, red);
     flush_counter(&ctl->degexam, degexam, red);
     flush_counter(&ctl->degx, degx, red);
@@ -977,11 +980,9 @@ __device__ inline void ph_afterburn(const Level &L, LpExport ex, Grid G, char *a
         f2 = warp_sum_i32(f2);
         if (lane == 0) {
             if (ex.f2) ex.f2[v] = f2;
-            if (f2 >= 0) {
-                L.mstamp[v] = it;
-                L.listM[atomicAdd(&ctl->nM, 1)] = v;
-            }
+            if (f2 >= 0) L.mstamp[v] = it;
         }
+        mapp.add(lane == 0 && f2 >= 0, v);   // the block's M staging: no global atomic per row
     };
     auto hub_row = [&](int32_t v) { afterburn_block_row<EW>(L, ex, v, it, red); };
     for (int64_t p = 0; dl.live(p); ++p) {
@@ -1025,11 +1026,13 @@ __device__ inline void ph_afterburn(const Level &L, LpExport ex, Grid G, char *a
         }
         mapp.add(inM, v);
         bigs.add(big, v);
-        mapp.flush(&ctl->nM, L.listM, false);
+        // room for this pass's adds and a whole drain of warp rows
+        mapp.flush(&ctl->nM, L.listM, false, 1 + kBigCap / (int)blockDim.x);
         bigs.drain(false, L.g.xadj, big_row, hub_row, L.hub_deg);
     }
     mapp.flush(&ctl->nM, L.listM, true);
     bigs.drain(true, L.g.xadj, big_row, hub_row, L.hub_deg);
+    mapp.flush(&ctl->nM, L.listM, true);
 }
 
 // ---------------------------------------------------------------------------
