@@ -1241,16 +1241,14 @@ __device__ __forceinline__ int32_t random_B(const Level &L, int32_t v, int32_t i
     return L.Bs[h % (uint64_t)nB];
 }
 
-// Adds w into bucketw[key] with one atomic per distinct key in the warp.
+// Adds w (a vertex weight, or 0) into bucketw[key] with one atomic per
+// distinct key in the warp: the lanes of one key reduce their weights with
+// one warp reduction (their sum is below 2^31: the library refuses graphs
+// whose total vertex weight is not).
 __device__ __forceinline__ void bucket_add(const Level &L, int32_t key, long long w) {
-    unsigned peers = __match_any_sync(0xffffffffu, key);
-    long long s = 0;
-#pragma unroll
-    for (int j = 0; j < 32; ++j) {
-        long long x = __shfl_sync(0xffffffffu, w, j);
-        if ((peers >> j) & 1u) s += x;
-    }
-    if (key >= 0 && (int)lane_id() == __ffs(peers) - 1) atomic_add_i64(&L.bucketw[key], s);
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    const int s = __reduce_add_sync(peers, (int)w);
+    if (key >= 0 && (int)lane_id() == __ffs(peers) - 1) atomic_add_i64(&L.bucketw[key], (long long)s);
 }
 
 // Per-block slot buckets in shared memory when nA * kSlots keys fit.
