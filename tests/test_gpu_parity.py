@@ -152,6 +152,30 @@ def test_rebalance_hand_cases(ctx, golden_dir):
 
 
 @pytest.mark.parametrize("name,g,unit", graphs_small(), ids=[x[0] for x in graphs_small()])
+@pytest.mark.parametrize("strong", [False, True])
+def test_rebalance_pass_many_oversized_parts(ctx, name, g, unit, strong):
+    """40 of 64 parts over the limit: more (part, slot) buckets than a block
+    keeps in shared memory, so the slot weights are summed per warp and key
+    (the warp-aggregated path), element by element against the oracle."""
+    k = 64
+    rng = np.random.default_rng(40)
+    part = rng.integers(0, 40, g.n).astype(np.int32)
+    vw, ew = _vw(g, unit), _ew(g, unit)
+    og = graphgen.Graph(g.n, g.xadj, g.adjncy, vw, ew)
+    if strong:
+        ref = oracle.jetrs(og, k, part, eps=0.03)
+    else:
+        ref = oracle.jetrw(og, k, part, eps=0.03, seed=17, it=5)
+    r = ctx.rebalance_pass(g.xadj, g.adjncy, vw, ew, k, part, eps=0.03, strong=strong, seed=17, it=5)
+    assert r["ncand"] == ref["ncand"]
+    loss = _np(r["loss"]).astype(np.int64)
+    refl = np.where(ref["loss"] == oracle.NONE, NONE32, ref["loss"])
+    assert (loss == refl).all()
+    assert (_np(r["dest"]) == ref["dest"]).all()
+    assert r["nmoves"] == ref["nmoves"]
+
+
+@pytest.mark.parametrize("name,g,unit", graphs_small(), ids=[x[0] for x in graphs_small()])
 @pytest.mark.parametrize("k", [2, 7, 64])
 @pytest.mark.parametrize("strong", [False, True])
 def test_rebalance_pass_random(ctx, name, g, unit, k, strong):
